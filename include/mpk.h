@@ -1,0 +1,290 @@
+/*
+ * mpk.h - C ABI of the GB300 level-blocked matrix power kernel (MPK) library.
+ *
+ * What it computes (arXiv 2309.02228, "Algebraic Temporal Blocking for Sparse Iterative
+ * Solvers on Multi-Core CPUs"):
+ *   - Sec. 3, Alg. 1: the MPK, y_p = A^p x for p = 1..p_m into p_m vectors, here generalised
+ *     to the three-term recurrence y_k = a_k (A y_{k-1}) + b_k y_{k-1} + c_k y_{k-2} that covers
+ *     the monomial basis, the Newton basis of Sec. 4 (a=1, b=-theta_k, c=0) and the Chebyshev
+ *     basis of the polynomial smoother of Sec. 5.3 (three-term Chebyshev recursion).
+ *   - Sec. 3: temporal cache blocking by the level structure of a BFS on the graph of A and a
+ *     cache-size parameter C (levels grouped so that the working set of a p-deep wavefront
+ *     fits the cache); here the cache is the GPU's L2.
+ *   - Sec. 4, Alg. 3(c): s-step GMRES (MPK, block orthogonalisation, TSQR, convergence check),
+ *     with the MPK in the Newton basis.
+ * The paper is a CPU (OpenMP) study; this library is a single-GPU (sm_103a) design of the same
+ * method.  Everything runs in the library's own CUDA kernels; the host code only orders launches.
+ *
+ * Conventions for every entry point:
+ *   - Pointers named d_* or documented "device" are device pointers; "host" ones are host.
+ *   - Sizes are element counts.  Indices are 32-bit (Sec. 2.2: 32-bit integers), so
+ *     n < 2^31 and nnz < 2^31.
+ *   - Calls are asynchronous on the given stream unless stated otherwise; a NULL stream means
+ *     the legacy default stream.  Every call returns an mpk_status; no exception crosses the ABI.
+ *   - Errors detected on the device (a dependency wait that ran out) are latched in the plan
+ *     and returned by mpk_plan_sync(), which also clears them.
+ *   - The caller owns every buffer it passes; a plan owns its own device copies.
+ *   - One plan must not be used from two streams at the same time: it holds the workspace and
+ *     the dependency flags of its launches.
+ */
+#ifndef MPK_GB300_H
+#define MPK_GB300_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MPK_OK = 0,
+    MPK_ERR_ARG = 1,            /* invalid argument (null pointer, size, flag combination) */
+    MPK_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+    MPK_ERR_OOM = 3,            /* device allocation failed */
+    MPK_ERR_TIMEOUT = 4,        /* a bounded device-side wait ran out; results are invalid */
+    MPK_ERR_BREAKDOWN = 5,      /* Cholesky of a Gram matrix met a non-positive pivot */
+    MPK_ERR_NOT_CONVERGED = 6,  /* solver stopped at its iteration limit */
+    MPK_ERR_UNIMPLEMENTED = 7,  /* a combination this build does not support */
+    MPK_ERR_BUDGET = 8,         /* serving: the request can never fit the memory budget */
+    MPK_ERR_NOT_READY = 9       /* serving: nothing completed yet */
+} mpk_status;
+
+typedef enum { MPK_F32 = 0, MPK_F64 = 1 } mpk_dtype;
+
+/* A square sparse matrix in CRS/CSR form (Sec. 2.2, Alg. 1: val[nnz], col[nnz],
+ * rowPtr[n+1]).  DEVICE pointers, caller-owned; columns need not be sorted; duplicate
+ * entries are kept (and summed by the SpMV).  mpk_plan_create copies what it needs, so the
+ * arrays may be freed once it returns (after a stream synchronise). */
+typedef struct {
+    int64_t n;
+    int64_t nnz;
+    const int32_t *row_ptr;   /* n+1 entries, row_ptr[0] = 0, non-decreasing */
+    const int32_t *col;       /* nnz entries in [0, n) */
+    const void *val;          /* nnz entries of type dtype */
+    mpk_dtype dtype;
+} mpk_csr;
+
+/* Plan options (mpk_plan_opts_default fills the defaults). */
+typedef struct {
+    int64_t l2_budget_bytes;  /* level-group budget, the analogue of the paper's cache size
+                                 C (Sec. 4: C = 85 / 200 MB on its CPUs).  0 = half the L2. */
+    int32_t p_blk;            /* blocking depth the groups are sized for and the longest
+                                 segment one blocked launch runs (the paper's p_opt,
+                                 Sec. 3); 0 = p_max. */
+    int32_t root_rule;        /* 0 = George-Liu pseudo-peripheral root from row 0,
+                                 1 = row 0 */
+    int32_t n_sweeps;         /* George-Liu re-root sweeps (default 2) */
+    int32_t assume_symmetric; /* 1 = the pattern is structurally symmetric; skips building
+                                 A^T for the BFS and the dependency closure */
+    int32_t chunk_slices;     /* 32-row slices per blocked task (default 8) */
+    int32_t keep_f32;         /* keep an FP32 copy of the values (MPK in FP32) */
+    int32_t keep_f64;         /* keep an FP64 copy of the values (MPK / residual in FP64) */
+    int32_t ctas_per_sm;      /* persistent CTAs per SM for the blocked kernel (0 = auto) */
+    uint32_t wait_timeout_us; /* bound on every device-side dependency wait (default 2e6) */
+} mpk_plan_opts;
+
+typedef struct mpk_plan_s *mpk_plan_t;
+
+/* Statistics of a plan (host struct filled by mpk_plan_stats). */
+typedef struct {
+    int64_t n, nnz;
+    int32_t n_levels, n_groups, n_slices, n_chunks;
+    int32_t root;             /* BFS root (original row index) */
+    int32_t p_blk;
+    int64_t l2_budget_bytes;
+    int64_t sell_nnz;         /* stored SELL entries including padding */
+    int64_t device_bytes;     /* bytes the plan holds on the device */
+    double create_ms;         /* wall time of mpk_plan_create (synchronous part) */
+    int32_t bfs_sweeps;       /* BFS runs made by the root search */
+    int32_t max_level_rows;
+} mpk_plan_info;
+
+/* Coefficients of one MPK call (host memory, read during the call).
+ * Power k = 1..p uses a[k-1], b[k-1], c[k-1]; the c term multiplies y_{k-2} (y_{-1} := 0).
+ * gamma (optional, p+1 entries): with MPK_FINAL_ONLY the output is sum_k gamma[k] y_k
+ * (the polynomial P(A) x of Sec. 5.3, eq. (3)); NULL means the output is y_p. */
+typedef struct {
+    int32_t p;
+    const double *a;
+    const double *b;
+    const double *c;
+    const double *gamma;
+} mpk_coeffs;
+
+/* mpk_apply flags */
+#define MPK_PERMUTED_IO   0x01u  /* X, Y are in the plan's level order (see mpk_plan_perm) */
+#define MPK_FINAL_ONLY    0x02u  /* Y receives one block: y_p, or sum gamma_k y_k */
+#define MPK_HOST_IO       0x04u  /* X, Y are HOST pointers; the call copies them in and out
+                                    and returns after the result is in Y */
+#define MPK_UNBLOCKED     0x08u  /* p back-to-back SpMV launches (Alg. 1) instead of the
+                                    blocked schedule; same arithmetic, bit-identical result */
+#define MPK_Y0_IS_X       0x10u  /* block 0 of Y already holds x; X is ignored (needs
+                                    MPK_PERMUTED_IO, not MPK_FINAL_ONLY) */
+#define MPK_RHS_INTERLEAVED 0x20u /* X and Y blocks are row-major n x n_rhs (element (i,r) at
+                                    i*n_rhs + r) instead of column-major with leading dim. */
+#define MPK_DEBUG_DROP_FLAG 0x40000000u /* test aid: the blocked task (chunk 0, power 1)
+                                    does not publish its flag, so the waits on it run out and
+                                    the call reports MPK_ERR_TIMEOUT at mpk_plan_sync */
+
+/* Default options. */
+mpk_status mpk_plan_opts_default(mpk_plan_opts *o);
+
+/* Build a plan for A (Sec. 3 pre-processing), entirely on the device:
+ *   1. BFS levels of the graph of A + A^T from the root (George-Liu search or row 0);
+ *      unreached rows continue from the lowest-index unvisited row one level higher;
+ *   2. rows ordered by (level, original index): perm, iperm, level_ptr;
+ *   3. B = P A P^T with columns ascending per row, values in FP32 and/or FP64;
+ *   4. level groups: consecutive levels joined while
+ *        p_blk*(4*rows + (4+w)*nnz) + (p_blk+1)*w*rows <= l2_budget_bytes
+ *      (w = value bytes of the MPK precision), a level over budget being a group of its own;
+ *   5. SELL-32 slices inside each group, tasks of chunk_slices slices, per-task dependency
+ *      ranges and the dependency flags.
+ * p_max: largest number of powers a single mpk_apply will request (1..63).
+ * A: device CSR (see mpk_csr).  opts may be NULL (defaults).  stream: used for all work; the
+ * call synchronises it before returning (the host needs the level counts).
+ * On success *out is a new plan; on failure *out is NULL and nothing is leaked. */
+mpk_status mpk_plan_create(const mpk_csr *A, int32_t p_max, const mpk_plan_opts *opts,
+                           cudaStream_t stream, mpk_plan_t *out);
+
+mpk_status mpk_plan_destroy(mpk_plan_t plan);
+
+/* Fill *st (host). */
+mpk_status mpk_plan_stats(mpk_plan_t plan, mpk_plan_info *st);
+
+/* Copy the level structure out (DEVICE output buffers, any may be NULL):
+ *   perm[n]          original row at level-order position r
+ *   iperm[n]         level-order position of original row i
+ *   level[n]         BFS level of original row i
+ *   level_ptr[n_levels+1], group_ptr[n_groups+1] (group_ptr indexes levels).
+ * Asynchronous on stream. */
+mpk_status mpk_plan_perm(mpk_plan_t plan, int32_t *perm, int32_t *iperm, int32_t *level,
+                         int32_t *level_ptr, int32_t *group_ptr, cudaStream_t stream);
+
+/* Copy the permuted matrix B = P A P^T out (DEVICE outputs: row_ptr[n+1], col[nnz], val[nnz]
+ * of type dtype; the plan must keep that precision).  Asynchronous on stream. */
+mpk_status mpk_plan_csr(mpk_plan_t plan, mpk_dtype dtype, int32_t *row_ptr, int32_t *col,
+                        void *val, cudaStream_t stream);
+
+/* Replace the values of the plan's matrix by those of a matrix with the SAME pattern
+ * (device CSR in the original order), keeping the level structure.  Asynchronous. */
+mpk_status mpk_plan_update_values(mpk_plan_t plan, const mpk_csr *A, cudaStream_t stream);
+
+/* Matrix power kernel (Sec. 3, Alg. 1 / blocked):
+ *   y_0 = x,  y_k = a_k (A y_{k-1}) + b_k y_{k-1} + c_k y_{k-2}   (k = 1..p, y_{-1} = 0)
+ * for n_rhs right-hand sides at once.
+ *   co     coefficients (host), 1 <= co->p <= 63
+ *   dtype  arithmetic and storage type of X and Y (the plan must keep that precision); the
+ *          row sums accumulate in dtype
+ *   X      n x n_rhs input block (column-major, leading dimension ldx >= n; or row-major with
+ *          MPK_RHS_INTERLEAVED)
+ *   Y      output: p+1 blocks y_0..y_p (block k at Y + k*ldy*n_rhs elements), or with
+ *          MPK_FINAL_ONLY one block; ldy >= n
+ *   flags  MPK_* above
+ * Blocked launches run the level-group wavefront with device-side dependency flags; results
+ * are bit-identical to MPK_UNBLOCKED on the same plan.  Asynchronous on stream (except with
+ * MPK_HOST_IO). */
+mpk_status mpk_apply(mpk_plan_t plan, const mpk_coeffs *co, mpk_dtype dtype, const void *X,
+                     int64_t ldx, void *Y, int64_t ldy, int32_t n_rhs, uint32_t flags,
+                     cudaStream_t stream);
+
+/* Wait for the plan's work on stream and report (then clear) a latched device error:
+ * MPK_OK or MPK_ERR_TIMEOUT.  Synchronous. */
+mpk_status mpk_plan_sync(mpk_plan_t plan, cudaStream_t stream);
+
+/* Host helpers for coefficient triples (host arrays of length p). */
+/* Chebyshev basis on [alpha, beta]: y_k = T_k((A - c0 I)/d) x, c0 = (alpha+beta)/2,
+ * d = (beta-alpha)/2 (three-term recursion; Sec. 5.3 Chebyshev smoother). */
+mpk_status mpk_coeffs_chebyshev(double alpha, double beta, int32_t p, double *a, double *b,
+                                double *c);
+/* Newton basis y_k = (A - theta_k I) y_{k-1} (Sec. 4). */
+mpk_status mpk_coeffs_newton(const double *theta, int32_t p, double *a, double *b, double *c);
+/* First `count` of `n` real values in Leja order (first = largest modulus; each next one
+ * maximises the product of distances to those chosen; ties -> smaller value); used for the
+ * Newton shifts from Ritz values (Sec. 4).  Host arrays. */
+mpk_status mpk_leja_order(const double *values, int32_t n, int32_t count, double *out);
+
+/* ------------------------------------------------------------------------------------------
+ * s-step GMRES (Sec. 4, Alg. 3(a)+(c)) with FP64 iterative refinement.
+ * ---------------------------------------------------------------------------------------- */
+typedef struct {
+    int32_t s;              /* block size = MPK powers per block (default 8) */
+    int32_t restart;        /* restart length m (default 48) */
+    double tol;             /* stop when ||b - A x||_2 <= tol ||b||_2 (FP64; default 1e-8) */
+    double inner_tol;       /* inner solve tolerance relative to its rhs (default 1e-5) */
+    int32_t max_outer;      /* refinement steps (default 50) */
+    int32_t inner_cycles;   /* restart cycles per inner solve (default 1) */
+    int32_t max_iters;      /* cap on inner iterations in total (default 100000) */
+    mpk_dtype basis;        /* MPK_F32: FP32 matrix + basis, FP64 Gram/Cholesky/H/x/r;
+                               MPK_F64: everything in FP64 */
+    int32_t bcgs_passes;    /* block classical Gram-Schmidt sweeps (1 or 2; default 1) */
+    const double *shifts;   /* host, s values, or NULL: Ritz values of a first plain GMRES
+                               cycle, Leja-ordered (Sec. 4) */
+} mpk_gmres_opts;
+
+typedef struct {
+    int32_t iters;          /* inner iterations (Krylov columns) in total */
+    int32_t outer;          /* refinement steps taken */
+    int32_t restarts;       /* restart cycles in total */
+    int32_t status;         /* mpk_status of the solve */
+    double rel_residual;    /* true ||b - A x|| / ||b|| in FP64 at exit */
+    double shifts[64];      /* shifts used (first s entries) */
+    double ms_total, ms_mpk, ms_ortho, ms_other;   /* CUDA-event timings per phase */
+} mpk_gmres_info;
+
+mpk_status mpk_gmres_opts_default(mpk_gmres_opts *o);
+
+/* Solve A x = b.  A: a plan holding the precision(s) the options need (FP64 values always,
+ * for the residual; FP32 too when basis = MPK_F32).  b, x: DEVICE FP64 vectors of length n in
+ * the original order; x holds the initial guess on entry and the solution on exit.  info
+ * (host) may be NULL.  Synchronous on stream (the host reads one status word per restart). */
+mpk_status sstep_gmres_solve(mpk_plan_t A, const double *b, double *x, const mpk_gmres_opts *o,
+                             mpk_gmres_info *info, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Serving: a continuously batched stream of s-step GMRES solves on one GPU.
+ * ---------------------------------------------------------------------------------------- */
+typedef struct {
+    int64_t hbm_budget_bytes;   /* device memory the server may hold for requests */
+    int32_t max_active;         /* requests advanced concurrently (slots) */
+    int32_t n_streams;          /* CUDA streams the slots are spread over */
+    mpk_gmres_opts gmres;       /* solver options applied to every request */
+} mpk_server_opts;
+
+typedef struct mpk_server_s *mpk_server_t;
+
+typedef struct {
+    int64_t id;                 /* the id returned by mpk_server_submit */
+    int32_t status;             /* mpk_status of the solve */
+    int32_t iters, outer;
+    double rel_residual;
+    double t_submit_ms, t_start_ms, t_done_ms;   /* host clock, ms since server creation */
+} mpk_server_result;
+
+mpk_status mpk_server_opts_default(mpk_server_opts *o);
+mpk_status mpk_server_create(const mpk_server_opts *o, mpk_server_t *out);
+/* Queue a solve of A x = b.  A: HOST CSR arrays (int32 row_ptr/col, FP64 val); b: HOST FP64,
+ * n entries; x_out: HOST FP64 buffer of n entries that receives the solution when the result
+ * is reported.  The server copies A and b before returning.  *id receives the request id.
+ * Returns MPK_ERR_BUDGET if the request alone exceeds the memory budget. */
+mpk_status mpk_server_submit(mpk_server_t srv, int64_t n, int64_t nnz, const int32_t *row_ptr,
+                             const int32_t *col, const double *val, const double *b,
+                             double *x_out, int64_t *id);
+/* Copy up to max_results finished results into out (host); *n_out receives the count.
+ * Non-blocking: drives the server one round (admission, progress) and returns. */
+mpk_status mpk_server_poll(mpk_server_t srv, mpk_server_result *out, int32_t max_results,
+                           int32_t *n_out);
+/* Number of requests queued or in flight. */
+mpk_status mpk_server_pending(mpk_server_t srv, int64_t *n_pending);
+mpk_status mpk_server_destroy(mpk_server_t srv);
+
+/* Human-readable name of a status. */
+const char *mpk_status_str(mpk_status s);
+
+/* Library build identifier (e.g. "mpk_gb300 sm_103a"). */
+const char *mpk_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPK_GB300_H */

@@ -1,0 +1,148 @@
+// Internal declarations of the GB300 MPK library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <map>
+#include <memory>
+#include <vector>
+
+#include "../../include/mpk.h"
+
+#define MPK_MAX_P 63
+
+// -------------------------------------------------------------------------------------------
+// Error plumbing: every CUDA call is checked; failures become an mpk_status.
+// -------------------------------------------------------------------------------------------
+#define MPK_CUDA(call)                                                                   \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            mpk_log_cuda_error(e_, #call, __FILE__, __LINE__);                           \
+            return e_ == cudaErrorMemoryAllocation ? MPK_ERR_OOM : MPK_ERR_CUDA;         \
+        }                                                                                \
+    } while (0)
+
+#define MPK_TRY(...)                                                                     \
+    do {                                                                                 \
+        mpk_status s_ = (__VA_ARGS__);                                                   \
+        if (s_ != MPK_OK) return s_;                                                     \
+    } while (0)
+
+void mpk_log_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+
+// Device buffer owned by the library (freed on destruction).
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    mpk_status alloc(size_t b) {
+        release();
+        if (b == 0) b = 16;
+        cudaError_t e = cudaMalloc(&p, b);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            cudaGetLastError();
+            return e == cudaErrorMemoryAllocation ? MPK_ERR_OOM : MPK_ERR_CUDA;
+        }
+        bytes = b;
+        return MPK_OK;
+    }
+    // grow-only
+    mpk_status ensure(size_t b) { return (bytes >= b && p) ? MPK_OK : alloc(b); }
+    template <typename T> T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+// Control block of the blocked MPK launches (device memory, one per plan).
+struct MpkCtrl {
+    uint32_t epoch;       // increments once per completed blocked launch
+    uint32_t ticket;      // task dispenser (reset by the last CTA)
+    uint32_t done_ctas;   // CTAs finished in this launch (reset by the last CTA)
+    uint32_t error;       // latched: 1 = a dependency wait ran out
+    uint32_t err_task;    // first task that timed out (diagnostics)
+    uint32_t pad[3];
+};
+
+// Cached blocked schedule for one (segment length) value.
+struct Schedule {
+    int32_t p = 0;
+    int64_t n_tasks = 0;
+    DevBuf tasks;   // uint32: chunk | (k << 24), k = 1..p (power within the segment)
+};
+
+// The plan: level structure, permuted matrix in SELL-32 form, blocked-task metadata.
+struct mpk_plan_s {
+    int device = 0;
+    int n_sm = 0;
+    int64_t l2_bytes = 0;
+    mpk_plan_opts opts{};
+    int32_t p_max = 0;
+    int32_t p_blk = 0;
+    mpk_dtype group_dtype = MPK_F64;   // precision the groups were sized for
+
+    int64_t n = 0, nnz = 0;
+    int32_t n_levels = 0, n_groups = 0, n_slices = 0, n_chunks = 0, root = 0;
+    int32_t bfs_sweeps = 0, max_level_rows = 0;
+    int64_t sell_nnz = 0;
+    double create_ms = 0.0;
+
+    // level structure
+    DevBuf perm, iperm, level, level_ptr, group_ptr;
+    std::vector<int32_t> h_level_ptr, h_group_ptr;
+
+    // permuted CSR (level order)
+    DevBuf rp, ci, val64, val32;
+    bool has64 = false, has32 = false;
+    // map from original CSR entry to permuted entry (for value updates)
+    DevBuf entry_map;
+
+    // SELL-32: slice s covers rows [slice_row[s], slice_row[s+1]) (<= 32 rows); entry (j, lane)
+    // at slice_ptr[s] + 32*j + lane; padding has col = -1.
+    DevBuf slice_row, slice_ptr, slice_len, s_col, s_val64, s_val32;
+
+    // blocked tasks: chunk c = slices [chunk_slice[c], chunk_slice[c+1]) inside one group
+    DevBuf chunk_slice, chunk_row, dep_lo, dep_hi;
+    std::vector<int32_t> h_chunk_group;   // group of each chunk
+    std::vector<int32_t> h_group_chunk;   // first chunk of each group (n_groups+1)
+    DevBuf flags;     // uint32 per chunk
+    DevBuf ctrl;      // MpkCtrl
+    uint64_t launches_since_reset = 0;
+    int ctas_per_sm = 0;
+    int blocked_block = 256;
+    std::map<int, std::unique_ptr<Schedule>> schedules;
+
+    // workspace for permuted / interleaved vectors
+    DevBuf ws_x, ws_y, ws_host;
+    uint32_t latched_error = 0;
+};
+
+// -------------------------------------------------------------------------------------------
+// Helpers implemented in the .cu files
+// -------------------------------------------------------------------------------------------
+// exclusive scan of int32 in[0..n) into out[0..n] (out[n] = total); 64-bit accumulation,
+// error if the total does not fit int32.  tmp: device scratch >= scan_tmp_bytes(n).
+size_t scan_tmp_bytes(int64_t n);
+mpk_status exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t n, void *tmp,
+                              cudaStream_t s);
+
+mpk_status mpk_get_schedule(mpk_plan_s *P, int p, Schedule **out, cudaStream_t s);
+mpk_status mpk_build_blocks(mpk_plan_s *P, cudaStream_t s);
+
+// Row-sum kernels shared by the MPK and the solver (apply.cu)
+mpk_status mpk_launch_residual(mpk_plan_s *P, const double *x, const double *b, double *r,
+                               cudaStream_t s);
+mpk_status mpk_apply_internal(mpk_plan_s *P, const mpk_coeffs *co, mpk_dtype dtype,
+                              const void *X, int64_t ldx, void *Y, int64_t ldy, int32_t n_rhs,
+                              uint32_t flags, cudaStream_t stream);
+
+static inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }

@@ -1,0 +1,1102 @@
+// Plan construction: the paper's pre-processing (Sec. 3) done on the GPU.
+//
+//   BFS levels of the graph of A + A^T (Sec. 3: RACE analyses the matrix graph by a BFS),
+//   George-Liu root search, rows sorted by (level, index), B = P A P^T, level groups under a
+//   byte budget (the cache-size parameter C of Sec. 4), SELL-32 slices inside each group,
+//   blocked tasks (chunks of slices) with their dependency ranges.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <numeric>
+
+#include "mpk_internal.cuh"
+
+void mpk_log_cuda_error(cudaError_t e, const char *what, const char *file, int line) {
+    fprintf(stderr, "[mpk] CUDA error %s (%d) in %s at %s:%d\n", cudaGetErrorString(e), (int)e,
+            what, file, line);
+}
+
+// ============================================================================================
+// Exclusive scan (int32 or int64 output, 64-bit accumulation), three phases.
+// ============================================================================================
+static constexpr int SCAN_BLOCK = 256;
+static constexpr int SCAN_ITEMS = 8;
+static constexpr int SCAN_TILE = SCAN_BLOCK * SCAN_ITEMS;
+
+template <typename TI>
+__global__ void scan_partials_kernel(const TI *in, int64_t n, long long *part) {
+    __shared__ long long sh[SCAN_BLOCK];
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    long long s = 0;
+    for (int i = 0; i < SCAN_ITEMS; i++) {
+        int64_t idx = base + (int64_t)i * SCAN_BLOCK + threadIdx.x;
+        if (idx < n) s += (long long)in[idx];
+    }
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int st = SCAN_BLOCK / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+// single block: exclusive scan of part[0..m) in place, total into part[m]
+__global__ void scan_top_kernel(long long *part, int64_t m) {
+    __shared__ long long sh[SCAN_BLOCK];
+    __shared__ long long carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < m; base += SCAN_BLOCK) {
+        int64_t idx = base + threadIdx.x;
+        long long v = idx < m ? part[idx] : 0;
+        sh[threadIdx.x] = v;
+        __syncthreads();
+        for (int off = 1; off < SCAN_BLOCK; off <<= 1) {
+            long long t = threadIdx.x >= off ? sh[threadIdx.x - off] : 0;
+            __syncthreads();
+            sh[threadIdx.x] += t;
+            __syncthreads();
+        }
+        if (idx < m) part[idx] = carry + sh[threadIdx.x] - v;
+        __syncthreads();
+        if (threadIdx.x == SCAN_BLOCK - 1) carry += sh[SCAN_BLOCK - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[m] = carry;
+}
+
+template <typename TI, typename TO>
+__global__ void scan_final_kernel(const TI *in, TO *out, int64_t n, const long long *part) {
+    __shared__ long long sh[SCAN_TILE];
+    int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+    // load tile (coalesced), then each thread scans SCAN_ITEMS consecutive entries
+    for (int i = 0; i < SCAN_ITEMS; i++) {
+        int64_t idx = base + (int64_t)i * SCAN_BLOCK + threadIdx.x;
+        sh[i * SCAN_BLOCK + threadIdx.x] = idx < n ? (long long)in[idx] : 0;
+    }
+    __syncthreads();
+    long long loc[SCAN_ITEMS];
+    long long s = 0;
+    for (int i = 0; i < SCAN_ITEMS; i++) {
+        loc[i] = s;
+        s += sh[threadIdx.x * SCAN_ITEMS + i];
+    }
+    __shared__ long long tsum[SCAN_BLOCK];
+    tsum[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < SCAN_BLOCK; off <<= 1) {
+        long long t = threadIdx.x >= off ? tsum[threadIdx.x - off] : 0;
+        __syncthreads();
+        tsum[threadIdx.x] += t;
+        __syncthreads();
+    }
+    long long excl = tsum[threadIdx.x] - s + part[blockIdx.x];
+    __syncthreads();
+    for (int i = 0; i < SCAN_ITEMS; i++) sh[threadIdx.x * SCAN_ITEMS + i] = excl + loc[i];
+    __syncthreads();
+    for (int i = 0; i < SCAN_ITEMS; i++) {
+        int64_t idx = base + (int64_t)i * SCAN_BLOCK + threadIdx.x;
+        if (idx < n) out[idx] = (TO)sh[i * SCAN_BLOCK + threadIdx.x];
+    }
+}
+
+template <typename TO> __global__ void scan_total_kernel(TO *out, int64_t n, const long long *part, int64_t m) {
+    out[n] = (TO)part[m];
+}
+
+size_t scan_tmp_bytes(int64_t n) { return (size_t)(ceil_div(n, SCAN_TILE) + 2) * sizeof(long long); }
+
+template <typename TI, typename TO>
+static mpk_status exclusive_scan(const TI *in, TO *out, int64_t n, void *tmp, cudaStream_t s) {
+    int64_t m = ceil_div(n, SCAN_TILE);
+    long long *part = (long long *)tmp;
+    if (m > 0) scan_partials_kernel<TI><<<(unsigned)m, SCAN_BLOCK, 0, s>>>(in, n, part);
+    scan_top_kernel<<<1, SCAN_BLOCK, 0, s>>>(part, m);
+    if (m > 0) scan_final_kernel<TI, TO><<<(unsigned)m, SCAN_BLOCK, 0, s>>>(in, out, n, part);
+    scan_total_kernel<TO><<<1, 1, 0, s>>>(out, n, part, m);
+    MPK_CUDA(cudaGetLastError());
+    return MPK_OK;
+}
+
+mpk_status exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t n, void *tmp,
+                              cudaStream_t s) {
+    return exclusive_scan<int32_t, int32_t>(in, out, n, tmp, s);
+}
+
+// ============================================================================================
+// Small element-wise kernels
+// ============================================================================================
+__global__ void fill_i32_kernel(int32_t *p, int64_t n, int32_t v) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+__global__ void iota_kernel(int32_t *p, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = (int32_t)i;
+}
+static unsigned grid_for(int64_t n, int block = 256) {
+    int64_t g = ceil_div(n, block);
+    if (g > 152 * 32) g = 152 * 32;
+    return (unsigned)std::max<int64_t>(g, 1);
+}
+
+// CSR validation: row_ptr monotone, row_ptr[0] = 0, row_ptr[n] = nnz, cols in range.
+__global__ void validate_kernel(const int32_t *rp, const int32_t *ci, int64_t n, int64_t nnz,
+                                unsigned *bad) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t a = rp[i], b = rp[i + 1];
+        if (a > b || a < 0 || (int64_t)b > nnz) { atomicOr(bad, 1u); continue; }
+        for (int32_t t = a; t < b; t++) {
+            int32_t c = ci[t];
+            if (c < 0 || (int64_t)c >= n) { atomicOr(bad, 2u); break; }
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (rp[0] != 0 || (int64_t)rp[n] != nnz) atomicOr(bad, 4u);
+    }
+}
+
+// ============================================================================================
+// Transpose pattern (for the BFS on A + A^T when the pattern may be unsymmetric)
+// ============================================================================================
+__global__ void col_count_kernel(const int32_t *ci, int64_t nnz, int32_t *cnt) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nnz;
+         t += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[ci[t]], 1);
+}
+__global__ void transpose_fill_kernel(const int32_t *rp, const int32_t *ci, int64_t n,
+                                      int32_t *cursor, int32_t *ciT) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        for (int32_t t = rp[i]; t < rp[i + 1]; t++) {
+            int32_t pos = atomicAdd(&cursor[ci[t]], 1);
+            ciT[pos] = (int32_t)i;
+        }
+}
+
+// ============================================================================================
+// BFS: one cooperative persistent kernel per component, level-synchronous, warp per frontier
+// vertex, with a bounded grid barrier (the wait gives up after timeout_ns and raises error).
+// ============================================================================================
+struct BfsCtl {
+    int32_t qsize[2];
+    uint32_t bar_count;
+    uint32_t bar_gen;
+    uint32_t error;
+    int32_t top;             // highest level assigned
+    long long visited;       // rows labelled by this BFS
+    unsigned long long argmin;   // (degree << 32) | row, minimum over the last level
+};
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// returns false (on every thread of the block) if the barrier timed out
+__device__ bool grid_barrier_bounded(BfsCtl *ctl, unsigned nblocks, uint64_t timeout_ns) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        uint32_t gen = ld_acquire_u32(&ctl->bar_gen);
+        __threadfence();
+        uint32_t arrived = atomicAdd(&ctl->bar_count, 1u);
+        if (arrived == nblocks - 1) {
+            ctl->bar_count = 0;
+            __threadfence();
+            st_release_u32(&ctl->bar_gen, gen + 1);
+        } else {
+            uint64_t t0 = globaltimer_ns();
+            unsigned backoff = 32;
+            while (ld_acquire_u32(&ctl->bar_gen) == gen) {
+                if (ld_acquire_u32(&ctl->error)) { ok = 0; break; }
+                if (globaltimer_ns() - t0 > timeout_ns) {
+                    atomicOr(&ctl->error, 1u);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(backoff);
+                if (backoff < 1024) backoff <<= 1;
+            }
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+struct BfsArgs {
+    int64_t n;
+    const int32_t *rp, *ci;      // A
+    const int32_t *rpT, *ciT;    // A^T (nullable: symmetric pattern)
+    int32_t *level;
+    int32_t *q0, *q1;
+    BfsCtl *ctl;
+    int32_t base;                // level of the root
+    uint64_t timeout_ns;
+};
+
+__device__ __forceinline__ long long degree_of(const BfsArgs &a, int32_t v) {
+    long long d = a.rp[v + 1] - a.rp[v];
+    if (a.rpT) d += a.rpT[v + 1] - a.rpT[v];
+    else d *= 2;   // symmetric pattern: column count equals row count
+    return d;
+}
+
+__device__ __forceinline__ void expand_list(const BfsArgs &a, const int32_t *adj, int32_t beg,
+                                            int32_t end, int32_t next_level, int32_t *out,
+                                            int32_t *out_size, int lane) {
+    for (int32_t t0 = beg; t0 < end; t0 += 32) {
+        int32_t t = t0 + lane;
+        bool push = false;
+        int32_t j = 0;
+        if (t < end) {
+            j = adj[t];
+            if (a.level[j] == -1) push = (atomicCAS(&a.level[j], -1, next_level) == -1);
+        }
+        unsigned m = __ballot_sync(0xffffffffu, push);
+        if (m) {
+            int32_t base = 0;
+            if (lane == 0) base = atomicAdd(out_size, __popc(m));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (push) out[base + __popc(m & ((1u << lane) - 1))] = j;
+        }
+    }
+}
+
+__global__ void bfs_kernel(BfsArgs a) {
+    const unsigned nblocks = gridDim.x;
+    const int lane = threadIdx.x & 31;
+    const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    int cur = 0;
+    int32_t L = a.base;
+    int32_t last_f = 0;
+    int last_buf = 0;
+    long long visited = 0;
+    while (true) {
+        int32_t f = *(volatile int32_t *)&a.ctl->qsize[cur];
+        if (f == 0) break;
+        visited += f;
+        last_f = f;
+        last_buf = cur;
+        const int32_t *in = cur ? a.q1 : a.q0;
+        int32_t *out = cur ? a.q0 : a.q1;
+        int32_t *osz = &a.ctl->qsize[cur ^ 1];
+        for (int64_t i = gwarp; i < f; i += nwarps) {
+            int32_t v = in[i];
+            expand_list(a, a.ci, a.rp[v], a.rp[v + 1], L + 1, out, osz, lane);
+            if (a.rpT) expand_list(a, a.ciT, a.rpT[v], a.rpT[v + 1], L + 1, out, osz, lane);
+        }
+        if (!grid_barrier_bounded(a.ctl, nblocks, a.timeout_ns)) return;
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->qsize[cur] = 0;
+        // the reset must be visible before the next level's pushes into this buffer's counter
+        if (!grid_barrier_bounded(a.ctl, nblocks, a.timeout_ns)) return;
+        cur ^= 1;
+        L++;
+    }
+    // L is one past the last level; the last frontier sits in buffer last_buf
+    const int32_t *lastq = last_buf ? a.q1 : a.q0;
+    int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t i = gtid; i < last_f; i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t v = lastq[i];
+        unsigned long long key = ((unsigned long long)degree_of(a, v) << 32) | (uint32_t)v;
+        atomicMin(&a.ctl->argmin, key);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.ctl->top = L - 1;
+        a.ctl->visited = visited;
+    }
+}
+
+__global__ void bfs_init_kernel(BfsCtl *ctl, int32_t *level, int32_t *q0, int32_t root,
+                                int32_t base) {
+    ctl->qsize[0] = 1;
+    ctl->qsize[1] = 0;
+    ctl->bar_count = 0;
+    ctl->bar_gen = 0;
+    ctl->error = 0;
+    ctl->top = base;
+    ctl->visited = 0;
+    ctl->argmin = ~0ull;
+    level[root] = base;
+    q0[0] = root;
+}
+
+// first index >= from with level == -1 inside [from, to); result via atomicMin
+__global__ void first_unvisited_kernel(const int32_t *level, int64_t from, int64_t to,
+                                       unsigned long long *res) {
+    for (int64_t i = from + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < to;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (level[i] == -1) { atomicMin(res, (unsigned long long)i); return; }
+}
+
+struct BfsResult {
+    int32_t top;
+    long long visited;
+    int32_t argmin_row;
+};
+
+struct BfsRunner {
+    BfsArgs args{};
+    DevBuf ctl_buf;
+    int grid = 0, block = 256;
+    mpk_status run(int32_t root, int32_t base, int32_t *level, cudaStream_t s, BfsResult *res) {
+        BfsCtl *ctl = ctl_buf.as<BfsCtl>();
+        bfs_init_kernel<<<1, 1, 0, s>>>(ctl, level, args.q0, root, base);
+        MPK_CUDA(cudaGetLastError());
+        BfsArgs a = args;
+        a.level = level;
+        a.ctl = ctl;
+        a.base = base;
+        void *kargs[] = {&a};
+        MPK_CUDA(cudaLaunchCooperativeKernel((void *)bfs_kernel, dim3(grid), dim3(block), kargs,
+                                             0, s));
+        BfsCtl h;
+        MPK_CUDA(cudaMemcpyAsync(&h, ctl, sizeof(h), cudaMemcpyDeviceToHost, s));
+        MPK_CUDA(cudaStreamSynchronize(s));
+        if (h.error) return MPK_ERR_TIMEOUT;
+        res->top = h.top;
+        res->visited = h.visited;
+        res->argmin_row = (int32_t)(h.argmin & 0xffffffffull);
+        return MPK_OK;
+    }
+};
+
+// ============================================================================================
+// Stable LSD radix sort of (key = level, value = row) by 8-bit digits.
+// ============================================================================================
+static constexpr int RS_BLOCK = 256;
+static constexpr int RS_ITEMS = 8;
+static constexpr int RS_TILE = RS_BLOCK * RS_ITEMS;
+
+__global__ void rs_hist_kernel(const int32_t *keys, int64_t n, int shift, int32_t *hist,
+                               int64_t n_tiles) {
+    __shared__ int32_t cnt[256];
+    cnt[threadIdx.x] = 0;
+    __syncthreads();
+    int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    for (int i = 0; i < RS_ITEMS; i++) {
+        int64_t idx = base + (int64_t)i * RS_BLOCK + threadIdx.x;
+        if (idx < n) atomicAdd(&cnt[(keys[idx] >> shift) & 255], 1);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * n_tiles + blockIdx.x] = cnt[threadIdx.x];
+}
+
+// order inside a tile: round r handles items base + r*256 + tid, so the tile is visited in
+// index order; ranks among equal digits come from warp match masks and per-warp counts.
+__global__ void rs_scatter_kernel(const int32_t *keys, const int32_t *vals, int64_t n, int shift,
+                                  const int32_t *offs, int64_t n_tiles, int32_t *keys_out,
+                                  int32_t *vals_out) {
+    __shared__ int32_t wcnt[RS_BLOCK / 32][256];
+    __shared__ int32_t run[256];
+    __shared__ int32_t tot[256];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    run[tid] = offs[(int64_t)tid * n_tiles + blockIdx.x];
+    int64_t base = (int64_t)blockIdx.x * RS_TILE;
+    for (int r = 0; r < RS_ITEMS; r++) {
+        for (int q = 0; q < RS_BLOCK / 32; q++) wcnt[q][tid] = 0;
+        __syncthreads();
+        int64_t idx = base + (int64_t)r * RS_BLOCK + tid;
+        bool valid = idx < n;
+        int32_t key = valid ? keys[idx] : 0;
+        int32_t val = valid ? vals[idx] : 0;
+        unsigned d = valid ? (unsigned)((key >> shift) & 255) : 256u;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        int rank = __popc(peers & ((1u << lane) - 1));
+        if (valid && rank == 0) wcnt[w][d] = __popc(peers);
+        __syncthreads();
+        {   // exclusive prefix over warps for digit tid
+            int32_t acc = 0;
+            for (int q = 0; q < RS_BLOCK / 32; q++) {
+                int32_t t = wcnt[q][tid];
+                wcnt[q][tid] = acc;
+                acc += t;
+            }
+            tot[tid] = acc;
+        }
+        __syncthreads();
+        if (valid) {
+            int32_t pos = run[d] + wcnt[w][d] + rank;
+            keys_out[pos] = key;
+            vals_out[pos] = val;
+        }
+        __syncthreads();
+        run[tid] += tot[tid];
+        __syncthreads();
+    }
+}
+
+// ============================================================================================
+// Permutation, level pointer, permuted CSR
+// ============================================================================================
+__global__ void iperm_kernel(const int32_t *perm, int64_t n, int32_t *iperm) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x)
+        iperm[perm[r]] = (int32_t)r;
+}
+__global__ void level_hist_kernel(const int32_t *level, int64_t n, int32_t *cnt) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&cnt[level[i]], 1);
+}
+__global__ void perm_rowlen_kernel(const int32_t *rp, const int32_t *perm, int64_t n, int32_t *len) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        int32_t o = perm[r];
+        len[r] = rp[o + 1] - rp[o];
+    }
+}
+
+// warp per row of length <= 32: bitonic sort of (new column, stored position) keys
+template <typename TV>
+__global__ void permute_rows_warp_kernel(const int32_t *rp, const int32_t *ci, const TV *val,
+                                         const int32_t *perm, const int32_t *iperm,
+                                         const int32_t *rp_new, int64_t n, int32_t *ci_new,
+                                         double *v64, float *v32, int32_t *entry_map,
+                                         int32_t *long_rows, int32_t *n_long) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n;
+         r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        int32_t o = perm[r];
+        int32_t beg = rp[o], len = rp[o + 1] - beg;
+        if (len > 32) {
+            if (lane == 0) long_rows[atomicAdd(n_long, 1)] = (int32_t)r;
+            continue;
+        }
+        unsigned long long key = ~0ull;
+        if (lane < len) key = ((unsigned long long)(uint32_t)iperm[ci[beg + lane]] << 32) | (uint32_t)lane;
+        // bitonic sort ascending across the warp
+        for (int k = 2; k <= 32; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                unsigned long long other = __shfl_xor_sync(0xffffffffu, key, j);
+                bool up = ((lane & k) == 0);
+                bool lower = ((lane & j) == 0);
+                unsigned long long mn = key < other ? key : other;
+                unsigned long long mx = key < other ? other : key;
+                key = (lower == up) ? mn : mx;
+            }
+        }
+        if (lane < len) {
+            int32_t src = beg + (int32_t)(key & 0xffffffffull);
+            int32_t dst = rp_new[r] + lane;
+            ci_new[dst] = (int32_t)(key >> 32);
+            TV v = val[src];
+            if (v64) v64[dst] = (double)v;
+            if (v32) v32[dst] = (float)v;
+            entry_map[src] = dst;
+        }
+    }
+}
+
+// block per long row: rank of each entry among (new column, stored position) by counting
+template <typename TV>
+__global__ void permute_rows_long_kernel(const int32_t *rp, const int32_t *ci, const TV *val,
+                                         const int32_t *perm, const int32_t *iperm,
+                                         const int32_t *rp_new, const int32_t *long_rows,
+                                         int32_t *ci_new, double *v64, float *v32,
+                                         int32_t *entry_map) {
+    int32_t r = long_rows[blockIdx.x];
+    int32_t o = perm[r];
+    int32_t beg = rp[o], len = rp[o + 1] - beg;
+    for (int32_t t = threadIdx.x; t < len; t += blockDim.x) {
+        int32_t ct = iperm[ci[beg + t]];
+        int32_t rank = 0;
+        for (int32_t u = 0; u < len; u++) {
+            int32_t cu = iperm[ci[beg + u]];
+            rank += (cu < ct) || (cu == ct && u < t);
+        }
+        int32_t dst = rp_new[r] + rank;
+        ci_new[dst] = ct;
+        TV v = val[beg + t];
+        if (v64) v64[dst] = (double)v;
+        if (v32) v32[dst] = (float)v;
+        entry_map[beg + t] = dst;
+    }
+}
+
+template <typename TV>
+__global__ void update_values_kernel(const TV *val, const int32_t *entry_map, int64_t nnz,
+                                     double *v64, float *v32) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nnz;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int32_t d = entry_map[t];
+        TV v = val[t];
+        if (v64) v64[d] = (double)v;
+        if (v32) v32[d] = (float)v;
+    }
+}
+
+__global__ void gather_rp_kernel(const int32_t *rp, const int32_t *idx, int64_t m, int32_t *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = rp[idx[i]];
+}
+
+// ============================================================================================
+// SELL-32 slices, chunks, dependency ranges
+// ============================================================================================
+__global__ void slice_len_kernel(const int32_t *rp, const int32_t *slice_row, int64_t n_slices,
+                                 int32_t *slice_len) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < n_slices;
+         s += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        int32_t r0 = slice_row[s], r1 = slice_row[s + 1];
+        int32_t r = r0 + lane;
+        int32_t len = r < r1 ? rp[r + 1] - rp[r] : 0;
+        for (int o = 16; o > 0; o >>= 1) len = max(len, __shfl_xor_sync(0xffffffffu, len, o));
+        if (lane == 0) slice_len[s] = len;
+    }
+}
+
+__global__ void sell_fill_kernel(const int32_t *rp, const int32_t *ci, const double *v64,
+                                 const float *v32, const int32_t *slice_row,
+                                 const int32_t *slice_len, const long long *slice_ptr,
+                                 int64_t n_slices, int32_t *s_col, double *s64, float *s32) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < n_slices;
+         s += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        int32_t r0 = slice_row[s], r1 = slice_row[s + 1];
+        int32_t r = r0 + lane;
+        int32_t beg = 0, len = 0;
+        if (r < r1) { beg = rp[r]; len = rp[r + 1] - beg; }
+        int32_t L = slice_len[s];
+        long long p0 = 32ll * slice_ptr[s];
+        for (int32_t j = 0; j < L; j++) {
+            long long d = p0 + 32ll * j + lane;
+            if (j < len) {
+                s_col[d] = ci[beg + j];
+                if (s64) s64[d] = v64[beg + j];
+                if (s32) s32[d] = v32[beg + j];
+            } else {
+                s_col[d] = -1;
+                if (s64) s64[d] = 0.0;
+                if (s32) s32[d] = 0.0f;
+            }
+        }
+    }
+}
+
+__global__ void row_chunk_kernel(const int32_t *chunk_row, int64_t n_chunks, int32_t *row_chunk) {
+    for (int64_t c = blockIdx.x; c < n_chunks; c += gridDim.x)
+        for (int32_t r = chunk_row[c] + threadIdx.x; r < chunk_row[c + 1]; r += blockDim.x)
+            row_chunk[r] = (int32_t)c;
+}
+
+// dependency range of a chunk: the chunks holding any column of its rows (and itself); with
+// `sym_close` also the chunks whose rows reference it (closure over A^T), which the 3-buffer
+// ring of MPK_FINAL_ONLY needs for unsymmetric patterns.
+__global__ void dep_kernel(const int32_t *rp, const int32_t *ci, const int32_t *row_chunk,
+                           int64_t n, int sym_close, int32_t *dep_lo, int32_t *dep_hi) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        int32_t c = row_chunk[r];
+        int32_t lo = c, hi = c;
+        int32_t beg = rp[r], end = rp[r + 1];
+        if (end > beg) {
+            // columns are ascending inside each row
+            lo = min(lo, row_chunk[ci[beg]]);
+            hi = max(hi, row_chunk[ci[end - 1]]);
+        }
+        atomicMin(&dep_lo[c], lo);
+        atomicMax(&dep_hi[c], hi);
+        if (sym_close)
+            for (int32_t t = beg; t < end; t++) {
+                int32_t cc = row_chunk[ci[t]];
+                atomicMin(&dep_lo[cc], c);
+                atomicMax(&dep_hi[cc], c);
+            }
+    }
+}
+
+// ============================================================================================
+// Host orchestration
+// ============================================================================================
+extern "C" mpk_status mpk_plan_opts_default(mpk_plan_opts *o) {
+    if (!o) return MPK_ERR_ARG;
+    memset(o, 0, sizeof(*o));
+    o->l2_budget_bytes = 0;
+    o->p_blk = 0;
+    o->root_rule = 0;
+    o->n_sweeps = 2;
+    o->assume_symmetric = 0;
+    o->chunk_slices = 8;
+    o->keep_f32 = 0;
+    o->keep_f64 = 0;
+    o->ctas_per_sm = 0;
+    o->wait_timeout_us = 2000000u;
+    return MPK_OK;
+}
+
+template <typename T> static mpk_status upload(DevBuf &b, const std::vector<T> &h, cudaStream_t s) {
+    MPK_TRY(b.alloc(std::max<size_t>(h.size(), 1) * sizeof(T)));
+    if (!h.empty())
+        MPK_CUDA(cudaMemcpyAsync(b.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    return MPK_OK;
+}
+
+static mpk_status plan_create_impl(const mpk_csr *A, int32_t p_max, const mpk_plan_opts *opts,
+                                   cudaStream_t s, mpk_plan_s *P) {
+    auto t0 = std::chrono::steady_clock::now();
+    if (opts) P->opts = *opts;
+    else mpk_plan_opts_default(&P->opts);
+    mpk_plan_opts &o = P->opts;
+    if (o.n_sweeps < 0 || o.chunk_slices <= 0 || o.root_rule < 0 || o.root_rule > 1)
+        return MPK_ERR_ARG;
+    const int64_t n = A->n, nnz = A->nnz;
+    P->n = n;
+    P->nnz = nnz;
+    P->p_max = p_max;
+    P->p_blk = (o.p_blk > 0 && o.p_blk < p_max) ? o.p_blk : p_max;
+    if (!o.keep_f32 && !o.keep_f64) {
+        if (A->dtype == MPK_F64) o.keep_f64 = 1;
+        else o.keep_f32 = 1;
+    }
+    P->has64 = o.keep_f64 != 0;
+    P->has32 = o.keep_f32 != 0;
+    // the groups are sized for the MPK precision: FP32 whenever an FP32 copy is kept (the
+    // FP64 copy then only serves residuals), else FP64
+    P->group_dtype = P->has32 ? MPK_F32 : MPK_F64;
+
+    MPK_CUDA(cudaGetDevice(&P->device));
+    MPK_CUDA(cudaDeviceGetAttribute(&P->n_sm, cudaDevAttrMultiProcessorCount, P->device));
+    int l2 = 0;
+    MPK_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, P->device));
+    P->l2_bytes = l2;
+    if (o.l2_budget_bytes <= 0) o.l2_budget_bytes = P->l2_bytes / 2;
+    if (o.wait_timeout_us == 0) o.wait_timeout_us = 2000000u;
+
+    // ---- control block and flags allocated early so an empty matrix still has them
+    MPK_TRY(P->ctrl.alloc(sizeof(MpkCtrl)));
+    MPK_CUDA(cudaMemsetAsync(P->ctrl.p, 0, sizeof(MpkCtrl), s));
+    {
+        uint32_t one = 1;   // epoch starts at 1 so that zeroed flags are below every target
+        MPK_CUDA(cudaMemcpyAsync(P->ctrl.p, &one, sizeof(one), cudaMemcpyHostToDevice, s));
+    }
+
+    // ---- validation (row pointer monotone and consistent, columns in range)
+    if (n > 0) {
+        DevBuf bad;
+        MPK_TRY(bad.alloc(sizeof(unsigned)));
+        MPK_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(unsigned), s));
+        validate_kernel<<<grid_for(n), 256, 0, s>>>(A->row_ptr, A->col, n, nnz, bad.as<unsigned>());
+        MPK_CUDA(cudaGetLastError());
+        unsigned hbad = 0;
+        MPK_CUDA(cudaMemcpyAsync(&hbad, bad.p, sizeof(hbad), cudaMemcpyDeviceToHost, s));
+        MPK_CUDA(cudaStreamSynchronize(s));
+        if (hbad) return MPK_ERR_ARG;
+    }
+
+    const size_t tmp_bytes = std::max(scan_tmp_bytes(n + 1), scan_tmp_bytes(nnz + 1));
+    DevBuf tmp;
+    MPK_TRY(tmp.alloc(std::max<size_t>(tmp_bytes, 256 * 8192 * 8)));
+
+    // ---- transpose pattern (unless the caller states the pattern is symmetric)
+    DevBuf rpT, ciT, cursor;
+    const bool sym = o.assume_symmetric != 0;
+    if (!sym) {
+        MPK_TRY(cursor.alloc((n + 1) * sizeof(int32_t)));
+        MPK_TRY(rpT.alloc((n + 1) * sizeof(int32_t)));
+        MPK_TRY(ciT.alloc(std::max<int64_t>(nnz, 1) * sizeof(int32_t)));
+        MPK_CUDA(cudaMemsetAsync(cursor.p, 0, (n + 1) * sizeof(int32_t), s));
+        col_count_kernel<<<grid_for(nnz), 256, 0, s>>>(A->col, nnz, cursor.as<int32_t>());
+        MPK_TRY(exclusive_scan<int32_t, int32_t>(cursor.as<int32_t>(), rpT.as<int32_t>(), n, tmp.p, s));
+        MPK_CUDA(cudaMemcpyAsync(cursor.p, rpT.p, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+        transpose_fill_kernel<<<grid_for(n), 256, 0, s>>>(A->row_ptr, A->col, n, cursor.as<int32_t>(), ciT.as<int32_t>());
+        MPK_CUDA(cudaGetLastError());
+    }
+
+    // ---- BFS levels + George-Liu root
+    MPK_TRY(P->level.alloc(n * sizeof(int32_t)));
+    DevBuf lev2, q0, q1;
+    MPK_TRY(lev2.alloc(n * sizeof(int32_t)));
+    MPK_TRY(q0.alloc(n * sizeof(int32_t)));
+    MPK_TRY(q1.alloc(n * sizeof(int32_t)));
+    BfsRunner bfs;
+    MPK_TRY(bfs.ctl_buf.alloc(sizeof(BfsCtl)));
+    {
+        int occ = 0;
+        MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bfs_kernel, bfs.block, 0));
+        bfs.grid = P->n_sm * std::max(1, std::min(occ, 4));
+        bfs.args.n = n;
+        bfs.args.rp = A->row_ptr;
+        bfs.args.ci = A->col;
+        bfs.args.rpT = sym ? nullptr : rpT.as<int32_t>();
+        bfs.args.ciT = sym ? nullptr : ciT.as<int32_t>();
+        bfs.args.q0 = q0.as<int32_t>();
+        bfs.args.q1 = q1.as<int32_t>();
+        bfs.args.timeout_ns = (uint64_t)o.wait_timeout_us * 1000ull;
+    }
+    int32_t n_levels = 0;
+    if (n > 0) {
+        int32_t *levA = P->level.as<int32_t>(), *levB = lev2.as<int32_t>();
+        fill_i32_kernel<<<grid_for(n), 256, 0, s>>>(levA, n, -1);
+        BfsResult cur;
+        MPK_TRY(bfs.run(0, 0, levA, s, &cur));
+        P->bfs_sweeps = 1;
+        int32_t root = 0;
+        if (o.root_rule == 0) {
+            for (int sw = 0; sw < o.n_sweeps; sw++) {
+                int32_t cand = cur.argmin_row;
+                fill_i32_kernel<<<grid_for(n), 256, 0, s>>>(levB, n, -1);
+                BfsResult nxt;
+                MPK_TRY(bfs.run(cand, 0, levB, s, &nxt));
+                P->bfs_sweeps++;
+                if (nxt.top > cur.top) {
+                    std::swap(levA, levB);
+                    root = cand;
+                    cur = nxt;
+                } else {
+                    break;
+                }
+            }
+        }
+        if (levA != P->level.as<int32_t>())
+            MPK_CUDA(cudaMemcpyAsync(P->level.p, levA, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+        levA = P->level.as<int32_t>();
+        P->root = root;
+        // remaining components: lowest-index unvisited row, one level above the last
+        long long visited = cur.visited;
+        int32_t top = cur.top;
+        int64_t scan_pos = 0;
+        const int64_t W = 1 << 20;
+        DevBuf resb;
+        MPK_TRY(resb.alloc(sizeof(unsigned long long)));
+        unsigned long long *res = resb.as<unsigned long long>();
+        while (visited < n) {
+            unsigned long long h = ~0ull;
+            while (h == ~0ull && scan_pos < n) {
+                MPK_CUDA(cudaMemsetAsync(res, 0xff, sizeof(*res), s));
+                int64_t to = std::min<int64_t>(n, scan_pos + W);
+                first_unvisited_kernel<<<grid_for(to - scan_pos), 256, 0, s>>>(levA, scan_pos, to, res);
+                MPK_CUDA(cudaMemcpyAsync(&h, res, sizeof(h), cudaMemcpyDeviceToHost, s));
+                MPK_CUDA(cudaStreamSynchronize(s));
+                if (h == ~0ull) scan_pos = to;
+            }
+            if (h == ~0ull) return MPK_ERR_CUDA;   // visited count and labels disagree
+            scan_pos = (int64_t)h;
+            BfsResult cr;
+            MPK_TRY(bfs.run((int32_t)h, top + 1, levA, s, &cr));
+            visited += cr.visited;
+            top = cr.top;
+        }
+        n_levels = top + 1;
+    }
+    P->n_levels = n_levels;
+    q1.release();
+
+    // ---- stable sort of rows by level: perm, iperm, level_ptr
+    MPK_TRY(P->perm.alloc(n * sizeof(int32_t)));
+    MPK_TRY(P->iperm.alloc(n * sizeof(int32_t)));
+    MPK_TRY(P->level_ptr.alloc((n_levels + 1) * sizeof(int32_t)));
+    if (n > 0) {
+        DevBuf kA, kB, vA, vB, hist;
+        MPK_TRY(kA.alloc(n * 4));
+        MPK_TRY(kB.alloc(n * 4));
+        MPK_TRY(vA.alloc(n * 4));
+        MPK_TRY(vB.alloc(n * 4));
+        int64_t n_tiles = ceil_div(n, RS_TILE);
+        MPK_TRY(hist.alloc((256 * n_tiles + 1) * sizeof(int32_t)));
+        DevBuf offs;
+        MPK_TRY(offs.alloc((256 * n_tiles + 1) * sizeof(int32_t)));
+        DevBuf stmp;
+        MPK_TRY(stmp.alloc(scan_tmp_bytes(256 * n_tiles + 1)));
+        MPK_CUDA(cudaMemcpyAsync(kA.p, P->level.p, n * 4, cudaMemcpyDeviceToDevice, s));
+        iota_kernel<<<grid_for(n), 256, 0, s>>>(vA.as<int32_t>(), n);
+        int32_t *ki = kA.as<int32_t>(), *ko = kB.as<int32_t>();
+        int32_t *vi = vA.as<int32_t>(), *vo = vB.as<int32_t>();
+        for (int shift = 0; shift == 0 || (shift < 31 && ((int64_t)1 << shift) < n_levels); shift += 8) {
+            rs_hist_kernel<<<(unsigned)n_tiles, RS_BLOCK, 0, s>>>(ki, n, shift, hist.as<int32_t>(), n_tiles);
+            MPK_TRY(exclusive_scan<int32_t, int32_t>(hist.as<int32_t>(), offs.as<int32_t>(), 256 * n_tiles, stmp.p, s));
+            rs_scatter_kernel<<<(unsigned)n_tiles, RS_BLOCK, 0, s>>>(ki, vi, n, shift, offs.as<int32_t>(), n_tiles, ko, vo);
+            MPK_CUDA(cudaGetLastError());
+            std::swap(ki, ko);
+            std::swap(vi, vo);
+        }
+        MPK_CUDA(cudaMemcpyAsync(P->perm.p, vi, n * 4, cudaMemcpyDeviceToDevice, s));
+        iperm_kernel<<<grid_for(n), 256, 0, s>>>(P->perm.as<int32_t>(), n, P->iperm.as<int32_t>());
+        DevBuf cnt;
+        MPK_TRY(cnt.alloc((n_levels + 1) * 4));
+        MPK_CUDA(cudaMemsetAsync(cnt.p, 0, (n_levels + 1) * 4, s));
+        level_hist_kernel<<<grid_for(n), 256, 0, s>>>(P->level.as<int32_t>(), n, cnt.as<int32_t>());
+        MPK_TRY(exclusive_scan<int32_t, int32_t>(cnt.as<int32_t>(), P->level_ptr.as<int32_t>(), n_levels, tmp.p, s));
+    } else {
+        MPK_CUDA(cudaMemsetAsync(P->level_ptr.p, 0, 4, s));
+    }
+    rpT.release();
+    ciT.release();
+    cursor.release();
+    lev2.release();
+
+    // ---- permuted CSR B = P A P^T, columns ascending per row
+    MPK_TRY(P->rp.alloc((n + 1) * 4));
+    MPK_TRY(P->ci.alloc(std::max<int64_t>(nnz, 1) * 4));
+    MPK_TRY(P->entry_map.alloc(std::max<int64_t>(nnz, 1) * 4));
+    if (P->has64) MPK_TRY(P->val64.alloc(std::max<int64_t>(nnz, 1) * 8));
+    if (P->has32) MPK_TRY(P->val32.alloc(std::max<int64_t>(nnz, 1) * 4));
+    if (n > 0) {
+        DevBuf len;
+        MPK_TRY(len.alloc(n * 4));
+        perm_rowlen_kernel<<<grid_for(n), 256, 0, s>>>(A->row_ptr, P->perm.as<int32_t>(), n, len.as<int32_t>());
+        MPK_TRY(exclusive_scan<int32_t, int32_t>(len.as<int32_t>(), P->rp.as<int32_t>(), n, tmp.p, s));
+        DevBuf longr, nlong;
+        MPK_TRY(longr.alloc(n * 4));
+        MPK_TRY(nlong.alloc(4));
+        MPK_CUDA(cudaMemsetAsync(nlong.p, 0, 4, s));
+        double *v64 = P->has64 ? P->val64.as<double>() : nullptr;
+        float *v32 = P->has32 ? P->val32.as<float>() : nullptr;
+        unsigned g = grid_for(n * 32);
+        if (A->dtype == MPK_F64)
+            permute_rows_warp_kernel<double><<<g, 256, 0, s>>>(A->row_ptr, A->col, (const double *)A->val, P->perm.as<int32_t>(), P->iperm.as<int32_t>(), P->rp.as<int32_t>(), n, P->ci.as<int32_t>(), v64, v32, P->entry_map.as<int32_t>(), longr.as<int32_t>(), nlong.as<int32_t>());
+        else
+            permute_rows_warp_kernel<float><<<g, 256, 0, s>>>(A->row_ptr, A->col, (const float *)A->val, P->perm.as<int32_t>(), P->iperm.as<int32_t>(), P->rp.as<int32_t>(), n, P->ci.as<int32_t>(), v64, v32, P->entry_map.as<int32_t>(), longr.as<int32_t>(), nlong.as<int32_t>());
+        MPK_CUDA(cudaGetLastError());
+        int32_t hlong = 0;
+        MPK_CUDA(cudaMemcpyAsync(&hlong, nlong.p, 4, cudaMemcpyDeviceToHost, s));
+        MPK_CUDA(cudaStreamSynchronize(s));
+        if (hlong > 0) {
+            if (A->dtype == MPK_F64)
+                permute_rows_long_kernel<double><<<hlong, 256, 0, s>>>(A->row_ptr, A->col, (const double *)A->val, P->perm.as<int32_t>(), P->iperm.as<int32_t>(), P->rp.as<int32_t>(), longr.as<int32_t>(), P->ci.as<int32_t>(), v64, v32, P->entry_map.as<int32_t>());
+            else
+                permute_rows_long_kernel<float><<<hlong, 256, 0, s>>>(A->row_ptr, A->col, (const float *)A->val, P->perm.as<int32_t>(), P->iperm.as<int32_t>(), P->rp.as<int32_t>(), longr.as<int32_t>(), P->ci.as<int32_t>(), v64, v32, P->entry_map.as<int32_t>());
+            MPK_CUDA(cudaGetLastError());
+        }
+    } else {
+        MPK_CUDA(cudaMemsetAsync(P->rp.p, 0, 4, s));
+    }
+
+    // ---- level groups (host, integer-exact): per-level rows and nnz from level_ptr and rp
+    P->h_level_ptr.assign(n_levels + 1, 0);
+    std::vector<int32_t> h_rp_at(n_levels + 1, 0);
+    if (n > 0) {
+        MPK_CUDA(cudaMemcpyAsync(P->h_level_ptr.data(), P->level_ptr.p, (n_levels + 1) * 4, cudaMemcpyDeviceToHost, s));
+        DevBuf at;
+        MPK_TRY(at.alloc((n_levels + 1) * 4));
+        gather_rp_kernel<<<grid_for(n_levels + 1), 256, 0, s>>>(P->rp.as<int32_t>(), P->level_ptr.as<int32_t>(), n_levels + 1, at.as<int32_t>());
+        MPK_CUDA(cudaMemcpyAsync(h_rp_at.data(), at.p, (n_levels + 1) * 4, cudaMemcpyDeviceToHost, s));
+        MPK_CUDA(cudaStreamSynchronize(s));
+    }
+    {
+        const int64_t w = P->group_dtype == MPK_F64 ? 8 : 4;
+        const int64_t pb = P->p_blk;
+        const int64_t budget = o.l2_budget_bytes;
+        std::vector<int32_t> gp;
+        int64_t rows = 0, z = 0;
+        bool open = false;
+        for (int32_t l = 0; l < n_levels; l++) {
+            int64_t r = (int64_t)P->h_level_ptr[l + 1] - P->h_level_ptr[l];
+            int64_t zz = (int64_t)h_rp_at[l + 1] - h_rp_at[l];
+            P->max_level_rows = std::max<int32_t>(P->max_level_rows, (int32_t)r);
+            if (open) {
+                int64_t R = rows + r, Z = z + zz;
+                int64_t cost = pb * (4 * R + (4 + w) * Z) + (pb + 1) * w * R;
+                if (cost <= budget) { rows = R; z = Z; continue; }
+            }
+            gp.push_back(l);
+            rows = r;
+            z = zz;
+            open = true;
+        }
+        gp.push_back(n_levels);
+        P->h_group_ptr = gp;
+        P->n_groups = (int32_t)gp.size() - 1;
+        MPK_TRY(upload(P->group_ptr, gp, s));
+    }
+
+    // ---- SELL-32 slices inside groups, chunks of chunk_slices slices
+    std::vector<int32_t> h_slice_row, h_chunk_slice, h_chunk_row;
+    P->h_group_chunk.clear();
+    P->h_chunk_group.clear();
+    for (int32_t g = 0; g < P->n_groups; g++) {
+        int32_t r0 = P->h_level_ptr[P->h_group_ptr[g]];
+        int32_t r1 = P->h_level_ptr[P->h_group_ptr[g + 1]];
+        P->h_group_chunk.push_back((int32_t)h_chunk_slice.size());
+        int32_t first_slice = (int32_t)h_slice_row.size();
+        for (int32_t r = r0; r < r1; r += 32) h_slice_row.push_back(r);
+        int32_t last_slice = (int32_t)h_slice_row.size();
+        for (int32_t sl = first_slice; sl < last_slice; sl += o.chunk_slices) {
+            h_chunk_slice.push_back(sl);
+            h_chunk_row.push_back(h_slice_row[sl]);
+            P->h_chunk_group.push_back(g);
+        }
+    }
+    P->h_group_chunk.push_back((int32_t)h_chunk_slice.size());
+    P->n_slices = (int32_t)h_slice_row.size();
+    P->n_chunks = (int32_t)h_chunk_slice.size();
+    h_slice_row.push_back((int32_t)n);
+    h_chunk_slice.push_back(P->n_slices);
+    h_chunk_row.push_back((int32_t)n);
+    MPK_TRY(upload(P->slice_row, h_slice_row, s));
+    MPK_TRY(upload(P->chunk_slice, h_chunk_slice, s));
+    MPK_TRY(upload(P->chunk_row, h_chunk_row, s));
+    MPK_TRY(P->slice_len.alloc((P->n_slices + 1) * 4));
+    MPK_TRY(P->slice_ptr.alloc((P->n_slices + 1) * 8));
+    if (P->n_slices > 0) {
+        slice_len_kernel<<<grid_for((int64_t)P->n_slices * 32), 256, 0, s>>>(P->rp.as<int32_t>(), P->slice_row.as<int32_t>(), P->n_slices, P->slice_len.as<int32_t>());
+        DevBuf st;
+        MPK_TRY(st.alloc(scan_tmp_bytes(P->n_slices + 1)));
+        MPK_TRY((exclusive_scan<int32_t, long long>(P->slice_len.as<int32_t>(), P->slice_ptr.as<long long>(), P->n_slices, st.p, s)));
+        long long total = 0;
+        MPK_CUDA(cudaMemcpyAsync(&total, P->slice_ptr.as<long long>() + P->n_slices, 8, cudaMemcpyDeviceToHost, s));
+        MPK_CUDA(cudaStreamSynchronize(s));
+        P->sell_nnz = total * 32;
+    }
+    MPK_TRY(P->s_col.alloc(std::max<int64_t>(P->sell_nnz, 1) * 4));
+    if (P->has64) MPK_TRY(P->s_val64.alloc(std::max<int64_t>(P->sell_nnz, 1) * 8));
+    if (P->has32) MPK_TRY(P->s_val32.alloc(std::max<int64_t>(P->sell_nnz, 1) * 4));
+    mpk_status st = mpk_build_blocks(P, s);
+    if (st != MPK_OK) return st;
+
+    // ---- blocked-task dependency ranges and flags
+    MPK_TRY(P->dep_lo.alloc((P->n_chunks + 1) * 4));
+    MPK_TRY(P->dep_hi.alloc((P->n_chunks + 1) * 4));
+    MPK_TRY(P->flags.alloc((P->n_chunks + 1) * 4));
+    MPK_CUDA(cudaMemsetAsync(P->flags.p, 0, (P->n_chunks + 1) * 4, s));
+    if (P->n_chunks > 0) {
+        DevBuf row_chunk;
+        MPK_TRY(row_chunk.alloc(n * 4));
+        row_chunk_kernel<<<(unsigned)std::min<int64_t>(P->n_chunks, 65535), 256, 0, s>>>(P->chunk_row.as<int32_t>(), P->n_chunks, row_chunk.as<int32_t>());
+        fill_i32_kernel<<<grid_for(P->n_chunks), 256, 0, s>>>(P->dep_lo.as<int32_t>(), P->n_chunks, 0x7fffffff);
+        fill_i32_kernel<<<grid_for(P->n_chunks), 256, 0, s>>>(P->dep_hi.as<int32_t>(), P->n_chunks, -1);
+        dep_kernel<<<grid_for(n), 256, 0, s>>>(P->rp.as<int32_t>(), P->ci.as<int32_t>(), row_chunk.as<int32_t>(), n, sym ? 0 : 1, P->dep_lo.as<int32_t>(), P->dep_hi.as<int32_t>());
+        MPK_CUDA(cudaGetLastError());
+        MPK_CUDA(cudaStreamSynchronize(s));
+    }
+    P->ctas_per_sm = o.ctas_per_sm > 0 ? o.ctas_per_sm : 4;
+    MPK_CUDA(cudaStreamSynchronize(s));
+    auto t1 = std::chrono::steady_clock::now();
+    P->create_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    return MPK_OK;
+}
+
+// SELL fill (shared with value updates)
+mpk_status mpk_build_blocks(mpk_plan_s *P, cudaStream_t s) {
+    if (P->n_slices == 0) return MPK_OK;
+    sell_fill_kernel<<<grid_for((int64_t)P->n_slices * 32), 256, 0, s>>>(
+        P->rp.as<int32_t>(), P->ci.as<int32_t>(), P->has64 ? P->val64.as<double>() : nullptr,
+        P->has32 ? P->val32.as<float>() : nullptr, P->slice_row.as<int32_t>(),
+        P->slice_len.as<int32_t>(), P->slice_ptr.as<long long>(), P->n_slices,
+        P->s_col.as<int32_t>(), P->has64 ? P->s_val64.as<double>() : nullptr,
+        P->has32 ? P->s_val32.as<float>() : nullptr);
+    MPK_CUDA(cudaGetLastError());
+    return MPK_OK;
+}
+
+// slice_ptr holds the running sum of slice lengths: entry (j, lane) of slice s lives at
+// 32*slice_ptr[s] + 32*j + lane in s_col / s_val*.
+
+extern "C" mpk_status mpk_plan_create(const mpk_csr *A, int32_t p_max, const mpk_plan_opts *opts,
+                                      cudaStream_t stream, mpk_plan_t *out) {
+    if (!out) return MPK_ERR_ARG;
+    *out = nullptr;
+    if (!A || A->n < 0 || A->nnz < 0 || A->n >= (1ll << 31) - 1 || A->nnz >= (1ll << 31) - 1)
+        return MPK_ERR_ARG;
+    if (p_max < 1 || p_max > MPK_MAX_P) return MPK_ERR_ARG;
+    if (A->dtype != MPK_F32 && A->dtype != MPK_F64) return MPK_ERR_ARG;
+    if (A->n > 0 && !A->row_ptr) return MPK_ERR_ARG;
+    if (A->nnz > 0 && (!A->col || !A->val)) return MPK_ERR_ARG;
+    if (A->n == 0 && A->nnz != 0) return MPK_ERR_ARG;
+    mpk_plan_s *P = new (std::nothrow) mpk_plan_s();
+    if (!P) return MPK_ERR_OOM;
+    mpk_status st = plan_create_impl(A, p_max, opts, stream, P);
+    if (st != MPK_OK) {
+        cudaStreamSynchronize(stream);
+        cudaGetLastError();
+        delete P;
+        return st;
+    }
+    *out = P;
+    return MPK_OK;
+}
+
+extern "C" mpk_status mpk_plan_destroy(mpk_plan_t plan) {
+    if (!plan) return MPK_ERR_ARG;
+    cudaDeviceSynchronize();
+    delete plan;
+    return MPK_OK;
+}
+
+extern "C" mpk_status mpk_plan_stats(mpk_plan_t P, mpk_plan_info *st) {
+    if (!P || !st) return MPK_ERR_ARG;
+    memset(st, 0, sizeof(*st));
+    st->n = P->n;
+    st->nnz = P->nnz;
+    st->n_levels = P->n_levels;
+    st->n_groups = P->n_groups;
+    st->n_slices = P->n_slices;
+    st->n_chunks = P->n_chunks;
+    st->root = P->root;
+    st->p_blk = P->p_blk;
+    st->l2_budget_bytes = P->opts.l2_budget_bytes;
+    st->sell_nnz = P->sell_nnz;
+    size_t b = 0;
+    for (const DevBuf *d : {&P->perm, &P->iperm, &P->level, &P->level_ptr, &P->group_ptr, &P->rp,
+                            &P->ci, &P->val64, &P->val32, &P->entry_map, &P->slice_row,
+                            &P->slice_ptr, &P->slice_len, &P->s_col, &P->s_val64, &P->s_val32,
+                            &P->chunk_slice, &P->chunk_row, &P->dep_lo, &P->dep_hi, &P->flags,
+                            &P->ctrl, &P->ws_x, &P->ws_y})
+        b += d->bytes;
+    st->device_bytes = (int64_t)b;
+    st->create_ms = P->create_ms;
+    st->bfs_sweeps = P->bfs_sweeps;
+    st->max_level_rows = P->max_level_rows;
+    return MPK_OK;
+}
+
+extern "C" mpk_status mpk_plan_perm(mpk_plan_t P, int32_t *perm, int32_t *iperm, int32_t *level,
+                                    int32_t *level_ptr, int32_t *group_ptr, cudaStream_t s) {
+    if (!P) return MPK_ERR_ARG;
+    const size_t nb = P->n * sizeof(int32_t);
+    if (perm && nb) MPK_CUDA(cudaMemcpyAsync(perm, P->perm.p, nb, cudaMemcpyDeviceToDevice, s));
+    if (iperm && nb) MPK_CUDA(cudaMemcpyAsync(iperm, P->iperm.p, nb, cudaMemcpyDeviceToDevice, s));
+    if (level && nb) MPK_CUDA(cudaMemcpyAsync(level, P->level.p, nb, cudaMemcpyDeviceToDevice, s));
+    if (level_ptr)
+        MPK_CUDA(cudaMemcpyAsync(level_ptr, P->level_ptr.p, (P->n_levels + 1) * 4, cudaMemcpyDeviceToDevice, s));
+    if (group_ptr)
+        MPK_CUDA(cudaMemcpyAsync(group_ptr, P->group_ptr.p, (P->n_groups + 1) * 4, cudaMemcpyDeviceToDevice, s));
+    return MPK_OK;
+}
+
+extern "C" mpk_status mpk_plan_csr(mpk_plan_t P, mpk_dtype dtype, int32_t *row_ptr, int32_t *col,
+                                   void *val, cudaStream_t s) {
+    if (!P) return MPK_ERR_ARG;
+    if (dtype == MPK_F64 && val && !P->has64) return MPK_ERR_ARG;
+    if (dtype == MPK_F32 && val && !P->has32) return MPK_ERR_ARG;
+    if (row_ptr) MPK_CUDA(cudaMemcpyAsync(row_ptr, P->rp.p, (P->n + 1) * 4, cudaMemcpyDeviceToDevice, s));
+    if (col && P->nnz) MPK_CUDA(cudaMemcpyAsync(col, P->ci.p, P->nnz * 4, cudaMemcpyDeviceToDevice, s));
+    if (val && P->nnz)
+        MPK_CUDA(cudaMemcpyAsync(val, dtype == MPK_F64 ? P->val64.p : P->val32.p,
+                                 P->nnz * (dtype == MPK_F64 ? 8 : 4), cudaMemcpyDeviceToDevice, s));
+    return MPK_OK;
+}
+
+extern "C" mpk_status mpk_plan_update_values(mpk_plan_t P, const mpk_csr *A, cudaStream_t s) {
+    if (!P || !A || A->n != P->n || A->nnz != P->nnz) return MPK_ERR_ARG;
+    if (P->nnz == 0) return MPK_OK;
+    if (!A->val) return MPK_ERR_ARG;
+    double *v64 = P->has64 ? P->val64.as<double>() : nullptr;
+    float *v32 = P->has32 ? P->val32.as<float>() : nullptr;
+    if (A->dtype == MPK_F64)
+        update_values_kernel<double><<<grid_for(P->nnz), 256, 0, s>>>((const double *)A->val, P->entry_map.as<int32_t>(), P->nnz, v64, v32);
+    else
+        update_values_kernel<float><<<grid_for(P->nnz), 256, 0, s>>>((const float *)A->val, P->entry_map.as<int32_t>(), P->nnz, v64, v32);
+    MPK_CUDA(cudaGetLastError());
+    return mpk_build_blocks(P, s);
+}

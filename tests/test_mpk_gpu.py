@@ -1,0 +1,314 @@
+"""GPU parity: the plan (levels, permutation, groups, permuted CSR) bit-exact against the
+oracle, and the MPK within the stated tolerance of the oracle (FP64: 64*k*2^-53, FP32:
+64*k*2^-24, per entry relative to (|A_theta|^k |x|)_i), blocked bit-identical to unblocked.
+
+All calls go through the C ABI (ctypes binding)."""
+import numpy as np
+import pytest
+
+import mpk_inputs as mi
+import oracle
+from oracle import sstep
+from tests.gpu_util import U32, U64, abs_powers, max_rel_err, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def m():
+    import torch
+    from paper_2309_02228_gb300 import build
+    build.build()
+    import paper_2309_02228_gb300 as mod
+    torch.cuda.set_device(0)
+    return mod
+
+
+def _mats():
+    out = {
+        "poisson64": mi.poisson2d_5pt(64),
+        "s27_12": mi.stencil27(12, seed=2),
+        "diff7_10": mi.diffusion7_lognormal(10),
+        "rand_nonsym_3c": mi.random_sparse(300, 0.01, 1, symmetric=False, components=3),
+        "rand_sym": mi.random_sparse(200, 0.03, 2, symmetric=True),
+        "aniso27": mi.anisotropic(9, 27, 30.0),
+    }
+    return out
+
+
+MATS = _mats()
+
+
+def _check_plan(m, A, opts, p_blk, val_bytes=8):
+    import torch
+    rp, ci, vv = to_dev(A)
+    plan = m.mpk_plan_create(rp, ci, vv, p_blk, opts)
+    st = m.mpk_plan_stats(plan)
+    lev, root, nl, perm, iperm, lp = oracle.level_structure(A, root_rule=opts.root_rule,
+                                                            n_sweeps=opts.n_sweeps)
+    P = m.mpk_plan_perm(plan)
+    torch.cuda.synchronize()
+    assert st["root"] == root and st["n_levels"] == nl
+    assert np.array_equal(P["level"].cpu().numpy(), lev)
+    assert np.array_equal(P["perm"].cpu().numpy(), perm)
+    assert np.array_equal(P["iperm"].cpu().numpy(), iperm)
+    assert np.array_equal(P["level_ptr"].cpu().numpy(), lp)
+    brp, bci, bval = oracle.permute_csr(A, perm, iperm)
+    grp, gci, gval = m.mpk_plan_csr(plan, torch.float64)
+    assert np.array_equal(grp.cpu().numpy(), brp)
+    assert np.array_equal(gci.cpu().numpy(), bci)
+    assert np.array_equal(gval.cpu().numpy().view(np.uint8), bval.view(np.uint8))
+    gp = oracle.level_groups(lp, brp, val_bytes, st["p_blk"], st["l2_budget_bytes"])
+    assert np.array_equal(P["group_ptr"].cpu().numpy(), gp)
+    return plan
+
+
+@pytest.mark.parametrize("name", sorted(MATS))
+@pytest.mark.parametrize("root_rule", [0, 1])
+def test_plan_bit_exact(m, name, root_rule):
+    A = MATS[name]
+    for budget in (20_000, 400_000, 1 << 30):
+        opts = m.mpk_plan_opts_default(l2_budget_bytes=budget, root_rule=root_rule)
+        _check_plan(m, A, opts, 4)
+
+
+def test_plan_edge_cases(m):
+    import torch
+    # one row; an empty row; a long row (> 32 entries, block sort path); unsorted columns and
+    # duplicate entries; a diagonal matrix (n components)
+    cases = []
+    cases.append(mi.CSR(np.array([0, 1], np.int32), np.array([0], np.int32), np.array([2.0])))
+    n = 70
+    rows = [[0, 5, 69], [], list(range(0, 70, 2))[::-1], [3, 3, 1], [4]] + [[i, (i * 7) % n] for i in range(5, n)]
+    rp = np.zeros(n + 1, np.int32)
+    rp[1:] = np.cumsum([len(r) for r in rows])
+    col = np.array([c for r in rows for c in r], np.int32)
+    val = np.arange(1, col.size + 1, dtype=np.float64) * 0.25
+    cases.append(mi.CSR(rp, col, val))
+    d = 500
+    cases.append(mi.CSR(np.arange(d + 1, dtype=np.int32), np.arange(d, dtype=np.int32), np.linspace(1, 2, d)))
+    for A in cases:
+        opts = m.mpk_plan_opts_default(l2_budget_bytes=4096)
+        plan = _check_plan(m, A, opts, 3)
+        x = mi.uniform_vectors(A.n, 5)[0]
+        cf = sstep.newton_coeffs([0.5, -1.0, 2.0])
+        X = torch.from_numpy(x).cuda()
+        Y = torch.empty(4 * A.n, dtype=torch.float64, device="cuda")
+        m.mpk_apply(plan, cf, X, Y)
+        assert m.mpk_plan_sync(plan) == m.MPK_OK
+        ref = oracle.mpk(A, 3, cf, x)
+        den = abs_powers(A, cf, x)
+        got = Y.view(4, A.n).cpu().numpy()
+        for k in range(4):
+            assert max_rel_err(got[k], ref[k], den[k]) <= 64 * max(k, 1) * U64
+
+
+def test_empty_matrix(m):
+    import torch
+    rp = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ci = torch.zeros(0, dtype=torch.int32, device="cuda")
+    vv = torch.zeros(0, dtype=torch.float64, device="cuda")
+    plan = m.mpk_plan_create(rp, ci, vv, 2)
+    st = m.mpk_plan_stats(plan)
+    assert st["n"] == 0 and st["n_levels"] == 0
+    X = torch.zeros(1, dtype=torch.float64, device="cuda")
+    Y = torch.zeros(3, dtype=torch.float64, device="cuda")
+    m.mpk_apply(plan, sstep.monomial_coeffs(2), X, Y, ldx=1, ldy=1)
+
+
+def test_invalid_csr_rejected(m):
+    import torch
+    A = mi.poisson2d_5pt(8)
+    rp, ci, vv = to_dev(A)
+    ci[5] = 10_000
+    with pytest.raises(m.MpkError) as e:
+        m.mpk_plan_create(rp, ci, vv, 2)
+    assert e.value.status == m.MPK_ERR_ARG
+
+
+def _run(m, plan, A, cf, x, flags=0, dtype=None, n_rhs=1):
+    import torch
+    dt = torch.float64 if dtype is None else dtype
+    p = len(cf)
+    X = torch.from_numpy(np.ascontiguousarray(x.reshape(-1))).to("cuda", dt)
+    nb = 1 if flags & m.MPK_FINAL_ONLY else p + 1
+    Y = torch.full((nb * A.n * n_rhs,), float("nan"), dtype=dt, device="cuda")
+    m.mpk_apply(plan, cf, X, Y, n_rhs=n_rhs, flags=flags)
+    assert m.mpk_plan_sync(plan) == m.MPK_OK
+    return Y.cpu().numpy().astype(np.float64).reshape(nb, -1)
+
+
+BASES = {
+    "monomial": lambda p: sstep.monomial_coeffs(p),
+    "newton": lambda p: sstep.newton_coeffs(mi.leja_points_interval(0.0, 8.0, p)),
+    "chebyshev": lambda p: sstep.chebyshev_coeffs(0.1, 8.0, p),
+}
+
+
+@pytest.mark.parametrize("basis", sorted(BASES))
+@pytest.mark.parametrize("name", ["poisson64", "s27_12", "diff7_10", "rand_nonsym_3c"])
+def test_mpk_fp64_vs_oracle(m, basis, name):
+    A = MATS[name]
+    p = 5
+    cf = BASES[basis](p)
+    x = mi.uniform_vectors(A.n, 0)[0]
+    ref = oracle.mpk(A, p, cf, x)
+    den = abs_powers(A, cf, x)
+    rp, ci, vv = to_dev(A)
+    for budget, cs in ((30_000, 1), (300_000, 2), (1 << 30, 8)):
+        plan = m.mpk_plan_create(rp, ci, vv, p, m.mpk_plan_opts_default(l2_budget_bytes=budget, chunk_slices=cs))
+        got_b = _run(m, plan, A, cf, x)
+        got_u = _run(m, plan, A, cf, x, flags=m.MPK_UNBLOCKED)
+        assert np.array_equal(got_b, got_u)            # blocked == unblocked, bit for bit
+        assert np.array_equal(got_b[0], x)
+        for k in range(1, p + 1):
+            assert max_rel_err(got_b[k], ref[k], den[k]) <= 64 * k * U64, (k, budget)
+
+
+@pytest.mark.parametrize("name", ["poisson64", "s27_12", "diff7_10"])
+def test_mpk_fp32_vs_oracle(m, name):
+    import torch
+    A = MATS[name]
+    A32 = mi.CSR(A.row_ptr, A.col, A.val.astype(np.float32).astype(np.float64))
+    p = 6
+    cf = sstep.chebyshev_coeffs(0.1, 8.0, p)
+    x = mi.uniform_vectors(A.n, 1)[0].astype(np.float32).astype(np.float64)
+    ref = oracle.mpk(A32, p, cf, x)
+    den = abs_powers(A32, cf, x)
+    rp, ci, vv = to_dev(A, np.float32)
+    plan = m.mpk_plan_create(rp, ci, vv, p, m.mpk_plan_opts_default(l2_budget_bytes=50_000))
+    got = _run(m, plan, A, cf, x, dtype=torch.float32)
+    got_u = _run(m, plan, A, cf, x, dtype=torch.float32, flags=m.MPK_UNBLOCKED)
+    assert np.array_equal(got, got_u)
+    for k in range(1, p + 1):
+        assert max_rel_err(got[k], ref[k], den[k]) <= 64 * k * U32
+
+
+def test_permuted_io_and_y0_is_x(m):
+    import torch
+    A = MATS["s27_12"]
+    p = 4
+    cf = BASES["newton"](p)
+    x = mi.uniform_vectors(A.n, 3)[0]
+    ref = oracle.mpk(A, p, cf, x)
+    rp, ci, vv = to_dev(A)
+    plan = m.mpk_plan_create(rp, ci, vv, p, m.mpk_plan_opts_default(l2_budget_bytes=100_000))
+    perm = m.mpk_plan_perm(plan)["perm"].cpu().numpy()
+    got = _run(m, plan, A, cf, x[perm], flags=m.MPK_PERMUTED_IO)
+    full = _run(m, plan, A, cf, x)
+    assert np.array_equal(got, full[:, perm])
+    Y = torch.empty((p + 1) * A.n, dtype=torch.float64, device="cuda")
+    Y[: A.n] = torch.from_numpy(x[perm]).cuda()
+    m.mpk_apply(plan, cf, None, Y, flags=m.MPK_PERMUTED_IO | m.MPK_Y0_IS_X)
+    assert m.mpk_plan_sync(plan) == m.MPK_OK
+    assert np.array_equal(Y.view(p + 1, -1).cpu().numpy(), got)
+    den = abs_powers(A, cf, x)
+    for k in range(1, p + 1):
+        assert max_rel_err(full[k], ref[k], den[k]) <= 64 * k * U64
+
+
+@pytest.mark.parametrize("n_rhs", [1, 3, 8, 16, 32])
+@pytest.mark.parametrize("interleaved", [False, True])
+def test_block_mpk_n_rhs(m, n_rhs, interleaved):
+    import torch
+    A = MATS["s27_12"]
+    p = 6
+    cf = sstep.chebyshev_coeffs(0.1, 52.0, p)
+    Xc = mi.uniform_vectors(A.n, 6, n_rhs=n_rhs).astype(np.float32).astype(np.float64)  # (n_rhs, n)
+    A32 = mi.CSR(A.row_ptr, A.col, A.val.astype(np.float32).astype(np.float64))
+    rp, ci, vv = to_dev(A, np.float32)
+    plan = m.mpk_plan_create(rp, ci, vv, p, m.mpk_plan_opts_default(l2_budget_bytes=200_000))
+    flags = m.MPK_RHS_INTERLEAVED if interleaved else 0
+    xin = Xc.T.copy() if interleaved else Xc   # row-major n x n_rhs, or column-major
+    got = _run(m, plan, A, cf, xin, dtype=torch.float32, n_rhs=n_rhs, flags=flags)
+    got_u = _run(m, plan, A, cf, xin, dtype=torch.float32, n_rhs=n_rhs, flags=flags | m.MPK_UNBLOCKED)
+    assert np.array_equal(got, got_u)
+    got = got.reshape(p + 1, A.n, n_rhs) if interleaved else got.reshape(p + 1, n_rhs, A.n).transpose(0, 2, 1)
+    for q in range(n_rhs):
+        ref = oracle.mpk(A32, p, cf, Xc[q])
+        den = abs_powers(A32, cf, Xc[q])
+        for k in range(1, p + 1):
+            assert max_rel_err(got[k, :, q], ref[k], den[k]) <= 64 * k * U32
+
+
+def test_final_only_gamma_and_segments(m):
+    import torch
+    A = MATS["diff7_10"]
+    p = 9
+    cf = sstep.chebyshev_coeffs(0.05, 12.0, p)
+    gamma = np.linspace(1.0, -0.5, p + 1)
+    x = mi.uniform_vectors(A.n, 8)[0]
+    ref = oracle.mpk(A, p, cf, x)
+    den = abs_powers(A, cf, x)
+    rp, ci, vv = to_dev(A)
+    # p_blk = 4 -> segments of 4, 4, 1 powers (the remainder launch)
+    plan = m.mpk_plan_create(rp, ci, vv, p, m.mpk_plan_opts_default(l2_budget_bytes=60_000, p_blk=4))
+    full = _run(m, plan, A, cf, x)
+    for k in range(1, p + 1):
+        assert max_rel_err(full[k], ref[k], den[k]) <= 64 * k * U64
+    fin = _run(m, plan, A, cf, x, flags=m.MPK_FINAL_ONLY)
+    assert np.array_equal(fin[0], full[p])
+    co = m.Coeffs.from_triples(cf, gamma=gamma)
+    X = torch.from_numpy(x).cuda()
+    Y = torch.empty(A.n, dtype=torch.float64, device="cuda")
+    for fl in (m.MPK_FINAL_ONLY, m.MPK_FINAL_ONLY | m.MPK_UNBLOCKED):
+        m.mpk_apply(plan, co, X, Y, flags=fl)
+        assert m.mpk_plan_sync(plan) == m.MPK_OK
+        poly = Y.cpu().numpy()
+        want = sum(gamma[k] * ref[k] for k in range(p + 1))
+        dsum = sum(abs(gamma[k]) * den[k] for k in range(p + 1))
+        assert max_rel_err(poly, want, dsum) <= 64 * (p + 1) * U64
+
+
+def test_host_io(m):
+    import torch
+    A = MATS["poisson64"]
+    p = 4
+    cf = BASES["newton"](p)
+    x = mi.uniform_vectors(A.n, 0)[0]
+    rp, ci, vv = to_dev(A)
+    plan = m.mpk_plan_create(rp, ci, vv, p)
+    Xh = torch.from_numpy(x.copy()).pin_memory()
+    Yh = torch.empty((p + 1) * A.n, dtype=torch.float64).pin_memory()
+    m.mpk_apply(plan, cf, Xh, Yh, flags=m.MPK_HOST_IO)
+    dev = _run(m, plan, A, cf, x)
+    assert np.array_equal(Yh.numpy().reshape(p + 1, -1), dev)
+
+
+def test_timeout_is_reported_and_plan_recovers(m):
+    """A flag that nothing publishes: the waits on it run out (short bound), the call reports
+    MPK_ERR_TIMEOUT, and the plan works again afterwards."""
+    A = MATS["s27_12"]
+    p = 3
+    cf = BASES["monomial"](p)
+    x = mi.uniform_vectors(A.n, 0)[0]
+    rp, ci, vv = to_dev(A)
+    plan = m.mpk_plan_create(rp, ci, vv, p, m.mpk_plan_opts_default(l2_budget_bytes=30_000, wait_timeout_us=20_000))
+    import torch
+    X = torch.from_numpy(x).cuda()
+    Y = torch.empty((p + 1) * A.n, dtype=torch.float64, device="cuda")
+    m.mpk_apply(plan, cf, X, Y, flags=m.MPK_DEBUG_DROP_FLAG)
+    assert m.mpk_plan_sync(plan) == m.MPK_ERR_TIMEOUT
+    got = _run(m, plan, A, cf, x)
+    ref = oracle.mpk(A, p, cf, x)
+    den = abs_powers(A, cf, x)
+    for k in range(1, p + 1):
+        assert max_rel_err(got[k], ref[k], den[k]) <= 64 * k * U64
+
+
+def test_update_values_keeps_structure(m):
+    import torch
+    A = mi.anisotropic(10, 7, 3.0)
+    B = mi.anisotropic(10, 7, 50.0)
+    p = 4
+    cf = BASES["monomial"](p)
+    x = mi.uniform_vectors(A.n, 2)[0]
+    rp, ci, vv = to_dev(A)
+    plan = m.mpk_plan_create(rp, ci, vv, p)
+    _, _, vb = to_dev(B)
+    m.mpk_plan_update_values(plan, rp, ci, vb)
+    got = _run(m, plan, B, cf, x)
+    ref = oracle.mpk(B, p, cf, x)
+    den = abs_powers(B, cf, x)
+    for k in range(1, p + 1):
+        assert max_rel_err(got[k], ref[k], den[k]) <= 64 * k * U64
