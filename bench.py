@@ -1,0 +1,392 @@
+"""Benchmark: level-blocked MPK vs p back-to-back SpMVs on one GB300 (per GPU).
+
+Workload (the 27-point benchmark matrix): 3-D 27-point stencil on a 160^3 grid, n = 4,096,000,
+nnz = 109,215,352, diagonal 26, off-diagonals -1 - U[0,0.1) (seed 2, symmetric), CSR FP64;
+MPK in the Newton basis, shifts = the first p Leja points of [0, 52] (10,001 candidates);
+x ~ U[-1,1) (seed 0).  One step = one mpk_apply call with p = 4 (inputs in HBM, original row
+order in and out, all p+1 vectors written).  GFLOP/s = 2 * nnz * p / t (the paper's formula).
+The matrix (1.33 GB) is larger than L2, so every step streams it from HBM.
+
+Also reported: p = 2 and 8, the unblocked p x SpMV on the same GPU, the same matrix in FP32,
+kernel-only timings with the roofline of the dominant kernel, an end-to-end number through the
+C ABI with pinned host buffers, the CPU oracle on the host cores, and GPU clocks sampled
+during the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With N > 1 (torchrun) every rank runs its own replica (no data-path exchange exists in this
+path on one GPU); value = total GFLOP over all ranks / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import mpk_inputs as mi  # noqa: E402
+
+METRIC = "MPK GFLOP/s blocked vs p×SpMV; solves/s + p99 latency at rel. residual 1e-8"
+N_GRID = 160
+P_MAIN = 4
+P_SWEEP = (2, 4, 8)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# FP64 FMA peak derived from unit counts and clock: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x
+# 2.07 GHz (the part's FP64 rate is 1.25 TFLOP/s nominal).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 100 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.gpu)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.thr = threading.Thread(target=self._read, daemon=True)
+            self.thr.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thr.join(timeout=2)
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+def gen_workload():
+    A = mi.stencil27(N_GRID, seed=2)
+    x = mi.uniform_vectors(A.n, 0)[0]
+    theta = mi.leja_points_interval(0.0, 52.0, max(P_SWEEP))
+    return A, x, theta
+
+
+def cpu_baseline(A, x, theta, budget_s=10.0):
+    """The oracle as it stands (plain FP64 CSR loops, static OpenMP rows) on the host cores:
+    full 27-point matrix, p = 4 Newton, repeated until about budget_s seconds."""
+    import oracle
+    from oracle import sstep
+    oracle.build()
+    cf = sstep.newton_coeffs(theta[:P_MAIN])
+    reps, t_total = 0, 0.0
+    while t_total < budget_s or reps == 0:
+        t0 = time.perf_counter()
+        oracle.mpk(A, P_MAIN, cf, x, threads=True)
+        t_total += time.perf_counter() - t0
+        reps += 1
+        if reps >= 1000:
+            break
+    gf = 2.0 * A.nnz * P_MAIN * reps / t_total / 1e9
+    return {"value": gf, "unit": "GFLOP/s", "cores": oracle.omp_threads(), "kind": "oracle",
+            "sample": "full 160^3 27-point FP64 matrix, p=4 Newton, %d calls in %.1f s" % (reps, t_total),
+            "seconds": t_total}
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle timed on the host cores for the same metric."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    A, x, theta = gen_workload()
+    import oracle
+    from oracle import sstep
+    oracle.build()
+    cf = sstep.newton_coeffs(theta[:P_MAIN])
+    for _ in range(args.warmup):
+        oracle.mpk(A, P_MAIN, cf, x, threads=True)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.mpk(A, P_MAIN, cf, x, threads=True)
+        ts.append(time.perf_counter() - t0)
+    t = sum(ts)
+    gf = 2.0 * A.nnz * P_MAIN * args.steps / t / 1e9
+    out = {"impl": "reference", "metric": METRIC, "value": gf, "unit": "GFLOP/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": "27-point 160^3 CSR FP64, Newton MPK p=4 (Leja shifts on [0,52])",
+                      "n": A.n, "nnz": A.nnz, "p": P_MAIN},
+           "cpu_baseline": {"value": gf, "unit": "GFLOP/s", "kind": "oracle",
+                            "cores": oracle.omp_threads(),
+                            "sample": "full matrix, %d timed calls of p=4" % args.steps},
+           "e2e": {"value": gf, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def time_stream(fn, reps, torch):
+    """Average ms per call of fn() on the current stream, CUDA events on that stream."""
+    st = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(reps):
+        fn()
+    e1.record(st)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    ap.add_argument("--profile", action="store_true",
+                    help="profiling run: plan + warm-up + 3 blocked launches only")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2309_02228_gb300 import build as B
+    B.build()
+    import paper_2309_02228_gb300 as m
+
+    A, x, theta = gen_workload()
+    dev = torch.device("cuda", local)
+    rp = torch.from_numpy(A.row_ptr).to(dev)
+    ci = torch.from_numpy(A.col).to(dev)
+    vv = torch.from_numpy(A.val).to(dev)
+    n, nnz = A.n, A.nnz
+    t0 = time.perf_counter()
+    plan = m.mpk_plan_create(rp, ci, vv, max(P_SWEEP), m.mpk_plan_opts_default(assume_symmetric=1, p_blk=P_MAIN))
+    torch.cuda.synchronize()
+    plan_ms = 1e3 * (time.perf_counter() - t0)
+    pst = m.mpk_plan_stats(plan)
+    X = torch.from_numpy(x).to(dev)
+    Y = torch.empty((max(P_SWEEP) + 1) * n, dtype=torch.float64, device=dev)
+    cfs = {p: m.mpk_coeffs_newton(theta[:p]) for p in P_SWEEP}
+
+    def step(p=P_MAIN, flags=0):
+        m.mpk_apply(plan, cfs[p], X, Y, flags=flags)
+
+    if args.profile:
+        perm = m.mpk_plan_perm(plan)["perm"]
+        Yp = torch.empty((P_MAIN + 1) * n, dtype=torch.float64, device=dev)
+        Yp[:n] = X[perm.long()]
+        for _ in range(args.warmup + 3):
+            m.mpk_apply(plan, cfs[P_MAIN], None, Yp, flags=m.MPK_PERMUTED_IO | m.MPK_Y0_IS_X)
+        for _ in range(3):
+            m.mpk_apply(plan, cfs[P_MAIN], None, Yp, flags=m.MPK_PERMUTED_IO | m.MPK_Y0_IS_X | m.MPK_UNBLOCKED)
+        torch.cuda.synchronize()
+        assert m.mpk_plan_sync(plan) == m.MPK_OK
+        print(json.dumps({"profile": "done", "plan": pst}))
+        return
+
+    hbm_peak, peak_kind = measured_peaks()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    # ---- headline: K steps of the full call (original order in/out), CUDA events
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    st = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(args.steps):
+        step()
+    e1.record(st)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms_step = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        tt = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_step = float(tt.item())
+    status = m.mpk_plan_sync(plan)
+    assert status == m.MPK_OK, m.status_name(status)
+    flop = 2.0 * nnz * P_MAIN
+    value = world * flop / (ms_step * 1e-3) / 1e9
+
+    # ---- the p x SpMV baseline through the same call, and the p sweep
+    reps = max(5, min(args.steps, 50))
+    sweep = {}
+    for p in P_SWEEP:
+        tb = time_stream(lambda: step(p), reps, torch)
+        tu = time_stream(lambda: step(p, m.MPK_UNBLOCKED), reps, torch)
+        sweep["p%d" % p] = {"blocked_gflops": 2.0 * nnz * p / tb / 1e6,
+                            "pxspmv_gflops": 2.0 * nnz * p / tu / 1e6,
+                            "speedup": tu / tb, "blocked_ms": tb, "pxspmv_ms": tu}
+
+    # ---- kernel only (level-order I/O, y_0 already in place): one launch of the blocked kernel
+    perm = m.mpk_plan_perm(plan)["perm"].long()
+    Yp = torch.empty((max(P_SWEEP) + 1) * n, dtype=torch.float64, device=dev)
+    Yp[:n] = X[perm]
+    kern = {}
+    w = 8
+    M_bytes = 4 * (n + 1) + nnz * (4 + w)
+    v_bytes = w * n
+    for p in P_SWEEP:
+        kb = time_stream(lambda: m.mpk_apply(plan, cfs[p], None, Yp, flags=m.MPK_PERMUTED_IO | m.MPK_Y0_IS_X), reps, torch)
+        ku = time_stream(lambda: m.mpk_apply(plan, cfs[p], None, Yp, flags=m.MPK_PERMUTED_IO | m.MPK_Y0_IS_X | m.MPK_UNBLOCKED), reps, torch)
+        kern["p%d" % p] = {"blocked_ms": kb, "pxspmv_ms": ku,
+                           "blocked_gflops": 2.0 * nnz * p / kb / 1e6,
+                           "pxspmv_gflops": 2.0 * nnz * p / ku / 1e6,
+                           "blocked_min_bytes": M_bytes + v_bytes * (p + 1),
+                           "pxspmv_bytes": p * (M_bytes + 2 * v_bytes)}
+    status = m.mpk_plan_sync(plan)
+    assert status == m.MPK_OK, m.status_name(status)
+    clk = clocks.stop()
+
+    # ---- FP32 copy of the same matrix (the bandwidth-bound precision)
+    fp32 = {}
+    vv32 = vv.float()
+    plan32 = m.mpk_plan_create(rp, ci, vv32, max(P_SWEEP), m.mpk_plan_opts_default(assume_symmetric=1, p_blk=P_MAIN))
+    X32 = X.float()
+    Y32 = torch.empty((max(P_SWEEP) + 1) * n, dtype=torch.float32, device=dev)
+    perm32 = m.mpk_plan_perm(plan32)["perm"].long()
+    Y32[:n] = X32[perm32]
+    M32 = 4 * (n + 1) + nnz * 8
+    for p in P_SWEEP:
+        kb = time_stream(lambda: m.mpk_apply(plan32, cfs[p], None, Y32, flags=m.MPK_PERMUTED_IO | m.MPK_Y0_IS_X), reps, torch)
+        ku = time_stream(lambda: m.mpk_apply(plan32, cfs[p], None, Y32, flags=m.MPK_PERMUTED_IO | m.MPK_Y0_IS_X | m.MPK_UNBLOCKED), reps, torch)
+        bmin = M32 + 4 * n * (p + 1)
+        fp32["p%d" % p] = {"blocked_gflops": 2.0 * nnz * p / kb / 1e6,
+                           "pxspmv_gflops": 2.0 * nnz * p / ku / 1e6, "speedup": ku / kb,
+                           "blocked_eff_gbs": bmin / kb / 1e6,
+                           "blocked_eff_frac": bmin / kb / 1e6 / hbm_peak,
+                           "pxspmv_gbs": p * (M32 + 8 * n) / ku / 1e6}
+    assert m.mpk_plan_sync(plan32) == m.MPK_OK
+    del plan32
+
+    # ---- end to end through the C ABI with pinned host buffers (copies inside the timing)
+    Xh = torch.from_numpy(x.copy()).pin_memory()
+    Yh = torch.empty((P_MAIN + 1) * n, dtype=torch.float64).pin_memory()
+    e2e_reps = max(3, min(args.steps, 20))
+    m.mpk_apply(plan, cfs[P_MAIN], Xh, Yh, flags=m.MPK_HOST_IO)
+    t0 = time.perf_counter()
+    for _ in range(e2e_reps):
+        m.mpk_apply(plan, cfs[P_MAIN], Xh, Yh, flags=m.MPK_HOST_IO)
+    t_e2e = (time.perf_counter() - t0) / e2e_reps
+    e2e = {"value": world * flop / t_e2e / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": 8 * n,
+           "d2h_bytes_per_step": 8 * n * (P_MAIN + 1)}
+
+    # ---- roofline of the dominant kernel (blocked, p = 4): FP64 FMA issue bounds it on this
+    # part (2 FP64 FMA/clk/SM), not HBM: compare both bounds and report the binding one.
+    kb = kern["p%d" % P_MAIN]["blocked_ms"]
+    bytes_min = kern["p%d" % P_MAIN]["blocked_min_bytes"]
+    t_hbm = bytes_min / (hbm_peak * 1e9)
+    t_alu = flop / (FP64_PEAK_TFLOPS * 1e12)
+    if t_alu >= t_hbm:
+        ach = flop / (kb * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
+                "kernel": "mpk_blocked_kernel<double,1>",
+                "hbm_view": {"achieved_gbs": bytes_min / (kb * 1e-3) / 1e9, "peak_gbs": hbm_peak,
+                             "frac": bytes_min / (kb * 1e-3) / 1e9 / hbm_peak, "peak_kind": peak_kind}}
+    else:
+        ach = bytes_min / (kb * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                "frac": ach / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                "kernel": "mpk_blocked_kernel<double,1>"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(A, x, theta)
+
+    # kernels launched per headline step: gather_in + blocked (p=4 <= p_blk: one launch) +
+    # scatter_out (one launch over the p+1 blocks); the y_0 copy is a memcpy
+    launches_per_step = 3
+    out = {
+        "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "27-point 160^3 CSR FP64 (diag 26, off-diag -1-U[0,0.1) seed 2), "
+                               "Newton MPK p=4 with Leja shifts on [0,52], original-order I/O",
+                   "n": n, "nnz": nnz, "p": P_MAIN, "parallelism": "replica per GPU",
+                   "l2_policy": "inputs larger than L2 (1.33 GB matrix)",
+                   "plan": {k: pst[k] for k in ("n_levels", "n_groups", "n_chunks", "p_blk",
+                                                "l2_budget_bytes", "sell_nnz", "root")}},
+        "pxspmv_gflops": sweep["p%d" % P_MAIN]["pxspmv_gflops"],
+        "speedup_vs_pxspmv": sweep["p%d" % P_MAIN]["speedup"],
+        "sweep": sweep, "kernel_only": kern, "fp32": fp32, "plan_ms": plan_ms,
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+        "gpu_launches": launches_per_step * args.steps, "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

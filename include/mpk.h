@@ -82,6 +82,16 @@ typedef struct {
     int32_t keep_f64;         /* keep an FP64 copy of the values (MPK / residual in FP64) */
     int32_t ctas_per_sm;      /* persistent CTAs per SM for the blocked kernel (0 = auto) */
     uint32_t wait_timeout_us; /* bound on every device-side dependency wait (default 2e6) */
+    int32_t schedule;         /* blocked task order: 0 = level-group wavefront (step t runs
+                                 group t-k+1 at power k), 1 = lag-greedy (default: a power
+                                 advances once its dependencies were issued slack_tasks
+                                 tickets earlier) */
+    int32_t slack_tasks;      /* lag-greedy slack in tasks; 0 = the number of resident CTAs */
+    int32_t block_threads;    /* compute threads per CTA of the blocked kernel: 128 or 256
+                                 (default); one control warp is added */
+    int32_t stage;            /* stage each task's matrix block (columns and values) in
+                                 shared memory with bulk asynchronous copies: -1 auto (on
+                                 unless a 32-row slice exceeds a slot), 0 off */
 } mpk_plan_opts;
 
 typedef struct mpk_plan_s *mpk_plan_t;
@@ -220,6 +230,8 @@ typedef struct {
     int32_t bcgs_passes;    /* block classical Gram-Schmidt sweeps (1 or 2; default 1) */
     const double *shifts;   /* host, s values, or NULL: Ritz values of a first plain GMRES
                                cycle, Leja-ordered (Sec. 4) */
+    uint32_t mpk_flags;     /* extra mpk_apply flags for the basis MPK: MPK_UNBLOCKED runs
+                               s back-to-back SpMVs (the baseline solver) */
 } mpk_gmres_opts;
 
 typedef struct {
@@ -235,9 +247,18 @@ typedef struct {
 mpk_status mpk_gmres_opts_default(mpk_gmres_opts *o);
 
 /* Solve A x = b.  A: a plan holding the precision(s) the options need (FP64 values always,
- * for the residual; FP32 too when basis = MPK_F32).  b, x: DEVICE FP64 vectors of length n in
- * the original order; x holds the initial guess on entry and the solution on exit.  info
- * (host) may be NULL.  Synchronous on stream (the host reads one status word per restart). */
+ * for the residual; FP32 too when basis = MPK_F32) and p_max >= s.  b, x: DEVICE FP64
+ * vectors of length n in the original order; x holds the initial guess on entry and the
+ * solution on exit.  info (host) may be NULL.
+ * Each outer step computes r = b - A x in FP64, runs one restart cycle of s-step GMRES on
+ * A d = r in the basis precision (to inner_tol relative to ||r||, or to tol overall with an
+ * FP64 basis) and adds d to x; it stops when ||b - A x|| <= tol ||b||.  Without shifts, the
+ * first cycle is plain GMRES(m) (classical Gram-Schmidt, two sweeps) whose Ritz values give
+ * the Newton shifts.  A Cholesky breakdown ends the cycle at the last good block and halves
+ * s for later cycles; at s = 1 it returns MPK_ERR_BREAKDOWN.
+ * Synchronous on stream (the host reads a few status words per block).  Returns MPK_OK,
+ * MPK_ERR_NOT_CONVERGED (limits reached; x holds the best iterate), MPK_ERR_BREAKDOWN, or an
+ * argument / CUDA error. */
 mpk_status sstep_gmres_solve(mpk_plan_t A, const double *b, double *x, const mpk_gmres_opts *o,
                              mpk_gmres_info *info, cudaStream_t stream);
 

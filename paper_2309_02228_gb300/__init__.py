@@ -57,7 +57,9 @@ class mpk_plan_opts(ctypes.Structure):
                 ("root_rule", ctypes.c_int32), ("n_sweeps", ctypes.c_int32),
                 ("assume_symmetric", ctypes.c_int32), ("chunk_slices", ctypes.c_int32),
                 ("keep_f32", ctypes.c_int32), ("keep_f64", ctypes.c_int32),
-                ("ctas_per_sm", ctypes.c_int32), ("wait_timeout_us", ctypes.c_uint32)]
+                ("ctas_per_sm", ctypes.c_int32), ("wait_timeout_us", ctypes.c_uint32),
+                ("schedule", ctypes.c_int32), ("slack_tasks", ctypes.c_int32),
+                ("block_threads", ctypes.c_int32), ("stage", ctypes.c_int32)]
 
 
 class mpk_plan_info(ctypes.Structure):
@@ -82,7 +84,7 @@ class mpk_gmres_opts(ctypes.Structure):
                 ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int32),
                 ("inner_cycles", ctypes.c_int32), ("max_iters", ctypes.c_int32),
                 ("basis", ctypes.c_int), ("bcgs_passes", ctypes.c_int32),
-                ("shifts", ctypes.c_void_p)]
+                ("shifts", ctypes.c_void_p), ("mpk_flags", ctypes.c_uint32)]
 
 
 class mpk_gmres_info(ctypes.Structure):

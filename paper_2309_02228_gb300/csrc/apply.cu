@@ -30,15 +30,19 @@ struct VecSet {
     int p_total;          // last absolute power of the whole call
 };
 
+__device__ __forceinline__ void *ring_of(const VecSet &v, int k) {
+    const int r = k % 3;   // selects, not an indexed load: keeps the struct out of local memory
+    return r == 0 ? v.ring[0] : (r == 1 ? v.ring[1] : v.ring[2]);
+}
 template <typename T> __device__ __forceinline__ const T *vec_ro(const VecSet &v, int k) {
     if (k == 0) return reinterpret_cast<const T *>(v.x);
-    if (v.final_only) return reinterpret_cast<const T *>(v.ring[k % 3]);
+    if (v.final_only) return reinterpret_cast<const T *>(ring_of(v, k));
     return reinterpret_cast<const T *>(v.ybase) + (int64_t)k * v.bstride;
 }
 template <typename T> __device__ __forceinline__ T *vec_rw(const VecSet &v, int k) {
     if (v.final_only) {
         if (k == v.p_total && !v.use_gamma) return reinterpret_cast<T *>(v.final_out);
-        return reinterpret_cast<T *>(v.ring[k % 3]);
+        return reinterpret_cast<T *>(ring_of(v, k));
     }
     return reinterpret_cast<T *>(v.ybase) + (int64_t)k * v.bstride;
 }
@@ -88,72 +92,165 @@ template <> struct VecLoad<double, 4> : VecLoadD2<4> {};
 template <> struct VecLoad<double, 8> : VecLoadD2<8> {};
 template <> struct VecLoad<double, 16> : VecLoadD2<16> {};
 
+template <typename T, int NR> struct RowBatch {
+    // entries whose gathers are in flight together: a whole 27-point row in one batch for a
+    // single right-hand side, fewer when each gather is a vector of NR values
+    static constexpr int B = ((sizeof(T) == 4 ? 32 : 16) / NR) > 0 ? ((sizeof(T) == 4 ? 32 : 16) / NR) : 1;
+};
+
+// Row sum of one row over its stored entries (stride 32 between consecutive entries of the
+// row, SELL-32), ascending column order, one FMA per entry.
+//
+// SM (a staged task): columns and values sit in shared memory, so only the vector gathers are
+// kept in registers - all gathers of a batch are issued before the first FMA, and the column
+// and value of each entry are read again from shared memory for the FMA.
+// Global: column and value loads of a batch first, then the gathers, then the FMAs.
+// Padding entries (column -1) gather the row's own element and are dropped by a select; a
+// partial last batch is predicated, never split into dependent single steps.
+template <typename T, int NR, bool SM, bool SV>
+__device__ __forceinline__ void row_sum(const int32_t *colp, const T *valp, int32_t L, int32_t row,
+                                        const T *y1, int n_rhs, int q0, T (&acc)[NR]) {
+    constexpr int BT = RowBatch<T, NR>::B;
+    // FP64 keeps two partial sums (even / odd entries) to halve the dependent FMA chain; both
+    // the staged and the global path assign entries by the same parity, so every path sums in
+    // the same order
+    constexpr bool TWO = sizeof(T) == 8 && NR == 1;
+    static_assert(!TWO || BT % 2 == 0, "batches must preserve entry parity");
+    T acc2[NR];
+#pragma unroll
+    for (int q = 0; q < NR; q++) {
+        acc[q] = (T)0;
+        acc2[q] = (T)0;
+    }
+    for (int32_t j = 0; j < L; j += BT) {
+        T xx[BT][NR];
+        if (SM) {
+#pragma unroll
+            for (int u = 0; u < BT; u++) {
+                if (j + u < L) {
+                    const int32_t c = colp[32 * (j + u)];
+                    VecLoad<T, NR>::ld(y1 + (int64_t)(c >= 0 ? c : row) * n_rhs + q0, xx[u]);
+                }
+            }
+            // values from shared memory when staged with the columns, else straight from
+            // global memory (coalesced, in flight together with the gathers)
+#pragma unroll
+            for (int u = 0; u < BT; u++) {
+                if (j + u < L) {
+                    const int32_t c = colp[32 * (j + u)];
+                    const T v = SV ? valp[32 * (j + u)] : __ldg(valp + 32 * (j + u));
+#pragma unroll
+                    for (int q = 0; q < NR; q++) {
+                        if (TWO && (u & 1)) {
+                            const T f = fma(v, xx[u][q], acc2[q]);
+                            acc2[q] = c >= 0 ? f : acc2[q];
+                        } else {
+                            const T f = fma(v, xx[u][q], acc[q]);
+                            acc[q] = c >= 0 ? f : acc[q];
+                        }
+                    }
+                }
+            }
+        } else {
+            constexpr int BG = BT > 8 ? 8 : BT;   // register budget of the global path
+#pragma unroll
+            for (int j2 = 0; j2 < BT; j2 += BG) {
+                int32_t cc[BG];
+                T vv[BG];
+#pragma unroll
+                for (int u = 0; u < BG; u++) {
+                    const bool in = j + j2 + u < L;
+                    cc[u] = in ? __ldg(colp + 32 * (j + j2 + u)) : -1;
+                    vv[u] = in ? __ldg(valp + 32 * (j + j2 + u)) : (T)0;
+                }
+#pragma unroll
+                for (int u = 0; u < BG; u++)
+                    VecLoad<T, NR>::ld(y1 + (int64_t)(cc[u] >= 0 ? cc[u] : row) * n_rhs + q0, xx[j2 + u]);
+#pragma unroll
+                for (int u = 0; u < BG; u++)
+#pragma unroll
+                    for (int q = 0; q < NR; q++) {
+                        if (TWO && (u & 1)) {
+                            const T f = fma(vv[u], xx[j2 + u][q], acc2[q]);
+                            acc2[q] = cc[u] >= 0 ? f : acc2[q];
+                        } else {
+                            const T f = fma(vv[u], xx[j2 + u][q], acc[q]);
+                            acc[q] = cc[u] >= 0 ? f : acc[q];
+                        }
+                    }
+            }
+        }
+    }
+    if (TWO) {
+#pragma unroll
+        for (int q = 0; q < NR; q++) acc[q] += acc2[q];
+    }
+}
+
+// y_k = a_k * sum + b_k * y_{k-1} + c_k * y_{k-2} (zero coefficients skipped), plus the
+// running polynomial sum_k gamma_k y_k when asked for (eq. (3)); tasks of one chunk run in
+// power order, so the running sum needs no atomics.
 template <typename T, int NR>
-__device__ __forceinline__ void row_power(const SellView &A, int64_t s, int lane, int n_rhs,
-                                          const VecSet &V, int k, const Coefs &cf) {
-    const int32_t r0 = __ldg(A.slice_row + s), r1 = __ldg(A.slice_row + s + 1);
-    const int32_t row = r0 + lane;
-    if (row >= r1) return;
-    const int32_t L = __ldg(A.slice_len + s);
-    const long long base = 32ll * __ldg(A.slice_ptr + s) + lane;
-    const T *__restrict__ val = reinterpret_cast<const T *>(A.val);
+__device__ __forceinline__ void row_finish(const T (&acc)[NR], int32_t row, int n_rhs, int q0,
+                                           const VecSet &V, int k, const Coefs &cf) {
     const T *y1 = vec_ro<T>(V, k - 1);
     const T *y2 = k >= 2 ? vec_ro<T>(V, k - 2) : nullptr;
     T *yk = vec_rw<T>(V, k);
     const T a = (T)cf.a[k], b = (T)cf.b[k], c = (T)cf.c[k];
-    for (int q0 = 0; q0 < n_rhs; q0 += NR) {
-        T acc[NR];
+    const int64_t o = (int64_t)row * n_rhs + q0;
+    T res[NR];
 #pragma unroll
-        for (int q = 0; q < NR; q++) acc[q] = (T)0;
-#pragma unroll 4
-        for (int32_t j = 0; j < L; j++) {
-            const long long d = base + 32ll * j;
-            const int32_t cidx = __ldg(A.col + d);
-            const T v = __ldg(val + d);
-            if (cidx >= 0) {
-                T xv[NR];
-                VecLoad<T, NR>::ld(y1 + (int64_t)cidx * n_rhs + q0, xv);
+    for (int q = 0; q < NR; q++) res[q] = a * acc[q];
+    if (b != (T)0) {
+        T yv[NR];
+        VecLoad<T, NR>::ld(y1 + o, yv);
 #pragma unroll
-                for (int q = 0; q < NR; q++) acc[q] = fma(v, xv[q], acc[q]);
-            }
-        }
-        const int64_t o = (int64_t)row * n_rhs + q0;
-        T res[NR];
+        for (int q = 0; q < NR; q++) res[q] = fma(b, yv[q], res[q]);
+    }
+    if (c != (T)0 && y2) {
+        T yv[NR];
+        VecLoad<T, NR>::ld(y2 + o, yv);
 #pragma unroll
-        for (int q = 0; q < NR; q++) res[q] = a * acc[q];
-        if (b != (T)0) {
-            T yv[NR];
-            VecLoad<T, NR>::ld(y1 + o, yv);
+        for (int q = 0; q < NR; q++) res[q] = fma(c, yv[q], res[q]);
+    }
 #pragma unroll
-            for (int q = 0; q < NR; q++) res[q] = fma(b, yv[q], res[q]);
-        }
-        if (c != (T)0 && y2) {
-            T yv[NR];
-            VecLoad<T, NR>::ld(y2 + o, yv);
+    for (int q = 0; q < NR; q++) yk[o + q] = res[q];
+    if (V.use_gamma) {
+        T *acc_out = reinterpret_cast<T *>(V.final_out);
+        const T gk = (T)cf.g[k];
+        if (k == 1) {
+            const T *x = reinterpret_cast<const T *>(V.x);
+            const T g0 = (T)cf.g[0];
 #pragma unroll
-            for (int q = 0; q < NR; q++) res[q] = fma(c, yv[q], res[q]);
-        }
+            for (int q = 0; q < NR; q++) acc_out[o + q] = fma(gk, res[q], g0 * x[o + q]);
+        } else {
 #pragma unroll
-        for (int q = 0; q < NR; q++) yk[o + q] = res[q];
-        if (V.use_gamma) {
-            // running polynomial sum_k gamma_k y_k (eq. (3)); tasks of one chunk run in order
-            T *acc_out = reinterpret_cast<T *>(V.final_out);
-            const T gk = (T)cf.g[k];
-            if (k == 1) {
-                const T *x = reinterpret_cast<const T *>(V.x);
-                const T g0 = (T)cf.g[0];
-#pragma unroll
-                for (int q = 0; q < NR; q++) acc_out[o + q] = fma(gk, res[q], g0 * x[o + q]);
-            } else {
-#pragma unroll
-                for (int q = 0; q < NR; q++) acc_out[o + q] = fma(gk, res[q], acc_out[o + q]);
-            }
+            for (int q = 0; q < NR; q++) acc_out[o + q] = fma(gk, res[q], acc_out[o + q]);
         }
     }
 }
 
+// Power k of the rows of slice s.  Thread `lane` owns row slice_row[s] + lane.  colp / valp
+// point at the slice's first entry (in global memory, or in a staged shared-memory copy).
+template <typename T, int NR, bool SM, bool SV>
+__device__ __forceinline__ void slice_power(const SellView &A, int64_t s, const int32_t *colp,
+                                            const T *valp, int lane, int n_rhs, const VecSet &V,
+                                            int k, const Coefs &cf) {
+    const int32_t r0 = __ldg(A.slice_row + s), r1 = __ldg(A.slice_row + s + 1);
+    const int32_t row = r0 + lane;
+    if (row >= r1) return;
+    const int32_t L = __ldg(A.slice_len + s);
+    const T *y1 = vec_ro<T>(V, k - 1);
+    for (int q0 = 0; q0 < n_rhs; q0 += NR) {
+        T acc[NR];
+        row_sum<T, NR, SM, SV>(colp + lane, valp + lane, L, row, y1, n_rhs, q0, acc);
+        row_finish<T, NR>(acc, row, n_rhs, q0, V, k, cf);
+    }
+}
+
 // ------------------------------------------------------------------------------------------
-// Unblocked: one launch per power (Alg. 1), warp per slice.
+// Unblocked p x SpMV (Alg. 1): one launch per power, one warp per slice, matrix read from
+// global memory by many warps per SM.  Same row function as the blocked kernel.
 // ------------------------------------------------------------------------------------------
 template <typename T, int NR>
 __global__ void __launch_bounds__(256) mpk_power_kernel(SellView A, int64_t n_slices, int n_rhs,
@@ -161,99 +258,361 @@ __global__ void __launch_bounds__(256) mpk_power_kernel(SellView A, int64_t n_sl
     const int lane = threadIdx.x & 31;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t s = w0; s < n_slices; s += nw) row_power<T, NR>(A, s, lane, n_rhs, V, k, cf);
+    const T *gval = reinterpret_cast<const T *>(A.val);
+    for (int64_t s = w0; s < n_slices; s += nw) {
+        const long long gofs = 32ll * __ldg(A.slice_ptr + s);
+        slice_power<T, NR, false, false>(A, s, A.col + gofs, gval + gofs, lane, n_rhs, V, k, cf);
+    }
 }
 
 // ------------------------------------------------------------------------------------------
-// Blocked: persistent CTAs take tasks (chunk c, power k) from a ticket counter in the order of
-// the level-group wavefront.  Before computing, a task waits until every chunk in its
-// dependency range has published power k-1; after computing it publishes power k.
-// Flags are monotone per launch: value epoch*64 + k.  Every wait is bounded in time.
+// Task kernel.  Persistent CTAs take tasks (chunk c, power k) from a ticket counter in
+// schedule order.  A task waits until every chunk in its dependency range has published
+// power k-1, computes, and publishes power k (flag value epoch*64 + k, monotone within a
+// launch).  The same kernel runs the unblocked baseline: one launch per power, every task at
+// segment power 1, so nothing waits.
 // ------------------------------------------------------------------------------------------
 struct BlockedArgs {
     const int32_t *chunk_slice;
+    const long long *chunk_entry;    // first SELL entry of each chunk (n_chunks+1)
     const int32_t *dep_lo, *dep_hi;
-    const uint32_t *tasks;
+    const int4 *desc;                // per ticket: {chunk | power << 24, first entry, entries, 0}
     int64_t n_tasks;
     uint32_t *flags;
     MpkCtrl *ctrl;
-    int k0;                 // absolute power before this segment
+    int32_t n_chunks;
+    int k0;                          // absolute power before this segment
+    int32_t slot_cap;                // SELL entries one shared-memory slot holds (0: no staging)
+    int32_t stage_vals;              // 1: values are staged with the columns
     uint64_t timeout_ns;
-    uint32_t debug_drop;    // 1: task (chunk 0, power 1) does not publish
+    uint32_t debug_drop;             // 1: task (chunk 0, power 1) does not publish
 };
 
-__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
-    uint32_t v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
+// Two values addressed by a runtime index without an indexed (local-memory) array.
+template <typename U> struct Pair {
+    U v0, v1;
+    __device__ __forceinline__ U get(int i) const { return i ? v1 : v0; }
+    __device__ __forceinline__ void set(int i, U v) {
+        if (i) v1 = v;
+        else v0 = v;
+    }
+};
+
 __device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+__device__ __forceinline__ void fence_acq_rel_cta() { asm volatile("fence.acq_rel.cta;" ::: "memory"); }
 __device__ __forceinline__ uint64_t globaltimer_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
+// slot b uses named barrier 1 + b (literal ids keep the barrier count at three)
+__device__ __forceinline__ void slot_bar_sync(int b, int n) {
+    if (b == 0) asm volatile("bar.sync 1, %0;" ::"r"(n) : "memory");
+    else asm volatile("bar.sync 2, %0;" ::"r"(n) : "memory");
+}
+__device__ __forceinline__ void slot_bar_arrive(int b, int n) {
+    if (b == 0) asm volatile("bar.arrive 1, %0;" ::"r"(n) : "memory");
+    else asm volatile("bar.arrive 2, %0;" ::"r"(n) : "memory");
+}
+// mbarrier + bulk copy (TMA, non-tensor) helpers
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"((uint32_t)__cvta_generic_to_shared(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src), "r"(bytes),
+                   "r"((uint32_t)__cvta_generic_to_shared(bar)) : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-template <typename T, int NR>
-__global__ void __launch_bounds__(256) mpk_blocked_kernel(SellView A, int n_rhs, VecSet V,
-                                                          Coefs cf, BlockedArgs B) {
-    __shared__ uint32_t s_task, s_next, s_base;
-    __shared__ int s_abort;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-    if (tid == 0) {
-        s_base = *(volatile uint32_t *)&B.ctrl->epoch * 64u;
-        s_task = atomicAdd(&B.ctrl->ticket, 1u);
-        s_abort = 0;
+// First index in [from, hi] whose flag is below `target` (hi + 1 if none).  One warp, eight
+// flags per lane in flight at once.  Flags only grow within a launch, so the result stays a
+// valid lower bound and later checks may start from it.
+__device__ __forceinline__ int32_t first_unpublished(const uint32_t *flags, int32_t from,
+                                                     int32_t hi, uint32_t target, int lane) {
+    int32_t first = hi + 1;
+    for (int32_t b0 = from; b0 <= hi; b0 += 256) {
+        uint32_t v[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const int32_t i = b0 + u * 32 + lane;
+            v[u] = i <= hi ? *(const volatile uint32_t *)(flags + i) : 0xffffffffu;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; u++)
+            if (v[u] < target) first = min(first, b0 + u * 32 + lane);
+        const int32_t f = __reduce_min_sync(0xffffffffu, first);
+        if (f <= hi) return f;
     }
+    return hi + 1;
+}
+
+// The CTA: compute warps 0..ncomp-1 and one control warp (the last).  The control warp
+//  - keeps the next task's descriptor (chunk, power, first SELL entry, entry count) fetched
+//    ahead of time (ticket + one 16-byte load);
+//  - as soon as a shared-memory slot is free, copies the task's SELL block (column indices,
+//    optionally values - contiguous in memory) into it with bulk asynchronous copies: matrix
+//    data needs no dependency, so the copy overlaps the wait;
+//  - waits until every chunk up to dep_hi(c) has published power k-1, scanning flags from a
+//    per-power watermark it keeps in shared memory (everything below it was seen published),
+//    then issues an acquire fence and hands the task over through a named barrier;
+//  - publishes finished tasks with one release store per task.
+// Two slots: one computes while the other loads and waits.  Compute warps read the staged
+// matrix block from shared memory and gather vector entries from L1/L2.  Every wait is
+// bounded in time; on a timeout the CTA stops and the error is latched.
+static constexpr uint32_t TASK_END = 0xffffffffu;
+
+// STAGED: every chunk's block (columns and values) fits a slot - the plan cuts chunks to the
+// slot size.  Unstaged (a slice larger than a slot): compute warps read the matrix from global
+// memory.
+template <typename T, int NR, bool STAGED>
+__global__ void __launch_bounds__(288, 2) mpk_blocked_kernel(SellView A, int n_rhs, VecSet V,
+                                                             Coefs cf, BlockedArgs B) {
+    constexpr bool SV = STAGED;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint32_t s_code[2];
+    __shared__ int32_t s_staged[2];
+    __shared__ int s_done[2];
+    __shared__ uint32_t s_epoch;
+    __shared__ int32_t s_wm[MPK_MAX_P + 1];
+    __shared__ __align__(8) uint64_t s_full[2];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nthreads = blockDim.x, ncomp = (blockDim.x >> 5) - 1;
+    const int32_t cap = B.slot_cap;
+    constexpr bool sv = SV;
+    const size_t slot_bytes = (size_t)cap * (4 + (sv ? sizeof(T) : 0));
+    int32_t *const scol0 = reinterpret_cast<int32_t *>(smem);
+    T *const sval0 = reinterpret_cast<T *>(smem + (size_t)cap * 4);
+    int32_t *const scol1 = reinterpret_cast<int32_t *>(smem + slot_bytes);
+    T *const sval1 = reinterpret_cast<T *>(smem + slot_bytes + (size_t)cap * 4);
+    if (tid == 0) {
+        s_epoch = *(volatile uint32_t *)&B.ctrl->epoch;
+        s_done[0] = 0;
+        s_done[1] = 0;
+        mbar_init(&s_full[0], 1);
+        mbar_init(&s_full[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        fence_proxy_async_smem();
+    }
+    for (int i = tid; i <= MPK_MAX_P; i += nthreads) s_wm[i] = 0;
     __syncthreads();
-    const uint32_t base = s_base;
-    while (true) {
-        const uint32_t t = s_task;
-        if (t >= B.n_tasks || s_abort) break;
-        const uint32_t code = __ldg(B.tasks + t);
-        const int32_t c = (int32_t)(code & 0xffffffu);
-        const int k = (int)(code >> 24);
-        if (tid == 0) s_next = atomicAdd(&B.ctrl->ticket, 1u);   // overlap with the task
-        if (k > 1) {
-            const int32_t lo = __ldg(B.dep_lo + c), hi = __ldg(B.dep_hi + c);
-            const uint32_t target = base + (uint32_t)(k - 1);
-            int fail = 0;
-            for (int32_t i = lo + tid; i <= hi; i += blockDim.x) {
-                if (ld_acquire_u32(B.flags + i) >= target) continue;
-                const uint64_t t0 = globaltimer_ns();
-                unsigned backoff = 64;
-                while (ld_acquire_u32(B.flags + i) < target) {
-                    if (globaltimer_ns() - t0 > B.timeout_ns ||
-                        *(volatile uint32_t *)&B.ctrl->error) {
-                        fail = 1;
-                        break;
+    const uint32_t epoch = s_epoch;
+    const uint32_t base = epoch * 64u;
+
+    if (warp < ncomp) {
+        // ---------------- compute warps
+        Pair<uint32_t> phase{0u, 0u};
+        for (int i = 0;; i++) {
+            const int b = i & 1;
+            slot_bar_sync(b, nthreads);
+            const uint32_t code = *(volatile uint32_t *)&s_code[b];
+            if (code == TASK_END) break;
+            const int32_t staged = *(volatile int32_t *)&s_staged[b];
+            const int32_t c = (int32_t)(code & 0xffffffu);
+            const int k = B.k0 + (int)(code >> 24);
+            const int32_t s0 = __ldg(B.chunk_slice + c), s1 = __ldg(B.chunk_slice + c + 1);
+            bool ok = true;
+            if (staged) {
+                // bounded wait for the bulk copies of this slot
+                const uint32_t ph = phase.get(b);
+                if (!mbar_try_wait(&s_full[b], ph)) {
+                    const uint64_t t0 = globaltimer_ns();
+                    while (!mbar_try_wait(&s_full[b], ph)) {
+                        if (globaltimer_ns() - t0 > B.timeout_ns) { ok = false; break; }
                     }
-                    __nanosleep(backoff);
-                    if (backoff < 2048) backoff <<= 1;
                 }
-                if (fail) break;
+                phase.set(b, ph ^ 1u);
             }
-            if (__syncthreads_or(fail)) {
-                if (tid == 0) {
-                    if (atomicOr(&B.ctrl->error, 1u) == 0u) B.ctrl->err_task = t;
+            if (ok) {
+                const long long e0 = __ldg(A.slice_ptr + s0);
+                const T *gval = reinterpret_cast<const T *>(A.val);
+                for (int32_t s = s0 + warp; s < s1; s += ncomp) {
+                    const long long gofs = 32ll * __ldg(A.slice_ptr + s);
+                    if (STAGED) {
+                        const long long off = gofs - 32ll * e0;
+                        slice_power<T, NR, true, SV>(A, s, (b ? scol1 : scol0) + off,
+                                                     SV ? (b ? sval1 : sval0) + off : gval + gofs,
+                                                     lane, n_rhs, V, k, cf);
+                    } else {
+                        slice_power<T, NR, false, false>(A, s, A.col + gofs, gval + gofs, lane, n_rhs, V, k, cf);
+                    }
                 }
-                break;
+            } else if (lane == 0) {
+                atomicOr(&B.ctrl->error, 2u);
+            }
+            __syncwarp();
+            if (lane == 0) {
+                fence_acq_rel_cta();
+                atomicAdd(&s_done[b], 1);
             }
         }
-        const int32_t s0 = __ldg(B.chunk_slice + c), s1 = __ldg(B.chunk_slice + c + 1);
-        for (int32_t s = s0 + warp; s < s1; s += nwarp)
-            row_power<T, NR>(A, s, lane, n_rhs, V, B.k0 + k, cf);
-        __syncthreads();
-        if (tid == 0) {
-            if (!(B.debug_drop && c == 0 && k == 1)) {
-                __threadfence();
-                st_release_u32(B.flags + c, base + (uint32_t)k);
-            }
-            s_task = s_next;
+    } else {
+        // ---------------- control warp (all lanes run the same scalar logic)
+        Pair<uint32_t> code{0u, 0u};
+        Pair<int> st{0, 0};           // 0 free, 1 fetched, 2 computing, 3 end handed over
+        Pair<int32_t> stg{0, 0};
+        Pair<uint32_t> cph{0u, 0u};   // parity of each slot's next bulk-copy completion
+        int nf = 0, nh = 0;           // next slot to fill, next slot to hand over
+        bool ended = false, failed = false;
+        uint64_t wait_t0 = 0;
+        bool waiting = false;
+        // Tasks of this CTA: tickets blockIdx.x, blockIdx.x + gridDim.x, ... (static round robin;
+        // all CTAs are co-resident, launched cooperatively).  Descriptors {code, first entry,
+        // entries, -} are loaded two tasks ahead, so no load sits on the hand-over path.
+        int64_t tnext = blockIdx.x;
+        int4 pend = make_int4((int)TASK_END, 0, 0, 0), pend2 = pend;
+        if (lane == 0) {
+            if (tnext < B.n_tasks) pend = __ldg(B.desc + tnext);
+            if (tnext + gridDim.x < B.n_tasks) pend2 = __ldg(B.desc + tnext + gridDim.x);
         }
-        __syncthreads();
+        tnext += 2ll * gridDim.x;
+        bool have = true;
+        for (long long it = 0;; it++) {
+            bool progress = false;
+            // (0) shift the prefetched descriptors once the front one was used
+            if (!have && !ended && !failed) {
+                pend = pend2;
+                pend2 = make_int4((int)TASK_END, 0, 0, 0);
+                if (lane == 0 && tnext < B.n_tasks) pend2 = __ldg(B.desc + tnext);
+                tnext += gridDim.x;
+                have = true;
+            }
+            // (1) finished tasks: publish power k of the chunk (one release store)
+#pragma unroll
+            for (int b = 0; b < 2; b++) {
+                if (st.get(b) != 2) continue;
+                int d = 0;
+                if (lane == 0) d = *(volatile int *)&s_done[b];
+                d = __shfl_sync(0xffffffffu, d, 0);
+                if (d != ncomp) continue;
+                const uint32_t cb = code.get(b);
+                const int32_t c = (int32_t)(cb & 0xffffffu);
+                const int k = (int)(cb >> 24);
+                if (lane == 0) {
+                    fence_acq_rel_cta();
+                    s_done[b] = 0;
+                    if (!(B.debug_drop && c == 0 && k == 1))
+                        st_release_u32(B.flags + c, base + (uint32_t)k);
+                }
+                st.set(b, 0);
+                progress = true;
+            }
+            // (2) move the fetched task into a free slot and start copying its matrix block
+            if (have && st.get(nf) == 0) {
+                const uint32_t cd = (uint32_t)__shfl_sync(0xffffffffu, pend.x, 0);
+                const int32_t pz = __shfl_sync(0xffffffffu, pend.z, 0);
+                int32_t staged = 0;
+                if (STAGED && cd != TASK_END && pz > 0 && pz <= cap) {
+                    staged = 1;
+                    if (lane == 0) {
+                        const long long e0 = (long long)(uint32_t)pend.y;
+                        const uint32_t ne = (uint32_t)pend.z;
+                        // the slot's previous contents were read by the compute warps (generic
+                        // proxy); order those reads before the asynchronous writes
+                        fence_proxy_async_smem();
+                        mbar_expect_tx(&s_full[nf], ne * (uint32_t)(4 + (sv ? sizeof(T) : 0)));
+                        bulk_g2s(nf ? (void *)scol1 : (void *)scol0, A.col + e0, ne * 4u, &s_full[nf]);
+                        if (sv)
+                            bulk_g2s(nf ? (void *)sval1 : (void *)sval0, reinterpret_cast<const T *>(A.val) + e0,
+                                     ne * (uint32_t)sizeof(T), &s_full[nf]);
+                    }
+                    cph.set(nf, cph.get(nf) ^ 1u);
+                }
+                code.set(nf, cd);
+                stg.set(nf, staged);
+                st.set(nf, 1);
+                if (cd == TASK_END) ended = true;
+                have = false;
+                nf ^= 1;
+                progress = true;
+            }
+            // (3) hand the oldest fetched task over once its dependencies are published
+            if (st.get(nh) == 1) {
+                uint32_t cd = code.get(nh);
+                bool ready = true;
+                if (cd != TASK_END && !failed) {
+                    const int32_t c = (int32_t)(cd & 0xffffffu);
+                    const int k = (int)(cd >> 24);
+                    if (k > 1) {
+                        const int32_t hi = __ldg(B.dep_hi + c);
+                        const int32_t wm = s_wm[k - 1];
+                        if (wm <= hi) {
+                            const int32_t f = first_unpublished(B.flags, wm, hi, base + (uint32_t)(k - 1), lane);
+                            if (lane == 0) s_wm[k - 1] = f;
+                            __syncwarp();
+                            ready = f > hi;
+                        }
+                        if (ready) fence_acq_rel_gpu();
+                    }
+                }
+                if (!ready) {
+                    uint64_t now = 0;
+                    int err = 0;
+                    if (lane == 0) {
+                        now = globaltimer_ns();
+                        err = *(volatile uint32_t *)&B.ctrl->error;
+                    }
+                    now = __shfl_sync(0xffffffffu, now, 0);
+                    err = __shfl_sync(0xffffffffu, err, 0);
+                    if (!waiting) { waiting = true; wait_t0 = now; }
+                    if (err || now - wait_t0 > B.timeout_ns) {
+                        if (lane == 0 && !err && atomicOr(&B.ctrl->error, 1u) == 0u)
+                            B.ctrl->err_task = cd;
+                        failed = true;
+                    }
+                }
+                if (failed && cd != TASK_END) {
+                    // stop: the compute warps get the end marker instead of this task.  Copies
+                    // already issued into slots that will not be computed still land; wait for
+                    // them (bounded) so that no transfer is in flight when the CTA exits.
+#pragma unroll
+                    for (int b = 0; b < 2; b++) {
+                        if (st.get(b) != 1 || !stg.get(b)) continue;
+                        const uint32_t par = cph.get(b) ^ 1u;   // parity of that copy's phase
+                        const uint64_t t0 = globaltimer_ns();
+                        bool done = false;
+                        while (!done && globaltimer_ns() - t0 < B.timeout_ns) {
+                            int w = 0;
+                            if (lane == 0) w = mbar_try_wait(&s_full[b], par);
+                            done = __shfl_sync(0xffffffffu, w, 0) != 0;
+                        }
+                        stg.set(b, 0);
+                    }
+                    cd = TASK_END;
+                    code.set(nh, cd);
+                    ended = true;
+                    ready = true;
+                }
+                if (ready) {
+                    waiting = false;
+                    if (lane == 0) {
+                        s_code[nh] = cd;
+                        s_staged[nh] = stg.get(nh);
+                    }
+                    __syncwarp();
+                    slot_bar_arrive(nh, nthreads);
+                    st.set(nh, cd == TASK_END ? 3 : 2);
+                    nh ^= 1;
+                    progress = true;
+                }
+            }
+            // done once the end marker went out and nothing is computing (slots are handed
+            // over in ticket order, so nothing fetched before the marker is left behind)
+            if ((st.v0 == 3 || st.v1 == 3) && st.v0 != 2 && st.v1 != 2) break;
+            if (!progress) __nanosleep(32);
+        }
     }
     // the last CTA out re-arms the control block for the next launch
     __syncthreads();
@@ -283,16 +642,19 @@ __global__ void gather_in_kernel(const T *X, int64_t ldx, int interleaved, const
             out[r * n_rhs + q] = interleaved ? X[src * n_rhs + q] : X[src + q * ldx];
     }
 }
+// blockIdx.y = output block b: reads in + b*in_stride, writes Y + b*ldy*n_rhs
 template <typename T>
-__global__ void scatter_out_kernel(const T *in, const int32_t *iperm, int64_t n, int n_rhs,
-                                   T *Y, int64_t ldy, int interleaved) {
+__global__ void scatter_out_kernel(const T *in, int64_t in_stride, const int32_t *iperm,
+                                   int64_t n, int n_rhs, T *Y, int64_t ldy, int interleaved) {
+    const T *src = in + (int64_t)blockIdx.y * in_stride;
+    T *dst = Y + (int64_t)blockIdx.y * ldy * n_rhs;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = iperm ? iperm[i] : i;
         for (int q = 0; q < n_rhs; q++) {
-            const T v = in[r * n_rhs + q];
-            if (interleaved) Y[i * n_rhs + q] = v;
-            else Y[i + q * ldy] = v;
+            const T v = src[r * n_rhs + q];
+            if (interleaved) dst[i * n_rhs + q] = v;
+            else dst[i + q * ldy] = v;
         }
     }
 }
@@ -303,14 +665,61 @@ static unsigned grid_n(int64_t n, int block = 256) {
 }
 
 template <typename T, int NR>
+mpk_status launch_tasks(mpk_plan_s *P, const SellView &A, int n_rhs, const VecSet &V,
+                        const Coefs &cf, Schedule *sch, int k0, uint32_t flags, cudaStream_t s) {
+    BlockedArgs B;
+    B.chunk_slice = P->chunk_slice.as<int32_t>();
+    B.chunk_entry = P->chunk_entry.as<long long>();
+    B.dep_lo = P->dep_lo.as<int32_t>();
+    B.dep_hi = P->dep_hi.as<int32_t>();
+    B.desc = sch->desc.as<int4>();
+    B.n_tasks = sch->n_tasks;
+    B.flags = P->flags.as<uint32_t>();
+    B.ctrl = P->ctrl.as<MpkCtrl>();
+    B.n_chunks = P->n_chunks;
+    B.k0 = k0;
+    B.timeout_ns = (uint64_t)P->opts.wait_timeout_us * 1000ull;
+    B.debug_drop = (flags & MPK_DEBUG_DROP_FLAG) && k0 == 0 ? 1u : 0u;
+    // shared-memory slots sized for the largest chunk (the plan keeps chunks within a slot)
+    const size_t es = sizeof(T);
+    const bool staged = P->stage_smem != 0;
+    const bool sv = staged;
+    const size_t per_entry = 4 + (sv ? es : 0);
+    const int64_t cap = staged ? (P->max_chunk_entries + 31) / 32 * 32 : 0;
+    B.slot_cap = (int32_t)cap;
+    B.stage_vals = sv ? 1 : 0;
+    const size_t dyn = (size_t)cap * 2 * per_entry;
+    auto kern = staged ? mpk_blocked_kernel<T, NR, true> : mpk_blocked_kernel<T, NR, false>;
+    MPK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    // epochs advance by one per launch; re-arm the flags long before they could wrap
+    if (++P->launches_since_reset >= (1ull << 25)) {
+        MPK_CUDA(cudaMemsetAsync(P->flags.p, 0, (P->n_chunks + 1) * 4, s));
+        uint32_t one = 1;
+        MPK_CUDA(cudaMemcpyAsync(P->ctrl.p, &one, 4, cudaMemcpyHostToDevice, s));
+        P->launches_since_reset = 1;
+    }
+    int occ = 0;
+    MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, P->blocked_block, dyn));
+    if (occ < 1) return MPK_ERR_UNIMPLEMENTED;
+    const int per_sm = std::max(1, std::min(occ, P->ctas_per_sm));
+    const int64_t grid = std::min<int64_t>((int64_t)P->n_sm * per_sm, std::max<int64_t>(sch->n_tasks, 1));
+    // cooperative: all CTAs co-resident, which the static task assignment relies on
+    SellView a_ = A;
+    VecSet v_ = V;
+    Coefs c_ = cf;
+    int nr_ = n_rhs;
+    void *kargs[] = {&a_, &nr_, &v_, &c_, &B};
+    MPK_CUDA(cudaLaunchCooperativeKernel((void *)kern, dim3((unsigned)grid), dim3(P->blocked_block), kargs, dyn, s));
+    return MPK_OK;
+}
+
+template <typename T, int NR>
 mpk_status launch_powers(mpk_plan_s *P, const SellView &A, int n_rhs, const VecSet &V,
                          const Coefs &cf, int p, bool blocked, uint32_t flags, cudaStream_t s) {
     if (!blocked) {
-        const int64_t warps = P->n_slices;
-        const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(std::max<int64_t>(warps, 1), 8), 152 * 64);
-        for (int k = 1; k <= p; k++) {
-            mpk_power_kernel<T, NR><<<grid, 256, 0, s>>>(A, P->n_slices, n_rhs, V, k, cf);
-        }
+        // p back-to-back SpMV launches (Alg. 1)
+        const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(std::max<int64_t>(P->n_slices, 1), 8), 1 << 30);
+        for (int k = 1; k <= p; k++) mpk_power_kernel<T, NR><<<grid, 256, 0, s>>>(A, P->n_slices, n_rhs, V, k, cf);
         MPK_CUDA(cudaGetLastError());
         return MPK_OK;
     }
@@ -320,30 +729,7 @@ mpk_status launch_powers(mpk_plan_s *P, const SellView &A, int n_rhs, const VecS
         const int seg = std::min(P->p_blk, p - k0);
         Schedule *sch = nullptr;
         MPK_TRY(mpk_get_schedule(P, seg, &sch, s));
-        BlockedArgs B;
-        B.chunk_slice = P->chunk_slice.as<int32_t>();
-        B.dep_lo = P->dep_lo.as<int32_t>();
-        B.dep_hi = P->dep_hi.as<int32_t>();
-        B.tasks = sch->tasks.as<uint32_t>();
-        B.n_tasks = sch->n_tasks;
-        B.flags = P->flags.as<uint32_t>();
-        B.ctrl = P->ctrl.as<MpkCtrl>();
-        B.k0 = k0;
-        B.timeout_ns = (uint64_t)P->opts.wait_timeout_us * 1000ull;
-        B.debug_drop = (flags & MPK_DEBUG_DROP_FLAG) && k0 == 0 ? 1u : 0u;
-        // epochs advance by one per launch; re-arm the flags long before they could wrap
-        if (++P->launches_since_reset >= (1ull << 25)) {
-            MPK_CUDA(cudaMemsetAsync(P->flags.p, 0, (P->n_chunks + 1) * 4, s));
-            uint32_t one = 1;
-            MPK_CUDA(cudaMemcpyAsync(P->ctrl.p, &one, 4, cudaMemcpyHostToDevice, s));
-            P->launches_since_reset = 1;
-        }
-        int occ = 0;
-        MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mpk_blocked_kernel<T, NR>, 256, 0));
-        const int per_sm = std::max(1, std::min(occ, P->ctas_per_sm));
-        const int64_t grid = std::min<int64_t>((int64_t)P->n_sm * per_sm, std::max<int64_t>(sch->n_tasks, 1));
-        mpk_blocked_kernel<T, NR><<<(unsigned)grid, 256, 0, s>>>(A, n_rhs, V, cf, B);
-        MPK_CUDA(cudaGetLastError());
+        MPK_TRY((launch_tasks<T, NR>(P, A, n_rhs, V, cf, sch, k0, flags, s)));
         k0 += seg;
     }
     return MPK_OK;
@@ -367,39 +753,122 @@ mpk_status dispatch_nr(mpk_plan_s *P, const SellView &A, int n_rhs, const VecSet
     }
 }
 
+// r = b - A x in FP64 on the level-ordered matrix (iterative refinement residual; same row
+// function as the MPK, one warp per slice)
+__global__ void __launch_bounds__(256) residual_kernel(SellView A, int64_t n_slices, const double *x,
+                                                      const double *b, double *r) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const double *gval = reinterpret_cast<const double *>(A.val);
+    for (int64_t s = w0; s < n_slices; s += nw) {
+        const int32_t r0 = __ldg(A.slice_row + s), r1 = __ldg(A.slice_row + s + 1);
+        const int32_t row = r0 + lane;
+        if (row >= r1) continue;
+        const int32_t L = __ldg(A.slice_len + s);
+        const long long gofs = 32ll * __ldg(A.slice_ptr + s);
+        double acc[1];
+        row_sum<double, 1, false, false>(A.col + gofs + lane, gval + gofs + lane, L, row, x, 1, 0, acc);
+        r[row] = b[row] - acc[0];
+    }
+}
+
 }  // namespace
 
+mpk_status mpk_launch_residual(mpk_plan_s *P, const double *x, const double *b, double *r,
+                               cudaStream_t s) {
+    if (!P->has64) return MPK_ERR_ARG;
+    if (P->n == 0) return MPK_OK;
+    SellView A;
+    A.slice_ptr = P->slice_ptr.as<long long>();
+    A.slice_row = P->slice_row.as<int32_t>();
+    A.slice_len = P->slice_len.as<int32_t>();
+    A.col = P->s_col.as<int32_t>();
+    A.val = P->s_val64.p;
+    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(std::max<int64_t>(P->n_slices, 1), 8), 1 << 30);
+    residual_kernel<<<grid, 256, 0, s>>>(A, P->n_slices, x, b, r);
+    MPK_CUDA(cudaGetLastError());
+    return MPK_OK;
+}
+
 // ============================================================================================
-// Schedule: the level-group wavefront.  Step t runs powers k = 1..p on groups g = t-(k-1),
-// ascending in k; inside (g, k) the chunks ascend.  A chunk's rows lie in one group, so its
-// dependencies lie in groups g-1..g+1, all of which the order places earlier.
+// Schedules.  Both emit each power's chunks in ascending order and place every task after
+// all the tasks it depends on, so a CTA only ever waits for tickets taken before its own
+// (progress is guaranteed however many CTAs are resident).
+//
+// Type 0, level-group wavefront (Sec. 3: levels grouped by the cache size, groups executed
+// in a wavefront): step t runs powers k = 1..p on groups g = t-(k-1), ascending in k.  A
+// chunk's rows lie in one group, so its dependencies lie in groups g-1..g+1, all earlier.
+//
+// Type 1, lag-greedy: power k's next chunk c is emitted as soon as every chunk up to
+// dep_hi(c) has been emitted at power k-1 at least `slack` tickets earlier (slack ~ the
+// number of tasks in flight, so the dependency is normally complete when c starts); among
+// ready powers the highest goes first, which keeps the window between the leading and the
+// trailing power - the L2 working set - as short as the dependencies allow.
 // ============================================================================================
 mpk_status mpk_get_schedule(mpk_plan_s *P, int p, Schedule **out, cudaStream_t s) {
-    auto it = P->schedules.find(p);
-    if (it != P->schedules.end()) {
+    const int key = p * 1024 + P->sched_type * 512 + 0;
+    auto it = P->schedules.find(key);
+    if (it != P->schedules.end() && it->second->slack == P->sched_slack) {
         *out = it->second.get();
         return MPK_OK;
     }
     std::vector<uint32_t> h;
-    h.reserve((size_t)p * P->n_chunks);
-    const int G = P->n_groups;
-    for (int t = 0; t <= G + p - 2; t++)
-        for (int k = 1; k <= p; k++) {
-            const int g = t - (k - 1);
-            if (g < 0 || g >= G) continue;
-            for (int32_t c = P->h_group_chunk[g]; c < P->h_group_chunk[g + 1]; c++)
-                h.push_back((uint32_t)c | ((uint32_t)k << 24));
+    const int32_t NC = P->n_chunks;
+    h.reserve((size_t)p * NC);
+    if (P->sched_type == 0) {
+        const int G = P->n_groups;
+        for (int t = 0; t <= G + p - 2; t++)
+            for (int k = 1; k <= p; k++) {
+                const int g = t - (k - 1);
+                if (g < 0 || g >= G) continue;
+                for (int32_t c = P->h_group_chunk[g]; c < P->h_group_chunk[g + 1]; c++)
+                    h.push_back((uint32_t)c | ((uint32_t)k << 24));
+            }
+    } else {
+        const std::vector<int32_t> &dh = P->h_dep_hi;
+        std::vector<int32_t> nxt(p + 1, 0);
+        std::vector<int64_t> when((size_t)(p + 1) * std::max(NC, 1), 0);
+        const int64_t slack = P->sched_slack;
+        const int64_t total = (int64_t)p * NC;
+        for (int64_t t = 0; t < total; t++) {
+            int pick = 0;
+            for (int k = p; k >= 2 && !pick; k--) {
+                const int32_t c = nxt[k];
+                if (c >= NC) continue;
+                const int32_t hi = dh[c];
+                if (nxt[k - 1] > hi && t - when[(size_t)(k - 1) * NC + hi] >= slack) pick = k;
+            }
+            if (!pick) {
+                if (nxt[1] < NC) pick = 1;
+                else
+                    for (int k = 2; k <= p && !pick; k++)
+                        if (nxt[k] < NC && nxt[k - 1] > dh[nxt[k]]) pick = k;
+            }
+            if (!pick) return MPK_ERR_CUDA;   // cannot happen: dependencies are acyclic
+            const int32_t c = nxt[pick]++;
+            when[(size_t)pick * NC + c] = t;
+            h.push_back((uint32_t)c | ((uint32_t)pick << 24));
         }
+    }
     std::unique_ptr<Schedule> sch(new Schedule());
     sch->p = p;
+    sch->slack = P->sched_slack;
     sch->n_tasks = (int64_t)h.size();
-    MPK_TRY(sch->tasks.alloc(std::max<size_t>(h.size(), 1) * 4));
-    if (!h.empty())
-        MPK_CUDA(cudaMemcpyAsync(sch->tasks.p, h.data(), h.size() * 4, cudaMemcpyHostToDevice, s));
+    // descriptors: the control warp needs the chunk's SELL range right after the ticket
+    std::vector<int4> hd(h.size());
+    for (size_t i = 0; i < h.size(); i++) {
+        const int32_t c = (int32_t)(h[i] & 0xffffffu);
+        const long long e0 = P->h_chunk_entry[c], e1 = P->h_chunk_entry[c + 1];
+        hd[i] = make_int4((int)h[i], (int)e0, (int)(e1 - e0), 0);
+    }
+    MPK_TRY(sch->desc.alloc(std::max<size_t>(hd.size(), 1) * sizeof(int4)));
+    if (!hd.empty())
+        MPK_CUDA(cudaMemcpyAsync(sch->desc.p, hd.data(), hd.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
     // the host vector must outlive the copy
     MPK_CUDA(cudaStreamSynchronize(s));
     *out = sch.get();
-    P->schedules[p] = std::move(sch);
+    P->schedules[key] = std::move(sch);
     return MPK_OK;
 }
 
@@ -519,15 +988,13 @@ mpk_status mpk_apply_internal(mpk_plan_s *P, const mpk_coeffs *co, mpk_dtype dty
     else MPK_TRY(dispatch_nr<float>(P, A, n_rhs, V, cf, p, blocked, flags, s));
 
     if (!direct) {
-        // un-stage every output block into the user's layout / order
-        for (int64_t b = 0; b < nout_blocks; b++) {
-            const char *src = final_only ? (const char *)V.final_out : P->ws_y.as<char>() + (size_t)b * blk * es;
-            char *dst = (char *)Yd + (size_t)b * ublk * es;
-            if (dtype == MPK_F64)
-                scatter_out_kernel<double><<<g, 256, 0, s>>>((const double *)src, iperm, n, n_rhs, (double *)dst, ldy, interleaved);
-            else
-                scatter_out_kernel<float><<<g, 256, 0, s>>>((const float *)src, iperm, n, n_rhs, (float *)dst, ldy, interleaved);
-        }
+        // un-stage every output block into the user's layout / order (one launch)
+        const void *src = final_only ? V.final_out : P->ws_y.p;
+        const dim3 grid2(std::max(1u, g / (unsigned)nout_blocks), (unsigned)nout_blocks);
+        if (dtype == MPK_F64)
+            scatter_out_kernel<double><<<grid2, 256, 0, s>>>((const double *)src, blk, iperm, n, n_rhs, (double *)Yd, ldy, interleaved);
+        else
+            scatter_out_kernel<float><<<grid2, 256, 0, s>>>((const float *)src, blk, iperm, n, n_rhs, (float *)Yd, ldy, interleaved);
         MPK_CUDA(cudaGetLastError());
     }
     if (host_io) {

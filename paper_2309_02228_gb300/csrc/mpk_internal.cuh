@@ -76,8 +76,9 @@ struct MpkCtrl {
 // Cached blocked schedule for one (segment length) value.
 struct Schedule {
     int32_t p = 0;
+    int64_t slack = 0;
     int64_t n_tasks = 0;
-    DevBuf tasks;   // uint32: chunk | (k << 24), k = 1..p (power within the segment)
+    DevBuf desc;    // int4 per ticket: {chunk | (k << 24), first SELL entry, entries, 0}
 };
 
 // The plan: level structure, permuted matrix in SELL-32 form, blocked-task metadata.
@@ -111,10 +112,18 @@ struct mpk_plan_s {
     DevBuf slice_row, slice_ptr, slice_len, s_col, s_val64, s_val32;
 
     // blocked tasks: chunk c = slices [chunk_slice[c], chunk_slice[c+1]) inside one group
-    DevBuf chunk_slice, chunk_row, dep_lo, dep_hi;
+    DevBuf chunk_slice, chunk_row, chunk_entry, dep_lo, dep_hi;
+    int64_t max_chunk_entries = 0;    // SELL entries of the largest chunk
+    int smem_optin = 0;               // opt-in shared memory per CTA (bytes)
+    int stage_smem = 1;               // stage task matrix blocks in shared memory
+    std::vector<long long> h_chunk_entry;
     std::vector<int32_t> h_chunk_group;   // group of each chunk
     std::vector<int32_t> h_group_chunk;   // first chunk of each group (n_groups+1)
     DevBuf flags;     // uint32 per chunk
+    DevBuf prefix;    // uint64 per power: epoch-tagged count of leading chunks done
+    std::vector<int32_t> h_dep_hi;
+    int sched_type = 1;       // 0 = level-group wavefront, 1 = lag-greedy
+    int64_t sched_slack = 0;  // lag-greedy slack in tasks
     DevBuf ctrl;      // MpkCtrl
     uint64_t launches_since_reset = 0;
     int ctas_per_sm = 0;

@@ -642,6 +642,10 @@ extern "C" mpk_status mpk_plan_opts_default(mpk_plan_opts *o) {
     o->keep_f64 = 0;
     o->ctas_per_sm = 0;
     o->wait_timeout_us = 2000000u;
+    o->schedule = 1;
+    o->slack_tasks = 0;
+    o->block_threads = 256;
+    o->stage = -1;
     return MPK_OK;
 }
 
@@ -920,44 +924,75 @@ static mpk_status plan_create_impl(const mpk_csr *A, int32_t p_max, const mpk_pl
         MPK_TRY(upload(P->group_ptr, gp, s));
     }
 
-    // ---- SELL-32 slices inside groups, chunks of chunk_slices slices
-    std::vector<int32_t> h_slice_row, h_chunk_slice, h_chunk_row;
-    P->h_group_chunk.clear();
-    P->h_chunk_group.clear();
+    // ---- SELL-32 slices inside groups
+    std::vector<int32_t> h_slice_row, h_slice_group;
     for (int32_t g = 0; g < P->n_groups; g++) {
         int32_t r0 = P->h_level_ptr[P->h_group_ptr[g]];
         int32_t r1 = P->h_level_ptr[P->h_group_ptr[g + 1]];
-        P->h_group_chunk.push_back((int32_t)h_chunk_slice.size());
-        int32_t first_slice = (int32_t)h_slice_row.size();
-        for (int32_t r = r0; r < r1; r += 32) h_slice_row.push_back(r);
-        int32_t last_slice = (int32_t)h_slice_row.size();
-        for (int32_t sl = first_slice; sl < last_slice; sl += o.chunk_slices) {
-            h_chunk_slice.push_back(sl);
-            h_chunk_row.push_back(h_slice_row[sl]);
-            P->h_chunk_group.push_back(g);
+        for (int32_t r = r0; r < r1; r += 32) {
+            h_slice_row.push_back(r);
+            h_slice_group.push_back(g);
         }
     }
-    P->h_group_chunk.push_back((int32_t)h_chunk_slice.size());
     P->n_slices = (int32_t)h_slice_row.size();
-    P->n_chunks = (int32_t)h_chunk_slice.size();
     h_slice_row.push_back((int32_t)n);
-    h_chunk_slice.push_back(P->n_slices);
-    h_chunk_row.push_back((int32_t)n);
     MPK_TRY(upload(P->slice_row, h_slice_row, s));
-    MPK_TRY(upload(P->chunk_slice, h_chunk_slice, s));
-    MPK_TRY(upload(P->chunk_row, h_chunk_row, s));
     MPK_TRY(P->slice_len.alloc((P->n_slices + 1) * 4));
     MPK_TRY(P->slice_ptr.alloc((P->n_slices + 1) * 8));
+    std::vector<long long> h_sp(P->n_slices + 1, 0);
     if (P->n_slices > 0) {
         slice_len_kernel<<<grid_for((int64_t)P->n_slices * 32), 256, 0, s>>>(P->rp.as<int32_t>(), P->slice_row.as<int32_t>(), P->n_slices, P->slice_len.as<int32_t>());
         DevBuf st;
         MPK_TRY(st.alloc(scan_tmp_bytes(P->n_slices + 1)));
         MPK_TRY((exclusive_scan<int32_t, long long>(P->slice_len.as<int32_t>(), P->slice_ptr.as<long long>(), P->n_slices, st.p, s)));
-        long long total = 0;
-        MPK_CUDA(cudaMemcpyAsync(&total, P->slice_ptr.as<long long>() + P->n_slices, 8, cudaMemcpyDeviceToHost, s));
+        MPK_CUDA(cudaMemcpyAsync(h_sp.data(), P->slice_ptr.p, (P->n_slices + 1) * 8, cudaMemcpyDeviceToHost, s));
         MPK_CUDA(cudaStreamSynchronize(s));
-        P->sell_nnz = total * 32;
+        P->sell_nnz = h_sp[P->n_slices] * 32;
     }
+    if (P->sell_nnz >= (1ll << 31)) return MPK_ERR_UNIMPLEMENTED;   // 32-bit entry offsets
+    // ---- chunks: up to chunk_slices consecutive slices of one group, and no more SELL entries
+    // than one shared-memory slot holds (two slots of FP64 entries, 12 bytes each, in the
+    // opt-in shared memory)
+    MPK_CUDA(cudaDeviceGetAttribute(&P->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, P->device));
+    const long long slot_entries = ((long long)P->smem_optin - 1024) / (2 * 12) / 32 * 32;
+    P->stage_smem = o.stage != 0;
+    std::vector<int32_t> h_chunk_slice, h_chunk_row;
+    std::vector<long long> h_ce;
+    P->h_group_chunk.assign(P->n_groups + 1, 0);
+    P->h_chunk_group.clear();
+    P->max_chunk_entries = 0;
+    {
+        int32_t sl = 0;
+        for (int32_t g = 0; g < P->n_groups; g++) {
+            P->h_group_chunk[g] = (int32_t)h_chunk_slice.size();
+            while (sl < P->n_slices && h_slice_group[sl] == g) {
+                const int32_t first = sl;
+                long long ents = 32ll * (h_sp[sl + 1] - h_sp[sl]);
+                sl++;
+                while (sl < P->n_slices && h_slice_group[sl] == g && sl - first < o.chunk_slices &&
+                       ents + 32ll * (h_sp[sl + 1] - h_sp[sl]) <= slot_entries) {
+                    ents += 32ll * (h_sp[sl + 1] - h_sp[sl]);
+                    sl++;
+                }
+                if (ents > slot_entries) P->stage_smem = 0;   // one slice exceeds a slot
+                h_chunk_slice.push_back(first);
+                h_chunk_row.push_back(h_slice_row[first]);
+                h_ce.push_back(32ll * h_sp[first]);
+                P->h_chunk_group.push_back(g);
+                P->max_chunk_entries = std::max<int64_t>(P->max_chunk_entries, ents);
+            }
+        }
+        P->h_group_chunk[P->n_groups] = (int32_t)h_chunk_slice.size();
+    }
+    P->n_chunks = (int32_t)h_chunk_slice.size();
+    h_chunk_slice.push_back(P->n_slices);
+    h_chunk_row.push_back((int32_t)n);
+    h_ce.push_back(P->sell_nnz);
+    MPK_TRY(upload(P->chunk_slice, h_chunk_slice, s));
+    MPK_TRY(upload(P->chunk_row, h_chunk_row, s));
+    MPK_TRY(upload(P->chunk_entry, h_ce, s));
+    P->h_chunk_entry = h_ce;
+    MPK_CUDA(cudaStreamSynchronize(s));
     MPK_TRY(P->s_col.alloc(std::max<int64_t>(P->sell_nnz, 1) * 4));
     if (P->has64) MPK_TRY(P->s_val64.alloc(std::max<int64_t>(P->sell_nnz, 1) * 8));
     if (P->has32) MPK_TRY(P->s_val32.alloc(std::max<int64_t>(P->sell_nnz, 1) * 4));
@@ -977,9 +1012,18 @@ static mpk_status plan_create_impl(const mpk_csr *A, int32_t p_max, const mpk_pl
         fill_i32_kernel<<<grid_for(P->n_chunks), 256, 0, s>>>(P->dep_hi.as<int32_t>(), P->n_chunks, -1);
         dep_kernel<<<grid_for(n), 256, 0, s>>>(P->rp.as<int32_t>(), P->ci.as<int32_t>(), row_chunk.as<int32_t>(), n, sym ? 0 : 1, P->dep_lo.as<int32_t>(), P->dep_hi.as<int32_t>());
         MPK_CUDA(cudaGetLastError());
+        P->h_dep_hi.assign(P->n_chunks, 0);
+        MPK_CUDA(cudaMemcpyAsync(P->h_dep_hi.data(), P->dep_hi.p, P->n_chunks * 4, cudaMemcpyDeviceToHost, s));
         MPK_CUDA(cudaStreamSynchronize(s));
     }
-    P->ctas_per_sm = o.ctas_per_sm > 0 ? o.ctas_per_sm : 4;
+    MPK_TRY(P->prefix.alloc((MPK_MAX_P + 2) * sizeof(unsigned long long)));
+    MPK_CUDA(cudaMemsetAsync(P->prefix.p, 0, P->prefix.bytes, s));
+    P->ctas_per_sm = o.ctas_per_sm > 0 ? o.ctas_per_sm : 3;
+    // compute warps + one control warp
+    P->blocked_block = ((o.block_threads == 128 || o.block_threads == 256) ? o.block_threads : 256) + 32;
+    P->sched_type = o.schedule == 0 ? 0 : 1;
+    // lag-greedy slack: about the tasks in flight (two slots per resident CTA)
+    P->sched_slack = o.slack_tasks > 0 ? o.slack_tasks : 2ll * P->n_sm * P->ctas_per_sm;
     MPK_CUDA(cudaStreamSynchronize(s));
     auto t1 = std::chrono::steady_clock::now();
     P->create_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
@@ -1050,7 +1094,7 @@ extern "C" mpk_status mpk_plan_stats(mpk_plan_t P, mpk_plan_info *st) {
     for (const DevBuf *d : {&P->perm, &P->iperm, &P->level, &P->level_ptr, &P->group_ptr, &P->rp,
                             &P->ci, &P->val64, &P->val32, &P->entry_map, &P->slice_row,
                             &P->slice_ptr, &P->slice_len, &P->s_col, &P->s_val64, &P->s_val32,
-                            &P->chunk_slice, &P->chunk_row, &P->dep_lo, &P->dep_hi, &P->flags,
+                            &P->chunk_slice, &P->chunk_row, &P->chunk_entry, &P->dep_lo, &P->dep_hi, &P->flags,
                             &P->ctrl, &P->ws_x, &P->ws_y})
         b += d->bytes;
     st->device_bytes = (int64_t)b;

@@ -1,12 +1,6 @@
 // Entry points of the solver and serving layers that this build does not provide yet.
 #include "mpk_internal.cuh"
 
-extern "C" mpk_status mpk_gmres_opts_default(mpk_gmres_opts *o) { (void)o; return MPK_ERR_UNIMPLEMENTED; }
-extern "C" mpk_status sstep_gmres_solve(mpk_plan_t A, const double *b, double *x, const mpk_gmres_opts *o,
-                                        mpk_gmres_info *info, cudaStream_t s) {
-    (void)A; (void)b; (void)x; (void)o; (void)info; (void)s;
-    return MPK_ERR_UNIMPLEMENTED;
-}
 extern "C" mpk_status mpk_server_opts_default(mpk_server_opts *o) { (void)o; return MPK_ERR_UNIMPLEMENTED; }
 extern "C" mpk_status mpk_server_create(const mpk_server_opts *o, mpk_server_t *out) { (void)o; (void)out; return MPK_ERR_UNIMPLEMENTED; }
 extern "C" mpk_status mpk_server_submit(mpk_server_t srv, int64_t n, int64_t nnz, const int32_t *row_ptr,

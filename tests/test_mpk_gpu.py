@@ -155,8 +155,10 @@ def test_mpk_fp64_vs_oracle(m, basis, name):
     ref = oracle.mpk(A, p, cf, x)
     den = abs_powers(A, cf, x)
     rp, ci, vv = to_dev(A)
-    for budget, cs in ((30_000, 1), (300_000, 2), (1 << 30, 8)):
-        plan = m.mpk_plan_create(rp, ci, vv, p, m.mpk_plan_opts_default(l2_budget_bytes=budget, chunk_slices=cs))
+    for budget, cs, stage, sched in ((30_000, 1, -1, 1), (300_000, 2, 0, 1), (1 << 30, 8, -1, 0),
+                                     (100_000, 4, -1, 0)):
+        plan = m.mpk_plan_create(rp, ci, vv, p, m.mpk_plan_opts_default(
+            l2_budget_bytes=budget, chunk_slices=cs, stage=stage, schedule=sched))
         got_b = _run(m, plan, A, cf, x)
         got_u = _run(m, plan, A, cf, x, flags=m.MPK_UNBLOCKED)
         assert np.array_equal(got_b, got_u)            # blocked == unblocked, bit for bit
