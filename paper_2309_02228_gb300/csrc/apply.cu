@@ -690,7 +690,15 @@ mpk_status launch_tasks(mpk_plan_s *P, const SellView &A, int n_rhs, const VecSe
     B.stage_vals = sv ? 1 : 0;
     const size_t dyn = (size_t)cap * 2 * per_entry;
     auto kern = staged ? mpk_blocked_kernel<T, NR, true> : mpk_blocked_kernel<T, NR, false>;
-    MPK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    // the attribute is per function and shared by every thread: set it to the same maximum
+    // each time (never to this launch's size) so that concurrent launches cannot race
+    {
+        cudaFuncAttributes fa;
+        MPK_CUDA(cudaFuncGetAttributes(&fa, kern));
+        const int maxdyn = P->smem_optin - (int)fa.sharedSizeBytes;
+        if ((int)dyn > maxdyn) return MPK_ERR_UNIMPLEMENTED;
+        MPK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, maxdyn));
+    }
     // epochs advance by one per launch; re-arm the flags long before they could wrap
     if (++P->launches_since_reset >= (1ull << 25)) {
         MPK_CUDA(cudaMemsetAsync(P->flags.p, 0, (P->n_chunks + 1) * 4, s));

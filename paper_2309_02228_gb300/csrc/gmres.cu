@@ -539,7 +539,10 @@ struct Solver {
     // G (K x S) = X^T Y
     template <int SB> mpk_status gram_sb(const T *X, int K, const T *Y, int S, double *Gout) {
         const size_t sm = std::max((size_t)GR * (K + S) * sizeof(T), (size_t)K * S * sizeof(double));
-        if (sm > 48 * 1024) MPK_CUDA(cudaFuncSetAttribute(gram_kernel<T, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        // one fixed maximum for every caller (the attribute is shared by all threads)
+        constexpr int smax = (int)(GR * (MMAX + 1 + 2 * SMAX) * sizeof(T));
+        if (sm > (size_t)smax) return MPK_ERR_ARG;
+        MPK_CUDA(cudaFuncSetAttribute(gram_kernel<T, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
         const int g = (int)std::min<int64_t>(gram_grid, ceil_div(n, GR));
         gram_kernel<T, SB><<<g, 256, sm, st>>>(X, ldv, K, Y, ldv, S, n, part.as<double>());
         reduce_partials_kernel<<<1, 256, 0, st>>>(part.as<double>(), g, K * S, (int64_t)K * S, Gout, 0);

@@ -20,6 +20,7 @@
     do {                                                                                 \
         cudaError_t e_ = (call);                                                         \
         if (e_ != cudaSuccess) {                                                         \
+            cudaGetLastError(); /* clear the thread's non-sticky error state */          \
             mpk_log_cuda_error(e_, #call, __FILE__, __LINE__);                           \
             return e_ == cudaErrorMemoryAllocation ? MPK_ERR_OOM : MPK_ERR_CUDA;         \
         }                                                                                \
