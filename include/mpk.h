@@ -202,6 +202,41 @@ mpk_status mpk_apply(mpk_plan_t plan, const mpk_coeffs *co, mpk_dtype dtype, con
  * MPK_OK or MPK_ERR_TIMEOUT.  Synchronous. */
 mpk_status mpk_plan_sync(mpk_plan_t plan, cudaStream_t stream);
 
+/* Allocation-free final-power MPK.  This entry point is the library's own addition: the
+ * paper has no counterpart.
+ *
+ * For callers that must not allocate device memory once set up: code that runs under a
+ * fixed device-memory budget (a serving loop that sized itself at start), and code on a
+ * latency-critical path, where cudaMalloc may synchronise the device and its time is
+ * unbounded.  mpk_apply allocates its workspace lazily, on the first call that needs it;
+ * this call never does.
+ *
+ * Computes the same result as mpk_apply(plan, co, dtype, X, n, Y, n, 1,
+ * MPK_FINAL_ONLY | MPK_UNBLOCKED | flags, stream), with the same kernels:
+ * Y = y_p, or sum_k gamma_k y_k when co->gamma is set (the recurrence of mpk_apply above),
+ * for ONE right-hand side, by p back-to-back SpMV launches (Alg. 1).
+ *   co     coefficients (host), 1 <= co->p <= 63
+ *   dtype  MPK_F64 or MPK_F32 (the plan must keep that precision)
+ *   X      device vector of n elements (original row order, or level order with
+ *          MPK_PERMUTED_IO); read only
+ *   Y      device vector of n elements, written (same order as X); must not overlap X
+ *   flags  0 or MPK_PERMUTED_IO; anything else is MPK_ERR_ARG
+ * Scratch: a fixed array of MPK_NOALLOC_SCRATCH_BYTES per device, static in the library and
+ * shared by every plan and thread of the process.  A call needs 3 vectors of n elements with
+ * MPK_PERMUTED_IO, else 5, each rounded up to 256 bytes: at 32 MiB, n <= 1,398,080 (FP64,
+ * level order) or 838,848 (FP64, original order); in FP32 n <= 2,796,160 or 1,677,696.  A larger plan returns
+ * MPK_ERR_ARG before any work, with a message on stderr naming the bytes it would need.
+ * Nothing in the scratch needs to start at zero or be cleared between calls.
+ * Races: calls on one device that can overlap in time (other streams, other host threads,
+ * other plans) share the one scratch array and corrupt each other's results.  Keep such
+ * calls ordered: one stream, or events between streams.
+ * Set-up: the first call on each device, with that device current, looks up the array's
+ * address (cudaGetSymbolAddress) and keeps it; make that first call before any stream capture
+ * begins on the device.  Asynchronous on stream. */
+#define MPK_NOALLOC_SCRATCH_BYTES (32u << 20)
+mpk_status mpk_apply_final_noalloc(mpk_plan_t plan, const mpk_coeffs *co, mpk_dtype dtype,
+                                   const void *X, void *Y, uint32_t flags, cudaStream_t stream);
+
 /* Host helpers for coefficient triples (host arrays of length p). */
 /* Chebyshev basis on [alpha, beta]: y_k = T_k((A - c0 I)/d) x, c0 = (alpha+beta)/2,
  * d = (beta-alpha)/2 (three-term recursion; Sec. 5.3 Chebyshev smoother). */

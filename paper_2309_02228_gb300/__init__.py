@@ -36,6 +36,7 @@ MPK_UNBLOCKED = 0x08
 MPK_Y0_IS_X = 0x10
 MPK_RHS_INTERLEAVED = 0x20
 MPK_DEBUG_DROP_FLAG = 0x40000000
+MPK_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
 class MpkError(RuntimeError):
@@ -128,6 +129,7 @@ _SIGS = [
     ("mpk_plan_update_values", ctypes.c_int, [_P, ctypes.POINTER(mpk_csr), _P]),
     ("mpk_apply", ctypes.c_int, [_P, ctypes.POINTER(mpk_coeffs), ctypes.c_int, _P, _I64, _P, _I64, _I32, _U32, _P]),
     ("mpk_plan_sync", ctypes.c_int, [_P, _P]),
+    ("mpk_apply_final_noalloc", ctypes.c_int, [_P, ctypes.POINTER(mpk_coeffs), ctypes.c_int, _P, _P, _U32, _P]),
     ("mpk_coeffs_chebyshev", ctypes.c_int, [_D, _D, _I32, _P, _P, _P]),
     ("mpk_coeffs_newton", ctypes.c_int, [_P, _I32, _P, _P, _P]),
     ("mpk_leja_order", ctypes.c_int, [_P, _I32, _I32, _P]),
@@ -319,6 +321,18 @@ def mpk_apply(plan, coeffs, X, Y, n_rhs=1, flags=0, ldx=None, ldy=None, dtype=No
     st = lib().mpk_apply(plan.handle, ctypes.byref(coeffs.struct), d, _ptr(X), int(ldx), _ptr(Y),
                          int(ldy), int(n_rhs), int(flags), _stream_ptr(stream))
     _check(st, "mpk_apply")
+
+
+def mpk_apply_final_noalloc(plan, coeffs, X, Y, flags=0, dtype=None, stream=None):
+    """Final power (or gamma sum) of one right-hand side without any device allocation; the
+    intermediate vectors live in the library's fixed per-device scratch array.  X, Y: CUDA
+    vectors of n elements.  Calls that may overlap in time on one device must be ordered."""
+    if not isinstance(coeffs, Coeffs):
+        coeffs = Coeffs.from_triples(coeffs)
+    d = _dtype_code(Y.dtype if dtype is None else dtype)
+    st = lib().mpk_apply_final_noalloc(plan.handle, ctypes.byref(coeffs.struct), d, _ptr(X),
+                                       _ptr(Y), int(flags), _stream_ptr(stream))
+    _check(st, "mpk_apply_final_noalloc")
 
 
 # ---------------------------------------------------------------------------------------------

@@ -1109,3 +1109,125 @@ extern "C" const char *mpk_status_str(mpk_status s) {
 }
 
 extern "C" const char *mpk_version(void) { return "mpk_gb300 1 sm_103a"; }
+
+// ==========================================================================================
+// Allocation-free final-power apply.  The library's own addition: the paper has no
+// counterpart.  Same arithmetic as mpk_apply(..., MPK_FINAL_ONLY | MPK_UNBLOCKED) with one
+// right-hand side, but every intermediate vector lives in the fixed array below instead of
+// the plan's lazily allocated workspace, so the call never allocates device memory.
+// ==========================================================================================
+#include <atomic>
+#include <cstdio>
+#include <mutex>
+static_assert(MPK_NOALLOC_SCRATCH_BYTES % 256 == 0, "scratch size must be a multiple of 256");
+
+// One array per device per process, part of the library's device image (loaded with it).
+// Nothing in it needs to start at zero: within a call every element is written before it is
+// read (y_1 reads only x; the gamma sum is initialised at k = 1).
+static __device__ __align__(256) unsigned char mpk_noalloc_scratch[MPK_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kNoAllocMaxDevices = 64;
+std::atomic<void *> g_noalloc_ptr[kNoAllocMaxDevices];
+std::mutex g_noalloc_mu;
+
+// Address of this device's scratch array, looked up once per device (with it current).
+mpk_status noalloc_scratch(void **out) {
+    int dev = 0;
+    MPK_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return MPK_ERR_UNIMPLEMENTED;
+    void *p = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+    if (!p) {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        p = g_noalloc_ptr[dev].load(std::memory_order_relaxed);
+        if (!p) {
+            MPK_CUDA(cudaGetSymbolAddress(&p, mpk_noalloc_scratch));
+            if (!p) return MPK_ERR_CUDA;
+            g_noalloc_ptr[dev].store(p, std::memory_order_release);
+        }
+    }
+    *out = p;
+    return MPK_OK;
+}
+
+inline size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+}  // namespace
+
+extern "C" mpk_status mpk_apply_final_noalloc(mpk_plan_t P, const mpk_coeffs *co,
+                                              mpk_dtype dtype, const void *X, void *Y,
+                                              uint32_t flags, cudaStream_t s) {
+    if (!P || !co || !X || !Y) return MPK_ERR_ARG;
+    const int p = co->p;
+    if (p < 1 || p > MPK_MAX_P || !co->a || !co->b || !co->c) return MPK_ERR_ARG;
+    if (dtype != MPK_F64 && dtype != MPK_F32) return MPK_ERR_ARG;
+    if ((dtype == MPK_F64 && !P->has64) || (dtype == MPK_F32 && !P->has32)) return MPK_ERR_ARG;
+    if (flags & ~(uint32_t)MPK_PERMUTED_IO) return MPK_ERR_ARG;
+    const bool permuted = (flags & MPK_PERMUTED_IO) != 0;
+    const int64_t n = P->n;
+    if (n == 0) return MPK_OK;
+    const size_t es = dtype == MPK_F64 ? 8 : 4;
+    const size_t vb = round256((size_t)n * es);
+    // level-order I/O: the three ring vectors; original order adds staged x and the result
+    const size_t need = (permuted ? 3 : 5) * vb;
+    if (need > (size_t)MPK_NOALLOC_SCRATCH_BYTES) {
+        fprintf(stderr,
+                "[mpk] mpk_apply_final_noalloc: n = %lld needs %zu bytes of scratch, above the "
+                "fixed limit of %zu bytes (MPK_NOALLOC_SCRATCH_BYTES)\n",
+                (long long)n, need, (size_t)MPK_NOALLOC_SCRATCH_BYTES);
+        return MPK_ERR_ARG;
+    }
+    void *base = nullptr;
+    MPK_TRY(noalloc_scratch(&base));
+    char *sc = static_cast<char *>(base);
+
+    Coefs cf;
+    memset(&cf, 0, sizeof(cf));
+    for (int k = 1; k <= p; k++) {
+        cf.a[k] = co->a[k - 1];
+        cf.b[k] = co->b[k - 1];
+        cf.c[k] = co->c[k - 1];
+    }
+    const bool use_gamma = co->gamma != nullptr;
+    if (use_gamma)
+        for (int k = 0; k <= p; k++) cf.g[k] = co->gamma[k];
+
+    VecSet V;
+    memset(&V, 0, sizeof(V));
+    V.final_only = 1;
+    V.use_gamma = use_gamma ? 1 : 0;
+    V.p_total = p;
+    for (int i = 0; i < 3; i++) V.ring[i] = sc + (size_t)i * vb;
+    const unsigned g = grid_n(n);
+    if (permuted) {
+        V.x = X;
+        V.final_out = Y;
+    } else {
+        void *xs = sc + 3 * vb, *ys = sc + 4 * vb;
+        if (dtype == MPK_F64)
+            gather_in_kernel<double><<<g, 256, 0, s>>>((const double *)X, n, false, P->perm.as<int32_t>(), n, 1, (double *)xs);
+        else
+            gather_in_kernel<float><<<g, 256, 0, s>>>((const float *)X, n, false, P->perm.as<int32_t>(), n, 1, (float *)xs);
+        MPK_CUDA(cudaGetLastError());
+        V.x = xs;
+        V.final_out = ys;
+    }
+
+    SellView A;
+    A.slice_ptr = P->slice_ptr.as<long long>();
+    A.slice_row = P->slice_row.as<int32_t>();
+    A.slice_len = P->slice_len.as<int32_t>();
+    A.col = P->s_col.as<int32_t>();
+    A.val = dtype == MPK_F64 ? P->s_val64.p : P->s_val32.p;
+    if (dtype == MPK_F64) MPK_TRY((launch_powers<double, 1>(P, A, 1, V, cf, p, false, 0, s)));
+    else MPK_TRY((launch_powers<float, 1>(P, A, 1, V, cf, p, false, 0, s)));
+
+    if (!permuted) {
+        const dim3 grid2(std::max(1u, g), 1u);
+        if (dtype == MPK_F64)
+            scatter_out_kernel<double><<<grid2, 256, 0, s>>>((const double *)V.final_out, n, P->iperm.as<int32_t>(), n, 1, (double *)Y, n, false);
+        else
+            scatter_out_kernel<float><<<grid2, 256, 0, s>>>((const float *)V.final_out, n, P->iperm.as<int32_t>(), n, 1, (float *)Y, n, false);
+        MPK_CUDA(cudaGetLastError());
+    }
+    return MPK_OK;
+}
