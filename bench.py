@@ -172,6 +172,88 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def solver_leg(m, torch, dev, n_edge=64, solves=5):
+    """s-step GMRES(s=8, restart 48) to rel. residual 1e-8 on the log-normal diffusion matrix
+    (7-point, sigma = 1, rows randomly permuted) at n_edge^3, FP32 basis + FP64 refinement vs an
+    FP64 basis: solves/s and per-solve latency (p50/p99) over `solves` solves each."""
+    A = mi.diffusion7_lognormal(n_edge)
+    b = mi.uniform_vectors(A.n, 4)[0]
+    rp = torch.from_numpy(A.row_ptr).to(dev)
+    ci = torch.from_numpy(A.col).to(dev)
+    vv = torch.from_numpy(A.val).to(dev)
+    plan = m.mpk_plan_create(rp, ci, vv, 8, m.mpk_plan_opts_default(keep_f64=1, keep_f32=1))
+    B = torch.from_numpy(b).to(dev)
+    out = {"workload": "7-point log-normal diffusion %d^3 (sigma 1, rows permuted seed 1), b ~ U[-1,1) "
+                       "seed 4, s=8, restart 48, tol 1e-8" % n_edge, "n": A.n, "nnz": A.nnz}
+    for basis in ("f32", "f64"):
+        lat, iters, rr, ok = [], [], [], True
+        for _ in range(solves + 1):
+            X = torch.zeros_like(B)
+            o = m.mpk_gmres_opts_default(s=8, restart=48, tol=1e-8,
+                                         basis=m.MPK_F32 if basis == "f32" else m.MPK_F64)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = m.sstep_gmres_solve(plan, B, X, o, check=False)
+            torch.cuda.synchronize()
+            lat.append(1e3 * (time.perf_counter() - t0))
+            iters.append(info["iters"])
+            rr.append(info["rel_residual"])
+            ok = ok and info["status_code"] == m.MPK_OK
+        lat = lat[1:]   # the first solve also loads the solver's kernels
+        out[basis] = {"solves_per_s": 1e3 * len(lat) / sum(lat), "p50_ms": float(np.percentile(lat, 50)),
+                      "p99_ms": float(np.percentile(lat, 99)), "iters": iters[-1],
+                      "rel_residual": max(rr[1:]), "converged": ok}
+    return out
+
+
+def serving_leg(m, n_req=32, n_min=32, n_max=64, seed=7):
+    """The solve stream (Poisson arrivals at 200/s, 7- or 27-point anisotropic diffusion,
+    anisotropy log-uniform in [1, 100], grid edge uniform in [n_min, n_max]) through the
+    server, FP32 basis + FP64 refinement to 1e-8, then the same stream with an FP64 basis."""
+    stream = mi.solve_stream(n_req, seed=seed, n_min=n_min, n_max=n_max)
+    mats = []
+    for r in stream:
+        A = mi.anisotropic(r["N"], r["stencil"], r["a"])
+        mats.append((A, mi.uniform_vectors(A.n, r["b_seed"] % 100000)[0]))
+    out = {"workload": "%d requests of the solve stream (seed %d, 200/s Poisson arrivals, grid edge "
+                       "%d..%d, 7/27-point, anisotropy 1..100), tol 1e-8" % (n_req, seed, n_min, n_max)}
+    for basis in ("f32", "f64"):
+        o = m.mpk_server_opts_default(hbm_budget_bytes=120 << 30)
+        o.gmres.basis = m.MPK_F32 if basis == "f32" else m.MPK_F64
+        srv = m.Server(o)
+        # warm-up: one request (kernels loaded before the timed stream)
+        A0, b0 = mats[0]
+        srv.submit(A0.row_ptr, A0.col, A0.val, b0)
+        while srv.pending():
+            srv.poll(64)
+            time.sleep(0.0005)
+        srv.poll(64)
+        t_start = time.perf_counter()
+        sub, done, ids = {}, {}, []
+        i = 0
+        while len(done) < n_req:
+            now = time.perf_counter() - t_start
+            while i < n_req and stream[i]["t_arrival"] <= now:
+                A, b = mats[i]
+                rid, _ = srv.submit(A.row_ptr, A.col, A.val, b)
+                sub[rid] = time.perf_counter()
+                ids.append(rid)
+                i += 1
+            for res in srv.poll(64):
+                if res["id"] in sub:
+                    done[res["id"]] = (time.perf_counter(), res)
+            time.sleep(0.0002)
+        t_end = time.perf_counter()
+        srv.close()
+        lat = [1e3 * (done[r][0] - sub[r]) for r in ids]
+        statuses = [done[r][1]["status"] for r in ids]
+        out[basis] = {"solves_per_s": n_req / (t_end - t_start), "p50_ms": float(np.percentile(lat, 50)),
+                      "p99_ms": float(np.percentile(lat, 99)),
+                      "all_converged": all(st == m.MPK_OK for st in statuses),
+                      "max_rel_residual": max(done[r][1]["rel_residual"] for r in ids)}
+    return out
+
+
 def time_stream(fn, reps, torch):
     """Average ms per call of fn() on the current stream, CUDA events on that stream."""
     st = torch.cuda.current_stream()
@@ -193,6 +275,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    ap.add_argument("--no-solver", action="store_true", help="skip the solver and serving legs")
     ap.add_argument("--profile", action="store_true",
                     help="profiling run: plan + warm-up + 3 blocked launches only")
     args = ap.parse_args()
@@ -221,6 +304,7 @@ def main():
     n, nnz = A.n, A.nnz
     t0 = time.perf_counter()
     plan = m.mpk_plan_create(rp, ci, vv, max(P_SWEEP), m.mpk_plan_opts_default(assume_symmetric=1, p_blk=P_MAIN))
+    # the pattern is symmetric (a 27-point stencil): the plan skips building A^T
     torch.cuda.synchronize()
     plan_ms = 1e3 * (time.perf_counter() - t0)
     pst = m.mpk_plan_stats(plan)
@@ -327,6 +411,12 @@ def main():
     assert m.mpk_plan_sync(plan32) == m.MPK_OK
     del plan32
 
+    # ---- solver and serving legs (solves/s and latency at rel. residual 1e-8)
+    solver = serving = None
+    if not args.no_solver:
+        solver = solver_leg(m, torch, dev)
+        serving = serving_leg(m)
+
     # ---- end to end through the C ABI with pinned host buffers (copies inside the timing)
     Xh = torch.from_numpy(x.copy()).pin_memory()
     Yh = torch.empty((P_MAIN + 1) * n, dtype=torch.float64).pin_memory()
@@ -350,14 +440,14 @@ def main():
         roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
                 "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
-                "kernel": "mpk_blocked_kernel<double,1>",
+                "kernel": "mpk_wave_kernel<double,1>",
                 "hbm_view": {"achieved_gbs": bytes_min / (kb * 1e-3) / 1e9, "peak_gbs": hbm_peak,
                              "frac": bytes_min / (kb * 1e-3) / 1e9 / hbm_peak, "peak_kind": peak_kind}}
     else:
         ach = bytes_min / (kb * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                 "frac": ach / hbm_peak, "traffic": None, "peak_kind": peak_kind,
-                "kernel": "mpk_blocked_kernel<double,1>"}
+                "kernel": "mpk_wave_kernel<double,1>"}
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -379,7 +469,7 @@ def main():
         "pxspmv_gflops": sweep["p%d" % P_MAIN]["pxspmv_gflops"],
         "speedup_vs_pxspmv": sweep["p%d" % P_MAIN]["speedup"],
         "sweep": sweep, "kernel_only": kern, "fp32": fp32, "plan_ms": plan_ms,
-        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "solver": solver, "serving": serving,
         "gpu_launches": launches_per_step * args.steps, "clocks": clk,
     }
     if rank == 0:

@@ -80,18 +80,25 @@ typedef struct {
     int32_t chunk_slices;     /* 32-row slices per blocked task (default 8) */
     int32_t keep_f32;         /* keep an FP32 copy of the values (MPK in FP32) */
     int32_t keep_f64;         /* keep an FP64 copy of the values (MPK / residual in FP64) */
-    int32_t ctas_per_sm;      /* persistent CTAs per SM for the blocked kernel (0 = auto) */
+    int32_t ctas_per_sm;      /* persistent CTAs per SM for the blocked kernel (0 = auto:
+                                 3 CTA-task CTAs, or as many warp-task CTAs as fit) */
     uint32_t wait_timeout_us; /* bound on every device-side dependency wait (default 2e6) */
     int32_t schedule;         /* blocked task order: 0 = level-group wavefront (step t runs
                                  group t-k+1 at power k), 1 = lag-greedy (default: a power
                                  advances once its dependencies were issued slack_tasks
                                  tickets earlier) */
-    int32_t slack_tasks;      /* lag-greedy slack in tasks; 0 = the number of resident CTAs */
+    int32_t slack_tasks;      /* lag-greedy slack in tasks; 0 = the number of resident CTAs
+                                 (CTA tasks) or 128 per SM (warp tasks) */
     int32_t block_threads;    /* compute threads per CTA of the blocked kernel: 128 or 256
                                  (default); one control warp is added */
-    int32_t stage;            /* stage each task's matrix block (columns and values) in
-                                 shared memory with bulk asynchronous copies: -1 auto (on
-                                 unless a 32-row slice exceeds a slot), 0 off */
+    int32_t stage;            /* CTA-task kernel only: stage each task's matrix block
+                                 (columns and values) in shared memory with bulk asynchronous
+                                 copies: -1 auto (on unless a 32-row slice exceeds a slot),
+                                 0 off */
+    int32_t kernel;           /* blocked kernel: 0 = warp tasks (default: every warp takes
+                                 tasks from a ticket dispenser and waits on per-block
+                                 completion counters), 1 = CTA tasks fed by a control warp,
+                                 2 = warp tasks in static round robin */
 } mpk_plan_opts;
 
 typedef struct mpk_plan_s *mpk_plan_t;

@@ -60,7 +60,8 @@ class mpk_plan_opts(ctypes.Structure):
                 ("keep_f32", ctypes.c_int32), ("keep_f64", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("wait_timeout_us", ctypes.c_uint32),
                 ("schedule", ctypes.c_int32), ("slack_tasks", ctypes.c_int32),
-                ("block_threads", ctypes.c_int32), ("stage", ctypes.c_int32)]
+                ("block_threads", ctypes.c_int32), ("stage", ctypes.c_int32),
+                ("kernel", ctypes.c_int32)]
 
 
 class mpk_plan_info(ctypes.Structure):

@@ -629,6 +629,142 @@ __global__ void __launch_bounds__(288, 2) mpk_blocked_kernel(SellView A, int n_r
 }
 
 // ------------------------------------------------------------------------------------------
+// Warp-task kernel.  Every warp of a persistent (cooperative) grid runs tasks (chunk c,
+// power k) of the schedule by static round robin: tickets w, w + W, w + 2W, ... for warp w of
+// W.  A task first waits until the counter blocks up to the one holding max(dep_hi(c), c)
+// have finished power k-1 (the schedule emits each power's chunks in ascending order, so a
+// prefix of blocks is what completes), then computes its slices with the same row function
+// as the unblocked kernel, then publishes: every lane fences its stores, one lane adds 1 to
+// the chunk's block counter.  Each warp keeps, per power, the first block it has not yet seen
+// complete, so a dependency check normally reads one counter per lane at most once.
+// Progress: each warp runs its tickets in ascending order and every task depends only on
+// earlier tickets, so the lowest unfinished ticket can always run.  Waits are bounded; on a
+// timeout the error is latched and every warp stops.
+// ------------------------------------------------------------------------------------------
+struct WaveArgs {
+    const int32_t *chunk_slice;
+    const int32_t *cblk_size;
+    const int4 *desc;                 // {chunk | power << 24, counter block, last block waited for, 0}
+    int64_t n_tasks;
+    uint32_t *cnt;                    // [(k) * n_cblk + b]
+    int32_t n_cblk;
+    int k0;
+    MpkCtrl *ctrl;
+    uint64_t timeout_ns;
+    uint32_t debug_drop;              // 1: task (chunk 0, power 1) does not publish
+    uint32_t dynamic;                 // 1: tickets from the control block's dispenser
+    uint32_t kep[MPK_MAX_P + 1];      // launches so far, this one included, that ran power k
+};
+
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void red_release_add_u32(uint32_t *p, uint32_t v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+static constexpr int WAVE_BLOCK = 256;
+
+template <typename T, int NR>
+__global__ void __launch_bounds__(WAVE_BLOCK, 4) mpk_wave_kernel(SellView A, int n_rhs, VecSet V,
+                                                                  Coefs cf, WaveArgs W) {
+    __shared__ int32_t s_wm[WAVE_BLOCK / 32][MPK_MAX_P + 1];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    for (int i = lane; i <= MPK_MAX_P; i += 32) s_wm[wib][i] = 0;
+    __syncwarp();
+    const int64_t nw = (int64_t)gridDim.x * (WAVE_BLOCK / 32);
+    const T *gval = reinterpret_cast<const T *>(A.val);
+    // tickets: dynamic (one atomic per task, taken one task ahead so that its latency overlaps
+    // the current task) or static round robin
+    auto next_ticket = [&](int64_t prev) -> int64_t {
+        if (!W.dynamic) return prev + nw;
+        uint32_t tk = 0;
+        if (lane == 0) tk = atomicAdd(&W.ctrl->ticket, 1u);
+        return (int64_t)__shfl_sync(0xffffffffu, tk, 0);
+    };
+    int64_t t = W.dynamic ? next_ticket(0) : (int64_t)blockIdx.x * (WAVE_BLOCK / 32) + wib;
+    bool stop = false;
+    while (t < W.n_tasks) {
+        const int4 cur = __ldg(W.desc + t);
+        const int64_t tn = next_ticket(t);
+        const int32_t c = cur.x & 0xffffff;
+        const int kl = (int)((uint32_t)cur.x >> 24);
+        if (kl > 1) {
+            const int32_t hb = cur.z;
+            int32_t wm = s_wm[wib][kl - 1];
+            if (wm <= hb) {
+                const uint32_t mult = W.kep[kl - 1];
+                const uint32_t *cp = W.cnt + (int64_t)(kl - 1) * W.n_cblk;
+                bool timing = false;
+                uint64_t t0 = 0;
+                while (wm <= hb) {
+                    const int32_t b = wm + lane;
+                    bool done = true;
+                    if (b <= hb) {
+                        const uint32_t v = ld_relaxed_u32(cp + b);
+                        done = (int32_t)(v - mult * (uint32_t)__ldg(W.cblk_size + b)) >= 0;
+                    }
+                    const unsigned nd = __ballot_sync(0xffffffffu, !done);
+                    if (nd == 0) {
+                        wm = min(wm + 32, hb + 1);
+                        continue;
+                    }
+                    wm += __ffs(nd) - 1;
+                    uint64_t now = 0;
+                    uint32_t err = 0;
+                    if (lane == 0) {
+                        now = globaltimer_ns();
+                        err = *(volatile uint32_t *)&W.ctrl->error;
+                    }
+                    now = __shfl_sync(0xffffffffu, now, 0);
+                    err = __shfl_sync(0xffffffffu, err, 0);
+                    if (err) { stop = true; break; }
+                    if (!timing) {
+                        timing = true;
+                        t0 = now;
+                    } else if (now - t0 > W.timeout_ns) {
+                        if (lane == 0 && atomicOr(&W.ctrl->error, 1u) == 0u) W.ctrl->err_task = (uint32_t)cur.x;
+                        stop = true;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+                if (stop) break;
+                if (lane == 0) s_wm[wib][kl - 1] = wm;
+                __syncwarp();
+            }
+            fence_acq_rel_gpu();   // acquire: counters observed above before the vectors below
+        }
+        const int k = W.k0 + kl;
+        const int32_t s0 = __ldg(W.chunk_slice + c), s1 = __ldg(W.chunk_slice + c + 1);
+        for (int32_t s = s0; s < s1; s++) {
+            const long long gofs = 32ll * __ldg(A.slice_ptr + s);
+            slice_power<T, NR, false, false>(A, s, A.col + gofs, gval + gofs, lane, n_rhs, V, k, cf);
+        }
+        // publish: the warp barrier orders every lane's results before lane 0's release add
+        __syncwarp();
+        if (lane == 0 && !(W.debug_drop && c == 0 && kl == 1))
+            red_release_add_u32(W.cnt + (int64_t)kl * W.n_cblk + cur.y, 1u);
+        t = tn;
+    }
+    // every CTA gets here (waits that fail leave the task loop, they do not return); the last
+    // one resets the ticket dispenser for the next launch
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const uint32_t d = atomicAdd(&W.ctrl->done_ctas, 1u);
+        if (d == gridDim.x - 1) {
+            W.ctrl->ticket = 0;
+            W.ctrl->done_ctas = 0;
+            __threadfence();
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
 // Staging: user layout (original or level order, column-major or interleaved) <-> the
 // kernel's interleaved level-order layout.
 // ------------------------------------------------------------------------------------------
@@ -722,6 +858,47 @@ mpk_status launch_tasks(mpk_plan_s *P, const SellView &A, int n_rhs, const VecSe
 }
 
 template <typename T, int NR>
+mpk_status launch_wave(mpk_plan_s *P, const SellView &A, int n_rhs, const VecSet &V,
+                       const Coefs &cf, Schedule *sch, int k0, int seg, uint32_t flags, cudaStream_t s) {
+    WaveArgs W;
+    memset(&W, 0, sizeof(W));
+    W.chunk_slice = P->chunk_slice.as<int32_t>();
+    W.cblk_size = P->cblk_size.as<int32_t>();
+    W.desc = sch->desc.as<int4>();
+    W.n_tasks = sch->n_tasks;
+    W.cnt = P->wave_cnt.as<uint32_t>();
+    W.n_cblk = P->n_cblk;
+    W.k0 = k0;
+    W.ctrl = P->ctrl.as<MpkCtrl>();
+    W.timeout_ns = (uint64_t)P->opts.wait_timeout_us * 1000ull;
+    W.debug_drop = (flags & MPK_DEBUG_DROP_FLAG) && k0 == 0 ? 1u : 0u;
+    W.dynamic = P->wave_dynamic ? 1u : 0u;
+    auto kern = mpk_wave_kernel<T, NR>;
+    int occ = 0;
+    MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, WAVE_BLOCK, 0));
+    if (occ < 1) return MPK_ERR_UNIMPLEMENTED;
+    const int per_sm = P->opts.ctas_per_sm > 0 ? std::min(occ, P->opts.ctas_per_sm) : occ;
+    const int64_t warps = std::max<int64_t>(sch->n_tasks, 1);
+    const int64_t grid = std::min<int64_t>((int64_t)P->n_sm * per_sm, ceil_div(warps, WAVE_BLOCK / 32));
+    // this launch runs local powers 1..seg once more
+    for (int k = 1; k <= seg; k++) P->kep[k] += 1u;
+    memcpy(W.kep, P->kep, sizeof(W.kep));
+    SellView a_ = A;
+    VecSet v_ = V;
+    Coefs c_ = cf;
+    int nr_ = n_rhs;
+    void *kargs[] = {&a_, &nr_, &v_, &c_, &W};
+    cudaError_t e = cudaLaunchCooperativeKernel((void *)kern, dim3((unsigned)grid), dim3(WAVE_BLOCK), kargs, 0, s);
+    if (e != cudaSuccess) {
+        for (int k = 1; k <= seg; k++) P->kep[k] -= 1u;
+        cudaGetLastError();
+        mpk_log_cuda_error(e, "cudaLaunchCooperativeKernel(mpk_wave_kernel)", __FILE__, __LINE__);
+        return MPK_ERR_CUDA;
+    }
+    return MPK_OK;
+}
+
+template <typename T, int NR>
 mpk_status launch_powers(mpk_plan_s *P, const SellView &A, int n_rhs, const VecSet &V,
                          const Coefs &cf, int p, bool blocked, uint32_t flags, cudaStream_t s) {
     if (!blocked) {
@@ -737,7 +914,8 @@ mpk_status launch_powers(mpk_plan_s *P, const SellView &A, int n_rhs, const VecS
         const int seg = std::min(P->p_blk, p - k0);
         Schedule *sch = nullptr;
         MPK_TRY(mpk_get_schedule(P, seg, &sch, s));
-        MPK_TRY((launch_tasks<T, NR>(P, A, n_rhs, V, cf, sch, k0, flags, s)));
+        if (P->wave) MPK_TRY((launch_wave<T, NR>(P, A, n_rhs, V, cf, sch, k0, seg, flags, s)));
+        else MPK_TRY((launch_tasks<T, NR>(P, A, n_rhs, V, cf, sch, k0, flags, s)));
         k0 += seg;
     }
     return MPK_OK;
@@ -815,9 +993,10 @@ mpk_status mpk_launch_residual(mpk_plan_s *P, const double *x, const double *b, 
 // trailing power - the L2 working set - as short as the dependencies allow.
 // ============================================================================================
 mpk_status mpk_get_schedule(mpk_plan_s *P, int p, Schedule **out, cudaStream_t s) {
-    const int key = p * 1024 + P->sched_type * 512 + 0;
+    const int key = p * 1024 + P->sched_type * 512 + (P->wave ? 256 : 0);
+    const int64_t slack_now = P->wave ? P->wave_slack : P->sched_slack;
     auto it = P->schedules.find(key);
-    if (it != P->schedules.end() && it->second->slack == P->sched_slack) {
+    if (it != P->schedules.end() && it->second->slack == slack_now) {
         *out = it->second.get();
         return MPK_OK;
     }
@@ -834,10 +1013,11 @@ mpk_status mpk_get_schedule(mpk_plan_s *P, int p, Schedule **out, cudaStream_t s
                     h.push_back((uint32_t)c | ((uint32_t)k << 24));
             }
     } else {
-        const std::vector<int32_t> &dh = P->h_dep_hi;
+        // the warp-task kernel waits for whole counter blocks: schedule against that bound
+        const std::vector<int32_t> &dh = P->wave ? P->h_dep_hi_blk : P->h_dep_hi;
         std::vector<int32_t> nxt(p + 1, 0);
         std::vector<int64_t> when((size_t)(p + 1) * std::max(NC, 1), 0);
-        const int64_t slack = P->sched_slack;
+        const int64_t slack = slack_now;
         const int64_t total = (int64_t)p * NC;
         for (int64_t t = 0; t < total; t++) {
             int pick = 0;
@@ -861,14 +1041,19 @@ mpk_status mpk_get_schedule(mpk_plan_s *P, int p, Schedule **out, cudaStream_t s
     }
     std::unique_ptr<Schedule> sch(new Schedule());
     sch->p = p;
-    sch->slack = P->sched_slack;
+    sch->slack = slack_now;
     sch->n_tasks = (int64_t)h.size();
-    // descriptors: the control warp needs the chunk's SELL range right after the ticket
+    // descriptors: the control warp needs the chunk's SELL range right after the ticket; a
+    // warp task needs its counter block and the last block it waits for
     std::vector<int4> hd(h.size());
     for (size_t i = 0; i < h.size(); i++) {
         const int32_t c = (int32_t)(h[i] & 0xffffffu);
-        const long long e0 = P->h_chunk_entry[c], e1 = P->h_chunk_entry[c + 1];
-        hd[i] = make_int4((int)h[i], (int)e0, (int)(e1 - e0), 0);
+        if (P->wave) {
+            hd[i] = make_int4((int)h[i], P->h_chunk_blk[c], P->h_wait_blk[c], 0);
+        } else {
+            const long long e0 = P->h_chunk_entry[c], e1 = P->h_chunk_entry[c + 1];
+            hd[i] = make_int4((int)h[i], (int)e0, (int)(e1 - e0), 0);
+        }
     }
     MPK_TRY(sch->desc.alloc(std::max<size_t>(hd.size(), 1) * sizeof(int4)));
     if (!hd.empty())
@@ -1025,9 +1210,12 @@ extern "C" mpk_status mpk_plan_sync(mpk_plan_t P, cudaStream_t s) {
     MPK_CUDA(cudaMemcpy(&h, P->ctrl.p, sizeof(h), cudaMemcpyDeviceToHost));
     if (h.error) {
         // clear the latched error; the flags of the aborted launch sit below every later
-        // launch's targets because each launch uses a new epoch
+        // launch's targets because each launch uses a new epoch.  The warp-task counters of an
+        // aborted launch are incomplete: start them over.
         uint32_t zero[2] = {0, 0};
         MPK_CUDA(cudaMemcpy(&P->ctrl.as<MpkCtrl>()->error, zero, 8, cudaMemcpyHostToDevice));
+        if (P->wave_cnt.p) MPK_CUDA(cudaMemset(P->wave_cnt.p, 0, P->wave_cnt.bytes));
+        memset(P->kep, 0, sizeof(P->kep));
         return MPK_ERR_TIMEOUT;
     }
     return MPK_OK;

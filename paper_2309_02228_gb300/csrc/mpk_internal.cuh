@@ -125,6 +125,19 @@ struct mpk_plan_s {
     std::vector<int32_t> h_dep_hi;
     int sched_type = 1;       // 0 = level-group wavefront, 1 = lag-greedy
     int64_t sched_slack = 0;  // lag-greedy slack in tasks
+    // warp-task kernel (wave): chunks are counted in blocks of up to 32 consecutive chunks of
+    // one group; a task waits until every block up to the one holding max(dep_hi(c), c) has
+    // finished the previous power.  Counters accumulate over launches: after the j-th launch
+    // that ran local power k, block b's counter reads j * cblk_size[b] (mod 2^32).
+    int wave = 1;                     // 1: warp-task kernel, 0: CTA-task kernel
+    int wave_dynamic = 1;             // warp tasks: 1 dynamic tickets, 0 static round robin
+    int32_t n_cblk = 0;
+    std::vector<int32_t> h_chunk_blk; // counter block of each chunk
+    std::vector<int32_t> h_wait_blk;  // last block a chunk's task waits for
+    std::vector<int32_t> h_dep_hi_blk;// dep_hi rounded up to the end of its block
+    DevBuf cblk_size, wave_cnt;       // chunks per block; counters [(k) * n_cblk + b]
+    uint32_t kep[MPK_MAX_P + 1] = {};
+    int64_t wave_slack = 0;
     DevBuf ctrl;      // MpkCtrl
     uint64_t launches_since_reset = 0;
     int ctas_per_sm = 0;

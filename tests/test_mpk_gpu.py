@@ -155,10 +155,15 @@ def test_mpk_fp64_vs_oracle(m, basis, name):
     ref = oracle.mpk(A, p, cf, x)
     den = abs_powers(A, cf, x)
     rp, ci, vv = to_dev(A)
-    for budget, cs, stage, sched in ((30_000, 1, -1, 1), (300_000, 2, 0, 1), (1 << 30, 8, -1, 0),
-                                     (100_000, 4, -1, 0)):
+    # kernel 0 = warp tasks with a ticket dispenser, 1 = CTA tasks, 2 = warp tasks in static
+    # round robin; slack 7 makes most warp tasks wait for their dependencies
+    for budget, cs, stage, sched, kern, slack in ((30_000, 1, -1, 1, 0, 0), (300_000, 2, 0, 1, 1, 0),
+                                                  (1 << 30, 8, -1, 0, 0, 0), (100_000, 4, -1, 0, 2, 0),
+                                                  (60_000, 1, -1, 1, 0, 7), (60_000, 2, -1, 1, 2, 7),
+                                                  (30_000, 1, -1, 1, 1, 0)):
         plan = m.mpk_plan_create(rp, ci, vv, p, m.mpk_plan_opts_default(
-            l2_budget_bytes=budget, chunk_slices=cs, stage=stage, schedule=sched))
+            l2_budget_bytes=budget, chunk_slices=cs, stage=stage, schedule=sched, kernel=kern,
+            slack_tasks=slack))
         got_b = _run(m, plan, A, cf, x)
         got_u = _run(m, plan, A, cf, x, flags=m.MPK_UNBLOCKED)
         assert np.array_equal(got_b, got_u)            # blocked == unblocked, bit for bit
@@ -233,7 +238,8 @@ def test_block_mpk_n_rhs(m, n_rhs, interleaved):
             assert max_rel_err(got[k, :, q], ref[k], den[k]) <= 64 * k * U32
 
 
-def test_final_only_gamma_and_segments(m):
+@pytest.mark.parametrize("kern", [0, 1, 2])
+def test_final_only_gamma_and_segments(m, kern):
     import torch
     A = MATS["diff7_10"]
     p = 9
@@ -244,7 +250,8 @@ def test_final_only_gamma_and_segments(m):
     den = abs_powers(A, cf, x)
     rp, ci, vv = to_dev(A)
     # p_blk = 4 -> segments of 4, 4, 1 powers (the remainder launch)
-    plan = m.mpk_plan_create(rp, ci, vv, p, m.mpk_plan_opts_default(l2_budget_bytes=60_000, p_blk=4))
+    plan = m.mpk_plan_create(rp, ci, vv, p, m.mpk_plan_opts_default(l2_budget_bytes=60_000, p_blk=4,
+                                                                     kernel=kern, slack_tasks=5))
     full = _run(m, plan, A, cf, x)
     for k in range(1, p + 1):
         assert max_rel_err(full[k], ref[k], den[k]) <= 64 * k * U64
@@ -277,15 +284,17 @@ def test_host_io(m):
     assert np.array_equal(Yh.numpy().reshape(p + 1, -1), dev)
 
 
-def test_timeout_is_reported_and_plan_recovers(m):
-    """A flag that nothing publishes: the waits on it run out (short bound), the call reports
-    MPK_ERR_TIMEOUT, and the plan works again afterwards."""
+@pytest.mark.parametrize("kern", [0, 1, 2])
+def test_timeout_is_reported_and_plan_recovers(m, kern):
+    """A completion that nothing publishes: the waits on it run out (short bound), the call
+    reports MPK_ERR_TIMEOUT, and the plan works again afterwards."""
     A = MATS["s27_12"]
     p = 3
     cf = BASES["monomial"](p)
     x = mi.uniform_vectors(A.n, 0)[0]
     rp, ci, vv = to_dev(A)
-    plan = m.mpk_plan_create(rp, ci, vv, p, m.mpk_plan_opts_default(l2_budget_bytes=30_000, wait_timeout_us=20_000))
+    plan = m.mpk_plan_create(rp, ci, vv, p, m.mpk_plan_opts_default(l2_budget_bytes=30_000, wait_timeout_us=20_000,
+                                                                     kernel=kern))
     import torch
     X = torch.from_numpy(x).cuda()
     Y = torch.empty((p + 1) * A.n, dtype=torch.float64, device="cuda")
