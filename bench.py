@@ -254,6 +254,40 @@ def serving_leg(m, n_req=32, n_min=32, n_max=64, seed=7):
     return out
 
 
+def run_profile(args, m, torch, local):
+    """Small profiling case (no timing printed): 27-point matrix on a --profile-n grid, default
+    plan, --profile-reps repetitions of one blocked and one unblocked call with y_0 already in
+    level order.  The blocked kernel's launches are the (2r)-th kernel launches of this family."""
+    dev = torch.device("cuda", local)
+    A = mi.stencil27(args.profile_n, seed=2)
+    x = mi.uniform_vectors(A.n, 0)[0]
+    p = args.profile_p
+    theta = mi.leja_points_interval(0.0, 52.0, p)
+    dt = torch.float64 if args.profile_dtype == "f64" else torch.float32
+    rp = torch.from_numpy(A.row_ptr).to(dev)
+    ci = torch.from_numpy(A.col).to(dev)
+    vv = torch.from_numpy(A.val).to(dev).to(dt)
+    opts = m.mpk_plan_opts_default(assume_symmetric=1, p_blk=p)
+    if args.profile_cs > 0:
+        opts.chunk_slices = args.profile_cs
+    if args.profile_slack > 0:
+        opts.slack_tasks = args.profile_slack
+    plan = m.mpk_plan_create(rp, ci, vv, p, opts)
+    perm = m.mpk_plan_perm(plan)["perm"].long()
+    Y = torch.empty((p + 1) * A.n, dtype=dt, device=dev)
+    Y[:A.n] = torch.from_numpy(x).to(dev).to(dt)[perm]
+    co = m.mpk_coeffs_newton(theta)
+    fl = m.MPK_PERMUTED_IO | m.MPK_Y0_IS_X
+    for _ in range(args.profile_reps):
+        m.mpk_apply(plan, co, None, Y, flags=fl)
+        m.mpk_apply(plan, co, None, Y, flags=fl | m.MPK_UNBLOCKED)
+    torch.cuda.synchronize()
+    status = m.mpk_plan_sync(plan)
+    print(json.dumps({"profile": "done", "status": status, "n": A.n, "nnz": A.nnz, "p": p,
+                      "dtype": args.profile_dtype, "plan": m.mpk_plan_stats(plan)}))
+    return 0 if status == m.MPK_OK else 1
+
+
 def time_stream(fn, reps, torch):
     """Average ms per call of fn() on the current stream, CUDA events on that stream."""
     st = torch.cuda.current_stream()
@@ -277,7 +311,14 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--no-solver", action="store_true", help="skip the solver and serving legs")
     ap.add_argument("--profile", action="store_true",
-                    help="profiling run: plan + warm-up + 3 blocked launches only")
+                    help="profiling run: plan, then per repetition one blocked and one unblocked "
+                         "call (level-order I/O) on the 27-point matrix of --profile-n")
+    ap.add_argument("--profile-n", type=int, default=N_GRID, help="grid edge of the profiling case")
+    ap.add_argument("--profile-dtype", default="f64", choices=["f32", "f64"])
+    ap.add_argument("--profile-p", type=int, default=P_MAIN)
+    ap.add_argument("--profile-reps", type=int, default=3)
+    ap.add_argument("--profile-cs", type=int, default=0, help="chunk_slices (0: plan default)")
+    ap.add_argument("--profile-slack", type=int, default=0, help="slack_tasks (0: plan default)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -296,6 +337,8 @@ def main():
     B.build()
     import paper_2309_02228_gb300 as m
 
+    if args.profile:
+        return run_profile(args, m, torch, local)
     A, x, theta = gen_workload()
     dev = torch.device("cuda", local)
     rp = torch.from_numpy(A.row_ptr).to(dev)
@@ -314,19 +357,6 @@ def main():
 
     def step(p=P_MAIN, flags=0):
         m.mpk_apply(plan, cfs[p], X, Y, flags=flags)
-
-    if args.profile:
-        perm = m.mpk_plan_perm(plan)["perm"]
-        Yp = torch.empty((P_MAIN + 1) * n, dtype=torch.float64, device=dev)
-        Yp[:n] = X[perm.long()]
-        for _ in range(args.warmup + 3):
-            m.mpk_apply(plan, cfs[P_MAIN], None, Yp, flags=m.MPK_PERMUTED_IO | m.MPK_Y0_IS_X)
-        for _ in range(3):
-            m.mpk_apply(plan, cfs[P_MAIN], None, Yp, flags=m.MPK_PERMUTED_IO | m.MPK_Y0_IS_X | m.MPK_UNBLOCKED)
-        torch.cuda.synchronize()
-        assert m.mpk_plan_sync(plan) == m.MPK_OK
-        print(json.dumps({"profile": "done", "plan": pst}))
-        return
 
     hbm_peak, peak_kind = measured_peaks()
     clocks = ClockSampler(local)
@@ -479,4 +509,4 @@ def main():
 
 
 if __name__ == "__main__":
-    main()
+    sys.exit(main() or 0)

@@ -667,33 +667,40 @@ __device__ __forceinline__ void red_release_add_u32(uint32_t *p, uint32_t v) {
 }
 
 static constexpr int WAVE_BLOCK = 256;
+// resident CTAs per SM the warp-task kernel is compiled for: the row function of one or two
+// FP32 right-hand sides fits 40 registers (48 warps per SM), FP64 fits 48; wider blocks of
+// right-hand sides keep 64
+template <typename T, int NR> constexpr int wave_min_blocks() {
+    return sizeof(T) == 4 ? (NR <= 2 ? 6 : 4) : (NR == 1 ? 5 : 4);
+}
 
 template <typename T, int NR>
-__global__ void __launch_bounds__(WAVE_BLOCK, 4) mpk_wave_kernel(SellView A, int n_rhs, VecSet V,
-                                                                  Coefs cf, WaveArgs W) {
+__global__ void __launch_bounds__(WAVE_BLOCK, (wave_min_blocks<T, NR>())) mpk_wave_kernel(SellView A, int n_rhs, VecSet V,
+                                                                                Coefs cf, WaveArgs W) {
     __shared__ int32_t s_wm[WAVE_BLOCK / 32][MPK_MAX_P + 1];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     for (int i = lane; i <= MPK_MAX_P; i += 32) s_wm[wib][i] = 0;
     __syncwarp();
-    const int64_t nw = (int64_t)gridDim.x * (WAVE_BLOCK / 32);
+    const int32_t nw = (int32_t)gridDim.x * (WAVE_BLOCK / 32);
+    const int32_t n_tasks = (int32_t)W.n_tasks;
     const T *gval = reinterpret_cast<const T *>(A.val);
-    // tickets: dynamic (one atomic per task, taken one task ahead so that its latency overlaps
-    // the current task) or static round robin
-    auto next_ticket = [&](int64_t prev) -> int64_t {
+    // tickets: dynamic (one atomic per task, taken when the previous task has published, so
+    // that at most one ticket per warp is outstanding and a dependency issued more than about
+    // one ticket per warp earlier is normally complete) or static round robin
+    auto next_ticket = [&](int32_t prev) -> int32_t {
         if (!W.dynamic) return prev + nw;
         uint32_t tk = 0;
         if (lane == 0) tk = atomicAdd(&W.ctrl->ticket, 1u);
-        return (int64_t)__shfl_sync(0xffffffffu, tk, 0);
+        return (int32_t)__shfl_sync(0xffffffffu, tk, 0);
     };
-    int64_t t = W.dynamic ? next_ticket(0) : (int64_t)blockIdx.x * (WAVE_BLOCK / 32) + wib;
+    int32_t t = W.dynamic ? next_ticket(0) : (int32_t)blockIdx.x * (WAVE_BLOCK / 32) + wib;
     bool stop = false;
-    while (t < W.n_tasks) {
-        const int4 cur = __ldg(W.desc + t);
-        const int64_t tn = next_ticket(t);
-        const int32_t c = cur.x & 0xffffff;
-        const int kl = (int)((uint32_t)cur.x >> 24);
+    while (t >= 0 && t < n_tasks) {
+        const int code = __ldg(&W.desc[t].x);
+        const int32_t c = code & 0xffffff;
+        const int kl = (int)((uint32_t)code >> 24);
         if (kl > 1) {
-            const int32_t hb = cur.z;
+            const int32_t hb = __ldg(&W.desc[t].z);
             int32_t wm = s_wm[wib][kl - 1];
             if (wm <= hb) {
                 const uint32_t mult = W.kep[kl - 1];
@@ -726,7 +733,7 @@ __global__ void __launch_bounds__(WAVE_BLOCK, 4) mpk_wave_kernel(SellView A, int
                         timing = true;
                         t0 = now;
                     } else if (now - t0 > W.timeout_ns) {
-                        if (lane == 0 && atomicOr(&W.ctrl->error, 1u) == 0u) W.ctrl->err_task = (uint32_t)cur.x;
+                        if (lane == 0 && atomicOr(&W.ctrl->error, 1u) == 0u) W.ctrl->err_task = (uint32_t)code;
                         stop = true;
                         break;
                     }
@@ -739,16 +746,16 @@ __global__ void __launch_bounds__(WAVE_BLOCK, 4) mpk_wave_kernel(SellView A, int
             fence_acq_rel_gpu();   // acquire: counters observed above before the vectors below
         }
         const int k = W.k0 + kl;
-        const int32_t s0 = __ldg(W.chunk_slice + c), s1 = __ldg(W.chunk_slice + c + 1);
-        for (int32_t s = s0; s < s1; s++) {
+        const int32_t s1 = __ldg(W.chunk_slice + c + 1);
+        for (int32_t s = __ldg(W.chunk_slice + c); s < s1; s++) {
             const long long gofs = 32ll * __ldg(A.slice_ptr + s);
             slice_power<T, NR, false, false>(A, s, A.col + gofs, gval + gofs, lane, n_rhs, V, k, cf);
         }
         // publish: the warp barrier orders every lane's results before lane 0's release add
         __syncwarp();
         if (lane == 0 && !(W.debug_drop && c == 0 && kl == 1))
-            red_release_add_u32(W.cnt + (int64_t)kl * W.n_cblk + cur.y, 1u);
-        t = tn;
+            red_release_add_u32(W.cnt + (int64_t)kl * W.n_cblk + __ldg(&W.desc[t].y), 1u);
+        t = next_ticket(t);
     }
     // every CTA gets here (waits that fail leave the task loop, they do not return); the last
     // one resets the ticket dispenser for the next launch
@@ -866,6 +873,7 @@ mpk_status launch_wave(mpk_plan_s *P, const SellView &A, int n_rhs, const VecSet
     W.cblk_size = P->cblk_size.as<int32_t>();
     W.desc = sch->desc.as<int4>();
     W.n_tasks = sch->n_tasks;
+    if (sch->n_tasks >= (1ll << 30)) return MPK_ERR_UNIMPLEMENTED;   // 32-bit tickets
     W.cnt = P->wave_cnt.as<uint32_t>();
     W.n_cblk = P->n_cblk;
     W.k0 = k0;
