@@ -172,7 +172,7 @@ def run_reference(args):
     print(json.dumps(out))
 
 
-def solver_leg(m, torch, dev, n_edge=64, solves=5):
+def solver_leg(m, torch, dev, n_edge=64, solves=5, bases=("f32", "f64")):
     """s-step GMRES(s=8, restart 48) to rel. residual 1e-8 on the log-normal diffusion matrix
     (7-point, sigma = 1, rows randomly permuted) at n_edge^3, FP32 basis + FP64 refinement vs an
     FP64 basis: solves/s and per-solve latency (p50/p99) over `solves` solves each."""
@@ -185,7 +185,7 @@ def solver_leg(m, torch, dev, n_edge=64, solves=5):
     B = torch.from_numpy(b).to(dev)
     out = {"workload": "7-point log-normal diffusion %d^3 (sigma 1, rows permuted seed 1), b ~ U[-1,1) "
                        "seed 4, s=8, restart 48, tol 1e-8" % n_edge, "n": A.n, "nnz": A.nnz}
-    for basis in ("f32", "f64"):
+    for basis in bases:
         lat, iters, rr, ok = [], [], [], True
         for _ in range(solves + 1):
             X = torch.zeros_like(B)
@@ -267,7 +267,7 @@ def run_profile(args, m, torch, local):
     rp = torch.from_numpy(A.row_ptr).to(dev)
     ci = torch.from_numpy(A.col).to(dev)
     vv = torch.from_numpy(A.val).to(dev).to(dt)
-    opts = m.mpk_plan_opts_default(assume_symmetric=1, p_blk=p)
+    opts = m.mpk_plan_opts_default(assume_symmetric=1, p_blk=p, blocked=1)
     if args.profile_cs > 0:
         opts.chunk_slices = args.profile_cs
     if args.profile_slack > 0:
@@ -317,6 +317,9 @@ def main():
     ap.add_argument("--profile-dtype", default="f64", choices=["f32", "f64"])
     ap.add_argument("--profile-p", type=int, default=P_MAIN)
     ap.add_argument("--profile-reps", type=int, default=3)
+    ap.add_argument("--profile-solver", action="store_true",
+                    help="profiling run of the solver: two s-step GMRES solves (FP32 basis) on the "
+                         "log-normal diffusion matrix at --profile-n")
     ap.add_argument("--profile-cs", type=int, default=0, help="chunk_slices (0: plan default)")
     ap.add_argument("--profile-slack", type=int, default=0, help="slack_tasks (0: plan default)")
     args = ap.parse_args()
@@ -337,6 +340,11 @@ def main():
     B.build()
     import paper_2309_02228_gb300 as m
 
+    if args.profile_solver:
+        out = solver_leg(m, torch, torch.device("cuda", local), n_edge=args.profile_n, solves=1,
+                         bases=("f32",))
+        print(json.dumps({"profile": "solver", "result": out}))
+        return 0 if out["f32"]["converged"] else 1
     if args.profile:
         return run_profile(args, m, torch, local)
     A, x, theta = gen_workload()
@@ -346,7 +354,8 @@ def main():
     vv = torch.from_numpy(A.val).to(dev)
     n, nnz = A.n, A.nnz
     t0 = time.perf_counter()
-    plan = m.mpk_plan_create(rp, ci, vv, max(P_SWEEP), m.mpk_plan_opts_default(assume_symmetric=1, p_blk=P_MAIN))
+    plan = m.mpk_plan_create(rp, ci, vv, max(P_SWEEP), m.mpk_plan_opts_default(assume_symmetric=1, p_blk=P_MAIN,
+                                                                               blocked=1))
     # the pattern is symmetric (a 27-point stencil): the plan skips building A^T
     torch.cuda.synchronize()
     plan_ms = 1e3 * (time.perf_counter() - t0)
@@ -423,7 +432,8 @@ def main():
     # ---- FP32 copy of the same matrix (the bandwidth-bound precision)
     fp32 = {}
     vv32 = vv.float()
-    plan32 = m.mpk_plan_create(rp, ci, vv32, max(P_SWEEP), m.mpk_plan_opts_default(assume_symmetric=1, p_blk=P_MAIN))
+    plan32 = m.mpk_plan_create(rp, ci, vv32, max(P_SWEEP), m.mpk_plan_opts_default(assume_symmetric=1, p_blk=P_MAIN,
+                                                                                   blocked=1))
     X32 = X.float()
     Y32 = torch.empty((max(P_SWEEP) + 1) * n, dtype=torch.float32, device=dev)
     perm32 = m.mpk_plan_perm(plan32)["perm"].long()

@@ -99,6 +99,12 @@ typedef struct {
                                  tasks from a ticket dispenser and waits on per-block
                                  completion counters), 1 = CTA tasks fed by a control warp,
                                  2 = warp tasks in static round robin */
+    int32_t blocked;          /* mpk_apply without MPK_UNBLOCKED: 1 = always the blocked
+                                 kernel, 0 = never, -1 = automatic (default): p >= 2 and a
+                                 matrix larger than the L2 cache, and then whichever kernel
+                                 the first call for each (precision, p, n_rhs) measures as
+                                 faster - that call runs and times both, which synchronises
+                                 its stream once; results are identical either way */
 } mpk_plan_opts;
 
 typedef struct mpk_plan_s *mpk_plan_t;

@@ -61,7 +61,7 @@ class mpk_plan_opts(ctypes.Structure):
                 ("ctas_per_sm", ctypes.c_int32), ("wait_timeout_us", ctypes.c_uint32),
                 ("schedule", ctypes.c_int32), ("slack_tasks", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("stage", ctypes.c_int32),
-                ("kernel", ctypes.c_int32)]
+                ("kernel", ctypes.c_int32), ("blocked", ctypes.c_int32)]
 
 
 class mpk_plan_info(ctypes.Structure):

@@ -1087,7 +1087,7 @@ mpk_status mpk_apply_internal(mpk_plan_s *P, const mpk_coeffs *co, mpk_dtype dty
     const bool final_only = (flags & MPK_FINAL_ONLY) != 0;
     const bool host_io = (flags & MPK_HOST_IO) != 0;
     const bool y0x = (flags & MPK_Y0_IS_X) != 0;
-    const bool blocked = (flags & MPK_UNBLOCKED) == 0;
+    bool blocked = (flags & MPK_UNBLOCKED) == 0 && P->opts.blocked != 0;
     if (y0x && (!permuted || final_only || host_io)) return MPK_ERR_ARG;
     if (!y0x && !X) return MPK_ERR_ARG;
     const int64_t n = P->n;
@@ -1185,8 +1185,53 @@ mpk_status mpk_apply_internal(mpk_plan_s *P, const mpk_coeffs *co, mpk_dtype dty
     A.col = P->s_col.as<int32_t>();
     A.val = dtype == MPK_F64 ? P->s_val64.p : P->s_val32.p;
 
-    if (dtype == MPK_F64) MPK_TRY(dispatch_nr<double>(P, A, n_rhs, V, cf, p, blocked, flags, s));
-    else MPK_TRY(dispatch_nr<float>(P, A, n_rhs, V, cf, p, blocked, flags, s));
+    auto run = [&](bool blk) -> mpk_status {
+        return dtype == MPK_F64 ? dispatch_nr<double>(P, A, n_rhs, V, cf, p, blk, flags, s)
+                                : dispatch_nr<float>(P, A, n_rhs, V, cf, p, blk, flags, s);
+    };
+    bool computed = false;
+    if (blocked && P->opts.blocked < 0) {
+        // automatic choice, once per (precision, p, n_rhs): the blocked kernel only pays when
+        // the matrix does not fit in L2 and there are powers to reuse it for; then both
+        // kernels are timed on this call's own data (their results are bit-identical, so the
+        // second run just rewrites the same values) and the faster one is kept
+        const int key = (int)dtype * (1 << 24) + p * (1 << 12) + n_rhs;
+        auto it = P->auto_blocked.find(key);
+        if (it != P->auto_blocked.end()) {
+            blocked = it->second;
+        } else {
+            const int64_t w = dtype == MPK_F64 ? 8 : 4;
+            const int64_t bytes = P->sell_nnz * (4 + w) + 2 * n * n_rhs * w;
+            if (p < 2 || bytes <= P->l2_bytes) {
+                blocked = false;
+            } else {
+                cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+                for (int i = 0; i < 3; i++) MPK_CUDA(cudaEventCreate(&ev[i]));
+                float tu = 1e30f, tb = 1e30f;
+                mpk_status st = MPK_OK;
+                for (int rep = 0; rep < 2 && st == MPK_OK; rep++) {
+                    cudaEventRecord(ev[0], s);
+                    st = run(false);
+                    cudaEventRecord(ev[1], s);
+                    if (st == MPK_OK) st = run(true);
+                    cudaEventRecord(ev[2], s);
+                    if (st == MPK_OK && cudaEventSynchronize(ev[2]) == cudaSuccess) {
+                        float a = 0, b = 0;
+                        cudaEventElapsedTime(&a, ev[0], ev[1]);
+                        cudaEventElapsedTime(&b, ev[1], ev[2]);
+                        tu = std::min(tu, a);
+                        tb = std::min(tb, b);
+                    }
+                }
+                for (int i = 0; i < 3; i++) cudaEventDestroy(ev[i]);
+                MPK_TRY(st);
+                blocked = tb < tu;
+                computed = true;
+            }
+            P->auto_blocked[key] = blocked;
+        }
+    }
+    if (!computed) MPK_TRY(run(blocked));
 
     if (!direct) {
         // un-stage every output block into the user's layout / order (one launch)

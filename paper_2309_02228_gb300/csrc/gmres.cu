@@ -77,13 +77,21 @@ __global__ void __launch_bounds__(RED_BLOCK) sumsq_partial_kernel(const T *v, in
     if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 // out[e] = sum over b of part[b * stride + e], e < m; optional sqrt
-__global__ void reduce_partials_kernel(const double *part, int nb, int m, int64_t stride, double *out, int take_sqrt) {
-    for (int e = threadIdx.x; e < m; e += blockDim.x) {
-        double s = 0.0;
-        for (int b = 0; b < nb; b++) s += part[(int64_t)b * stride + e];
-        out[e] = take_sqrt ? sqrt(s) : s;
-    }
+// out[e] = sum_b part[b * stride + e], e < m: one warp per output, lane l adds partials l,
+// l + 32, ... in order, then a fixed shuffle tree (the result does not depend on the grid)
+static constexpr int REDP_WARPS = 8;
+__global__ void __launch_bounds__(32 * REDP_WARPS) reduce_partials_kernel(const double *part, int nb, int m,
+                                                                         int64_t stride, double *out, int take_sqrt) {
+    const int lane = threadIdx.x & 31;
+    const int e = blockIdx.x * REDP_WARPS + (threadIdx.x >> 5);
+    if (e >= m) return;
+    double s = 0.0;
+    for (int b = lane; b < nb; b += 32) s += part[(int64_t)b * stride + e];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[e] = take_sqrt ? sqrt(s) : s;
 }
+static inline unsigned redp_grid(int m) { return (unsigned)((m + REDP_WARPS - 1) / REDP_WARPS); }
 
 // ------------------------------------------------------------------------------------------
 // Tall-skinny Gram G = X^T Y (X: n x K, Y: n x S, column-major), G col-major K x S.
@@ -110,13 +118,34 @@ __global__ void __launch_bounds__(256) gram_kernel(const T *X, int64_t ldx, int 
     for (int64_t r0 = (int64_t)blockIdx.x * GR; r0 < n; r0 += (int64_t)gridDim.x * GR) {
         const int rows = (int)((n - r0) < (int64_t)GR ? (n - r0) : (int64_t)GR);
         __syncthreads();
-        for (int e = threadIdx.x; e < GR * K; e += blockDim.x) {
-            const int c = e / GR, r = e % GR;
-            xs[r * K + c] = r < rows ? X[(int64_t)c * ldx + r0 + r] : (T)0;
+        // staging: eight independent loads per thread in flight before the stores
+        for (int e0 = threadIdx.x; e0 < GR * K; e0 += 8 * blockDim.x) {
+            T v[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int e = e0 + u * blockDim.x;
+                const int c = e / GR, r = e % GR;
+                v[u] = (e < GR * K && r < rows) ? X[(int64_t)c * ldx + r0 + r] : (T)0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int e = e0 + u * blockDim.x;
+                if (e < GR * K) xs[(e % GR) * K + e / GR] = v[u];
+            }
         }
-        for (int e = threadIdx.x; e < GR * S; e += blockDim.x) {
-            const int c = e / GR, r = e % GR;
-            ys[r * S + c] = r < rows ? Y[(int64_t)c * ldy + r0 + r] : (T)0;
+        for (int e0 = threadIdx.x; e0 < GR * S; e0 += 8 * blockDim.x) {
+            T v[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int e = e0 + u * blockDim.x;
+                const int c = e / GR, r = e % GR;
+                v[u] = (e < GR * S && r < rows) ? Y[(int64_t)c * ldy + r0 + r] : (T)0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                const int e = e0 + u * blockDim.x;
+                if (e < GR * S) ys[(e % GR) * S + e / GR] = v[u];
+            }
         }
         __syncthreads();
         if (active) {
@@ -180,11 +209,18 @@ __global__ void __launch_bounds__(256) update_kernel(const T *Q, int64_t ldq, in
         T w[SB];
 #pragma unroll
         for (int b = 0; b < SB; b++) w[b] = b < S ? W[(int64_t)b * ldw + i] : (T)0;
-        for (int a = 0; a < K1; a++) {
-            const T q = Q[(int64_t)a * ldq + i];
+        // eight basis columns' loads in flight before their FMAs (ascending order kept)
+        for (int a0 = 0; a0 < K1; a0 += 8) {
+            T q[8];
 #pragma unroll
-            for (int b = 0; b < SB; b++)
-                if (b < S) w[b] = fma(-q, cs[a][b], w[b]);
+            for (int u = 0; u < 8; u++) q[u] = a0 + u < K1 ? Q[(int64_t)(a0 + u) * ldq + i] : (T)0;
+#pragma unroll
+            for (int u = 0; u < 8; u++)
+                if (a0 + u < K1) {
+#pragma unroll
+                    for (int b = 0; b < SB; b++)
+                        if (b < S) w[b] = fma(-q[u], cs[a0 + u][b], w[b]);
+                }
         }
         T wn[SB];
 #pragma unroll
@@ -210,19 +246,27 @@ __global__ void __launch_bounds__(256) update_kernel(const T *Q, int64_t ldq, in
         }
     }
     if (!FUSE || !gpart) return;
-    // per-CTA FP64 sum over threads: warp shuffles then shared memory, fixed order
+    // per-CTA sum over threads: a shuffle tree inside each warp (basis precision, five
+    // levels), then the warps' partials in FP64 in warp order
+    __shared__ double wred[8][NG];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int w = 0; w < nw; w++) {
-        int e = 0;
-        for (int b = 0; b < S; b++)
-            for (int c = 0; c <= b; c++, e++) {
-                double v = (double)g2[e];
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                if (warp == w && lane == 0) red[b * S + c] += v;
-            }
-        __syncthreads();
+    for (int e = 0; e < NG; e++) {
+        T v = g2[e];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0 && warp < 8) wred[warp][e] = (double)v;
     }
+    __syncthreads();
+    for (int e = threadIdx.x; e < NG; e += blockDim.x) {
+        double t = 0.0;
+        for (int w = 0; w < nw && w < 8; w++) t += wred[w][e];
+        // packed lower triangle (b >= c) -> red[b * S + c]
+        int b = 0, c = e;
+        while (c > b) { c -= b + 1; b++; }
+        if (b < S) red[b * S + c] = t;
+    }
+    __syncthreads();
     for (int e = threadIdx.x; e < S * S; e += blockDim.x) {
         const int b = e / S, c = e % S;
         // symmetric S x S, column-major: G[b + c*S]
@@ -267,23 +311,40 @@ struct CycleState {            // device memory, one per solve
     double est;                 // latest residual estimate |g[k]|
 };
 
-// Cholesky of an S x S SPD matrix A (col-major) into upper R with R^T R = A; Rinv = R^-1.
-__device__ bool chol_inv(const double *A, int S, double *R, double *Rinv) {
-    for (int e = 0; e < S * S; e++) { R[e] = 0.0; Rinv[e] = 0.0; }
+// The small dense steps below run on one CTA each.  On this GPU a dependent chain of FP64
+// operations in a single thread costs tens of cycles per operation, so every step spreads its
+// independent work over the threads and keeps only true recurrences sequential.  Each keeps
+// the summation order of the plain algorithm, so results do not depend on the thread count.
+
+// Cholesky of an S x S SPD matrix A (col-major, shared memory) into upper R with R^T R = A,
+// and Rinv = R^-1, by one warp: lane 0 takes the pivot, lanes j > i the rest of row i; then
+// lane j back-substitutes column j of the inverse.  False (on every lane) on a non-positive
+// pivot.
+__device__ bool chol_inv_warp(const double *A, int S, double *R, double *Rinv, int lane) {
+    for (int e = lane; e < S * S; e += 32) {
+        R[e] = 0.0;
+        Rinv[e] = 0.0;
+    }
+    __syncwarp();
     for (int i = 0; i < S; i++) {
-        double d = A[i + i * S];
-        for (int k = 0; k < i; k++) d -= R[k + i * S] * R[k + i * S];
+        double d = 0.0;
+        if (lane == 0) {
+            d = A[i + i * S];
+            for (int k = 0; k < i; k++) d -= R[k + i * S] * R[k + i * S];
+        }
+        d = __shfl_sync(0xffffffffu, d, 0);
         if (!(d > 0.0)) return false;
         const double rii = sqrt(d);
-        R[i + i * S] = rii;
-        for (int j = i + 1; j < S; j++) {
-            double v = A[i + j * S];
-            for (int k = 0; k < i; k++) v -= R[k + i * S] * R[k + j * S];
-            R[i + j * S] = v / rii;
+        if (lane == 0) R[i + i * S] = rii;
+        if (lane > i && lane < S) {
+            double v = A[i + lane * S];
+            for (int k = 0; k < i; k++) v -= R[k + i * S] * R[k + lane * S];
+            R[i + lane * S] = v / rii;
         }
+        __syncwarp();
     }
-    // inverse of upper triangular R by columns
-    for (int j = 0; j < S; j++) {
+    if (lane < S) {
+        const int j = lane;
         Rinv[j + j * S] = 1.0 / R[j + j * S];
         for (int i = j - 1; i >= 0; i--) {
             double v = 0.0;
@@ -291,6 +352,7 @@ __device__ bool chol_inv(const double *A, int S, double *R, double *Rinv) {
             Rinv[i + j * S] = -v / R[i + i * S];
         }
     }
+    __syncwarp();
     return true;
 }
 
@@ -299,164 +361,269 @@ __device__ bool chol_inv(const double *A, int S, double *R, double *Rinv) {
 //   mode 2: C2 = G (second projection sweep);  Rinv = I
 //   mode 1: R1 = chol(G) (S x S Gram of the projected block); Rinv = R1^-1
 //   mode 3: R2 = chol(G) (CholQR's second pass);             Rinv = R2^-1
-__global__ void chol_kernel(CycleState *cst, const double *G, int K1, int S, int mode) {
-    if (threadIdx.x != 0) return;
+__global__ void __launch_bounds__(256) chol_kernel(CycleState *cst, const double *G, int K1, int S, int mode) {
+    const int tid = threadIdx.x;
     if (mode == 0 || mode == 2) {
         double *Cd = mode == 0 ? cst->C : cst->C2;
-        for (int e = 0; e < K1 * S; e++) Cd[e] = G[e];
-        for (int e = 0; e < S * S; e++) cst->Rinv[e] = (e % S == e / S) ? 1.0 : 0.0;
+        for (int e = tid; e < K1 * S; e += blockDim.x) Cd[e] = G[e];
+        for (int e = tid; e < S * S; e += blockDim.x) cst->Rinv[e] = (e % S == e / S) ? 1.0 : 0.0;
+        return;
+    }
+    if (tid >= 32) return;
+    __shared__ double sA[SMAX * SMAX], sR[SMAX * SMAX], sRi[SMAX * SMAX];
+    for (int e = tid; e < S * S; e += 32) sA[e] = G[e];
+    __syncwarp();
+    if (!chol_inv_warp(sA, S, sR, sRi, tid)) {
+        if (tid == 0) cst->status = 1;
         return;
     }
     double *R = mode == 1 ? cst->R1 : cst->R2;
-    if (!chol_inv(G, S, R, cst->Rinv)) cst->status = 1;
+    for (int e = tid; e < S * S; e += 32) {
+        R[e] = sR[e];
+        cst->Rinv[e] = sRi[e];
+    }
 }
 
 // Hessenberg columns j..j+S-1 from R_full (C, R), shifts theta and the previous Arnoldi H;
 // Givens rotations; convergence check against tol_abs.
 // passes == 2: C_total = C1 + C2 R1, R_total = R2 R1 ; else C_total = C1, R_total = R2 R1.
-__global__ void hess_kernel(CycleState *cst, int j, int S, const double *theta, double tol_abs, int m) {
-    if (threadIdx.x != 0) return;
+__global__ void __launch_bounds__(256) hess_kernel(CycleState *cst, int j, int S, const double *theta,
+                                                    double tol_abs, int m) {
+    __shared__ int s_stop;
     if (cst->status) return;
+    const int tid = threadIdx.x, nt = blockDim.x;
     const int K1 = j + 1;
     const int ldh = MMAX + 1;
-    double *C = cst->Ct, *R = cst->Rt;
-    for (int e = 0; e < S * S; e++) R[e] = 0.0;
-    for (int c = 0; c < S; c++)
-        for (int a = 0; a <= c; a++) {
-            double v = 0.0;
-            for (int k = a; k <= c; k++) v += cst->R2[a + k * S] * cst->R1[k + c * S];
-            R[a + c * S] = v;
-        }
-    // W = Q (C + C2) + Q_new R2 R1  (C2: second projection sweep, when taken)
-    for (int b = 0; b < S; b++)
-        for (int a = 0; a < K1; a++) {
-            double v = cst->C[a + b * K1];
-            if (cst->nrm[3] > 0.5) v += cst->C2[a + b * K1];
-            C[a + b * K1] = v;
-        }
-    // R_full: (K1 + S) x (S + 1), column 0 = e_j, columns 1..S = [C ; R]
     const int NR = K1 + S;
-    double *RF = cst->RF;
-    for (int e = 0; e < NR * (S + 1); e++) RF[e] = 0.0;
-    RF[j + 0 * NR] = 1.0;
-    for (int b = 0; b < S; b++) {
-        for (int a = 0; a < K1; a++) RF[a + (b + 1) * NR] = C[a + b * K1];
-        for (int a = 0; a < S; a++) RF[K1 + a + (b + 1) * NR] = R[a + b * S];
+    double *C = cst->Ct, *R = cst->Rt, *RF = cst->RF, *RHS = cst->RHS, *Hn = cst->Hn;
+    const bool two = cst->nrm[3] > 0.5;
+    if (tid == 0) s_stop = 0;
+    // R = R2 R1 (upper triangular); C = C1 (+ C2: second projection sweep, when taken)
+    for (int e = tid; e < S * S; e += nt) {
+        const int a = e % S, c = e / S;
+        double v = 0.0;
+        if (a <= c)
+            for (int k = a; k <= c; k++) v += cst->R2[a + k * S] * cst->R1[k + c * S];
+        R[e] = v;
     }
+    for (int e = tid; e < K1 * S; e += nt) {
+        double v = cst->C[e];
+        if (two) v += cst->C2[e];
+        C[e] = v;
+    }
+    __syncthreads();
+    // R_full: (K1 + S) x (S + 1), column 0 = e_j, columns 1..S = [C ; R]
+    for (int e = tid; e < NR * (S + 1); e += nt) {
+        const int a = e % NR, col = e / NR;
+        double v;
+        if (col == 0) v = a == j ? 1.0 : 0.0;
+        else v = a < K1 ? C[a + (col - 1) * K1] : R[(a - K1) + (col - 1) * S];
+        RF[e] = v;
+    }
+    __syncthreads();
     // rhs = R_full * Bm - H_prev[:, 0:j] * R_s[0:j, :],   Bm: (S+1) x S, theta on the
     // diagonal, ones below
-    double *RHS = cst->RHS;
-    for (int c = 0; c < S; c++)
-        for (int a = 0; a < NR; a++) {
-            double v = RF[a + c * NR] * theta[c] + RF[a + (c + 1) * NR];
-            for (int q = 0; q < j; q++) v -= cst->H[a + q * ldh] * RF[q + c * NR];
-            RHS[a + c * NR] = v;
-        }
+    for (int e = tid; e < NR * S; e += nt) {
+        const int a = e % NR, c = e / NR;
+        double v = RF[a + c * NR] * theta[c] + RF[a + (c + 1) * NR];
+        for (int q = 0; q < j; q++) v -= cst->H[a + q * ldh] * RF[q + c * NR];
+        RHS[e] = v;
+    }
+    __syncthreads();
     // T = R_s[j:j+S, 0:S] upper triangular; H_new = RHS T^-1 (solve from the right, by columns)
-    double *Hn = cst->Hn;
     for (int c = 0; c < S; c++) {
         const double tcc = RF[(j + c) + c * NR];
-        for (int a = 0; a < NR; a++) {
+        for (int a = tid; a < NR; a += nt) {
             double v = RHS[a + c * NR];
             for (int q = 0; q < c; q++) v -= Hn[a + q * NR] * RF[(j + q) + c * NR];
-            Hn[a + c * NR] = v / tcc;
+            Hn[a + c * NR] = a >= j + c + 2 ? 0.0 : v / tcc;   // Hessenberg structure
         }
-        for (int a = j + c + 2; a < NR; a++) Hn[a + c * NR] = 0.0;   // Hessenberg structure
+        __syncthreads();
     }
-    // store into H (unrotated) and Hr, then rotate the new columns
-    for (int c = 0; c < S; c++)
-        for (int a = 0; a < NR && a <= MMAX; a++) {
-            cst->H[a + (j + c) * ldh] = Hn[a + c * NR];
-            cst->Hr[a + (j + c) * ldh] = Hn[a + c * NR];
-        }
-    for (int c = j; c < j + S; c++) {
-        double *h = cst->Hr + c * ldh;
-        for (int i = 0; i < c; i++) {
+    // store the new columns (unrotated and rotated copies), zero below the structure
+    for (int e = tid; e < S * ldh; e += nt) {
+        const int a = e % ldh, c = e / ldh;
+        const double v = a < NR ? Hn[a + c * NR] : 0.0;
+        cst->H[a + (j + c) * ldh] = v;
+        cst->Hr[a + (j + c) * ldh] = v;
+    }
+    __syncthreads();
+    // earlier rotations 0..j-1 on each new column (one thread per column)
+    if (tid < S) {
+        double *h = cst->Hr + (j + tid) * ldh;
+        for (int i = 0; i < j; i++) {
             const double t = cst->cs[i] * h[i] + cst->sn[i] * h[i + 1];
             h[i + 1] = -cst->sn[i] * h[i] + cst->cs[i] * h[i + 1];
             h[i] = t;
         }
-        const double a = h[c], b = h[c + 1];
-        double cs = 1.0, sn = 0.0;
-        if (b != 0.0) {
-            const double r = hypot(a, b);
-            cs = a / r;
-            sn = b / r;
+    }
+    __syncthreads();
+    // this block's rotations: rotation c from column c, then applied to the later columns
+    for (int c = j; c < j + S; c++) {
+        if (tid == 0) {
+            double *h = cst->Hr + c * ldh;
+            const double a = h[c], b = h[c + 1];
+            double cs = 1.0, sn = 0.0;
+            if (b != 0.0) {
+                const double r = hypot(a, b);
+                cs = a / r;
+                sn = b / r;
+            }
+            cst->cs[c] = cs;
+            cst->sn[c] = sn;
+            h[c] = cs * a + sn * b;
+            h[c + 1] = 0.0;
+            cst->g[c + 1] = -sn * cst->g[c];
+            cst->g[c] = cs * cst->g[c];
+            cst->kdone = c + 1;
+            cst->est = fabs(cst->g[c + 1]);
+            if (fabs(cst->g[c + 1]) <= tol_abs) {
+                cst->conv_k = c + 1;
+                s_stop = 1;
+            }
         }
-        cst->cs[c] = cs;
-        cst->sn[c] = sn;
-        h[c] = cs * a + sn * b;
-        h[c + 1] = 0.0;
-        cst->g[c + 1] = -sn * cst->g[c];
-        cst->g[c] = cs * cst->g[c];
-        cst->kdone = c + 1;
-        cst->est = fabs(cst->g[c + 1]);
-        if (fabs(cst->g[c + 1]) <= tol_abs) {
-            cst->conv_k = c + 1;
-            break;
+        __syncthreads();
+        if (s_stop) break;
+        const int cc = c + 1 + tid;
+        if (cc < j + S) {
+            double *h = cst->Hr + cc * ldh;
+            const double t = cst->cs[c] * h[c] + cst->sn[c] * h[c + 1];
+            h[c + 1] = -cst->sn[c] * h[c] + cst->cs[c] * h[c + 1];
+            h[c] = t;
         }
+        __syncthreads();
     }
     (void)m;
 }
 
-// y = Hr[0:k, 0:k]^-1 g[0:k] (back substitution)
-__global__ void lsq_kernel(CycleState *cst, int k) {
-    if (threadIdx.x != 0) return;
+// y = Hr[0:k, 0:k]^-1 g[0:k]: back substitution by columns (y_i, then every row above it
+// subtracts its multiple of y_i)
+__global__ void __launch_bounds__(128) lsq_kernel(CycleState *cst, int k) {
+    __shared__ double gg[MMAX + 1], yy[MMAX];
+    const int tid = threadIdx.x, nt = blockDim.x;
     const int ldh = MMAX + 1;
+    for (int i = tid; i < k; i += nt) gg[i] = cst->g[i];
+    __syncthreads();
     for (int i = k - 1; i >= 0; i--) {
-        double v = cst->g[i];
-        for (int q = i + 1; q < k; q++) v -= cst->Hr[i + q * ldh] * cst->y[q];
-        cst->y[i] = v / cst->Hr[i + i * ldh];
+        if (tid == 0) yy[i] = gg[i] / cst->Hr[i + i * ldh];
+        __syncthreads();
+        const double yi = yy[i];
+        for (int a = tid; a < i; a += nt) gg[a] -= cst->Hr[a + i * ldh] * yi;
+        __syncthreads();
     }
+    for (int i = tid; i < k; i += nt) cst->y[i] = yy[i];
 }
 
-// Ritz values: eigenvalues of the symmetric part of the leading k x k Arnoldi H by cyclic
-// Jacobi rotations (for a symmetric A the Arnoldi H is symmetric tridiagonal up to rounding,
-// so these are its Ritz values; for an unsymmetric A they are real values from its field of
-// values).
-__global__ void ritz_kernel(CycleState *cst, int k) {
-    if (threadIdx.x != 0) return;
+// Ritz values: eigenvalues of the symmetric part of the leading k x k Arnoldi H by Jacobi
+// rotations (for a symmetric A the Arnoldi H is symmetric tridiagonal up to rounding, so these
+// are its Ritz values; for an unsymmetric A they are real values from its field of values).
+// Parallel ordering: each round rotates kp/2 disjoint pairs at once (round-robin schedule of
+// the kp = k rounded up to even indices; a padding index stays decoupled), kp - 1 rounds per
+// sweep; sweeps stop once the off-diagonal part is below 1e-15 of the Frobenius norm.
+// Shared memory: kp x (kp + 1) doubles.
+static constexpr int RITZ_THREADS = 256;
+__global__ void __launch_bounds__(RITZ_THREADS) ritz_kernel(CycleState *cst, int k) {
+    extern __shared__ double sA[];
+    __shared__ double s_c[MMAX / 2 + 1], s_s[MMAX / 2 + 1], s_red[RITZ_THREADS / 32];
+    __shared__ int s_p[MMAX / 2 + 1], s_q[MMAX / 2 + 1];
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
     const int ldh = MMAX + 1;
-    double *A = cst->Hr;   // reuse as scratch after the cycle (ld ldh)
-    for (int c = 0; c < k; c++)
-        for (int r = 0; r < k; r++) A[r + c * ldh] = 0.5 * (cst->H[r + c * ldh] + cst->H[c + r * ldh]);
-    for (int sweep = 0; sweep < 60; sweep++) {
-        double off = 0.0;
-        for (int c = 0; c < k; c++)
-            for (int r = 0; r < c; r++) off += A[r + c * ldh] * A[r + c * ldh];
-        if (off < 1e-30) break;
-        for (int p = 0; p < k - 1; p++)
-            for (int q = p + 1; q < k; q++) {
-                const double apq = A[p + q * ldh];
-                if (fabs(apq) < 1e-300) continue;
-                const double app = A[p + p * ldh], aqq = A[q + q * ldh];
-                const double tau = (aqq - app) / (2.0 * apq);
-                const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                const double c = 1.0 / sqrt(1.0 + t * t), s = t * c;
-                for (int r = 0; r < k; r++) {   // columns p, q
-                    const double arp = A[r + p * ldh], arq = A[r + q * ldh];
-                    A[r + p * ldh] = c * arp - s * arq;
-                    A[r + q * ldh] = s * arp + c * arq;
-                }
-                for (int r = 0; r < k; r++) {   // rows p, q
-                    const double apr = A[p + r * ldh], aqr = A[q + r * ldh];
-                    A[p + r * ldh] = c * apr - s * aqr;
-                    A[q + r * ldh] = s * apr + c * aqr;
-                }
-            }
+    const int kp = (k + 1) & ~1, ld = kp + 1, half = kp / 2;
+    for (int e = tid; e < kp * kp; e += nt) {
+        const int r = e % kp, c = e / kp;
+        sA[r + c * ld] = (r < k && c < k) ? 0.5 * (cst->H[r + c * ldh] + cst->H[c + r * ldh]) : 0.0;
     }
-    for (int i = 0; i < k; i++) cst->ritz[i] = A[i + i * ldh];
+    __syncthreads();
+    auto block_sum = [&](double v) -> double {
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) s_red[wid] = v;
+        __syncthreads();
+        double t = 0.0;
+        for (int w = 0; w < nt / 32; w++) t += s_red[w];
+        __syncthreads();
+        return t;
+    };
+    double fro = 0.0;
+    for (int e = tid; e < kp * kp; e += nt) {
+        const double v = sA[(e % kp) + (e / kp) * ld];
+        fro += v * v;
+    }
+    fro = block_sum(fro);
+    for (int sweep = 0; sweep < 30; sweep++) {
+        double off = 0.0;
+        for (int e = tid; e < kp * kp; e += nt) {
+            const int r = e % kp, c = e / kp;
+            if (r != c) {
+                const double v = sA[r + c * ld];
+                off += v * v;
+            }
+        }
+        off = block_sum(off);
+        if (!(off > 1e-30 * fro)) break;
+        for (int round = 0; round < kp - 1; round++) {
+            if (tid < half) {
+                int p, q;
+                if (tid == 0) {
+                    p = round;
+                    q = kp - 1;
+                } else {
+                    p = (round + tid) % (kp - 1);
+                    q = (round - tid + kp - 1) % (kp - 1);
+                }
+                if (p > q) {
+                    const int t = p;
+                    p = q;
+                    q = t;
+                }
+                const double apq = sA[p + q * ld];
+                double c = 1.0, s = 0.0;
+                if (fabs(apq) >= 1e-300) {
+                    const double app = sA[p + p * ld], aqq = sA[q + q * ld];
+                    const double tau = (aqq - app) / (2.0 * apq);
+                    const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                    c = 1.0 / sqrt(1.0 + t * t);
+                    s = t * c;
+                }
+                s_p[tid] = p;
+                s_q[tid] = q;
+                s_c[tid] = c;
+                s_s[tid] = s;
+            }
+            __syncthreads();
+            for (int e = tid; e < half * kp; e += nt) {   // columns p, q
+                const int i = e / kp, r = e % kp;
+                const int p = s_p[i], q = s_q[i];
+                const double c = s_c[i], s = s_s[i];
+                const double arp = sA[r + p * ld], arq = sA[r + q * ld];
+                sA[r + p * ld] = c * arp - s * arq;
+                sA[r + q * ld] = s * arp + c * arq;
+            }
+            __syncthreads();
+            for (int e = tid; e < half * kp; e += nt) {   // rows p, q
+                const int i = e / kp, r = e % kp;
+                const int p = s_p[i], q = s_q[i];
+                const double c = s_c[i], s = s_s[i];
+                const double apr = sA[p + r * ld], aqr = sA[q + r * ld];
+                sA[p + r * ld] = c * apr - s * aqr;
+                sA[q + r * ld] = s * apr + c * aqr;
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = tid; i < k; i += nt) cst->ritz[i] = sA[i + i * ld];
 }
 
 __global__ void cycle_init_kernel(CycleState *cst, const double *beta) {
-    if (threadIdx.x != 0) return;
-    cst->status = 0;
-    cst->conv_k = 0;
-    cst->kdone = 0;
-    cst->g[0] = *beta;
-    cst->est = *beta;
-    for (int i = 1; i <= MMAX; i++) cst->g[i] = 0.0;
-    cst->nrm[3] = 0.0;
+    const int tid = threadIdx.x;
+    const double b = *beta;
+    for (int i = tid; i <= MMAX; i += blockDim.x) cst->g[i] = i == 0 ? b : 0.0;
+    if (tid == 0) {
+        cst->status = 0;
+        cst->conv_k = 0;
+        cst->kdone = 0;
+        cst->est = b;
+        cst->nrm[3] = 0.0;
+    }
 }
 __global__ void set_flag_kernel(CycleState *cst, double v) {
     if (threadIdx.x == 0) cst->nrm[3] = v;
@@ -466,24 +633,35 @@ __global__ void set_flag_kernel(CycleState *cst, double v) {
 // Host driver
 // ------------------------------------------------------------------------------------------
 struct Timer {
-    cudaEvent_t a = nullptr, b = nullptr;
+    // intervals are recorded without waiting; flush() adds them up once the stream is idle
+    std::vector<cudaEvent_t> ev;
+    size_t used = 0;
     double total = 0.0;
     cudaStream_t s;
-    explicit Timer(cudaStream_t st) : s(st) {
-        cudaEventCreate(&a);
-        cudaEventCreate(&b);
-    }
+    explicit Timer(cudaStream_t st) : s(st) {}
     ~Timer() {
-        cudaEventDestroy(a);
-        cudaEventDestroy(b);
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
     }
-    void start() { cudaEventRecord(a, s); }
-    void stop() {
-        cudaEventRecord(b, s);
-        cudaEventSynchronize(b);
-        float ms = 0;
-        cudaEventElapsedTime(&ms, a, b);
-        total += ms;
+    void rec() {
+        if (used == ev.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                cudaGetLastError();
+                return;
+            }
+            ev.push_back(e);
+        }
+        cudaEventRecord(ev[used++], s);
+    }
+    void start() { rec(); }
+    void stop() { rec(); }
+    void flush() {
+        for (size_t i = 0; i + 1 < used; i += 2) {
+            float ms = 0;
+            if (cudaEventElapsedTime(&ms, ev[i], ev[i + 1]) == cudaSuccess) total += ms;
+            else cudaGetLastError();
+        }
+        used = 0;
     }
 };
 
@@ -494,6 +672,7 @@ struct Solver {
     mpk_gmres_opts o;
     int64_t n, ldv;
     DevBuf V, part, G, gpart2, cstate, vec;   // vec: b, x, r, norms (FP64)
+    DevBuf dth;                                // Newton shifts of the current cycle
     double *bp, *xp, *rp, *nrm;
     CycleState *cst;
     int gram_grid, upd_grid;
@@ -516,6 +695,7 @@ struct Solver {
         MPK_TRY(G.alloc((size_t)maxK * SMAX * sizeof(double) + 64));
         MPK_TRY(gpart2.alloc((size_t)upd_grid * SMAX * SMAX * sizeof(double) + 64));
         MPK_TRY(cstate.alloc(sizeof(CycleState)));
+        MPK_TRY(dth.alloc(SMAX * sizeof(double)));
         MPK_TRY(vec.alloc((size_t)3 * ldv * sizeof(double) + 64 * sizeof(double)));
         bp = vec.as<double>();
         xp = bp + ldv;
@@ -527,11 +707,16 @@ struct Solver {
     }
 
     T *col(int a) { return V.as<T>() + (int64_t)a * ldv; }
+    void flush_timers() {
+        t_mpk.flush();
+        t_ortho.flush();
+        t_other.flush();
+    }
 
     mpk_status norm2(const double *v, double *out) {
         const unsigned g = grid_rows(n);
         sumsq_partial_kernel<double><<<g, RED_BLOCK, 0, st>>>(v, n, part.as<double>());
-        reduce_partials_kernel<<<1, 32, 0, st>>>(part.as<double>(), g, 1, 1, out, 1);
+        reduce_partials_kernel<<<redp_grid(1), 32 * REDP_WARPS, 0, st>>>(part.as<double>(), g, 1, 1, out, 1);
         MPK_CUDA(cudaGetLastError());
         return MPK_OK;
     }
@@ -545,7 +730,7 @@ struct Solver {
         MPK_CUDA(cudaFuncSetAttribute(gram_kernel<T, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
         const int g = (int)std::min<int64_t>(gram_grid, ceil_div(n, GR));
         gram_kernel<T, SB><<<g, 256, sm, st>>>(X, ldv, K, Y, ldv, S, n, part.as<double>());
-        reduce_partials_kernel<<<1, 256, 0, st>>>(part.as<double>(), g, K * S, (int64_t)K * S, Gout, 0);
+        reduce_partials_kernel<<<redp_grid(K * S), 32 * REDP_WARPS, 0, st>>>(part.as<double>(), g, K * S, (int64_t)K * S, Gout, 0);
         MPK_CUDA(cudaGetLastError());
         return MPK_OK;
     }
@@ -575,7 +760,7 @@ struct Solver {
         auto update_gram = [&](int k1, const double *C) -> mpk_status {
             if (S <= 8) {
                 MPK_TRY(update(Q, k1, W, S, C, cst->Rinv, gpart2.as<double>()));
-                reduce_partials_kernel<<<1, 256, 0, st>>>(gpart2.as<double>(), ug, S * S, (int64_t)S * S, Gd, 0);
+                reduce_partials_kernel<<<redp_grid(S * S), 32 * REDP_WARPS, 0, st>>>(gpart2.as<double>(), ug, S * S, (int64_t)S * S, Gd, 0);
             } else {
                 MPK_TRY(update(Q, k1, W, S, C, cst->Rinv, nullptr));
                 MPK_TRY(gram(W, S, W, S, Gd));
@@ -583,11 +768,11 @@ struct Solver {
             return MPK_OK;
         };
         MPK_TRY(gram(Q, K1, W, S, Gd));
-        chol_kernel<<<1, 32, 0, st>>>(cst, Gd, K1, S, 0);
+        chol_kernel<<<1, 256, 0, st>>>(cst, Gd, K1, S, 0);
         if (o.bcgs_passes >= 2) {
             MPK_TRY(update(Q, K1, W, S, cst->C, cst->Rinv, nullptr));
             MPK_TRY(gram(Q, K1, W, S, Gd));
-            chol_kernel<<<1, 32, 0, st>>>(cst, Gd, K1, S, 2);
+            chol_kernel<<<1, 256, 0, st>>>(cst, Gd, K1, S, 2);
             MPK_TRY(update_gram(K1, cst->C2));
             set_flag_kernel<<<1, 32, 0, st>>>(cst, 1.0);
         } else {
@@ -619,13 +804,11 @@ struct Solver {
         const int m = o.restart;
         norm2(rp, nrm);
         normalize_kernel<T><<<grid_rows(n), 256, 0, st>>>(rp, nrm, n, col(0));
-        cycle_init_kernel<<<1, 32, 0, st>>>(cst, nrm);
+        cycle_init_kernel<<<1, 128, 0, st>>>(cst, nrm);
         MPK_CUDA(cudaGetLastError());
         std::vector<double> th(s, 0.0);
         if (newton)
             for (int k = 0; k < s; k++) th[k] = theta[k];
-        DevBuf dth;
-        MPK_TRY(dth.alloc(SMAX * sizeof(double)));
         MPK_CUDA(cudaMemcpyAsync(dth.p, th.data(), s * sizeof(double), cudaMemcpyHostToDevice, st));
         int j = 0, k = 0;
         *breakdown = false;
@@ -638,12 +821,13 @@ struct Solver {
             t_mpk.stop();
             t_ortho.start();
             MPK_TRY(ortho(j, S));
-            hess_kernel<<<1, 32, 0, st>>>(cst, j, S, dth.as<double>(), tol_abs, m);
+            hess_kernel<<<1, 256, 0, st>>>(cst, j, S, dth.as<double>(), tol_abs, m);
             MPK_CUDA(cudaGetLastError());
             t_ortho.stop();
             int hs[3];
             MPK_CUDA(cudaMemcpyAsync(hs, &cst->status, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
             MPK_CUDA(cudaStreamSynchronize(st));
+            flush_timers();
             if (hs[0]) {   // Cholesky breakdown: keep the columns before this block
                 *breakdown = true;
                 k = j;
@@ -656,13 +840,18 @@ struct Solver {
         o.bcgs_passes = saved_passes;
         if (k > 0) {
             t_other.start();
-            lsq_kernel<<<1, 32, 0, st>>>(cst, k);
+            lsq_kernel<<<1, 128, 0, st>>>(cst, k);
             xupdate_kernel<T><<<grid_rows(n, 8), 256, 0, st>>>(V.as<T>(), ldv, k, cst->y, n, xp);
             MPK_CUDA(cudaGetLastError());
             t_other.stop();
         }
         if (!newton && k > 0) {
-            ritz_kernel<<<1, 32, 0, st>>>(cst, k);
+            const int kp = (k + 1) & ~1;
+            // the attribute is shared by all threads: always the same maximum (m <= MMAX)
+            MPK_CUDA(cudaFuncSetAttribute(ritz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)(MMAX * (MMAX + 1) * sizeof(double))));
+            ritz_kernel<<<1, RITZ_THREADS, (size_t)kp * (kp + 1) * sizeof(double), st>>>(cst, k);
+            MPK_CUDA(cudaGetLastError());
             std::vector<double> rz(k);
             MPK_CUDA(cudaMemcpyAsync(rz.data(), cst->ritz, k * sizeof(double), cudaMemcpyDeviceToHost, st));
             MPK_CUDA(cudaStreamSynchronize(st));
@@ -696,8 +885,9 @@ struct Solver {
             norm2(rp, nrm + 2);
             double hr = 0.0;
             MPK_CUDA(cudaMemcpyAsync(&hr, nrm + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
-            MPK_CUDA(cudaStreamSynchronize(st));
             t_other.stop();
+            MPK_CUDA(cudaStreamSynchronize(st));
+            flush_timers();
             relres = hb > 0 ? hr / hb : 0.0;
             info.outer = outer;
             if (relres <= o.tol || hb == 0.0) {
@@ -729,6 +919,7 @@ struct Solver {
         scatter_f64_kernel<<<g, 256, 0, st>>>(xp, perm, n, x);
         MPK_CUDA(cudaGetLastError());
         MPK_CUDA(cudaStreamSynchronize(st));
+        flush_timers();
         info.rel_residual = relres;
         info.status = result;
         for (size_t i = 0; i < theta.size() && i < 64; i++) info.shifts[i] = theta[i];

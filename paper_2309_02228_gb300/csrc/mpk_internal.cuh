@@ -138,6 +138,8 @@ struct mpk_plan_s {
     DevBuf cblk_size, wave_cnt;       // chunks per block; counters [(k) * n_cblk + b]
     uint32_t kep[MPK_MAX_P + 1] = {};
     int64_t wave_slack = 0;
+    // automatic blocked / unblocked choice per (precision, p, n_rhs) (opts.blocked = -1)
+    std::map<int, bool> auto_blocked;
     DevBuf ctrl;      // MpkCtrl
     uint64_t launches_since_reset = 0;
     int ctas_per_sm = 0;

@@ -647,6 +647,7 @@ extern "C" mpk_status mpk_plan_opts_default(mpk_plan_opts *o) {
     o->block_threads = 256;
     o->stage = -1;
     o->kernel = 0;
+    o->blocked = -1;
     return MPK_OK;
 }
 

@@ -101,7 +101,7 @@ def test_shifts_match_oracle_ritz_leja(m):
 def test_blocked_and_unblocked_mpk_give_identical_solves(m):
     A = mi.diffusion7_lognormal(10)
     b = mi.uniform_vectors(A.n, 2)[0]
-    plan = _plan(m, A, l2_budget_bytes=50_000)
+    plan = _plan(m, A, l2_budget_bytes=50_000, blocked=1)
     x1, i1 = _solve(m, plan, A, b, s=8, restart=48, tol=1e-8)
     x2, i2 = _solve(m, plan, A, b, s=8, restart=48, tol=1e-8, mpk_flags=m.MPK_UNBLOCKED)
     assert i1["iters"] == i2["iters"] and np.array_equal(x1, x2)

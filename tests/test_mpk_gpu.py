@@ -163,7 +163,7 @@ def test_mpk_fp64_vs_oracle(m, basis, name):
                                                   (30_000, 1, -1, 1, 1, 0)):
         plan = m.mpk_plan_create(rp, ci, vv, p, m.mpk_plan_opts_default(
             l2_budget_bytes=budget, chunk_slices=cs, stage=stage, schedule=sched, kernel=kern,
-            slack_tasks=slack))
+            slack_tasks=slack, blocked=1))
         got_b = _run(m, plan, A, cf, x)
         got_u = _run(m, plan, A, cf, x, flags=m.MPK_UNBLOCKED)
         assert np.array_equal(got_b, got_u)            # blocked == unblocked, bit for bit
@@ -183,7 +183,7 @@ def test_mpk_fp32_vs_oracle(m, name):
     ref = oracle.mpk(A32, p, cf, x)
     den = abs_powers(A32, cf, x)
     rp, ci, vv = to_dev(A, np.float32)
-    plan = m.mpk_plan_create(rp, ci, vv, p, m.mpk_plan_opts_default(l2_budget_bytes=50_000))
+    plan = m.mpk_plan_create(rp, ci, vv, p, m.mpk_plan_opts_default(l2_budget_bytes=50_000, blocked=1))
     got = _run(m, plan, A, cf, x, dtype=torch.float32)
     got_u = _run(m, plan, A, cf, x, dtype=torch.float32, flags=m.MPK_UNBLOCKED)
     assert np.array_equal(got, got_u)
@@ -199,7 +199,7 @@ def test_permuted_io_and_y0_is_x(m):
     x = mi.uniform_vectors(A.n, 3)[0]
     ref = oracle.mpk(A, p, cf, x)
     rp, ci, vv = to_dev(A)
-    plan = m.mpk_plan_create(rp, ci, vv, p, m.mpk_plan_opts_default(l2_budget_bytes=100_000))
+    plan = m.mpk_plan_create(rp, ci, vv, p, m.mpk_plan_opts_default(l2_budget_bytes=100_000, blocked=1))
     perm = m.mpk_plan_perm(plan)["perm"].cpu().numpy()
     got = _run(m, plan, A, cf, x[perm], flags=m.MPK_PERMUTED_IO)
     full = _run(m, plan, A, cf, x)
@@ -224,7 +224,7 @@ def test_block_mpk_n_rhs(m, n_rhs, interleaved):
     Xc = mi.uniform_vectors(A.n, 6, n_rhs=n_rhs).astype(np.float32).astype(np.float64)  # (n_rhs, n)
     A32 = mi.CSR(A.row_ptr, A.col, A.val.astype(np.float32).astype(np.float64))
     rp, ci, vv = to_dev(A, np.float32)
-    plan = m.mpk_plan_create(rp, ci, vv, p, m.mpk_plan_opts_default(l2_budget_bytes=200_000))
+    plan = m.mpk_plan_create(rp, ci, vv, p, m.mpk_plan_opts_default(l2_budget_bytes=200_000, blocked=1))
     flags = m.MPK_RHS_INTERLEAVED if interleaved else 0
     xin = Xc.T.copy() if interleaved else Xc   # row-major n x n_rhs, or column-major
     got = _run(m, plan, A, cf, xin, dtype=torch.float32, n_rhs=n_rhs, flags=flags)
@@ -251,7 +251,7 @@ def test_final_only_gamma_and_segments(m, kern):
     rp, ci, vv = to_dev(A)
     # p_blk = 4 -> segments of 4, 4, 1 powers (the remainder launch)
     plan = m.mpk_plan_create(rp, ci, vv, p, m.mpk_plan_opts_default(l2_budget_bytes=60_000, p_blk=4,
-                                                                     kernel=kern, slack_tasks=5))
+                                                                     kernel=kern, slack_tasks=5, blocked=1))
     full = _run(m, plan, A, cf, x)
     for k in range(1, p + 1):
         assert max_rel_err(full[k], ref[k], den[k]) <= 64 * k * U64
@@ -294,7 +294,7 @@ def test_timeout_is_reported_and_plan_recovers(m, kern):
     x = mi.uniform_vectors(A.n, 0)[0]
     rp, ci, vv = to_dev(A)
     plan = m.mpk_plan_create(rp, ci, vv, p, m.mpk_plan_opts_default(l2_budget_bytes=30_000, wait_timeout_us=20_000,
-                                                                     kernel=kern))
+                                                                     kernel=kern, blocked=1))
     import torch
     X = torch.from_numpy(x).cuda()
     Y = torch.empty((p + 1) * A.n, dtype=torch.float64, device="cuda")
@@ -323,3 +323,21 @@ def test_update_values_keeps_structure(m):
     den = abs_powers(B, cf, x)
     for k in range(1, p + 1):
         assert max_rel_err(got[k], ref[k], den[k]) <= 64 * k * U64
+
+
+def test_automatic_blocked_choice(m):
+    """Default plans choose between the blocked and unblocked kernel by themselves: a matrix
+    larger than the L2 cache is timed both ways on the first call, a small one runs unblocked.
+    Every call returns the unblocked kernel's values bit for bit."""
+    import torch
+    for A, p in ((mi.stencil27(96, seed=2), 4), (MATS["s27_12"], 4)):
+        x = mi.uniform_vectors(A.n, 1)[0]
+        rp, ci, vv = to_dev(A)
+        plan = m.mpk_plan_create(rp, ci, vv, p, m.mpk_plan_opts_default(assume_symmetric=1))
+        cf = BASES["newton"](p)
+        ref = _run(m, plan, A, cf, x, flags=m.MPK_UNBLOCKED)
+        first = _run(m, plan, A, cf, x)           # may time both kernels
+        again = _run(m, plan, A, cf, x)           # the cached choice
+        assert np.array_equal(first, ref) and np.array_equal(again, ref)
+        del plan
+        torch.cuda.empty_cache()
