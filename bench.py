@@ -55,6 +55,12 @@ def measured_peaks():
 # 2.07 GHz (the part's FP64 rate is 1.25 TFLOP/s nominal).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
+# DRAM bytes (read + write) of one blocked FP64 p = 4 launch of the headline matrix, from an ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum) of the same kernel on the 27-point
+# 128^3 matrix (3.066 GB), scaled by stored SELL entries (109,664,800 / 56,041,696).  Valid
+# for the kernel as captured; set to None when the kernel changes until it is captured again.
+TRAFFIC_F64_P4_BYTES = 6.00e9
+
 
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons, sampled every 100 ms while running."""
@@ -454,7 +460,8 @@ def main():
     # ---- solver and serving legs (solves/s and latency at rel. residual 1e-8)
     solver = serving = None
     if not args.no_solver:
-        solver = solver_leg(m, torch, dev)
+        solver = {"n64": solver_leg(m, torch, dev, n_edge=64, solves=5),
+                  "n128": solver_leg(m, torch, dev, n_edge=128, solves=2)}
         serving = serving_leg(m)
 
     # ---- end to end through the C ABI with pinned host buffers (copies inside the timing)
@@ -478,7 +485,10 @@ def main():
     if t_alu >= t_hbm:
         ach = flop / (kb * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                "frac": ach / FP64_PEAK_TFLOPS,
+                "traffic": TRAFFIC_F64_P4_BYTES if P_MAIN == 4 else None,
+                "traffic_note": "ncu DRAM bytes on the 128^3 case scaled by stored entries; "
+                                "algorithmic minimum %.3g bytes" % bytes_min,
                 "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
                 "kernel": "mpk_wave_kernel<double,1>",
                 "hbm_view": {"achieved_gbs": bytes_min / (kb * 1e-3) / 1e9, "peak_gbs": hbm_peak,

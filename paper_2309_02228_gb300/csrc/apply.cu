@@ -653,7 +653,10 @@ struct WaveArgs {
     uint64_t timeout_ns;
     uint32_t debug_drop;              // 1: task (chunk 0, power 1) does not publish
     uint32_t dynamic;                 // 1: tickets from the control block's dispenser
-    uint32_t kep[MPK_MAX_P + 1];      // launches so far, this one included, that ran power k
+    uint32_t *kep;                    // device: earlier launches that ran each local power k;
+                                      // the last CTA out adds this launch (powers 1..seg), so
+                                      // a captured graph can replay the launch
+    int seg;
 };
 
 __device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p) {
@@ -703,7 +706,7 @@ __global__ void __launch_bounds__(WAVE_BLOCK, (wave_min_blocks<T, NR>())) mpk_wa
             const int32_t hb = __ldg(&W.desc[t].z);
             int32_t wm = s_wm[wib][kl - 1];
             if (wm <= hb) {
-                const uint32_t mult = W.kep[kl - 1];
+                const uint32_t mult = *(volatile uint32_t *)(W.kep + kl - 1) + 1u;
                 const uint32_t *cp = W.cnt + (int64_t)(kl - 1) * W.n_cblk;
                 bool timing = false;
                 uint64_t t0 = 0;
@@ -758,7 +761,7 @@ __global__ void __launch_bounds__(WAVE_BLOCK, (wave_min_blocks<T, NR>())) mpk_wa
         t = next_ticket(t);
     }
     // every CTA gets here (waits that fail leave the task loop, they do not return); the last
-    // one resets the ticket dispenser for the next launch
+    // one resets the ticket dispenser and counts this launch for every power it ran
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -766,6 +769,7 @@ __global__ void __launch_bounds__(WAVE_BLOCK, (wave_min_blocks<T, NR>())) mpk_wa
         if (d == gridDim.x - 1) {
             W.ctrl->ticket = 0;
             W.ctrl->done_ctas = 0;
+            for (int k = 1; k <= W.seg; k++) W.kep[k] += 1u;
             __threadfence();
         }
     }
@@ -888,21 +892,22 @@ mpk_status launch_wave(mpk_plan_s *P, const SellView &A, int n_rhs, const VecSet
     const int per_sm = P->opts.ctas_per_sm > 0 ? std::min(occ, P->opts.ctas_per_sm) : occ;
     const int64_t warps = std::max<int64_t>(sch->n_tasks, 1);
     const int64_t grid = std::min<int64_t>((int64_t)P->n_sm * per_sm, ceil_div(warps, WAVE_BLOCK / 32));
-    // this launch runs local powers 1..seg once more
-    for (int k = 1; k <= seg; k++) P->kep[k] += 1u;
-    memcpy(W.kep, P->kep, sizeof(W.kep));
-    SellView a_ = A;
-    VecSet v_ = V;
-    Coefs c_ = cf;
-    int nr_ = n_rhs;
-    void *kargs[] = {&a_, &nr_, &v_, &c_, &W};
-    cudaError_t e = cudaLaunchCooperativeKernel((void *)kern, dim3((unsigned)grid), dim3(WAVE_BLOCK), kargs, 0, s);
-    if (e != cudaSuccess) {
-        for (int k = 1; k <= seg; k++) P->kep[k] -= 1u;
-        cudaGetLastError();
-        mpk_log_cuda_error(e, "cudaLaunchCooperativeKernel(mpk_wave_kernel)", __FILE__, __LINE__);
-        return MPK_ERR_CUDA;
-    }
+    W.kep = P->wave_kep.as<uint32_t>();
+    W.seg = seg;
+    // cooperative (all CTAs co-resident, which the ticket order relies on); launched through
+    // cudaLaunchKernelEx so that stream capture can record it
+    cudaLaunchConfig_t lc;
+    memset(&lc, 0, sizeof(lc));
+    lc.gridDim = dim3((unsigned)grid);
+    lc.blockDim = dim3(WAVE_BLOCK);
+    lc.dynamicSmemBytes = 0;
+    lc.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    MPK_CUDA(cudaLaunchKernelEx(&lc, kern, A, n_rhs, V, cf, W));
     return MPK_OK;
 }
 
@@ -1268,7 +1273,7 @@ extern "C" mpk_status mpk_plan_sync(mpk_plan_t P, cudaStream_t s) {
         uint32_t zero[2] = {0, 0};
         MPK_CUDA(cudaMemcpy(&P->ctrl.as<MpkCtrl>()->error, zero, 8, cudaMemcpyHostToDevice));
         if (P->wave_cnt.p) MPK_CUDA(cudaMemset(P->wave_cnt.p, 0, P->wave_cnt.bytes));
-        memset(P->kep, 0, sizeof(P->kep));
+        if (P->wave_kep.p) MPK_CUDA(cudaMemset(P->wave_kep.p, 0, P->wave_kep.bytes));
         return MPK_ERR_TIMEOUT;
     }
     return MPK_OK;

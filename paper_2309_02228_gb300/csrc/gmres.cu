@@ -164,23 +164,33 @@ __global__ void __launch_bounds__(256) gram_kernel(const T *X, int64_t ldx, int 
             }
         }
     }
-    // combine the groups of the CTA in FP64 (fixed order), one partial per CTA
+    // combine the groups of the CTA: every thread parks its tile in shared memory, then one
+    // thread per output adds the groups in FP64 in group order; one partial per CTA
     __syncthreads();
-    double *red = reinterpret_cast<double *>(gsm);      // K x S doubles
-    const int KS = K * S;
-    for (int e = threadIdx.x; e < KS; e += blockDim.x) red[e] = 0.0;
-    __syncthreads();
-    for (int g = 0; g < ngroup; g++) {
-        if (active && group == g) {
+    T *park = reinterpret_cast<T *>(gsm);               // [group][b][tile * 4 + a]
+    const int KP = ntile * 4;
+    if (active) {
 #pragma unroll
-            for (int a = 0; a < 4; a++)
+        for (int a = 0; a < 4; a++)
 #pragma unroll
-                for (int b = 0; b < SB; b++)
-                    if (b < S && tile * 4 + a < K) red[b * K + tile * 4 + a] += (double)acc[a][b];
-        }
-        __syncthreads();
+            for (int b = 0; b < SB; b++)
+                if (b < S) park[((int64_t)group * S + b) * KP + tile * 4 + a] = acc[a][b];
     }
-    for (int e = threadIdx.x; e < KS; e += blockDim.x) part[(int64_t)blockIdx.x * KS + e] = red[e];
+    __syncthreads();
+    const int KS = K * S;
+    for (int e = threadIdx.x; e < KS; e += blockDim.x) {
+        const int a = e % K, b = e / K;
+        double t = 0.0;
+        for (int g = 0; g < ngroup; g++) t += (double)park[((int64_t)g * S + b) * KP + a];
+        part[(int64_t)blockIdx.x * KS + e] = t;
+    }
+}
+
+// shared memory of one gram_kernel launch: the staged chunk, or the parked tiles
+template <typename T> static size_t gram_smem(int K, int S) {
+    const int ntile = (K + 3) / 4;
+    const int ngroup = std::max(1, 256 / ntile);
+    return std::max((size_t)GR * (K + S) * sizeof(T), (size_t)ngroup * S * ntile * 4 * sizeof(T));
 }
 
 // ------------------------------------------------------------------------------------------
@@ -688,7 +698,7 @@ struct Solver {
         ldv = (n + 31) / 32 * 32;
         const int m = o.restart;
         MPK_TRY(V.alloc((size_t)(m + 1) * ldv * sizeof(T)));
-        gram_grid = 2 * P->n_sm;
+        gram_grid = 4 * P->n_sm;
         upd_grid = 4 * P->n_sm;
         const int maxK = m + 1 + SMAX;
         MPK_TRY(part.alloc((size_t)std::max(gram_grid, upd_grid) * maxK * SMAX * sizeof(double) + 4096));
@@ -723,9 +733,9 @@ struct Solver {
 
     // G (K x S) = X^T Y
     template <int SB> mpk_status gram_sb(const T *X, int K, const T *Y, int S, double *Gout) {
-        const size_t sm = std::max((size_t)GR * (K + S) * sizeof(T), (size_t)K * S * sizeof(double));
+        const size_t sm = gram_smem<T>(K, S);
         // one fixed maximum for every caller (the attribute is shared by all threads)
-        constexpr int smax = (int)(GR * (MMAX + 1 + 2 * SMAX) * sizeof(T));
+        constexpr int smax = 160 * 1024;
         if (sm > (size_t)smax) return MPK_ERR_ARG;
         MPK_CUDA(cudaFuncSetAttribute(gram_kernel<T, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
         const int g = (int)std::min<int64_t>(gram_grid, ceil_div(n, GR));
@@ -939,7 +949,7 @@ extern "C" mpk_status mpk_gmres_opts_default(mpk_gmres_opts *o) {
     o->restart = 48;
     o->tol = 1e-8;
     o->inner_tol = 1e-5;
-    o->max_outer = 50;
+    o->max_outer = 200;
     o->inner_cycles = 1;
     o->max_iters = 100000;
     o->basis = MPK_F32;

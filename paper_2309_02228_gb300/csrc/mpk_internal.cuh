@@ -136,7 +136,7 @@ struct mpk_plan_s {
     std::vector<int32_t> h_wait_blk;  // last block a chunk's task waits for
     std::vector<int32_t> h_dep_hi_blk;// dep_hi rounded up to the end of its block
     DevBuf cblk_size, wave_cnt;       // chunks per block; counters [(k) * n_cblk + b]
-    uint32_t kep[MPK_MAX_P + 1] = {};
+    DevBuf wave_kep;                  // uint32 per local power: launches that ran it
     int64_t wave_slack = 0;
     // automatic blocked / unblocked choice per (precision, p, n_rhs) (opts.blocked = -1)
     std::map<int, bool> auto_blocked;

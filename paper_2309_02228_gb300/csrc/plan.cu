@@ -1044,7 +1044,8 @@ static mpk_status plan_create_impl(const mpk_csr *A, int32_t p_max, const mpk_pl
         MPK_TRY(upload(P->cblk_size, h_cbs, s));
         MPK_TRY(P->wave_cnt.alloc((size_t)(P->p_blk + 1) * std::max(P->n_cblk, 1) * 4));
         MPK_CUDA(cudaMemsetAsync(P->wave_cnt.p, 0, P->wave_cnt.bytes, s));
-        memset(P->kep, 0, sizeof(P->kep));
+        MPK_TRY(P->wave_kep.alloc((MPK_MAX_P + 1) * 4));
+        MPK_CUDA(cudaMemsetAsync(P->wave_kep.p, 0, P->wave_kep.bytes, s));
     }
     MPK_TRY(P->prefix.alloc((MPK_MAX_P + 2) * sizeof(unsigned long long)));
     MPK_CUDA(cudaMemsetAsync(P->prefix.p, 0, P->prefix.bytes, s));

@@ -341,3 +341,32 @@ def test_automatic_blocked_choice(m):
         assert np.array_equal(first, ref) and np.array_equal(again, ref)
         del plan
         torch.cuda.empty_cache()
+
+
+def test_graph_capture_replays_the_blocked_kernel(m):
+    """A blocked mpk_apply captured in a CUDA graph (after one ordinary call, which builds the
+    schedule) replays correctly: the per-power launch counts the dependency waits compare
+    against live in device memory, so each replay is a fresh launch.  Each replay's result
+    equals the unblocked kernel's bit for bit."""
+    import torch
+    A = MATS["s27_12"]
+    p = 5
+    cf = BASES["newton"](p)
+    rp, ci, vv = to_dev(A)
+    plan = m.mpk_plan_create(rp, ci, vv, p, m.mpk_plan_opts_default(l2_budget_bytes=40_000, blocked=1,
+                                                                     slack_tasks=5))
+    X = torch.from_numpy(mi.uniform_vectors(A.n, 2)[0]).cuda()
+    Y = torch.empty((p + 1) * A.n, dtype=torch.float64, device="cuda")
+    m.mpk_apply(plan, cf, X, Y)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, capture_error_mode="relaxed"):
+        m.mpk_apply(plan, cf, X, Y)
+    for seed in (3, 4, 5):
+        xs = mi.uniform_vectors(A.n, seed)[0]
+        X.copy_(torch.from_numpy(xs))
+        g.replay()
+        torch.cuda.synchronize()
+        assert m.mpk_plan_sync(plan) == m.MPK_OK
+        ref = _run(m, plan, A, cf, xs, flags=m.MPK_UNBLOCKED)
+        assert np.array_equal(Y.cpu().numpy().reshape(p + 1, -1), ref)
