@@ -294,6 +294,57 @@ def run_profile(args, m, torch, local):
     return 0 if status == m.MPK_OK else 1
 
 
+def block_mpk_leg(m, torch, dev, hbm_peak, reps=20):
+    """Block MPK as an AMG polynomial smoother: 27-point 128^3 matrix (seed 5) in FP32,
+    Chebyshev basis p = 6 on [0.1, 52], n_rhs = 8, 16, 32 right-hand sides interleaved in level
+    order (X ~ U[-1,1), seed 6).  Each variant is captured once in a CUDA graph and replayed;
+    modes: all p+1 powers out (basis) and the final polynomial sum_k y_k only (smoother).
+    GFLOP/s = 2 nnz p n_rhs / t; effective GB/s = the algorithmic minimum bytes / t."""
+    A = mi.stencil27(128, seed=5)
+    n, nnz, p = A.n, A.nnz, 6
+    rp = torch.from_numpy(A.row_ptr).to(dev)
+    ci = torch.from_numpy(A.col).to(dev)
+    vv = torch.from_numpy(A.val.astype(np.float32)).to(dev)
+    co = m.mpk_coeffs_chebyshev(0.1, 52.0, p)
+    cog = m.Coeffs(co.a, co.b, co.c, gamma=np.ones(p + 1))
+    M = 4 * (n + 1) + nnz * 8
+    out = {"workload": "27-point 128^3 FP32 (seed 5), Chebyshev p=6 on [0.1,52], X ~ U[-1,1) seed 6, "
+                       "interleaved level-order I/O, one graph-captured call per step",
+           "n": n, "nnz": nnz, "p": p}
+    plans = {}
+    for mode in ("blocked", "unblocked", "auto"):
+        opts = m.mpk_plan_opts_default(assume_symmetric=1, p_blk=p,
+                                       blocked={"blocked": 1, "unblocked": 0, "auto": -1}[mode])
+        plans[mode] = m.mpk_plan_create(rp, ci, vv, p, opts)
+    for n_rhs in (8, 16, 32):
+        X = torch.from_numpy(mi.uniform_vectors(n, 6, n_rhs).T.copy()).to(dev, torch.float32)   # n x n_rhs
+        Y = torch.empty((p + 1) * n * n_rhs, dtype=torch.float32, device=dev)
+        res = {}
+        for final in (False, True):
+            fl = m.MPK_PERMUTED_IO | m.MPK_RHS_INTERLEAVED | (m.MPK_FINAL_ONLY if final else 0)
+            cc = cog if final else co
+            bmin = M + 4 * n * n_rhs * (2 if final else p + 2)
+            for mode, plan in plans.items():
+                call = lambda: m.mpk_apply(plan, cc, X, Y, n_rhs=n_rhs, flags=fl)
+                call()                                  # schedule, automatic choice
+                torch.cuda.synchronize()
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, capture_error_mode="relaxed"):
+                    call()
+                g.replay()
+                torch.cuda.synchronize()
+                ms = time_stream(g.replay, reps, torch)
+                assert m.mpk_plan_sync(plan) == m.MPK_OK
+                res["%s_%s" % ("final" if final else "basis", mode)] = {
+                    "ms": ms, "gflops": 2.0 * nnz * p * n_rhs / ms / 1e6,
+                    "eff_gbs": bmin / ms / 1e6, "eff_frac": bmin / ms / 1e6 / hbm_peak}
+        out["n_rhs%d" % n_rhs] = res
+        del X, Y
+    del plans
+    torch.cuda.empty_cache()
+    return out
+
+
 def time_stream(fn, reps, torch):
     """Average ms per call of fn() on the current stream, CUDA events on that stream."""
     st = torch.cuda.current_stream()
@@ -316,6 +367,7 @@ def main():
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--no-solver", action="store_true", help="skip the solver and serving legs")
+    ap.add_argument("--no-block", action="store_true", help="skip the n_rhs block MPK leg")
     ap.add_argument("--profile", action="store_true",
                     help="profiling run: plan, then per repetition one blocked and one unblocked "
                          "call (level-order I/O) on the 27-point matrix of --profile-n")
@@ -463,6 +515,9 @@ def main():
         solver = {"n64": solver_leg(m, torch, dev, n_edge=64, solves=5),
                   "n128": solver_leg(m, torch, dev, n_edge=128, solves=2)}
         serving = serving_leg(m)
+    block = None
+    if not args.no_block:
+        block = block_mpk_leg(m, torch, dev, hbm_peak)
 
     # ---- end to end through the C ABI with pinned host buffers (copies inside the timing)
     Xh = torch.from_numpy(x.copy()).pin_memory()
@@ -520,6 +575,7 @@ def main():
         "speedup_vs_pxspmv": sweep["p%d" % P_MAIN]["speedup"],
         "sweep": sweep, "kernel_only": kern, "fp32": fp32, "plan_ms": plan_ms,
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "solver": solver, "serving": serving,
+        "block_mpk": block,
         "gpu_launches": launches_per_step * args.steps, "clocks": clk,
     }
     if rank == 0:

@@ -107,7 +107,7 @@ template <typename T, int NR> struct RowBatch {
 // Global: column and value loads of a batch first, then the gathers, then the FMAs.
 // Padding entries (column -1) gather the row's own element and are dropped by a select; a
 // partial last batch is predicated, never split into dependent single steps.
-template <typename T, int NR, bool SM, bool SV>
+template <typename T, int NR, bool SM, bool SV, int BGMAX = 8>
 __device__ __forceinline__ void row_sum(const int32_t *colp, const T *valp, int32_t L, int32_t row,
                                         const T *y1, int n_rhs, int q0, T (&acc)[NR]) {
     constexpr int BT = RowBatch<T, NR>::B;
@@ -152,7 +152,7 @@ __device__ __forceinline__ void row_sum(const int32_t *colp, const T *valp, int3
                 }
             }
         } else {
-            constexpr int BG = BT > 8 ? 8 : BT;   // register budget of the global path
+            constexpr int BG = BT > BGMAX ? BGMAX : BT;   // register budget of the global path
 #pragma unroll
             for (int j2 = 0; j2 < BT; j2 += BG) {
                 int32_t cc[BG];
@@ -232,10 +232,138 @@ __device__ __forceinline__ void row_finish(const T (&acc)[NR], int32_t row, int 
 
 // Power k of the rows of slice s.  Thread `lane` owns row slice_row[s] + lane.  colp / valp
 // point at the slice's first entry (in global memory, or in a staged shared-memory copy).
-template <typename T, int NR, bool SM, bool SV>
+// Two slices per warp at once, one right-hand side: for short rows (a 7-point stencil
+// stores 7 entries per row) a single slice is one short chain of dependent loads, so a warp
+// interleaves the batches of two slices to keep twice the loads in flight.  Each row's sum
+// is the same as in row_sum (ascending entries, FP64 even/odd partial sums), so the values
+// are identical.
+template <typename T>
+__device__ __forceinline__ void slice_pair_power(const SellView &A, int64_t sa, int64_t sb, int lane,
+                                                 const VecSet &V, int k, const Coefs &cf) {
+    constexpr bool TWO = sizeof(T) == 8;
+    constexpr int BG = 8;
+    const T *gval = reinterpret_cast<const T *>(A.val);
+    const int32_t ra0 = __ldg(A.slice_row + sa), ra1 = __ldg(A.slice_row + sa + 1);
+    const int32_t rb0 = __ldg(A.slice_row + sb), rb1 = __ldg(A.slice_row + sb + 1);
+    const int32_t La = __ldg(A.slice_len + sa), Lb = __ldg(A.slice_len + sb);
+    const long long oa = 32ll * __ldg(A.slice_ptr + sa) + lane, ob = 32ll * __ldg(A.slice_ptr + sb) + lane;
+    const int32_t rowa = ra0 + lane, rowb = rb0 + lane;
+    const bool va = rowa < ra1, vb = rowb < rb1;
+    const int32_t La_ = va ? La : 0, Lb_ = vb ? Lb : 0;
+    const T *y1 = vec_ro<T>(V, k - 1);
+    T a0 = 0, a1 = 0, b0 = 0, b1 = 0;
+    const int32_t Lm = La_ > Lb_ ? La_ : Lb_;
+    for (int32_t j = 0; j < Lm; j += BG) {
+        int32_t ca[BG], cb[BG];
+        T wa[BG], wb[BG];
+#pragma unroll
+        for (int u = 0; u < BG; u++) {
+            const bool ia = j + u < La_, ib = j + u < Lb_;
+            ca[u] = ia ? __ldg(A.col + oa + 32 * (j + u)) : -1;
+            wa[u] = ia ? __ldg(gval + oa + 32 * (j + u)) : (T)0;
+            cb[u] = ib ? __ldg(A.col + ob + 32 * (j + u)) : -1;
+            wb[u] = ib ? __ldg(gval + ob + 32 * (j + u)) : (T)0;
+        }
+        T xa[BG], xb[BG];
+#pragma unroll
+        for (int u = 0; u < BG; u++) {
+            xa[u] = y1[ca[u] >= 0 ? ca[u] : ra0];
+            xb[u] = y1[cb[u] >= 0 ? cb[u] : rb0];
+        }
+#pragma unroll
+        for (int u = 0; u < BG; u++) {
+            if (TWO && (u & 1)) {
+                const T fa = fma(wa[u], xa[u], a1), fb = fma(wb[u], xb[u], b1);
+                a1 = ca[u] >= 0 ? fa : a1;
+                b1 = cb[u] >= 0 ? fb : b1;
+            } else {
+                const T fa = fma(wa[u], xa[u], a0), fb = fma(wb[u], xb[u], b0);
+                a0 = ca[u] >= 0 ? fa : a0;
+                b0 = cb[u] >= 0 ? fb : b0;
+            }
+        }
+    }
+    if (TWO) {
+        a0 += a1;
+        b0 += b1;
+    }
+    T acc[1];
+    if (va) {
+        acc[0] = a0;
+        row_finish<T, 1>(acc, rowa, 1, 0, V, k, cf);
+    }
+    if (vb) {
+        acc[0] = b0;
+        row_finish<T, 1>(acc, rowb, 1, 0, V, k, cf);
+    }
+}
+
+// Wide blocks of right-hand sides: LPR lanes share a row, each holding NRL = NR / LPR
+// consecutive right-hand sides (one 16-byte vector), so the gathers of a row's entry are
+// contiguous across its lanes; a warp covers 32 / LPR rows per pass and LPR passes per slice.
+// Per (row, right-hand side) the sum runs over the entries in ascending order with one FMA
+// each, exactly as in the one-row-per-lane path, so both give identical values.
+template <typename T, int NR> struct RowGroup {
+    static constexpr int VW = 16 / (int)sizeof(T);                 // elements per 16 bytes
+    static constexpr int LPR = NR / VW < 8 ? NR / VW : 8;           // lanes per row
+    static constexpr int NRL = NR / LPR;                            // right-hand sides per lane
+    static constexpr bool USE = NR / VW >= 4;   // measured: 8 FP32 rhs run faster one row per lane
+};
+
+template <typename T, int NR>
+__device__ __forceinline__ void slice_power_grouped(const SellView &A, int64_t s, const int32_t *colp,
+                                                    const T *valp, int lane, int n_rhs, const VecSet &V,
+                                                    int k, const Coefs &cf) {
+    constexpr int LPR = RowGroup<T, NR>::LPR, NRL = RowGroup<T, NR>::NRL, G = 32 / LPR;
+    constexpr int B = 8;   // entries whose loads are in flight together
+    const int32_t r0 = __ldg(A.slice_row + s), r1 = __ldg(A.slice_row + s + 1);
+    const int32_t L = __ldg(A.slice_len + s);
+    const T *y1 = vec_ro<T>(V, k - 1);
+    const int sub = lane / LPR, part = lane % LPR;
+    for (int q0 = 0; q0 < n_rhs; q0 += NR) {
+        const int qa = q0 + part * NRL;
+#pragma unroll 1
+        for (int pass = 0; pass < LPR; pass++) {
+            const int ris = pass * G + sub;                 // row inside the slice
+            const int32_t row = r0 + ris;
+            if (r0 + pass * G >= r1) break;                 // the rest of the slice is empty
+            T acc[NRL];
+#pragma unroll
+            for (int q = 0; q < NRL; q++) acc[q] = (T)0;
+            for (int32_t j = 0; j < L; j += B) {
+                int32_t cc[B];
+                T vv[B];
+#pragma unroll
+                for (int u = 0; u < B; u++) {
+                    const bool in = j + u < L;
+                    cc[u] = in ? __ldg(colp + 32 * (j + u) + ris) : -1;
+                    vv[u] = in ? __ldg(valp + 32 * (j + u) + ris) : (T)0;
+                }
+                T xx[B][NRL];
+#pragma unroll
+                for (int u = 0; u < B; u++)
+                    VecLoad<T, NRL>::ld(y1 + (int64_t)(cc[u] >= 0 ? cc[u] : r0) * n_rhs + qa, xx[u]);
+#pragma unroll
+                for (int u = 0; u < B; u++)
+#pragma unroll
+                    for (int q = 0; q < NRL; q++) {
+                        const T f = fma(vv[u], xx[u][q], acc[q]);
+                        acc[q] = cc[u] >= 0 ? f : acc[q];
+                    }
+            }
+            if (row < r1) row_finish<T, NRL>(acc, row, n_rhs, qa, V, k, cf);
+        }
+    }
+}
+
+template <typename T, int NR, bool SM, bool SV, int BGMAX = 8>
 __device__ __forceinline__ void slice_power(const SellView &A, int64_t s, const int32_t *colp,
                                             const T *valp, int lane, int n_rhs, const VecSet &V,
                                             int k, const Coefs &cf) {
+    if constexpr (!SM && RowGroup<T, NR>::USE) {
+        slice_power_grouped<T, NR>(A, s, colp, valp, lane, n_rhs, V, k, cf);
+        return;
+    }
     const int32_t r0 = __ldg(A.slice_row + s), r1 = __ldg(A.slice_row + s + 1);
     const int32_t row = r0 + lane;
     if (row >= r1) return;
@@ -243,7 +371,7 @@ __device__ __forceinline__ void slice_power(const SellView &A, int64_t s, const 
     const T *y1 = vec_ro<T>(V, k - 1);
     for (int q0 = 0; q0 < n_rhs; q0 += NR) {
         T acc[NR];
-        row_sum<T, NR, SM, SV>(colp + lane, valp + lane, L, row, y1, n_rhs, q0, acc);
+        row_sum<T, NR, SM, SV, BGMAX>(colp + lane, valp + lane, L, row, y1, n_rhs, q0, acc);
         row_finish<T, NR>(acc, row, n_rhs, q0, V, k, cf);
     }
 }
@@ -254,11 +382,21 @@ __device__ __forceinline__ void slice_power(const SellView &A, int64_t s, const 
 // ------------------------------------------------------------------------------------------
 template <typename T, int NR>
 __global__ void __launch_bounds__(256) mpk_power_kernel(SellView A, int64_t n_slices, int n_rhs,
-                                                        VecSet V, int k, Coefs cf) {
+                                                        VecSet V, int k, Coefs cf, int pairs) {
     const int lane = threadIdx.x & 31;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const T *gval = reinterpret_cast<const T *>(A.val);
+    if constexpr (NR == 1) {
+        if (pairs) {
+            for (int64_t s = 2 * w0; s < n_slices; s += 2 * nw) {
+                if (s + 1 < n_slices) slice_pair_power<T>(A, s, s + 1, lane, V, k, cf);
+                else slice_power<T, 1, false, false>(A, s, A.col + 32ll * __ldg(A.slice_ptr + s),
+                                                     gval + 32ll * __ldg(A.slice_ptr + s), lane, 1, V, k, cf);
+            }
+            return;
+        }
+    }
     for (int64_t s = w0; s < n_slices; s += nw) {
         const long long gofs = 32ll * __ldg(A.slice_ptr + s);
         slice_power<T, NR, false, false>(A, s, A.col + gofs, gval + gofs, lane, n_rhs, V, k, cf);
@@ -653,6 +791,7 @@ struct WaveArgs {
     uint64_t timeout_ns;
     uint32_t debug_drop;              // 1: task (chunk 0, power 1) does not publish
     uint32_t dynamic;                 // 1: tickets from the control block's dispenser
+    int pairs;                        // 1: a warp runs two slices at once (short rows)
     uint32_t *kep;                    // device: earlier launches that ran each local power k;
                                       // the last CTA out adds this launch (powers 1..seg), so
                                       // a captured graph can replay the launch
@@ -671,15 +810,16 @@ __device__ __forceinline__ void red_release_add_u32(uint32_t *p, uint32_t v) {
 
 static constexpr int WAVE_BLOCK = 256;
 // resident CTAs per SM the warp-task kernel is compiled for: the row function of one or two
-// FP32 right-hand sides fits 40 registers (48 warps per SM), FP64 fits 48; wider blocks of
-// right-hand sides keep 64
+// FP32 right-hand sides and the grouped row function of wide blocks fit 40 registers (48
+// warps per SM), single-rhs FP64 fits 48; the rest keep 64
 template <typename T, int NR> constexpr int wave_min_blocks() {
-    return sizeof(T) == 4 ? (NR <= 2 ? 6 : 4) : (NR == 1 ? 5 : 4);
+    return (NR >= 4 * (16 / (int)sizeof(T))) ? 6 : (sizeof(T) == 4 ? (NR <= 2 ? 6 : 4) : (NR == 1 ? 5 : 4));
 }
 
 template <typename T, int NR>
-__global__ void __launch_bounds__(WAVE_BLOCK, (wave_min_blocks<T, NR>())) mpk_wave_kernel(SellView A, int n_rhs, VecSet V,
-                                                                                Coefs cf, WaveArgs W) {
+__global__ void __launch_bounds__(WAVE_BLOCK, (wave_min_blocks<T, NR>())) mpk_wave_kernel(
+    SellView A, int n_rhs, VecSet V, Coefs cf, WaveArgs W) {
+    constexpr int BGMAX = 8;
     __shared__ int32_t s_wm[WAVE_BLOCK / 32][MPK_MAX_P + 1];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     for (int i = lane; i <= MPK_MAX_P; i += 32) s_wm[wib][i] = 0;
@@ -750,9 +890,14 @@ __global__ void __launch_bounds__(WAVE_BLOCK, (wave_min_blocks<T, NR>())) mpk_wa
         }
         const int k = W.k0 + kl;
         const int32_t s1 = __ldg(W.chunk_slice + c + 1);
-        for (int32_t s = __ldg(W.chunk_slice + c); s < s1; s++) {
+        int32_t s = __ldg(W.chunk_slice + c);
+        if constexpr (NR == 1) {
+            if (W.pairs)
+                for (; s + 1 < s1; s += 2) slice_pair_power<T>(A, s, s + 1, lane, V, k, cf);
+        }
+        for (; s < s1; s++) {
             const long long gofs = 32ll * __ldg(A.slice_ptr + s);
-            slice_power<T, NR, false, false>(A, s, A.col + gofs, gval + gofs, lane, n_rhs, V, k, cf);
+            slice_power<T, NR, false, false, BGMAX>(A, s, A.col + gofs, gval + gofs, lane, n_rhs, V, k, cf);
         }
         // publish: the warp barrier orders every lane's results before lane 0's release add
         __syncwarp();
@@ -894,6 +1039,7 @@ mpk_status launch_wave(mpk_plan_s *P, const SellView &A, int n_rhs, const VecSet
     const int64_t grid = std::min<int64_t>((int64_t)P->n_sm * per_sm, ceil_div(warps, WAVE_BLOCK / 32));
     W.kep = P->wave_kep.as<uint32_t>();
     W.seg = seg;
+    W.pairs = P->short_rows ? 1 : 0;
     // cooperative (all CTAs co-resident, which the ticket order relies on); launched through
     // cudaLaunchKernelEx so that stream capture can record it
     cudaLaunchConfig_t lc;
@@ -916,8 +1062,9 @@ mpk_status launch_powers(mpk_plan_s *P, const SellView &A, int n_rhs, const VecS
                          const Coefs &cf, int p, bool blocked, uint32_t flags, cudaStream_t s) {
     if (!blocked) {
         // p back-to-back SpMV launches (Alg. 1)
-        const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(std::max<int64_t>(P->n_slices, 1), 8), 1 << 30);
-        for (int k = 1; k <= p; k++) mpk_power_kernel<T, NR><<<grid, 256, 0, s>>>(A, P->n_slices, n_rhs, V, k, cf);
+        const int pairs = (NR == 1 && P->short_rows) ? 1 : 0;
+        const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(std::max<int64_t>(P->n_slices, 1), pairs ? 16 : 8), 1 << 30);
+        for (int k = 1; k <= p; k++) mpk_power_kernel<T, NR><<<grid, 256, 0, s>>>(A, P->n_slices, n_rhs, V, k, cf, pairs);
         MPK_CUDA(cudaGetLastError());
         return MPK_OK;
     }

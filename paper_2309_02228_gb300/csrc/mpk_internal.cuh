@@ -131,6 +131,7 @@ struct mpk_plan_s {
     // that ran local power k, block b's counter reads j * cblk_size[b] (mod 2^32).
     int wave = 1;                     // 1: warp-task kernel, 0: CTA-task kernel
     int wave_dynamic = 1;             // warp tasks: 1 dynamic tickets, 0 static round robin
+    int short_rows = 0;               // stored rows average <= 12 entries: two slices per warp
     int32_t n_cblk = 0;
     std::vector<int32_t> h_chunk_blk; // counter block of each chunk
     std::vector<int32_t> h_wait_blk;  // last block a chunk's task waits for

@@ -1056,6 +1056,7 @@ static mpk_status plan_create_impl(const mpk_csr *A, int32_t p_max, const mpk_pl
     // lag-greedy slack: about the tasks in flight (two slots per resident CTA)
     P->sched_slack = o.slack_tasks > 0 ? o.slack_tasks : 2ll * P->n_sm * P->ctas_per_sm;
     P->wave = o.kernel == 1 ? 0 : 1;
+    P->short_rows = (P->n_slices > 0 && P->sell_nnz <= 12ll * 32 * P->n_slices) ? 1 : 0;
     P->wave_dynamic = o.kernel == 2 ? 0 : 1;
     // warp tasks: four tasks per resident warp (32 per SM) - measured best on the 27-point
     // 160^3 matrix in FP32 and FP64; smaller slack makes warps wait for their dependencies
