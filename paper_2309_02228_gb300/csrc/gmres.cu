@@ -95,103 +95,73 @@ static inline unsigned redp_grid(int m) { return (unsigned)((m + REDP_WARPS - 1)
 
 // ------------------------------------------------------------------------------------------
 // Tall-skinny Gram G = X^T Y (X: n x K, Y: n x S, column-major), G col-major K x S.
-// CTA: rows in chunks of 64 staged in shared memory; thread (tile, group) accumulates a 4 x S
-// micro-tile over the rows of its group in the basis precision; per-CTA partials in FP64.
+// A warp owns a tile of CT columns of X and streams 32 rows per step straight from global
+// memory (lane l takes row r0 + l: every column load is one coalesced 128-byte line); each lane
+// keeps the CT x S products of its rows in registers (64 FMAs per CT + S loads).  With fewer
+// tiles than warps, the warps of a tile split the steps.  Sums: FP32 per lane over its rows,
+// an FP32 shuffle tree over the 32 lanes, FP64 over the warps of a tile (fixed order) and
+// over CTAs (one partial per CTA, reduced by reduce_partials_kernel).
 // ------------------------------------------------------------------------------------------
-constexpr int GR = 64;   // rows per chunk
+constexpr int GRAM_RANGE = 2048;       // rows a CTA takes per visit
 
 template <typename T, int SB>
-__global__ void __launch_bounds__(256) gram_kernel(const T *X, int64_t ldx, int K, const T *Y,
-                                                   int64_t ldy, int S, int64_t n, double *part) {
-    extern __shared__ __align__(16) unsigned char gsm[];
-    T *xs = reinterpret_cast<T *>(gsm);                 // GR x K   (row-major)
-    T *ys = xs + GR * K;                                // GR x S
-    const int ntile = (K + 3) / 4;
-    const int ngroup = max(1, (int)blockDim.x / ntile);
-    const int tile = threadIdx.x % ntile, group = threadIdx.x / ntile;
-    const bool active = group < ngroup && threadIdx.x < ngroup * ntile;
-    T acc[4][SB];
+__global__ void __launch_bounds__(256, 2) gram_kernel(const T *X, int64_t ldx, int K, const T *Y,
+                                                      int64_t ldy, int S, int64_t n, double *part) {
+    constexpr int ACC = sizeof(T) == 4 ? 64 : 32;   // accumulators per lane
+    constexpr int CT = ACC / SB;                     // X columns per tile
+    // per warp group: slot[rpart][a][b] (a < K, b < S); rsplit * K * S <= 8 * ACC fits
+    __shared__ double slot[(MMAX + 1 + SMAX) * SMAX];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ntiles = (K + CT - 1) / CT;
+    const bool many = ntiles >= 8;
+    const int rsplit = many ? 1 : 8 / ntiles;        // warps per tile
+    const int active = many ? 8 : ntiles * rsplit;
+    const int rpart = many ? 0 : warp / ntiles;
+    if (warp < active) {
+        for (int tile = many ? warp : warp % ntiles; tile < ntiles; tile += many ? 8 : ntiles) {
+            const int c0 = tile * CT;
+            T acc[CT][SB];
 #pragma unroll
-    for (int a = 0; a < 4; a++)
+            for (int a = 0; a < CT; a++)
 #pragma unroll
-        for (int b = 0; b < SB; b++) acc[a][b] = (T)0;
-    for (int64_t r0 = (int64_t)blockIdx.x * GR; r0 < n; r0 += (int64_t)gridDim.x * GR) {
-        const int rows = (int)((n - r0) < (int64_t)GR ? (n - r0) : (int64_t)GR);
-        __syncthreads();
-        // staging: eight independent loads per thread in flight before the stores
-        for (int e0 = threadIdx.x; e0 < GR * K; e0 += 8 * blockDim.x) {
-            T v[8];
+                for (int b = 0; b < SB; b++) acc[a][b] = (T)0;
+            for (int64_t base = (int64_t)blockIdx.x * GRAM_RANGE; base < n; base += (int64_t)gridDim.x * GRAM_RANGE) {
+                for (int st = rpart; st < GRAM_RANGE / 32; st += rsplit) {
+                    if (base + st * 32 >= n) break;
+                    const int64_t r = base + st * 32 + lane;
+                    const bool in = r < n;
+                    T xv[CT], yv[SB];
 #pragma unroll
-            for (int u = 0; u < 8; u++) {
-                const int e = e0 + u * blockDim.x;
-                const int c = e / GR, r = e % GR;
-                v[u] = (e < GR * K && r < rows) ? X[(int64_t)c * ldx + r0 + r] : (T)0;
-            }
+                    for (int a = 0; a < CT; a++) xv[a] = (in && c0 + a < K) ? X[(int64_t)(c0 + a) * ldx + r] : (T)0;
 #pragma unroll
-            for (int u = 0; u < 8; u++) {
-                const int e = e0 + u * blockDim.x;
-                if (e < GR * K) xs[(e % GR) * K + e / GR] = v[u];
-            }
-        }
-        for (int e0 = threadIdx.x; e0 < GR * S; e0 += 8 * blockDim.x) {
-            T v[8];
+                    for (int b = 0; b < SB; b++) yv[b] = (in && b < S) ? Y[(int64_t)b * ldy + r] : (T)0;
 #pragma unroll
-            for (int u = 0; u < 8; u++) {
-                const int e = e0 + u * blockDim.x;
-                const int c = e / GR, r = e % GR;
-                v[u] = (e < GR * S && r < rows) ? Y[(int64_t)c * ldy + r0 + r] : (T)0;
-            }
+                    for (int a = 0; a < CT; a++)
 #pragma unroll
-            for (int u = 0; u < 8; u++) {
-                const int e = e0 + u * blockDim.x;
-                if (e < GR * S) ys[(e % GR) * S + e / GR] = v[u];
-            }
-        }
-        __syncthreads();
-        if (active) {
-            for (int r = group; r < rows; r += ngroup) {
-                T xv[4];
-#pragma unroll
-                for (int a = 0; a < 4; a++) xv[a] = (tile * 4 + a < K) ? xs[r * K + tile * 4 + a] : (T)0;
-#pragma unroll
-                for (int b = 0; b < SB; b++) {
-                    if (b < S) {
-                        const T yv = ys[r * S + b];
-#pragma unroll
-                        for (int a = 0; a < 4; a++) acc[a][b] = fma(xv[a], yv, acc[a][b]);
-                    }
+                        for (int b = 0; b < SB; b++) acc[a][b] = fma(xv[a], yv[b], acc[a][b]);
                 }
             }
+#pragma unroll
+            for (int a = 0; a < CT; a++)
+#pragma unroll
+                for (int b = 0; b < SB; b++) {
+                    T v = acc[a][b];
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    if (lane == 0 && c0 + a < K && b < S) slot[((int64_t)rpart * K + c0 + a) * S + b] = (double)v;
+                }
         }
-    }
-    // combine the groups of the CTA: every thread parks its tile in shared memory, then one
-    // thread per output adds the groups in FP64 in group order; one partial per CTA
-    __syncthreads();
-    T *park = reinterpret_cast<T *>(gsm);               // [group][b][tile * 4 + a]
-    const int KP = ntile * 4;
-    if (active) {
-#pragma unroll
-        for (int a = 0; a < 4; a++)
-#pragma unroll
-            for (int b = 0; b < SB; b++)
-                if (b < S) park[((int64_t)group * S + b) * KP + tile * 4 + a] = acc[a][b];
     }
     __syncthreads();
     const int KS = K * S;
-    for (int e = threadIdx.x; e < KS; e += blockDim.x) {
+    for (int e = tid; e < KS; e += 256) {
         const int a = e % K, b = e / K;
         double t = 0.0;
-        for (int g = 0; g < ngroup; g++) t += (double)park[((int64_t)g * S + b) * KP + a];
-        part[(int64_t)blockIdx.x * KS + e] = t;
+        for (int ph = 0; ph < rsplit; ph++) t += slot[((int64_t)ph * K + a) * S + b];
+        part[(int64_t)blockIdx.x * KS + e] = t;   // G column-major [b * K + a]
     }
 }
 
-// shared memory of one gram_kernel launch: the staged chunk, or the parked tiles
-template <typename T> static size_t gram_smem(int K, int S) {
-    const int ntile = (K + 3) / 4;
-    const int ngroup = std::max(1, 256 / ntile);
-    return std::max((size_t)GR * (K + S) * sizeof(T), (size_t)ngroup * S * ntile * 4 * sizeof(T));
-}
 
 // ------------------------------------------------------------------------------------------
 // W <- (W - Q C) Rinv, row by row, and (optionally) the Gram of the new W for the next step.
@@ -698,7 +668,7 @@ struct Solver {
         ldv = (n + 31) / 32 * 32;
         const int m = o.restart;
         MPK_TRY(V.alloc((size_t)(m + 1) * ldv * sizeof(T)));
-        gram_grid = 4 * P->n_sm;
+        gram_grid = 8 * P->n_sm;
         upd_grid = 4 * P->n_sm;
         const int maxK = m + 1 + SMAX;
         MPK_TRY(part.alloc((size_t)std::max(gram_grid, upd_grid) * maxK * SMAX * sizeof(double) + 4096));
@@ -733,13 +703,9 @@ struct Solver {
 
     // G (K x S) = X^T Y
     template <int SB> mpk_status gram_sb(const T *X, int K, const T *Y, int S, double *Gout) {
-        const size_t sm = gram_smem<T>(K, S);
-        // one fixed maximum for every caller (the attribute is shared by all threads)
-        constexpr int smax = 160 * 1024;
-        if (sm > (size_t)smax) return MPK_ERR_ARG;
-        MPK_CUDA(cudaFuncSetAttribute(gram_kernel<T, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
-        const int g = (int)std::min<int64_t>(gram_grid, ceil_div(n, GR));
-        gram_kernel<T, SB><<<g, 256, sm, st>>>(X, ldv, K, Y, ldv, S, n, part.as<double>());
+        if (K > MMAX + 1 + SMAX || S > SB) return MPK_ERR_ARG;
+        const int g = (int)std::min<int64_t>(gram_grid, ceil_div(n, GRAM_RANGE));
+        gram_kernel<T, SB><<<g, 256, 0, st>>>(X, ldv, K, Y, ldv, S, n, part.as<double>());
         reduce_partials_kernel<<<redp_grid(K * S), 32 * REDP_WARPS, 0, st>>>(part.as<double>(), g, K * S, (int64_t)K * S, Gout, 0);
         MPK_CUDA(cudaGetLastError());
         return MPK_OK;
@@ -949,7 +915,7 @@ extern "C" mpk_status mpk_gmres_opts_default(mpk_gmres_opts *o) {
     o->restart = 48;
     o->tol = 1e-8;
     o->inner_tol = 1e-5;
-    o->max_outer = 200;
+    o->max_outer = 1000;
     o->inner_cycles = 1;
     o->max_iters = 100000;
     o->basis = MPK_F32;
