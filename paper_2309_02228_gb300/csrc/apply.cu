@@ -380,15 +380,15 @@ __device__ __forceinline__ void slice_power(const SellView &A, int64_t s, const 
 // Unblocked p x SpMV (Alg. 1): one launch per power, one warp per slice, matrix read from
 // global memory by many warps per SM.  Same row function as the blocked kernel.
 // ------------------------------------------------------------------------------------------
-template <typename T, int NR>
+template <typename T, int NR, bool PAIRS>
 __global__ void __launch_bounds__(256) mpk_power_kernel(SellView A, int64_t n_slices, int n_rhs,
-                                                        VecSet V, int k, Coefs cf, int pairs) {
+                                                        VecSet V, int k, Coefs cf) {
     const int lane = threadIdx.x & 31;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const T *gval = reinterpret_cast<const T *>(A.val);
-    if constexpr (NR == 1) {
-        if (pairs) {
+    if constexpr (NR == 1 && PAIRS) {
+        {
             for (int64_t s = 2 * w0; s < n_slices; s += 2 * nw) {
                 if (s + 1 < n_slices) slice_pair_power<T>(A, s, s + 1, lane, V, k, cf);
                 else slice_power<T, 1, false, false>(A, s, A.col + 32ll * __ldg(A.slice_ptr + s),
@@ -791,7 +791,6 @@ struct WaveArgs {
     uint64_t timeout_ns;
     uint32_t debug_drop;              // 1: task (chunk 0, power 1) does not publish
     uint32_t dynamic;                 // 1: tickets from the control block's dispenser
-    int pairs;                        // 1: a warp runs two slices at once (short rows)
     uint32_t *kep;                    // device: earlier launches that ran each local power k;
                                       // the last CTA out adds this launch (powers 1..seg), so
                                       // a captured graph can replay the launch
@@ -816,8 +815,8 @@ template <typename T, int NR> constexpr int wave_min_blocks() {
     return (NR >= 4 * (16 / (int)sizeof(T))) ? 6 : (sizeof(T) == 4 ? (NR <= 2 ? 6 : 4) : (NR == 1 ? 5 : 4));
 }
 
-template <typename T, int NR>
-__global__ void __launch_bounds__(WAVE_BLOCK, (wave_min_blocks<T, NR>())) mpk_wave_kernel(
+template <typename T, int NR, bool PAIRS>
+__global__ void __launch_bounds__(WAVE_BLOCK, (PAIRS ? 4 : wave_min_blocks<T, NR>())) mpk_wave_kernel(
     SellView A, int n_rhs, VecSet V, Coefs cf, WaveArgs W) {
     constexpr int BGMAX = 8;
     __shared__ int32_t s_wm[WAVE_BLOCK / 32][MPK_MAX_P + 1];
@@ -891,9 +890,8 @@ __global__ void __launch_bounds__(WAVE_BLOCK, (wave_min_blocks<T, NR>())) mpk_wa
         const int k = W.k0 + kl;
         const int32_t s1 = __ldg(W.chunk_slice + c + 1);
         int32_t s = __ldg(W.chunk_slice + c);
-        if constexpr (NR == 1) {
-            if (W.pairs)
-                for (; s + 1 < s1; s += 2) slice_pair_power<T>(A, s, s + 1, lane, V, k, cf);
+        if constexpr (NR == 1 && PAIRS) {
+            for (; s + 1 < s1; s += 2) slice_pair_power<T>(A, s, s + 1, lane, V, k, cf);
         }
         for (; s < s1; s++) {
             const long long gofs = 32ll * __ldg(A.slice_ptr + s);
@@ -1030,7 +1028,10 @@ mpk_status launch_wave(mpk_plan_s *P, const SellView &A, int n_rhs, const VecSet
     W.timeout_ns = (uint64_t)P->opts.wait_timeout_us * 1000ull;
     W.debug_drop = (flags & MPK_DEBUG_DROP_FLAG) && k0 == 0 ? 1u : 0u;
     W.dynamic = P->wave_dynamic ? 1u : 0u;
-    auto kern = mpk_wave_kernel<T, NR>;
+    auto kern = mpk_wave_kernel<T, NR, false>;
+    if constexpr (NR == 1) {
+        if (P->short_rows) kern = mpk_wave_kernel<T, 1, true>;
+    }
     int occ = 0;
     MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, WAVE_BLOCK, 0));
     if (occ < 1) return MPK_ERR_UNIMPLEMENTED;
@@ -1039,7 +1040,6 @@ mpk_status launch_wave(mpk_plan_s *P, const SellView &A, int n_rhs, const VecSet
     const int64_t grid = std::min<int64_t>((int64_t)P->n_sm * per_sm, ceil_div(warps, WAVE_BLOCK / 32));
     W.kep = P->wave_kep.as<uint32_t>();
     W.seg = seg;
-    W.pairs = P->short_rows ? 1 : 0;
     // cooperative (all CTAs co-resident, which the ticket order relies on); launched through
     // cudaLaunchKernelEx so that stream capture can record it
     cudaLaunchConfig_t lc;
@@ -1062,9 +1062,13 @@ mpk_status launch_powers(mpk_plan_s *P, const SellView &A, int n_rhs, const VecS
                          const Coefs &cf, int p, bool blocked, uint32_t flags, cudaStream_t s) {
     if (!blocked) {
         // p back-to-back SpMV launches (Alg. 1)
-        const int pairs = (NR == 1 && P->short_rows) ? 1 : 0;
+        const bool pairs = NR == 1 && P->short_rows;
         const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(std::max<int64_t>(P->n_slices, 1), pairs ? 16 : 8), 1 << 30);
-        for (int k = 1; k <= p; k++) mpk_power_kernel<T, NR><<<grid, 256, 0, s>>>(A, P->n_slices, n_rhs, V, k, cf, pairs);
+        auto kern = mpk_power_kernel<T, NR, false>;
+        if constexpr (NR == 1) {
+            if (pairs) kern = mpk_power_kernel<T, 1, true>;
+        }
+        for (int k = 1; k <= p; k++) kern<<<grid, 256, 0, s>>>(A, P->n_slices, n_rhs, V, k, cf);
         MPK_CUDA(cudaGetLastError());
         return MPK_OK;
     }
