@@ -9,6 +9,7 @@ leg of ``bench.py`` may import this package.  It shares no code with the GPU lib
   level groups.  ``build()`` compiles it with gcc.
 * ``sstep.py``: textbook GMRES and s-step GMRES (Alg. 3), CholQR2, Leja ordering, Chebyshev
   coefficients, FP64 iterative refinement, in NumPy.
+* ``poly.py``: the GMRES polynomial preconditioner (Sec. 5.2) and right-preconditioned GMRES.
 """
 from __future__ import annotations
 
