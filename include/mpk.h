@@ -280,6 +280,20 @@ typedef struct {
                                cycle, Leja-ordered (Sec. 4) */
     uint32_t mpk_flags;     /* extra mpk_apply flags for the basis MPK: MPK_UNBLOCKED runs
                                s back-to-back SpMVs (the baseline solver) */
+    int32_t poly_degree;    /* d > 0: GMRES-polynomial preconditioning of degree d (Sec. 5.2,
+                               Eq. (poly_precon)).  The first restart cycle (plain GMRES on A)
+                               supplies the polynomial q of its first d + 1 steps
+                               (x_{d+1} - x_0 = q(A) r0); later cycles run GMRES(restart) with
+                               single columns on A q(A) (right preconditioning: one MPK of d
+                               powers plus one SpMV per column) and add q(A) V y to x.  q is
+                               applied in root form, q(A) x = sum_k (1/theta_{k+1})
+                               prod_{i<=k} (I - A/theta_i) x, with the Leja-ordered harmonic
+                               Ritz values theta of those steps (a symmetric A is assumed: real
+                               roots; without a positive definite pencil no polynomial is
+                               used).  d <= min(63, restart - 1); default 0 (off) */
+    int32_t poly_f64;       /* 1 (default): apply A q(A) with the FP64 matrix values even with
+                               an FP32 basis (q evaluated in FP32 loses digits quickly with the
+                               degree); 0: in the basis precision */
 } mpk_gmres_opts;
 
 typedef struct {
@@ -290,6 +304,8 @@ typedef struct {
     double rel_residual;    /* true ||b - A x|| / ||b|| in FP64 at exit */
     double shifts[64];      /* shifts used (first s entries) */
     double ms_total, ms_mpk, ms_ortho, ms_other;   /* CUDA-event timings per phase */
+    int32_t poly_degree;    /* degree of the polynomial preconditioner used (0: none) */
+    double poly_interval[2];/* smallest and largest root of the polynomial */
 } mpk_gmres_info;
 
 mpk_status mpk_gmres_opts_default(mpk_gmres_opts *o);

@@ -17,6 +17,12 @@ taken from d GMRES steps.  Reading used here (the paper gives no formulas for th
   cycle): gamma_k follow from exact interpolation of q at the d + 1 Chebyshev nodes.  This is
   the polynomial of Eq. (poly_precon), evaluated by the stable three-term recurrence instead of
   the monomial sum (which loses all digits at degree 40-80).
+* The same q also has a root (product) form: with theta_1..theta_{d+1} the harmonic Ritz values
+  of the d + 1 Arnoldi steps (the roots of the GMRES residual polynomial pi, which satisfies
+  1 - t q(t) = pi(t) = prod_i (1 - t / theta_i)),
+      q(A) x = sum_{k=0}^{d} (1 / theta_{k+1}) prod_{i<=k} (I - A / theta_i) x,
+  stable in low precision when the roots are Leja-ordered.  For a symmetric A the harmonic Ritz
+  values are the eigenvalues of the pencil Hbar^T Hbar z = theta sym(H_{d+1}) z.
 * The solver is restarted GMRES(m) with right preconditioning: the first cycle runs on A and
   supplies the polynomial (its correction is kept); later cycles run on B = A p(A), and their
   correction is x += p(A) V y.
@@ -28,7 +34,8 @@ import numpy as np
 from . import mpk as _mpk
 from .sstep import chebyshev_coeffs, spmv
 
-__all__ = ["arnoldi", "arnoldi_poly", "poly_from_arnoldi", "apply_poly", "poly_gmres"]
+__all__ = ["arnoldi", "arnoldi_poly", "poly_from_arnoldi", "apply_poly", "harmonic_roots",
+           "apply_poly_roots", "poly_gmres"]
 
 
 def arnoldi(A, r0, k):
@@ -86,6 +93,29 @@ def apply_poly(A, gamma, alpha, beta_iv, x):
         return gamma[0] * x
     Y = _mpk(A, d, chebyshev_coeffs(alpha, beta_iv, d), x)
     return sum(gamma[k] * Y[k] for k in range(d + 1))
+
+
+def harmonic_roots(H, d):
+    """Harmonic Ritz values of the leading d + 1 Arnoldi steps (symmetric A): eigenvalues of
+    Hbar^T Hbar z = theta S z with Hbar = H[:d+2, :d+1], S the symmetric part of H[:d+1, :d+1];
+    Leja-ordered (sstep.leja_order)."""
+    import scipy.linalg
+    Hb = H[: d + 2, : d + 1]
+    Hs = H[: d + 1, : d + 1]
+    th = scipy.linalg.eigh(Hb.T @ Hb, 0.5 * (Hs + Hs.T), eigvals_only=True)
+    from .sstep import leja_order
+    return leja_order(th, d + 1)
+
+
+def apply_poly_roots(A, roots, x):
+    """q(A) x = sum_k (1 / theta_{k+1}) prod_{i<=k} (I - A / theta_i) x through the oracle MPK
+    (three-term recurrence with a_k = -1 / theta_k, b_k = 1, c_k = 0)."""
+    d = roots.shape[0] - 1
+    if d == 0:
+        return x / roots[0]
+    coeffs = [(-1.0 / roots[k], 1.0, 0.0) for k in range(d)]
+    Y = _mpk(A, d, coeffs, x)
+    return sum(Y[k] / roots[k] for k in range(d + 1))
 
 
 def _gmres_cycle(apply_op, r, m, tol_abs):

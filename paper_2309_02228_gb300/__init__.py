@@ -86,7 +86,8 @@ class mpk_gmres_opts(ctypes.Structure):
                 ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int32),
                 ("inner_cycles", ctypes.c_int32), ("max_iters", ctypes.c_int32),
                 ("basis", ctypes.c_int), ("bcgs_passes", ctypes.c_int32),
-                ("shifts", ctypes.c_void_p), ("mpk_flags", ctypes.c_uint32)]
+                ("shifts", ctypes.c_void_p), ("mpk_flags", ctypes.c_uint32),
+                ("poly_degree", ctypes.c_int32), ("poly_f64", ctypes.c_int32)]
 
 
 class mpk_gmres_info(ctypes.Structure):
@@ -94,7 +95,8 @@ class mpk_gmres_info(ctypes.Structure):
                 ("status", ctypes.c_int32), ("rel_residual", ctypes.c_double),
                 ("shifts", ctypes.c_double * 64), ("ms_total", ctypes.c_double),
                 ("ms_mpk", ctypes.c_double), ("ms_ortho", ctypes.c_double),
-                ("ms_other", ctypes.c_double)]
+                ("ms_other", ctypes.c_double), ("poly_degree", ctypes.c_int32),
+                ("poly_interval", ctypes.c_double * 2)]
 
 
 class mpk_server_opts(ctypes.Structure):
@@ -389,7 +391,8 @@ def sstep_gmres_solve(plan, b, x, opts=None, shifts=None, stream=None, check=Tru
     info = mpk_gmres_info()
     st = lib().sstep_gmres_solve(plan.handle, _ptr(b), _ptr(x), ctypes.byref(o),
                                  ctypes.byref(info), _stream_ptr(stream))
-    d = {f: getattr(info, f) for f, _ in info._fields_ if f != "shifts"}
+    d = {f: getattr(info, f) for f, _ in info._fields_ if f not in ("shifts", "poly_interval")}
+    d["poly_interval"] = (info.poly_interval[0], info.poly_interval[1])
     d["shifts"] = np.array(info.shifts[: o.s])
     d["status_code"] = int(st)
     if check:

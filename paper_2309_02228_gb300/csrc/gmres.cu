@@ -267,6 +267,30 @@ __global__ void xupdate_kernel(const T *V, int64_t ldv, int k, const double *y, 
     }
 }
 
+// out[i] = sum_a V[i, a] y[a] in the basis precision (a correction before the polynomial
+// preconditioner is applied to it); x[i] += d[i] in FP64
+template <typename T>
+__global__ void vy_kernel(const T *V, int64_t ldv, int k, const double *y, int64_t n, T *out) {
+    __shared__ T ys[MMAX + 1];
+    for (int a = threadIdx.x; a < k; a += blockDim.x) ys[a] = (T)y[a];
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        T d = (T)0;
+        for (int a = 0; a < k; a++) d = fma(V[(int64_t)a * ldv + i], ys[a], d);
+        out[i] = d;
+    }
+}
+template <typename A, typename B>
+__global__ void cvt_kernel(const A *in, int64_t n, B *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (B)in[i];
+}
+template <typename T>
+__global__ void add_f64_kernel(const T *d, int64_t n, double *x) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] += (double)d[i];
+}
+
 // ------------------------------------------------------------------------------------------
 // Small dense FP64 work, one CTA
 // ------------------------------------------------------------------------------------------
@@ -653,6 +677,13 @@ struct Solver {
     int64_t n, ldv;
     DevBuf V, part, G, gpart2, cstate, vec;   // vec: b, x, r, norms (FP64)
     DevBuf dth;                                // Newton shifts of the current cycle
+    DevBuf ptmp;                               // polynomial preconditioner: 2 vectors of T
+    DevBuf ptmp64;                             // and 2 FP64 vectors (FP64 polynomial)
+    // polynomial preconditioner (Sec. 5.2): degree, Chebyshev interval and coefficients
+    int poly_deg = 0;
+    bool poly_on = false;
+    double piv_lo = 0.0, piv_hi = 0.0;         // smallest and largest root
+    std::vector<double> pgam, pa, pb, pc;
     double *bp, *xp, *rp, *nrm;
     CycleState *cst;
     int gram_grid, upd_grid;
@@ -676,6 +707,8 @@ struct Solver {
         MPK_TRY(gpart2.alloc((size_t)upd_grid * SMAX * SMAX * sizeof(double) + 64));
         MPK_TRY(cstate.alloc(sizeof(CycleState)));
         MPK_TRY(dth.alloc(SMAX * sizeof(double)));
+        if (o.poly_degree > 0) MPK_TRY(ptmp.alloc((size_t)2 * ldv * sizeof(T)));
+        if (o.poly_degree > 0 && poly64()) MPK_TRY(ptmp64.alloc((size_t)2 * ldv * sizeof(double)));
         MPK_TRY(vec.alloc((size_t)3 * ldv * sizeof(double) + 64 * sizeof(double)));
         bp = vec.as<double>();
         xp = bp + ldv;
@@ -762,7 +795,38 @@ struct Solver {
         return MPK_OK;
     }
 
+    // out = q(A) in, or out = A in (level order, precision U): one final-only MPK
+    template <typename U> mpk_status apply_poly_u(const U *in, U *out) {
+        mpk_coeffs co{poly_deg, pa.data(), pb.data(), pc.data(), pgam.data()};
+        const uint32_t fl = MPK_PERMUTED_IO | MPK_FINAL_ONLY | (o.mpk_flags & MPK_UNBLOCKED);
+        return mpk_apply_internal(P, &co, sizeof(U) == 8 ? MPK_F64 : MPK_F32, in, ldv, out, ldv, 1, fl, st);
+    }
+    template <typename U> mpk_status apply_A_u(const U *in, U *out) {
+        double one = 1.0, zero = 0.0;
+        mpk_coeffs co{1, &one, &zero, &zero, nullptr};
+        const uint32_t fl = MPK_PERMUTED_IO | MPK_FINAL_ONLY | (o.mpk_flags & MPK_UNBLOCKED);
+        return mpk_apply_internal(P, &co, sizeof(U) == 8 ? MPK_F64 : MPK_F32, in, ldv, out, ldv, 1, fl, st);
+    }
+    // the polynomial runs with the FP64 matrix values although the basis is FP32
+    bool poly64() const { return sizeof(T) == 4 && o.poly_f64 != 0; }
+
     mpk_status mpk_block(int j, int S, bool newton) {
+        if (poly_on) {
+            // right-preconditioned column: v_{j+1} <- A q(A) v_j
+            if (poly64()) {
+                double *d0 = ptmp64.as<double>(), *d1 = d0 + ldv;
+                cvt_kernel<T, double><<<grid_rows(n), 256, 0, st>>>(col(j), n, d0);
+                MPK_CUDA(cudaGetLastError());
+                MPK_TRY(apply_poly_u<double>(d0, d1));
+                MPK_TRY(apply_A_u<double>(d1, d0));
+                cvt_kernel<double, T><<<grid_rows(n), 256, 0, st>>>(d0, n, col(j + 1));
+                MPK_CUDA(cudaGetLastError());
+                return MPK_OK;
+            }
+            T *t0 = ptmp.as<T>();
+            MPK_TRY(apply_poly_u<T>(col(j), t0));
+            return apply_A_u<T>(t0, col(j + 1));
+        }
         std::vector<double> a(S, 1.0), b(S, 0.0), c(S, 0.0);
         if (newton)
             for (int k = 0; k < S; k++) b[k] = -theta[k];
@@ -817,11 +881,27 @@ struct Solver {
         if (k > 0) {
             t_other.start();
             lsq_kernel<<<1, 128, 0, st>>>(cst, k);
-            xupdate_kernel<T><<<grid_rows(n, 8), 256, 0, st>>>(V.as<T>(), ldv, k, cst->y, n, xp);
+            if (poly_on) {
+                // x += q(A) V y
+                T *t0 = ptmp.as<T>(), *t1 = t0 + ldv;
+                vy_kernel<T><<<grid_rows(n, 8), 256, 0, st>>>(V.as<T>(), ldv, k, cst->y, n, t0);
+                MPK_CUDA(cudaGetLastError());
+                if (poly64()) {
+                    double *d0 = ptmp64.as<double>(), *d1 = d0 + ldv;
+                    cvt_kernel<T, double><<<grid_rows(n), 256, 0, st>>>(t0, n, d0);
+                    MPK_TRY(apply_poly_u<double>(d0, d1));
+                    add_f64_kernel<double><<<grid_rows(n), 256, 0, st>>>(d1, n, xp);
+                } else {
+                    MPK_TRY(apply_poly_u<T>(t0, t1));
+                    add_f64_kernel<T><<<grid_rows(n), 256, 0, st>>>(t1, n, xp);
+                }
+            } else {
+                xupdate_kernel<T><<<grid_rows(n, 8), 256, 0, st>>>(V.as<T>(), ldv, k, cst->y, n, xp);
+            }
             MPK_CUDA(cudaGetLastError());
             t_other.stop();
         }
-        if (!newton && k > 0) {
+        if (!newton && !poly_on && k > 0) {
             const int kp = (k + 1) & ~1;
             // the attribute is shared by all threads: always the same maximum (m <= MMAX)
             MPK_CUDA(cudaFuncSetAttribute(ritz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -838,6 +918,114 @@ struct Solver {
         return MPK_OK;
     }
 
+    // The GMRES polynomial of the setup cycle's first d + 1 steps (Sec. 5.2), in root form: the
+    // GMRES residual polynomial pi(t) = prod_i (1 - t / theta_i) has the harmonic Ritz values of
+    // those steps as roots, and q(t) = (1 - pi(t)) / t gives
+    //     q(A) x = sum_{k=0}^{d} (1 / theta_{k+1}) prod_{i<=k} (I - A / theta_i) x,
+    // an MPK of d powers with a_k = -1 / theta_k, b_k = 1 and gamma_k = 1 / theta_{k+1}; the
+    // roots are Leja-ordered, which keeps the partial products bounded.  For a symmetric A the
+    // harmonic Ritz values are the eigenvalues of the pencil Hbar^T Hbar z = theta S z (Hbar the
+    // leading (d+2) x (d+1) Arnoldi block, S the symmetric part of its square part), found by a
+    // Cholesky S = L L^T and Jacobi rotations on L^-1 Hbar^T Hbar L^-T.  Host arithmetic on
+    // O(d^2) numbers, like the Leja ordering of the shifts; no polynomial if S is not positive
+    // definite.
+    static bool jacobi_eigenvalues(std::vector<double> &Asym, int q, std::vector<double> &ev) {
+        double fro = 0.0;
+        for (double v : Asym) fro += v * v;
+        for (int sweep = 0; sweep < 60; sweep++) {
+            double off = 0.0;
+            for (int c = 0; c < q; c++)
+                for (int r = 0; r < q; r++)
+                    if (r != c) off += Asym[r + c * q] * Asym[r + c * q];
+            if (!(off > 1e-30 * fro)) break;
+            for (int p = 0; p < q - 1; p++)
+                for (int r = p + 1; r < q; r++) {
+                    const double apq = Asym[p + r * q];
+                    if (std::fabs(apq) < 1e-300) continue;
+                    const double tau = (Asym[r + r * q] - Asym[p + p * q]) / (2.0 * apq);
+                    const double t = (tau >= 0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
+                    const double c = 1.0 / std::sqrt(1.0 + t * t), sn = t * c;
+                    for (int i = 0; i < q; i++) {
+                        const double aip = Asym[i + p * q], aiq = Asym[i + r * q];
+                        Asym[i + p * q] = c * aip - sn * aiq;
+                        Asym[i + r * q] = sn * aip + c * aiq;
+                    }
+                    for (int i = 0; i < q; i++) {
+                        const double api = Asym[p + i * q], aqi = Asym[r + i * q];
+                        Asym[p + i * q] = c * api - sn * aqi;
+                        Asym[r + i * q] = sn * api + c * aqi;
+                    }
+                }
+        }
+        ev.resize(q);
+        for (int i = 0; i < q; i++) ev[i] = Asym[i + i * q];
+        return true;
+    }
+
+    mpk_status setup_poly(int k) {
+        const int dd = std::min(std::min(o.poly_degree, k - 1), MPK_MAX_P);
+        if (dd < 1) return MPK_OK;   // cycle too short: no polynomial
+        const int ldh = MMAX + 1, q = dd + 1;
+        std::vector<double> H((size_t)ldh * q);
+        MPK_CUDA(cudaMemcpyAsync(H.data(), cst->H, H.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        MPK_CUDA(cudaStreamSynchronize(st));
+        // G = Hbar^T Hbar, S = sym(H[0:q, 0:q])
+        std::vector<double> G((size_t)q * q, 0.0), L((size_t)q * q, 0.0), X((size_t)q * q, 0.0);
+        for (int a = 0; a < q; a++)
+            for (int b = 0; b < q; b++) {
+                double v = 0.0;
+                for (int r = 0; r <= q; r++) v += H[r + a * ldh] * H[r + b * ldh];
+                G[a + b * q] = v;
+            }
+        // Cholesky of S (lower L)
+        for (int c = 0; c < q; c++) {
+            for (int r = c; r < q; r++) {
+                double v = 0.5 * (H[r + c * ldh] + H[c + r * ldh]);
+                for (int t = 0; t < c; t++) v -= L[r + t * q] * L[c + t * q];
+                if (r == c) {
+                    if (!(v > 0.0)) return MPK_OK;   // not positive definite: no polynomial
+                    L[c + c * q] = std::sqrt(v);
+                } else {
+                    L[r + c * q] = v / L[c + c * q];
+                }
+            }
+        }
+        // X = L^-1 G, then C = L^-1 X^T (= L^-1 G L^-T for symmetric G)
+        auto fwd = [&](const std::vector<double> &B, std::vector<double> &Out, bool transpose_in) {
+            for (int c = 0; c < q; c++)
+                for (int r = 0; r < q; r++) {
+                    double v = transpose_in ? B[c + r * q] : B[r + c * q];
+                    for (int t = 0; t < r; t++) v -= L[r + t * q] * Out[t + c * q];
+                    Out[r + c * q] = v / L[r + r * q];
+                }
+        };
+        fwd(G, X, false);
+        std::vector<double> C((size_t)q * q, 0.0);
+        fwd(X, C, true);
+        for (int a = 0; a < q; a++)
+            for (int b = a + 1; b < q; b++) {
+                const double v = 0.5 * (C[a + b * q] + C[b + a * q]);
+                C[a + b * q] = v;
+                C[b + a * q] = v;
+            }
+        std::vector<double> ev, roots(q);
+        jacobi_eigenvalues(C, q, ev);
+        for (double v : ev)
+            if (!(v > 0.0) || !std::isfinite(v)) return MPK_OK;
+        MPK_TRY(mpk_leja_order(ev.data(), q, q, roots.data()));
+        pa.assign(dd, 0.0);
+        pb.assign(dd, 1.0);
+        pc.assign(dd, 0.0);
+        pgam.assign(dd + 1, 0.0);
+        for (int kk = 0; kk < dd; kk++) pa[kk] = -1.0 / roots[kk];
+        for (int kk = 0; kk <= dd; kk++) pgam[kk] = 1.0 / roots[kk];
+        poly_deg = dd;
+        piv_lo = *std::min_element(roots.begin(), roots.end());
+        piv_hi = *std::max_element(roots.begin(), roots.end());
+        poly_on = true;
+        return MPK_OK;
+    }
+
     mpk_status run(const double *b, double *x) {
         MPK_TRY(alloc());
         const unsigned g = grid_rows(n);
@@ -851,7 +1039,7 @@ struct Solver {
         MPK_CUDA(cudaStreamSynchronize(st));
         s_cur = o.s;
         if (o.shifts) theta.assign(o.shifts, o.shifts + o.s);
-        const bool need_shifts = !o.shifts;
+        const bool need_shifts = !o.shifts || o.poly_degree > 0;
         bool have_shifts = !need_shifts;
         mpk_status result = MPK_ERR_NOT_CONVERGED;
         double relres = 1.0;
@@ -881,6 +1069,9 @@ struct Solver {
             if (!have_shifts) {
                 MPK_TRY(cycle(tol_abs, false, 1, &k, &bd));
                 have_shifts = true;
+                if (o.poly_degree > 0) MPK_TRY(setup_poly(k));
+            } else if (poly_on) {
+                MPK_TRY(cycle(tol_abs, false, 1, &k, &bd));   // single columns on A q(A)
             } else {
                 MPK_TRY(cycle(tol_abs, true, s_cur, &k, &bd));
                 if (bd) {
@@ -899,6 +1090,9 @@ struct Solver {
         info.rel_residual = relres;
         info.status = result;
         for (size_t i = 0; i < theta.size() && i < 64; i++) info.shifts[i] = theta[i];
+        info.poly_degree = poly_deg;
+        info.poly_interval[0] = piv_lo;
+        info.poly_interval[1] = piv_hi;
         info.ms_mpk = t_mpk.total;
         info.ms_ortho = t_ortho.total;
         info.ms_other = t_other.total;
@@ -922,6 +1116,8 @@ extern "C" mpk_status mpk_gmres_opts_default(mpk_gmres_opts *o) {
     o->bcgs_passes = 1;
     o->shifts = nullptr;
     o->mpk_flags = 0;
+    o->poly_degree = 0;
+    o->poly_f64 = 1;
     return MPK_OK;
 }
 
@@ -933,10 +1129,12 @@ extern "C" mpk_status sstep_gmres_solve(mpk_plan_t A, const double *b, double *x
     if (opts) o = *opts;
     else mpk_gmres_opts_default(&o);
     if (o.s < 1 || o.s > SMAX || o.restart < o.s || o.restart > MMAX || !(o.tol > 0) ||
-        o.bcgs_passes < 1 || o.bcgs_passes > 2 || o.max_outer < 0)
+        o.bcgs_passes < 1 || o.bcgs_passes > 2 || o.max_outer < 0 || o.poly_degree < 0 ||
+        o.poly_degree > MPK_MAX_P)
         return MPK_ERR_ARG;
     if (!A->has64) return MPK_ERR_ARG;                       // FP64 residual needs FP64 values
     if (o.basis == MPK_F32 && !A->has32) return MPK_ERR_ARG;
+    if (o.poly_degree > 0 && o.basis == MPK_F32 && !o.poly_f64 && !A->has32) return MPK_ERR_ARG;
     if (o.s > A->p_max) return MPK_ERR_ARG;
     auto t0 = std::chrono::steady_clock::now();
     mpk_status st;

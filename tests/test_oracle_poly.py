@@ -87,3 +87,19 @@ def test_preconditioned_gmres_converges_faster():
     assert pre["iters"] < plain["iters"] / 2
     xs = np.linalg.solve(_dense(A), b)
     assert np.linalg.norm(pre["x"] - xs) <= np.linalg.cond(_dense(A)) * 2e-8 * np.linalg.norm(xs)
+
+
+def test_root_form_is_the_same_polynomial():
+    """The Leja-ordered harmonic-Ritz product form and the Chebyshev form evaluate the same q."""
+    for A, d in ((mi.poisson2d_5pt(14), 10), (mi.diffusion7_lognormal(8), 12), (mi.anisotropic(7, 27, 5.0), 8)):
+        r0 = mi.uniform_vectors(A.n, 3)[0]
+        V, H, beta, steps = poly.arnoldi(A, r0, d + 1)
+        lam = np.linalg.eigvalsh(_dense(A))
+        interval = (0.0, 1.1 * lam.max())
+        gamma, _ = poly.poly_from_arnoldi(H, beta, d, *interval)
+        z1 = poly.apply_poly(A, gamma, interval[0], interval[1], r0)
+        z2 = poly.apply_poly_roots(A, poly.harmonic_roots(H, d), r0)
+        assert np.linalg.norm(z1 - z2) <= 1e-8 * np.linalg.norm(z1), d
+        # 1 - A q(A) r0 is the GMRES residual of d + 1 steps
+        corr = V[:, : d + 1] @ np.linalg.lstsq(H[: d + 2, : d + 1], np.eye(d + 2)[0] * beta, rcond=None)[0]
+        assert np.linalg.norm(z2 - corr) <= 1e-8 * np.linalg.norm(corr)
