@@ -270,7 +270,9 @@ typedef struct {
     int32_t restart;        /* restart length m (default 48) */
     double tol;             /* stop when ||b - A x||_2 <= tol ||b||_2 (FP64; default 1e-8) */
     double inner_tol;       /* inner solve tolerance relative to its rhs (default 1e-5) */
-    int32_t max_outer;      /* refinement steps, one restart cycle each (default 1000) */
+    int32_t max_outer;      /* refinement steps, one restart cycle each (default 1000); the
+                               solve also stops (MPK_ERR_NOT_CONVERGED) after 50 steps without
+                               a new best true residual */
     int32_t inner_cycles;   /* restart cycles per inner solve (default 1) */
     int32_t max_iters;      /* cap on inner iterations in total (default 100000) */
     mpk_dtype basis;        /* MPK_F32: FP32 matrix + basis, FP64 Gram/Cholesky/H/x/r;

@@ -1042,7 +1042,8 @@ struct Solver {
         const bool need_shifts = !o.shifts || o.poly_degree > 0;
         bool have_shifts = !need_shifts;
         mpk_status result = MPK_ERR_NOT_CONVERGED;
-        double relres = 1.0;
+        double relres = 1.0, best_rel = 1e300;
+        int since_best = 0;
         for (int outer = 0; outer <= o.max_outer; outer++) {
             t_other.start();
             MPK_TRY(mpk_launch_residual(P, xp, bp, rp, st));
@@ -1060,6 +1061,13 @@ struct Solver {
             }
             if (outer == o.max_outer || info.iters >= o.max_iters) break;
             if (!std::isfinite(hr)) break;
+            // stagnation: no new best true residual (by 0.1 %) in 50 refinement steps
+            if (relres < 0.999 * best_rel) {
+                best_rel = relres;
+                since_best = 0;
+            } else if (++since_best >= 50) {
+                break;
+            }
             // one restart cycle on A d = r; target: inner_tol relative to ||r|| in the basis
             // precision, never tighter than the overall target
             double tol_abs = std::max(o.inner_tol * hr, 0.5 * o.tol * hb);
