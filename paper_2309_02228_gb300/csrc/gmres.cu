@@ -698,18 +698,18 @@ struct Solver {
         n = P->n;
         ldv = (n + 31) / 32 * 32;
         const int m = o.restart;
-        MPK_TRY(V.alloc((size_t)(m + 1) * ldv * sizeof(T)));
+        MPK_TRY(V.alloc_on((size_t)(m + 1) * ldv * sizeof(T), st));
         gram_grid = 8 * P->n_sm;
         upd_grid = 4 * P->n_sm;
         const int maxK = m + 1 + SMAX;
-        MPK_TRY(part.alloc((size_t)std::max(gram_grid, upd_grid) * maxK * SMAX * sizeof(double) + 4096));
-        MPK_TRY(G.alloc((size_t)maxK * SMAX * sizeof(double) + 64));
-        MPK_TRY(gpart2.alloc((size_t)upd_grid * SMAX * SMAX * sizeof(double) + 64));
-        MPK_TRY(cstate.alloc(sizeof(CycleState)));
-        MPK_TRY(dth.alloc(SMAX * sizeof(double)));
-        if (o.poly_degree > 0) MPK_TRY(ptmp.alloc((size_t)2 * ldv * sizeof(T)));
-        if (o.poly_degree > 0 && poly64()) MPK_TRY(ptmp64.alloc((size_t)2 * ldv * sizeof(double)));
-        MPK_TRY(vec.alloc((size_t)3 * ldv * sizeof(double) + 64 * sizeof(double)));
+        MPK_TRY(part.alloc_on((size_t)std::max(gram_grid, upd_grid) * maxK * SMAX * sizeof(double) + 4096, st));
+        MPK_TRY(G.alloc_on((size_t)maxK * SMAX * sizeof(double) + 64, st));
+        MPK_TRY(gpart2.alloc_on((size_t)upd_grid * SMAX * SMAX * sizeof(double) + 64, st));
+        MPK_TRY(cstate.alloc_on(sizeof(CycleState), st));
+        MPK_TRY(dth.alloc_on(SMAX * sizeof(double), st));
+        if (o.poly_degree > 0) MPK_TRY(ptmp.alloc_on((size_t)2 * ldv * sizeof(T), st));
+        if (o.poly_degree > 0 && poly64()) MPK_TRY(ptmp64.alloc_on((size_t)2 * ldv * sizeof(double), st));
+        MPK_TRY(vec.alloc_on((size_t)3 * ldv * sizeof(double) + 64 * sizeof(double), st));
         bp = vec.as<double>();
         xp = bp + ldv;
         rp = xp + ldv;

@@ -38,15 +38,25 @@ void mpk_log_cuda_error(cudaError_t e, const char *what, const char *file, int l
 struct DevBuf {
     void *p = nullptr;
     size_t bytes = 0;
+    cudaStream_t stream = nullptr;   // stream-ordered buffers: the stream that owns them
+    bool ordered = false;
     DevBuf() = default;
     DevBuf(const DevBuf &) = delete;
     DevBuf &operator=(const DevBuf &) = delete;
     ~DevBuf() { release(); }
     void release() {
-        if (p) cudaFree(p);
+        if (p) {
+            if (ordered) cudaFreeAsync(p, stream);
+            else cudaFree(p);
+        }
         p = nullptr;
         bytes = 0;
+        ordered = false;
     }
+    // Stream-ordered allocation from the library's memory pool: allocated and freed in the
+    // order of stream s, so neither waits for work on other streams (cudaFree synchronises the
+    // whole device).  Only for buffers that work on s alone uses.
+    mpk_status alloc_on(size_t b, cudaStream_t s);
     mpk_status alloc(size_t b) {
         release();
         if (b == 0) b = 16;

@@ -9,9 +9,61 @@
 #include <algorithm>
 #include <chrono>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 
 #include "mpk_internal.cuh"
+
+// The library's memory pool of each device (stream-ordered allocations), created once; freed
+// blocks stay in the pool for reuse instead of going back to the driver at every sync.
+static std::mutex g_pool_mu;
+static std::map<int, cudaMemPool_t> g_pools;
+
+static mpk_status mpk_pool(cudaMemPool_t *out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return MPK_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    auto it = g_pools.find(dev);
+    if (it != g_pools.end()) {
+        *out = it->second;
+        return MPK_OK;
+    }
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+        cudaGetLastError();
+        return MPK_ERR_CUDA;
+    }
+    uint64_t keep = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pools[dev] = pool;
+    *out = pool;
+    return MPK_OK;
+}
+
+mpk_status DevBuf::alloc_on(size_t b, cudaStream_t s) {
+    release();
+    if (b == 0) b = 16;
+    cudaMemPool_t pool;
+    MPK_TRY(mpk_pool(&pool));
+    cudaError_t e = cudaMallocFromPoolAsync(&p, b, pool, s);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? MPK_ERR_OOM : MPK_ERR_CUDA;
+    }
+    bytes = b;
+    stream = s;
+    ordered = true;
+    return MPK_OK;
+}
 
 void mpk_log_cuda_error(cudaError_t e, const char *what, const char *file, int line) {
     fprintf(stderr, "[mpk] CUDA error %s (%d) in %s at %s:%d\n", cudaGetErrorString(e), (int)e,
@@ -700,7 +752,7 @@ static mpk_status plan_create_impl(const mpk_csr *A, int32_t p_max, const mpk_pl
     // ---- validation (row pointer monotone and consistent, columns in range)
     if (n > 0) {
         DevBuf bad;
-        MPK_TRY(bad.alloc(sizeof(unsigned)));
+        MPK_TRY(bad.alloc_on(sizeof(unsigned), s));
         MPK_CUDA(cudaMemsetAsync(bad.p, 0, sizeof(unsigned), s));
         validate_kernel<<<grid_for(n), 256, 0, s>>>(A->row_ptr, A->col, n, nnz, bad.as<unsigned>());
         MPK_CUDA(cudaGetLastError());
@@ -712,15 +764,15 @@ static mpk_status plan_create_impl(const mpk_csr *A, int32_t p_max, const mpk_pl
 
     const size_t tmp_bytes = std::max(scan_tmp_bytes(n + 1), scan_tmp_bytes(nnz + 1));
     DevBuf tmp;
-    MPK_TRY(tmp.alloc(std::max<size_t>(tmp_bytes, 256 * 8192 * 8)));
+    MPK_TRY(tmp.alloc_on(std::max<size_t>(tmp_bytes, 256 * 8192 * 8), s));
 
     // ---- transpose pattern (unless the caller states the pattern is symmetric)
     DevBuf rpT, ciT, cursor;
     const bool sym = o.assume_symmetric != 0;
     if (!sym) {
-        MPK_TRY(cursor.alloc((n + 1) * sizeof(int32_t)));
-        MPK_TRY(rpT.alloc((n + 1) * sizeof(int32_t)));
-        MPK_TRY(ciT.alloc(std::max<int64_t>(nnz, 1) * sizeof(int32_t)));
+        MPK_TRY(cursor.alloc_on((n + 1) * sizeof(int32_t), s));
+        MPK_TRY(rpT.alloc_on((n + 1) * sizeof(int32_t), s));
+        MPK_TRY(ciT.alloc_on(std::max<int64_t>(nnz, 1) * sizeof(int32_t), s));
         MPK_CUDA(cudaMemsetAsync(cursor.p, 0, (n + 1) * sizeof(int32_t), s));
         col_count_kernel<<<grid_for(nnz), 256, 0, s>>>(A->col, nnz, cursor.as<int32_t>());
         MPK_TRY(exclusive_scan<int32_t, int32_t>(cursor.as<int32_t>(), rpT.as<int32_t>(), n, tmp.p, s));
@@ -732,15 +784,18 @@ static mpk_status plan_create_impl(const mpk_csr *A, int32_t p_max, const mpk_pl
     // ---- BFS levels + George-Liu root
     MPK_TRY(P->level.alloc(n * sizeof(int32_t)));
     DevBuf lev2, q0, q1;
-    MPK_TRY(lev2.alloc(n * sizeof(int32_t)));
-    MPK_TRY(q0.alloc(n * sizeof(int32_t)));
-    MPK_TRY(q1.alloc(n * sizeof(int32_t)));
+    MPK_TRY(lev2.alloc_on(n * sizeof(int32_t), s));
+    MPK_TRY(q0.alloc_on(n * sizeof(int32_t), s));
+    MPK_TRY(q1.alloc_on(n * sizeof(int32_t), s));
     BfsRunner bfs;
-    MPK_TRY(bfs.ctl_buf.alloc(sizeof(BfsCtl)));
+    MPK_TRY(bfs.ctl_buf.alloc_on(sizeof(BfsCtl), s));
     {
         int occ = 0;
         MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bfs_kernel, bfs.block, 0));
-        bfs.grid = P->n_sm * std::max(1, std::min(occ, 4));
+        // sized to the matrix: a cooperative launch holds every SM it spans until it ends, so a
+        // small matrix takes a few CTAs and leaves the rest of the GPU to concurrent work
+        bfs.grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)P->n_sm * std::max(1, std::min(occ, 4)),
+                                                               ceil_div(n, 2048)));
         bfs.args.n = n;
         bfs.args.rp = A->row_ptr;
         bfs.args.ci = A->col;
@@ -784,7 +839,7 @@ static mpk_status plan_create_impl(const mpk_csr *A, int32_t p_max, const mpk_pl
         int64_t scan_pos = 0;
         const int64_t W = 1 << 20;
         DevBuf resb;
-        MPK_TRY(resb.alloc(sizeof(unsigned long long)));
+        MPK_TRY(resb.alloc_on(sizeof(unsigned long long), s));
         unsigned long long *res = resb.as<unsigned long long>();
         while (visited < n) {
             unsigned long long h = ~0ull;
@@ -814,16 +869,16 @@ static mpk_status plan_create_impl(const mpk_csr *A, int32_t p_max, const mpk_pl
     MPK_TRY(P->level_ptr.alloc((n_levels + 1) * sizeof(int32_t)));
     if (n > 0) {
         DevBuf kA, kB, vA, vB, hist;
-        MPK_TRY(kA.alloc(n * 4));
-        MPK_TRY(kB.alloc(n * 4));
-        MPK_TRY(vA.alloc(n * 4));
-        MPK_TRY(vB.alloc(n * 4));
+        MPK_TRY(kA.alloc_on(n * 4, s));
+        MPK_TRY(kB.alloc_on(n * 4, s));
+        MPK_TRY(vA.alloc_on(n * 4, s));
+        MPK_TRY(vB.alloc_on(n * 4, s));
         int64_t n_tiles = ceil_div(n, RS_TILE);
-        MPK_TRY(hist.alloc((256 * n_tiles + 1) * sizeof(int32_t)));
+        MPK_TRY(hist.alloc_on((256 * n_tiles + 1) * sizeof(int32_t), s));
         DevBuf offs;
-        MPK_TRY(offs.alloc((256 * n_tiles + 1) * sizeof(int32_t)));
+        MPK_TRY(offs.alloc_on((256 * n_tiles + 1) * sizeof(int32_t), s));
         DevBuf stmp;
-        MPK_TRY(stmp.alloc(scan_tmp_bytes(256 * n_tiles + 1)));
+        MPK_TRY(stmp.alloc_on(scan_tmp_bytes(256 * n_tiles + 1), s));
         MPK_CUDA(cudaMemcpyAsync(kA.p, P->level.p, n * 4, cudaMemcpyDeviceToDevice, s));
         iota_kernel<<<grid_for(n), 256, 0, s>>>(vA.as<int32_t>(), n);
         int32_t *ki = kA.as<int32_t>(), *ko = kB.as<int32_t>();
@@ -839,7 +894,7 @@ static mpk_status plan_create_impl(const mpk_csr *A, int32_t p_max, const mpk_pl
         MPK_CUDA(cudaMemcpyAsync(P->perm.p, vi, n * 4, cudaMemcpyDeviceToDevice, s));
         iperm_kernel<<<grid_for(n), 256, 0, s>>>(P->perm.as<int32_t>(), n, P->iperm.as<int32_t>());
         DevBuf cnt;
-        MPK_TRY(cnt.alloc((n_levels + 1) * 4));
+        MPK_TRY(cnt.alloc_on((n_levels + 1) * 4, s));
         MPK_CUDA(cudaMemsetAsync(cnt.p, 0, (n_levels + 1) * 4, s));
         level_hist_kernel<<<grid_for(n), 256, 0, s>>>(P->level.as<int32_t>(), n, cnt.as<int32_t>());
         MPK_TRY(exclusive_scan<int32_t, int32_t>(cnt.as<int32_t>(), P->level_ptr.as<int32_t>(), n_levels, tmp.p, s));
@@ -859,12 +914,12 @@ static mpk_status plan_create_impl(const mpk_csr *A, int32_t p_max, const mpk_pl
     if (P->has32) MPK_TRY(P->val32.alloc(std::max<int64_t>(nnz, 1) * 4));
     if (n > 0) {
         DevBuf len;
-        MPK_TRY(len.alloc(n * 4));
+        MPK_TRY(len.alloc_on(n * 4, s));
         perm_rowlen_kernel<<<grid_for(n), 256, 0, s>>>(A->row_ptr, P->perm.as<int32_t>(), n, len.as<int32_t>());
         MPK_TRY(exclusive_scan<int32_t, int32_t>(len.as<int32_t>(), P->rp.as<int32_t>(), n, tmp.p, s));
         DevBuf longr, nlong;
-        MPK_TRY(longr.alloc(n * 4));
-        MPK_TRY(nlong.alloc(4));
+        MPK_TRY(longr.alloc_on(n * 4, s));
+        MPK_TRY(nlong.alloc_on(4, s));
         MPK_CUDA(cudaMemsetAsync(nlong.p, 0, 4, s));
         double *v64 = P->has64 ? P->val64.as<double>() : nullptr;
         float *v32 = P->has32 ? P->val32.as<float>() : nullptr;
@@ -894,7 +949,7 @@ static mpk_status plan_create_impl(const mpk_csr *A, int32_t p_max, const mpk_pl
     if (n > 0) {
         MPK_CUDA(cudaMemcpyAsync(P->h_level_ptr.data(), P->level_ptr.p, (n_levels + 1) * 4, cudaMemcpyDeviceToHost, s));
         DevBuf at;
-        MPK_TRY(at.alloc((n_levels + 1) * 4));
+        MPK_TRY(at.alloc_on((n_levels + 1) * 4, s));
         gather_rp_kernel<<<grid_for(n_levels + 1), 256, 0, s>>>(P->rp.as<int32_t>(), P->level_ptr.as<int32_t>(), n_levels + 1, at.as<int32_t>());
         MPK_CUDA(cudaMemcpyAsync(h_rp_at.data(), at.p, (n_levels + 1) * 4, cudaMemcpyDeviceToHost, s));
         MPK_CUDA(cudaStreamSynchronize(s));
@@ -945,7 +1000,7 @@ static mpk_status plan_create_impl(const mpk_csr *A, int32_t p_max, const mpk_pl
     if (P->n_slices > 0) {
         slice_len_kernel<<<grid_for((int64_t)P->n_slices * 32), 256, 0, s>>>(P->rp.as<int32_t>(), P->slice_row.as<int32_t>(), P->n_slices, P->slice_len.as<int32_t>());
         DevBuf st;
-        MPK_TRY(st.alloc(scan_tmp_bytes(P->n_slices + 1)));
+        MPK_TRY(st.alloc_on(scan_tmp_bytes(P->n_slices + 1), s));
         MPK_TRY((exclusive_scan<int32_t, long long>(P->slice_len.as<int32_t>(), P->slice_ptr.as<long long>(), P->n_slices, st.p, s)));
         MPK_CUDA(cudaMemcpyAsync(h_sp.data(), P->slice_ptr.p, (P->n_slices + 1) * 8, cudaMemcpyDeviceToHost, s));
         MPK_CUDA(cudaStreamSynchronize(s));
@@ -1008,7 +1063,7 @@ static mpk_status plan_create_impl(const mpk_csr *A, int32_t p_max, const mpk_pl
     MPK_CUDA(cudaMemsetAsync(P->flags.p, 0, (P->n_chunks + 1) * 4, s));
     if (P->n_chunks > 0) {
         DevBuf row_chunk;
-        MPK_TRY(row_chunk.alloc(n * 4));
+        MPK_TRY(row_chunk.alloc_on(n * 4, s));
         row_chunk_kernel<<<(unsigned)std::min<int64_t>(P->n_chunks, 65535), 256, 0, s>>>(P->chunk_row.as<int32_t>(), P->n_chunks, row_chunk.as<int32_t>());
         fill_i32_kernel<<<grid_for(P->n_chunks), 256, 0, s>>>(P->dep_lo.as<int32_t>(), P->n_chunks, 0x7fffffff);
         fill_i32_kernel<<<grid_for(P->n_chunks), 256, 0, s>>>(P->dep_hi.as<int32_t>(), P->n_chunks, -1);

@@ -133,11 +133,11 @@ struct mpk_server_s {
         mpk_plan_t plan = nullptr;
         int64_t plan_bytes = 0;
         do {
-            if ((st = rp.alloc((r.n + 1) * 4)) != MPK_OK) break;
-            if ((st = ci.alloc(std::max<int64_t>(r.nnz, 1) * 4)) != MPK_OK) break;
-            if ((st = val.alloc(std::max<int64_t>(r.nnz, 1) * 8)) != MPK_OK) break;
-            if ((st = b.alloc(std::max<int64_t>(r.n, 1) * 8)) != MPK_OK) break;
-            if ((st = x.alloc(std::max<int64_t>(r.n, 1) * 8)) != MPK_OK) break;
+            if ((st = rp.alloc_on((r.n + 1) * 4, s)) != MPK_OK) break;
+            if ((st = ci.alloc_on(std::max<int64_t>(r.nnz, 1) * 4, s)) != MPK_OK) break;
+            if ((st = val.alloc_on(std::max<int64_t>(r.nnz, 1) * 8, s)) != MPK_OK) break;
+            if ((st = b.alloc_on(std::max<int64_t>(r.n, 1) * 8, s)) != MPK_OK) break;
+            if ((st = x.alloc_on(std::max<int64_t>(r.n, 1) * 8, s)) != MPK_OK) break;
             cudaMemcpyAsync(rp.p, r.rp.data(), (r.n + 1) * 4, cudaMemcpyHostToDevice, s);
             if (r.nnz) {
                 cudaMemcpyAsync(ci.p, r.ci.data(), r.nnz * 4, cudaMemcpyHostToDevice, s);
