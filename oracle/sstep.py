@@ -321,3 +321,30 @@ def refine_solve(A, b, tol=1e-8, s=8, m=48, inner_tol=1e-5, max_outer=50, inner_
     r = b - spmv(A, x)
     relres.append(np.linalg.norm(r) / nb)
     return dict(x=x, outer=max_outer, inner_iters=inner_iters, relres=relres, shifts=th)
+
+
+def jacobi_right(A):
+    """Sec. 5.1, Eq. (Jacobi) with one iteration from zero: the diagonal preconditioner
+    P^-1 = D^-1 applied from the right, as the paper fuses it into the SpMV (A D^-1, a scaling
+    along the columns).  Returns (A D^-1 as a CSR with the same pattern, dinv) where dinv_j =
+    1 / a_jj, and 1 where the diagonal entry is missing or zero (no scaling of that column)."""
+    n = A.n
+    d = np.zeros(n)
+    for i in range(n):
+        for e in range(A.row_ptr[i], A.row_ptr[i + 1]):
+            if A.col[e] == i:
+                d[i] += A.val[e]
+    dinv = np.where(d != 0.0, 1.0 / np.where(d != 0.0, d, 1.0), 1.0)
+    val = A.val * dinv[A.col]
+    from mpk_inputs import CSR
+    return CSR(A.row_ptr.copy(), A.col.copy(), val), dinv
+
+
+def jacobi_gmres(A, b, s=8, m=48, tol=1e-8, max_restarts=1000):
+    """s-step GMRES on A D^-1 u = b, x = D^-1 u (right Jacobi preconditioning: the GMRES
+    residual is the true residual)."""
+    B, dinv = jacobi_right(A)
+    out = sstep_gmres(B, b, s=s, m=m, tol=tol, max_restarts=max_restarts)
+    out = dict(out)
+    out["x"] = dinv * out["x"]
+    return out
