@@ -178,16 +178,20 @@ def run_reference(args):
     print(json.dumps(out))
 
 
-def solver_leg(m, torch, dev, n_edge=64, solves=5, bases=("f32", "f64"), warm=True, poly_degree=0):
+def solver_leg(m, torch, dev, n_edge=64, solves=5, bases=("f32", "f64"), warm=True, poly_degree=0,
+               jacobi=0):
     """s-step GMRES(s=8, restart 48) to rel. residual 1e-8 on the log-normal diffusion matrix
     (7-point, sigma = 1, rows randomly permuted) at n_edge^3, FP32 basis + FP64 refinement vs an
-    FP64 basis: solves/s and per-solve latency (p50/p99) over `solves` solves each."""
+    FP64 basis: solves/s and per-solve latency (p50/p99) over `solves` solves each.  poly_degree:
+    GMRES-polynomial preconditioning (Sec. 5.2); jacobi: right Jacobi scaling fused into the
+    MPK (Sec. 5.1)."""
     A = mi.diffusion7_lognormal(n_edge)
     b = mi.uniform_vectors(A.n, 4)[0]
     rp = torch.from_numpy(A.row_ptr).to(dev)
     ci = torch.from_numpy(A.col).to(dev)
     vv = torch.from_numpy(A.val).to(dev)
-    plan = m.mpk_plan_create(rp, ci, vv, 8, m.mpk_plan_opts_default(keep_f64=1, keep_f32=1))
+    plan = m.mpk_plan_create(rp, ci, vv, 8, m.mpk_plan_opts_default(keep_f64=1, keep_f32=1,
+                                                                    jacobi=jacobi))
     B = torch.from_numpy(b).to(dev)
     out = {"workload": "7-point log-normal diffusion %d^3 (sigma 1, rows permuted seed 1), b ~ U[-1,1) "
                        "seed 4, s=8, restart 48, tol 1e-8" % n_edge, "n": A.n, "nnz": A.nnz}
@@ -196,7 +200,7 @@ def solver_leg(m, torch, dev, n_edge=64, solves=5, bases=("f32", "f64"), warm=Tr
         for _ in range(solves + (1 if warm else 0)):
             X = torch.zeros_like(B)
             o = m.mpk_gmres_opts_default(s=8, restart=48, tol=1e-8, poly_degree=poly_degree,
-                                         basis=m.MPK_F32 if basis == "f32" else m.MPK_F64)
+                                         jacobi=jacobi, basis=m.MPK_F32 if basis == "f32" else m.MPK_F64)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             info = m.sstep_gmres_solve(plan, B, X, o, check=False)
@@ -517,7 +521,10 @@ def main():
                   # the full-size workload (n = 16.8 M), one solve per basis (kernels already loaded)
                   "n256": solver_leg(m, torch, dev, n_edge=256, solves=1, warm=False),
                   # GMRES-polynomial preconditioning of degree 32 (Sec. 5.2) on the 64^3 matrix
-                  "n64_poly32": solver_leg(m, torch, dev, n_edge=64, solves=5, poly_degree=32)}
+                  "n64_poly32": solver_leg(m, torch, dev, n_edge=64, solves=5, poly_degree=32),
+                  # right Jacobi scaling fused into the MPK (Sec. 5.1), 64^3 and full size
+                  "n64_jacobi": solver_leg(m, torch, dev, n_edge=64, solves=5, jacobi=1),
+                  "n256_jacobi": solver_leg(m, torch, dev, n_edge=256, solves=1, warm=False, jacobi=1)}
         serving = serving_leg(m)
     block = None
     if not args.no_block:

@@ -105,6 +105,13 @@ typedef struct {
                                  the first call for each (precision, p, n_rhs) measures as
                                  faster - that call runs and times both, which synchronises
                                  its stream once; results are identical either way */
+    int32_t jacobi;           /* 1 = also keep the Jacobi-scaled matrix A D^-1 (Sec. 5.1,
+                                 Eq. (Jacobi): the diagonal preconditioner fused into the SpMV
+                                 as a scaling along the columns), D = diag(A), for
+                                 MPK_JACOBI: a second copy of the SELL values per kept
+                                 precision, b_ij = a_ij / a_jj (computed in FP64), plus
+                                 D^-1 in FP64.  A column whose diagonal entry is missing or
+                                 zero is not scaled (d_j^-1 := 1).  Default 0 */
 } mpk_plan_opts;
 
 typedef struct mpk_plan_s *mpk_plan_t;
@@ -146,6 +153,9 @@ typedef struct {
                                     MPK_PERMUTED_IO, not MPK_FINAL_ONLY) */
 #define MPK_RHS_INTERLEAVED 0x20u /* X and Y blocks are row-major n x n_rhs (element (i,r) at
                                     i*n_rhs + r) instead of column-major with leading dim. */
+#define MPK_JACOBI        0x80u  /* the powers are those of A D^-1 instead of A (right
+                                    Jacobi preconditioning, Sec. 5.1); needs a plan created
+                                    with opts.jacobi = 1, else MPK_ERR_ARG */
 #define MPK_DEBUG_DROP_FLAG 0x40000000u /* test aid: the blocked task (chunk 0, power 1)
                                     does not publish its flag, so the waits on it run out and
                                     the call reports MPK_ERR_TIMEOUT at mpk_plan_sync */
@@ -233,7 +243,7 @@ mpk_status mpk_plan_sync(mpk_plan_t plan, cudaStream_t stream);
  *   X      device vector of n elements (original row order, or level order with
  *          MPK_PERMUTED_IO); read only
  *   Y      device vector of n elements, written (same order as X); must not overlap X
- *   flags  0 or MPK_PERMUTED_IO; anything else is MPK_ERR_ARG
+ *   flags  0, MPK_PERMUTED_IO and/or MPK_JACOBI; anything else is MPK_ERR_ARG
  * Scratch: a fixed array of MPK_NOALLOC_SCRATCH_BYTES per device, static in the library and
  * shared by every plan and thread of the process.  A call needs 3 vectors of n elements with
  * MPK_PERMUTED_IO, else 5, each rounded up to 256 bytes: at 32 MiB, n <= 1,398,080 (FP64,
@@ -296,6 +306,12 @@ typedef struct {
     int32_t poly_f64;       /* 1 (default): apply A q(A) with the FP64 matrix values even with
                                an FP32 basis (q evaluated in FP32 loses digits quickly with the
                                degree); 0: in the basis precision */
+    int32_t jacobi;         /* 1: right Jacobi preconditioning (Sec. 5.1, Eq. (Jacobi)): every
+                               Krylov operator application is one of A D^-1 (MPK_JACOBI; with
+                               poly_degree the polynomial is built for A D^-1 too), and each
+                               correction u is added as x += D^-1 u.  The true residual
+                               b - A x is unchanged by right preconditioning, so tol keeps its
+                               meaning.  Needs a plan created with opts.jacobi = 1.  Default 0 */
 } mpk_gmres_opts;
 
 typedef struct {

@@ -35,6 +35,7 @@ MPK_HOST_IO = 0x04
 MPK_UNBLOCKED = 0x08
 MPK_Y0_IS_X = 0x10
 MPK_RHS_INTERLEAVED = 0x20
+MPK_JACOBI = 0x80
 MPK_DEBUG_DROP_FLAG = 0x40000000
 MPK_NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -61,7 +62,8 @@ class mpk_plan_opts(ctypes.Structure):
                 ("ctas_per_sm", ctypes.c_int32), ("wait_timeout_us", ctypes.c_uint32),
                 ("schedule", ctypes.c_int32), ("slack_tasks", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("stage", ctypes.c_int32),
-                ("kernel", ctypes.c_int32), ("blocked", ctypes.c_int32)]
+                ("kernel", ctypes.c_int32), ("blocked", ctypes.c_int32),
+                ("jacobi", ctypes.c_int32)]
 
 
 class mpk_plan_info(ctypes.Structure):
@@ -87,7 +89,8 @@ class mpk_gmres_opts(ctypes.Structure):
                 ("inner_cycles", ctypes.c_int32), ("max_iters", ctypes.c_int32),
                 ("basis", ctypes.c_int), ("bcgs_passes", ctypes.c_int32),
                 ("shifts", ctypes.c_void_p), ("mpk_flags", ctypes.c_uint32),
-                ("poly_degree", ctypes.c_int32), ("poly_f64", ctypes.c_int32)]
+                ("poly_degree", ctypes.c_int32), ("poly_f64", ctypes.c_int32),
+                ("jacobi", ctypes.c_int32)]
 
 
 class mpk_gmres_info(ctypes.Structure):
@@ -207,7 +210,10 @@ def _dtype_code(torch_dtype):
 def mpk_plan_opts_default(**overrides) -> mpk_plan_opts:
     o = mpk_plan_opts()
     _check(lib().mpk_plan_opts_default(ctypes.byref(o)), "mpk_plan_opts_default")
+    names = {f for f, _ in o._fields_}
     for k, v in overrides.items():
+        if k not in names:
+            raise TypeError("mpk_plan_opts has no field %r" % k)
         setattr(o, k, v)
     return o
 
@@ -375,7 +381,10 @@ def mpk_version() -> str:
 def mpk_gmres_opts_default(**overrides) -> mpk_gmres_opts:
     o = mpk_gmres_opts()
     _check(lib().mpk_gmres_opts_default(ctypes.byref(o)), "mpk_gmres_opts_default")
+    names = {f for f, _ in o._fields_}
     for k, v in overrides.items():
+        if k not in names:
+            raise TypeError("mpk_gmres_opts has no field %r" % k)
         setattr(o, k, v)
     return o
 
@@ -407,7 +416,10 @@ def sstep_gmres_solve(plan, b, x, opts=None, shifts=None, stream=None, check=Tru
 def mpk_server_opts_default(**overrides) -> mpk_server_opts:
     o = mpk_server_opts()
     _check(lib().mpk_server_opts_default(ctypes.byref(o)), "mpk_server_opts_default")
+    names = {f for f, _ in o._fields_}
     for k, v in overrides.items():
+        if k not in names:
+            raise TypeError("mpk_server_opts has no field %r" % k)
         setattr(o, k, v)
     return o
 

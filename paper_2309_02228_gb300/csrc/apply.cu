@@ -1238,6 +1238,8 @@ mpk_status mpk_apply_internal(mpk_plan_s *P, const mpk_coeffs *co, mpk_dtype dty
     if (n_rhs < 1 || n_rhs > 1024) return MPK_ERR_ARG;
     if (dtype == MPK_F64 && !P->has64) return MPK_ERR_ARG;
     if (dtype == MPK_F32 && !P->has32) return MPK_ERR_ARG;
+    const bool jacobi = (flags & MPK_JACOBI) != 0;
+    if (jacobi && !P->jacobi) return MPK_ERR_ARG;
     const bool interleaved = (flags & MPK_RHS_INTERLEAVED) != 0;
     const bool permuted = (flags & MPK_PERMUTED_IO) != 0;
     const bool final_only = (flags & MPK_FINAL_ONLY) != 0;
@@ -1339,7 +1341,9 @@ mpk_status mpk_apply_internal(mpk_plan_s *P, const mpk_coeffs *co, mpk_dtype dty
     A.slice_row = P->slice_row.as<int32_t>();
     A.slice_len = P->slice_len.as<int32_t>();
     A.col = P->s_col.as<int32_t>();
-    A.val = dtype == MPK_F64 ? P->s_val64.p : P->s_val32.p;
+    // MPK_JACOBI: the same kernels on the values of A D^-1 (Sec. 5.1)
+    A.val = dtype == MPK_F64 ? (jacobi ? P->s_jval64.p : P->s_val64.p)
+                             : (jacobi ? P->s_jval32.p : P->s_val32.p);
 
     auto run = [&](bool blk) -> mpk_status {
         return dtype == MPK_F64 ? dispatch_nr<double>(P, A, n_rhs, V, cf, p, blk, flags, s)
@@ -1558,8 +1562,10 @@ extern "C" mpk_status mpk_apply_final_noalloc(mpk_plan_t P, const mpk_coeffs *co
     if (p < 1 || p > MPK_MAX_P || !co->a || !co->b || !co->c) return MPK_ERR_ARG;
     if (dtype != MPK_F64 && dtype != MPK_F32) return MPK_ERR_ARG;
     if ((dtype == MPK_F64 && !P->has64) || (dtype == MPK_F32 && !P->has32)) return MPK_ERR_ARG;
-    if (flags & ~(uint32_t)MPK_PERMUTED_IO) return MPK_ERR_ARG;
+    if (flags & ~(uint32_t)(MPK_PERMUTED_IO | MPK_JACOBI)) return MPK_ERR_ARG;
     const bool permuted = (flags & MPK_PERMUTED_IO) != 0;
+    const bool jacobi = (flags & MPK_JACOBI) != 0;
+    if (jacobi && !P->jacobi) return MPK_ERR_ARG;
     const int64_t n = P->n;
     if (n == 0) return MPK_OK;
     const size_t es = dtype == MPK_F64 ? 8 : 4;
@@ -1614,7 +1620,8 @@ extern "C" mpk_status mpk_apply_final_noalloc(mpk_plan_t P, const mpk_coeffs *co
     A.slice_row = P->slice_row.as<int32_t>();
     A.slice_len = P->slice_len.as<int32_t>();
     A.col = P->s_col.as<int32_t>();
-    A.val = dtype == MPK_F64 ? P->s_val64.p : P->s_val32.p;
+    A.val = dtype == MPK_F64 ? (jacobi ? P->s_jval64.p : P->s_val64.p)
+                             : (jacobi ? P->s_jval32.p : P->s_val32.p);
     if (dtype == MPK_F64) MPK_TRY((launch_powers<double, 1>(P, A, 1, V, cf, p, false, 0, s)));
     else MPK_TRY((launch_powers<float, 1>(P, A, 1, V, cf, p, false, 0, s)));
 

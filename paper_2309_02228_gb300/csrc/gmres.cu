@@ -254,16 +254,18 @@ __global__ void __launch_bounds__(256) update_kernel(const T *Q, int64_t ldq, in
     }
 }
 
-// x[i] += sum_a V[i, a] y[a]  (correction in the basis precision, added to FP64 x)
+// x[i] += sum_a V[i, a] y[a]  (correction in the basis precision, added to FP64 x); with
+// right Jacobi scaling (dinv != nullptr) x[i] += dinv[i] * (V y)[i] in FP64 (Sec. 5.1)
 template <typename T>
-__global__ void xupdate_kernel(const T *V, int64_t ldv, int k, const double *y, int64_t n, double *x) {
+__global__ void xupdate_kernel(const T *V, int64_t ldv, int k, const double *y, int64_t n,
+                               const double *dinv, double *x) {
     __shared__ T ys[MMAX + 1];
     for (int a = threadIdx.x; a < k; a += blockDim.x) ys[a] = (T)y[a];
     __syncthreads();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         T d = (T)0;
         for (int a = 0; a < k; a++) d = fma(V[(int64_t)a * ldv + i], ys[a], d);
-        x[i] += (double)d;
+        x[i] += dinv ? dinv[i] * (double)d : (double)d;
     }
 }
 
@@ -286,9 +288,9 @@ __global__ void cvt_kernel(const A *in, int64_t n, B *out) {
         out[i] = (B)in[i];
 }
 template <typename T>
-__global__ void add_f64_kernel(const T *d, int64_t n, double *x) {
+__global__ void add_f64_kernel(const T *d, int64_t n, const double *dinv, double *x) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        x[i] += (double)d[i];
+        x[i] += dinv ? dinv[i] * (double)d[i] : (double)d[i];
 }
 
 // ------------------------------------------------------------------------------------------
@@ -798,15 +800,18 @@ struct Solver {
     // out = q(A) in, or out = A in (level order, precision U): one final-only MPK
     template <typename U> mpk_status apply_poly_u(const U *in, U *out) {
         mpk_coeffs co{poly_deg, pa.data(), pb.data(), pc.data(), pgam.data()};
-        const uint32_t fl = MPK_PERMUTED_IO | MPK_FINAL_ONLY | (o.mpk_flags & MPK_UNBLOCKED);
+        const uint32_t fl = MPK_PERMUTED_IO | MPK_FINAL_ONLY | (o.mpk_flags & MPK_UNBLOCKED) | jac_flag();
         return mpk_apply_internal(P, &co, sizeof(U) == 8 ? MPK_F64 : MPK_F32, in, ldv, out, ldv, 1, fl, st);
     }
     template <typename U> mpk_status apply_A_u(const U *in, U *out) {
         double one = 1.0, zero = 0.0;
         mpk_coeffs co{1, &one, &zero, &zero, nullptr};
-        const uint32_t fl = MPK_PERMUTED_IO | MPK_FINAL_ONLY | (o.mpk_flags & MPK_UNBLOCKED);
+        const uint32_t fl = MPK_PERMUTED_IO | MPK_FINAL_ONLY | (o.mpk_flags & MPK_UNBLOCKED) | jac_flag();
         return mpk_apply_internal(P, &co, sizeof(U) == 8 ? MPK_F64 : MPK_F32, in, ldv, out, ldv, 1, fl, st);
     }
+    // right Jacobi scaling: every operator application is one of A D^-1
+    uint32_t jac_flag() const { return o.jacobi ? MPK_JACOBI : 0u; }
+    const double *dinv() const { return o.jacobi ? P->dinv64.as<double>() : nullptr; }
     // the polynomial runs with the FP64 matrix values although the basis is FP32
     bool poly64() const { return sizeof(T) == 4 && o.poly_f64 != 0; }
 
@@ -832,7 +837,7 @@ struct Solver {
             for (int k = 0; k < S; k++) b[k] = -theta[k];
         mpk_coeffs co{S, a.data(), b.data(), c.data(), nullptr};
         const mpk_dtype dt = sizeof(T) == 8 ? MPK_F64 : MPK_F32;
-        const uint32_t fl = MPK_PERMUTED_IO | MPK_Y0_IS_X | (o.mpk_flags & MPK_UNBLOCKED);
+        const uint32_t fl = MPK_PERMUTED_IO | MPK_Y0_IS_X | (o.mpk_flags & MPK_UNBLOCKED) | jac_flag();
         MPK_TRY(mpk_apply_internal(P, &co, dt, nullptr, ldv, col(j), ldv, 1, fl, st));
         return MPK_OK;
     }
@@ -890,13 +895,13 @@ struct Solver {
                     double *d0 = ptmp64.as<double>(), *d1 = d0 + ldv;
                     cvt_kernel<T, double><<<grid_rows(n), 256, 0, st>>>(t0, n, d0);
                     MPK_TRY(apply_poly_u<double>(d0, d1));
-                    add_f64_kernel<double><<<grid_rows(n), 256, 0, st>>>(d1, n, xp);
+                    add_f64_kernel<double><<<grid_rows(n), 256, 0, st>>>(d1, n, dinv(), xp);
                 } else {
                     MPK_TRY(apply_poly_u<T>(t0, t1));
-                    add_f64_kernel<T><<<grid_rows(n), 256, 0, st>>>(t1, n, xp);
+                    add_f64_kernel<T><<<grid_rows(n), 256, 0, st>>>(t1, n, dinv(), xp);
                 }
             } else {
-                xupdate_kernel<T><<<grid_rows(n, 8), 256, 0, st>>>(V.as<T>(), ldv, k, cst->y, n, xp);
+                xupdate_kernel<T><<<grid_rows(n, 8), 256, 0, st>>>(V.as<T>(), ldv, k, cst->y, n, dinv(), xp);
             }
             MPK_CUDA(cudaGetLastError());
             t_other.stop();
@@ -1126,6 +1131,7 @@ extern "C" mpk_status mpk_gmres_opts_default(mpk_gmres_opts *o) {
     o->mpk_flags = 0;
     o->poly_degree = 0;
     o->poly_f64 = 1;
+    o->jacobi = 0;
     return MPK_OK;
 }
 
@@ -1144,6 +1150,7 @@ extern "C" mpk_status sstep_gmres_solve(mpk_plan_t A, const double *b, double *x
     if (o.basis == MPK_F32 && !A->has32) return MPK_ERR_ARG;
     if (o.poly_degree > 0 && o.basis == MPK_F32 && !o.poly_f64 && !A->has32) return MPK_ERR_ARG;
     if (o.s > A->p_max) return MPK_ERR_ARG;
+    if (o.jacobi && !A->jacobi) return MPK_ERR_ARG;          // the plan keeps no A D^-1
     auto t0 = std::chrono::steady_clock::now();
     mpk_status st;
     mpk_gmres_info inf{};

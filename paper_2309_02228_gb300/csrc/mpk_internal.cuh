@@ -121,6 +121,10 @@ struct mpk_plan_s {
     // SELL-32: slice s covers rows [slice_row[s], slice_row[s+1]) (<= 32 rows); entry (j, lane)
     // at slice_ptr[s] + 32*j + lane; padding has col = -1.
     DevBuf slice_row, slice_ptr, slice_len, s_col, s_val64, s_val32;
+    // right Jacobi scaling (opts.jacobi): SELL values of A D^-1 in the same layout, and
+    // D^-1 in level order (FP64; 1 where the diagonal entry is missing or zero)
+    bool jacobi = false;
+    DevBuf s_jval64, s_jval32, dinv64;
 
     // blocked tasks: chunk c = slices [chunk_slice[c], chunk_slice[c+1]) inside one group
     DevBuf chunk_slice, chunk_row, chunk_entry, dep_lo, dep_hi;

@@ -646,6 +646,40 @@ __global__ void sell_fill_kernel(const int32_t *rp, const int32_t *ci, const dou
     }
 }
 
+// Right Jacobi scaling (Sec. 5.1, Eq. (Jacobi)).  D^-1 of the level-order matrix:
+// d_i = the sum of row i's entries in column i (columns ascend inside a row), dinv_i = 1 / d_i,
+// or 1 where d_i is zero or the entry is missing (that column is left unscaled).
+template <typename TV>
+__global__ void jacobi_dinv_kernel(const int32_t *rp, const int32_t *ci, const TV *val, int64_t n,
+                                   double *dinv) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t lo = rp[i], hi = rp[i + 1];
+        while (lo < hi) {   // first entry with column >= i
+            const int32_t mid = lo + (hi - lo) / 2;
+            if (ci[mid] < i) lo = mid + 1;
+            else hi = mid;
+        }
+        double d = 0.0;
+        for (int32_t t = lo; t < rp[i + 1] && ci[t] == i; t++) d += (double)val[t];
+        dinv[i] = d != 0.0 ? 1.0 / d : 1.0;
+    }
+}
+
+// SELL values of A D^-1: b_e = a_e * dinv[col(e)], formed in FP64 and rounded once to each
+// kept precision; padding (col -1) stays 0
+__global__ void jacobi_scale_kernel(const int32_t *s_col, const double *s64, const float *s32,
+                                    int64_t ne, const double *dinv, double *j64, float *j32) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ne;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = s_col[e];
+        double b = 0.0;
+        if (c >= 0) b = (s64 ? s64[e] : (double)s32[e]) * dinv[c];
+        if (j64) j64[e] = b;
+        if (j32) j32[e] = (float)b;
+    }
+}
+
 __global__ void row_chunk_kernel(const int32_t *chunk_row, int64_t n_chunks, int32_t *row_chunk) {
     for (int64_t c = blockIdx.x; c < n_chunks; c += gridDim.x)
         for (int32_t r = chunk_row[c] + threadIdx.x; r < chunk_row[c + 1]; r += blockDim.x)
@@ -700,6 +734,7 @@ extern "C" mpk_status mpk_plan_opts_default(mpk_plan_opts *o) {
     o->stage = -1;
     o->kernel = 0;
     o->blocked = -1;
+    o->jacobi = 0;
     return MPK_OK;
 }
 
@@ -729,6 +764,7 @@ static mpk_status plan_create_impl(const mpk_csr *A, int32_t p_max, const mpk_pl
     }
     P->has64 = o.keep_f64 != 0;
     P->has32 = o.keep_f32 != 0;
+    P->jacobi = o.jacobi != 0;
     // the groups are sized for the MPK precision: FP32 whenever an FP32 copy is kept (the
     // FP64 copy then only serves residuals), else FP64
     P->group_dtype = P->has32 ? MPK_F32 : MPK_F64;
@@ -1053,6 +1089,11 @@ static mpk_status plan_create_impl(const mpk_csr *A, int32_t p_max, const mpk_pl
     MPK_TRY(P->s_col.alloc(std::max<int64_t>(P->sell_nnz, 1) * 4));
     if (P->has64) MPK_TRY(P->s_val64.alloc(std::max<int64_t>(P->sell_nnz, 1) * 8));
     if (P->has32) MPK_TRY(P->s_val32.alloc(std::max<int64_t>(P->sell_nnz, 1) * 4));
+    if (P->jacobi) {
+        MPK_TRY(P->dinv64.alloc(std::max<int64_t>(n, 1) * 8));
+        if (P->has64) MPK_TRY(P->s_jval64.alloc(std::max<int64_t>(P->sell_nnz, 1) * 8));
+        if (P->has32) MPK_TRY(P->s_jval32.alloc(std::max<int64_t>(P->sell_nnz, 1) * 4));
+    }
     mpk_status st = mpk_build_blocks(P, s);
     if (st != MPK_OK) return st;
 
@@ -1132,6 +1173,23 @@ mpk_status mpk_build_blocks(mpk_plan_s *P, cudaStream_t s) {
         P->s_col.as<int32_t>(), P->has64 ? P->s_val64.as<double>() : nullptr,
         P->has32 ? P->s_val32.as<float>() : nullptr);
     MPK_CUDA(cudaGetLastError());
+    if (P->jacobi) {
+        if (P->has64)
+            jacobi_dinv_kernel<double><<<grid_for(P->n), 256, 0, s>>>(
+                P->rp.as<int32_t>(), P->ci.as<int32_t>(), P->val64.as<double>(), P->n,
+                P->dinv64.as<double>());
+        else
+            jacobi_dinv_kernel<float><<<grid_for(P->n), 256, 0, s>>>(
+                P->rp.as<int32_t>(), P->ci.as<int32_t>(), P->val32.as<float>(), P->n,
+                P->dinv64.as<double>());
+        MPK_CUDA(cudaGetLastError());
+        jacobi_scale_kernel<<<grid_for(P->sell_nnz), 256, 0, s>>>(
+            P->s_col.as<int32_t>(), P->has64 ? P->s_val64.as<double>() : nullptr,
+            P->has64 ? nullptr : P->s_val32.as<float>(), P->sell_nnz,
+            P->dinv64.as<double>(), P->has64 ? P->s_jval64.as<double>() : nullptr,
+            P->has32 ? P->s_jval32.as<float>() : nullptr);
+        MPK_CUDA(cudaGetLastError());
+    }
     return MPK_OK;
 }
 
@@ -1186,7 +1244,7 @@ extern "C" mpk_status mpk_plan_stats(mpk_plan_t P, mpk_plan_info *st) {
     for (const DevBuf *d : {&P->perm, &P->iperm, &P->level, &P->level_ptr, &P->group_ptr, &P->rp,
                             &P->ci, &P->val64, &P->val32, &P->entry_map, &P->slice_row,
                             &P->slice_ptr, &P->slice_len, &P->s_col, &P->s_val64, &P->s_val32,
-                            &P->chunk_slice, &P->chunk_row, &P->chunk_entry, &P->dep_lo, &P->dep_hi, &P->flags,
+                            &P->s_jval64, &P->s_jval32, &P->dinv64, &P->chunk_slice, &P->chunk_row, &P->chunk_entry, &P->dep_lo, &P->dep_hi, &P->flags,
                             &P->ctrl, &P->ws_x, &P->ws_y})
         b += d->bytes;
     st->device_bytes = (int64_t)b;

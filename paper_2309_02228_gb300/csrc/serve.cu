@@ -84,13 +84,15 @@ struct mpk_server_s {
     double now_ms() const { return std::chrono::duration<double, std::milli>(clk::now() - t0).count(); }
 
     // device bytes a request needs: input CSR (FP64), plan (permuted CSR in FP64 and FP32,
-    // SELL copies, level arrays, a p_max-deep schedule) and the solver (basis of m+1 columns in
+    // SELL copies (with padding counted as a second copy), level arrays, a p_max-deep schedule) and the solver (basis of m+1 columns in
     // the basis precision, FP64 vectors and partial sums)
     int64_t estimate(int64_t n, int64_t nnz) const {
         const int64_t m = o.gmres.restart;
         const int64_t wb = o.gmres.basis == MPK_F64 ? 8 : 4;
         const int64_t csr_in = 12 * nnz + 4 * (n + 1);
-        const int64_t plan = 2 * (12 * nnz) + 2 * 8 * nnz + 64 * n + (8 << 20);
+        // Jacobi scaling adds a second SELL value copy per precision and D^-1
+        const int64_t jac = o.gmres.jacobi ? 2 * (8 + 4) * nnz + 8 * n : 0;
+        const int64_t plan = 2 * (12 * nnz) + 2 * 8 * nnz + 64 * n + (8 << 20) + jac;
         const int64_t solver = (m + 1) * wb * ((n + 31) / 32 * 32) + 24 * n + (16 << 20);
         return csr_in + plan + solver;
     }
@@ -115,6 +117,7 @@ struct mpk_server_s {
         mpk_plan_opts_default(&po);
         po.keep_f64 = 1;
         po.keep_f32 = o.gmres.basis == MPK_F32 ? 1 : 0;
+        po.jacobi = o.gmres.jacobi ? 1 : 0;
         mpk_csr A{r.n, r.nnz, drp, dci, dval, MPK_F64};
         MPK_TRY(mpk_plan_create(&A, std::max(o.gmres.s, 1), &po, s, out));
         mpk_plan_info pi;

@@ -141,3 +141,20 @@ def test_noalloc_argument_errors(m):
         with pytest.raises(m.MpkError) as e:
             m.mpk_apply_final_noalloc(plan, co, x, y, flags=flags)   # no FP64 values / bad flag
         assert e.value.status == m.MPK_ERR_ARG
+
+
+def test_noalloc_jacobi_matches_mpk_apply(m):
+    """MPK_JACOBI (powers of A D^-1) through the allocation-free call, both orders."""
+    import torch
+    A = mi.diffusion7_lognormal(20)
+    rp, ci, vv = to_dev(A)
+    plan = m.mpk_plan_create(rp, ci, vv, 6, m.mpk_plan_opts_default(jacobi=1))
+    coeffs = _newton(6, 0.0, 2.5)
+    co = m.Coeffs.from_triples(coeffs)
+    x = torch.from_numpy(mi.uniform_vectors(A.n, 9)[0]).cuda()
+    for flags in (m.MPK_JACOBI, m.MPK_JACOBI | m.MPK_PERMUTED_IO):
+        y = torch.full_like(x, float("nan"))
+        m.mpk_apply_final_noalloc(plan, co, x, y, flags=flags)
+        ref = _reference(m, plan, coeffs, x, flags, None)
+        torch.cuda.synchronize()
+        assert torch.equal(y, ref)
