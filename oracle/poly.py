@@ -32,10 +32,10 @@ from __future__ import annotations
 import numpy as np
 
 from . import mpk as _mpk
-from .sstep import chebyshev_coeffs, spmv
+from .sstep import chebyshev_coeffs, jacobi_sweeps, spmv
 
 __all__ = ["arnoldi", "arnoldi_poly", "poly_from_arnoldi", "apply_poly", "harmonic_roots",
-           "apply_poly_roots", "poly_gmres"]
+           "apply_poly_roots", "poly_gmres", "jacobi_sweeps_gmres"]
 
 
 def arnoldi(A, r0, k):
@@ -184,3 +184,21 @@ def poly_gmres(A, b, d, m=48, tol=1e-8, max_restarts=500):
         x = x + P(V @ y)
         iters += k
     return dict(x=x, iters=iters, converged=False, gamma=gamma, interval=interval, degree=dd)
+
+
+def jacobi_sweeps_gmres(A, b, k, m=48, tol=1e-8, max_restarts=500):
+    """Right-preconditioned restarted GMRES(m) with P^-1 = k Jacobi sweeps from zero
+    (Sec. 5.1: k Jacobi iterations act as a Neumann-series polynomial preconditioner).
+    Cycles as in poly_gmres, every cycle preconditioned; returns dict(x, iters, converged)."""
+    nb = np.linalg.norm(b)
+    x = np.zeros_like(b, dtype=np.float64)
+    P = lambda v: jacobi_sweeps(A, v, k)
+    iters = 0
+    for _ in range(max_restarts):
+        r = b - spmv(A, x)
+        if np.linalg.norm(r) <= tol * nb:
+            return dict(x=x, iters=iters, converged=True)
+        V, y, kk, _, _ = _gmres_cycle(lambda v: spmv(A, P(v)), r, m, tol * nb)
+        x = x + P(V @ y)
+        iters += kk
+    return dict(x=x, iters=iters, converged=False)

@@ -348,3 +348,28 @@ def jacobi_gmres(A, b, s=8, m=48, tol=1e-8, max_restarts=1000):
     out = dict(out)
     out["x"] = dinv * out["x"]
     return out
+
+
+def jacobi_sweeps(A, v, k):
+    """k Jacobi iterations from z^0 = 0 for P^-1 v (Sec. 5.1, Eq. (Jacobi)):
+        z^{j+1} = D^-1 v - D^-1 (L + U) z^j,
+    L + U the off-diagonal entries of A, D its diagonal.  Reading for a zero (or missing)
+    diagonal entry: D is taken with that entry replaced by 1, i.e. the splitting is
+    A = D~ + (A - D~); the extra term (D - D~) z joins L + U there."""
+    n = A.n
+    d = np.zeros(n)
+    for i in range(n):
+        for e in range(A.row_ptr[i], A.row_ptr[i + 1]):
+            if A.col[e] == i:
+                d[i] += A.val[e]
+    dt = np.where(d != 0.0, d, 1.0)
+    z = np.zeros(n)
+    for _ in range(k):
+        lu = np.zeros(n)
+        for i in range(n):
+            for e in range(A.row_ptr[i], A.row_ptr[i + 1]):
+                if A.col[e] != i:
+                    lu[i] += A.val[e] * z[A.col[e]]
+        lu += (d - dt) * z
+        z = v / dt - lu / dt
+    return z

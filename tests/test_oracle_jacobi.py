@@ -46,3 +46,60 @@ def test_jacobi_gmres_converges_in_fewer_iterations():
     assert jac["converged"]
     assert np.linalg.norm(b - sstep.spmv(A, jac["x"])) <= 1e-8 * np.linalg.norm(b)
     assert jac["iters"] < plain["iters"]
+
+
+def test_one_sweep_is_the_diagonal_scaling():
+    A = mi.random_sparse(60, 0.08, 7, symmetric=False, diag=False)
+    v = mi.uniform_vectors(A.n, 2)[0]
+    _, dinv = sstep.jacobi_right(A)
+    assert np.array_equal(sstep.jacobi_sweeps(A, v, 1), dinv * v)
+
+
+def test_sweeps_equal_the_neumann_series():
+    # k sweeps from zero: z_k = sum_{j<k} B^j D^-1 v with B = I - D^-1 A (Sec. 5.1); the zero
+    # diagonal of row 3 is read as 1
+    A = _zero_diag_small()
+    v = mi.uniform_vectors(A.n, 3)[0]
+    M = _dense(A)
+    d = np.diag(M).copy()
+    dt = np.where(d != 0, d, 1.0)
+    B = np.eye(A.n) - M / dt[:, None]
+    for k in (1, 2, 5, 9):
+        want = sum(np.linalg.matrix_power(B, j) @ (v / dt) for j in range(k))
+        got = sstep.jacobi_sweeps(A, v, k)
+        assert np.allclose(got, want, rtol=1e-13, atol=1e-13 * np.abs(want).max())
+
+
+def test_many_sweeps_solve_a_diagonally_dominant_system():
+    # rows of |off-diagonal| sum <= 0.5 |a_ii|: the iteration contracts by 0.5 per sweep
+    rng = np.random.default_rng(11)
+    n = 50
+    M = np.where(rng.random((n, n)) < 0.1, rng.uniform(-1, 1, (n, n)), 0.0)
+    np.fill_diagonal(M, 0.0)
+    M += np.diag(2.0 * np.abs(M).sum(axis=1) + rng.uniform(0.5, 1.0, n))
+    S = sp.csr_matrix(M)
+    A = mi.CSR(S.indptr.astype(np.int32), S.indices.astype(np.int32), S.data.astype(np.float64))
+    v = mi.uniform_vectors(n, 4)[0]
+    x = np.linalg.solve(M, v)
+    z = sstep.jacobi_sweeps(A, v, 60)
+    assert np.abs(z - x).max() <= 2 * 0.5 ** 60 * np.abs(x).max() * n + 1e-14
+
+
+def test_sweeps_preconditioned_gmres():
+    from oracle import poly
+    A = mi.diffusion7_lognormal(8)
+    b = mi.uniform_vectors(A.n, 4)[0]
+    one = sstep.jacobi_gmres(A, b, s=8, m=48, tol=1e-8)
+    four = poly.jacobi_sweeps_gmres(A, b, 4, m=48, tol=1e-8)
+    assert four["converged"]
+    assert np.linalg.norm(b - sstep.spmv(A, four["x"])) <= 1e-8 * np.linalg.norm(b)
+    assert four["iters"] < one["iters"]
+
+
+def _zero_diag_small():
+    A = mi.poisson2d_5pt(7)
+    val = A.val.copy()
+    for e in range(A.row_ptr[3], A.row_ptr[4]):
+        if A.col[e] == 3:
+            val[e] = 0.0
+    return mi.CSR(A.row_ptr, A.col, val)
