@@ -306,12 +306,21 @@ typedef struct {
     int32_t poly_f64;       /* 1 (default): apply A q(A) with the FP64 matrix values even with
                                an FP32 basis (q evaluated in FP32 loses digits quickly with the
                                degree); 0: in the basis precision */
-    int32_t jacobi;         /* 1: right Jacobi preconditioning (Sec. 5.1, Eq. (Jacobi)): every
-                               Krylov operator application is one of A D^-1 (MPK_JACOBI; with
+    int32_t jacobi;         /* k = 1: right Jacobi preconditioning (Sec. 5.1, Eq. (Jacobi)),
+                               one sweep from zero = the diagonal scaling D^-1: every Krylov
+                               operator application is one of A D^-1 (MPK_JACOBI; with
                                poly_degree the polynomial is built for A D^-1 too), and each
-                               correction u is added as x += D^-1 u.  The true residual
-                               b - A x is unchanged by right preconditioning, so tol keeps its
-                               meaning.  Needs a plan created with opts.jacobi = 1.  Default 0 */
+                               correction u is added as x += D^-1 u.
+                               k >= 2 (up to 64): k Jacobi sweeps from zero as the right
+                               preconditioner, P^-1 = D^-1 p(A D^-1) with the Neumann
+                               polynomial p(t) = sum_{j<k} (1 - t)^j (the sweeps' closed form);
+                               cycles run single columns on A D^-1 p(A D^-1), one final-only
+                               MPK of k - 1 powers plus one SpMV per column, applied in FP64
+                               unless poly_f64 = 0; excludes poly_degree.  info.poly_degree
+                               reports k - 1 and poly_interval {0, 0}.
+                               The true residual b - A x is unchanged by right preconditioning,
+                               so tol keeps its meaning.  Needs a plan created with
+                               opts.jacobi = 1.  Default 0 */
 } mpk_gmres_opts;
 
 typedef struct {

@@ -709,8 +709,8 @@ struct Solver {
         MPK_TRY(gpart2.alloc_on((size_t)upd_grid * SMAX * SMAX * sizeof(double) + 64, st));
         MPK_TRY(cstate.alloc_on(sizeof(CycleState), st));
         MPK_TRY(dth.alloc_on(SMAX * sizeof(double), st));
-        if (o.poly_degree > 0) MPK_TRY(ptmp.alloc_on((size_t)2 * ldv * sizeof(T), st));
-        if (o.poly_degree > 0 && poly64()) MPK_TRY(ptmp64.alloc_on((size_t)2 * ldv * sizeof(double), st));
+        if (uses_poly()) MPK_TRY(ptmp.alloc_on((size_t)2 * ldv * sizeof(T), st));
+        if (uses_poly() && poly64()) MPK_TRY(ptmp64.alloc_on((size_t)2 * ldv * sizeof(double), st));
         MPK_TRY(vec.alloc_on((size_t)3 * ldv * sizeof(double) + 64 * sizeof(double), st));
         bp = vec.as<double>();
         xp = bp + ldv;
@@ -809,6 +809,8 @@ struct Solver {
         const uint32_t fl = MPK_PERMUTED_IO | MPK_FINAL_ONLY | (o.mpk_flags & MPK_UNBLOCKED) | jac_flag();
         return mpk_apply_internal(P, &co, sizeof(U) == 8 ? MPK_F64 : MPK_F32, in, ldv, out, ldv, 1, fl, st);
     }
+    // a polynomial preconditioner: the GMRES polynomial, or k >= 2 Jacobi sweeps
+    bool uses_poly() const { return o.poly_degree > 0 || o.jacobi >= 2; }
     // right Jacobi scaling: every operator application is one of A D^-1
     uint32_t jac_flag() const { return o.jacobi ? MPK_JACOBI : 0u; }
     const double *dinv() const { return o.jacobi ? P->dinv64.as<double>() : nullptr; }
@@ -967,6 +969,22 @@ struct Solver {
         return true;
     }
 
+    // k Jacobi sweeps from zero (Sec. 5.1, Eq. (Jacobi)) as a right preconditioner: with
+    // B = I - D^-1 A the sweeps give z_k = sum_{j<k} B^j D^-1 v, and since
+    // B^j D^-1 = D^-1 (I - A D^-1)^j this is P^-1 = D^-1 p(A D^-1) with the Neumann polynomial
+    // p(t) = sum_{j<k} (1 - t)^j: one final-only MPK on A D^-1 with a_j = -1, b_j = 1,
+    // gamma_j = 1.  The Krylov operator is A D^-1 p(A D^-1) and the correction D^-1 p(A D^-1) V y.
+    void setup_sweeps(int k) {
+        const int dd = k - 1;
+        pa.assign(dd, -1.0);
+        pb.assign(dd, 1.0);
+        pc.assign(dd, 0.0);
+        pgam.assign(dd + 1, 1.0);
+        poly_deg = dd;
+        piv_lo = piv_hi = 0.0;
+        poly_on = true;
+    }
+
     mpk_status setup_poly(int k) {
         const int dd = std::min(std::min(o.poly_degree, k - 1), MPK_MAX_P);
         if (dd < 1) return MPK_OK;   // cycle too short: no polynomial
@@ -1044,7 +1062,11 @@ struct Solver {
         MPK_CUDA(cudaStreamSynchronize(st));
         s_cur = o.s;
         if (o.shifts) theta.assign(o.shifts, o.shifts + o.s);
-        const bool need_shifts = !o.shifts || o.poly_degree > 0;
+        bool need_shifts = !o.shifts || o.poly_degree > 0;
+        if (o.jacobi >= 2) {   // Jacobi sweeps: fixed polynomial, single-column cycles from the start
+            setup_sweeps(o.jacobi);
+            need_shifts = false;
+        }
         bool have_shifts = !need_shifts;
         mpk_status result = MPK_ERR_NOT_CONVERGED;
         double relres = 1.0, best_rel = 1e300;
@@ -1144,11 +1166,13 @@ extern "C" mpk_status sstep_gmres_solve(mpk_plan_t A, const double *b, double *x
     else mpk_gmres_opts_default(&o);
     if (o.s < 1 || o.s > SMAX || o.restart < o.s || o.restart > MMAX || !(o.tol > 0) ||
         o.bcgs_passes < 1 || o.bcgs_passes > 2 || o.max_outer < 0 || o.poly_degree < 0 ||
-        o.poly_degree > MPK_MAX_P)
+        o.poly_degree > MPK_MAX_P || o.jacobi < 0 || o.jacobi > MPK_MAX_P + 1 ||
+        (o.jacobi >= 2 && o.poly_degree > 0))
         return MPK_ERR_ARG;
     if (!A->has64) return MPK_ERR_ARG;                       // FP64 residual needs FP64 values
     if (o.basis == MPK_F32 && !A->has32) return MPK_ERR_ARG;
-    if (o.poly_degree > 0 && o.basis == MPK_F32 && !o.poly_f64 && !A->has32) return MPK_ERR_ARG;
+    if ((o.poly_degree > 0 || o.jacobi >= 2) && o.basis == MPK_F32 && !o.poly_f64 && !A->has32)
+        return MPK_ERR_ARG;
     if (o.s > A->p_max) return MPK_ERR_ARG;
     if (o.jacobi && !A->jacobi) return MPK_ERR_ARG;          // the plan keeps no A D^-1
     auto t0 = std::chrono::steady_clock::now();

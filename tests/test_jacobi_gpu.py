@@ -8,7 +8,10 @@ SpMV as A D^-1).
 * value updates refresh the scaled copy;
 * the Jacobi-preconditioned solve reaches the FP64 true residual 1e-8 (recomputed on the CPU)
   with fewer Krylov columns than the plain solve on the log-normal diffusion matrix, and its
-  solution agrees with the oracle's right-preconditioned s-step GMRES.
+  solution agrees with the oracle's right-preconditioned s-step GMRES;
+* k Jacobi sweeps (the Neumann polynomial in A D^-1 run by one final-only MPK) equal the
+  oracle's sweeps of Eq. (Jacobi), and the solve preconditioned by them needs fewer Krylov
+  columns than the diagonal scaling alone and agrees with the oracle's.
 All calls go through the C ABI."""
 import numpy as np
 import pytest
@@ -230,3 +233,63 @@ def test_jacobi_with_polynomial_and_blocked_equals_unblocked(m):
     x3, i3 = _solve(m, plan, b, s=8, restart=48, tol=1e-8, jacobi=1, poly_degree=12)
     assert i3["status_code"] == m.MPK_OK, i3
     assert np.linalg.norm(b - sstep.spmv(A, x3)) <= 1e-8 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("k", [2, 5])
+def test_neumann_mpk_equals_jacobi_sweeps(m, k):
+    """D^-1 p(A D^-1) v with p(t) = sum_{j<k} (1 - t)^j, one final-only MPK_JACOBI call with
+    a = -1, b = 1, gamma = 1, equals k Jacobi sweeps from zero (the oracle runs Eq. (Jacobi)
+    itself); compared as p(A D^-1) v = D~ z_k."""
+    import torch
+    A = MATS["zero_diag"]() if k == 2 else MATS["diff7_12"]()
+    B, dinv = sstep.jacobi_right(A)
+    cf = [(-1.0, 1.0, 0.0)] * (k - 1)
+    v = mi.uniform_vectors(A.n, 8)[0]
+    want = sstep.jacobi_sweeps(A, v, k) / dinv
+    den = abs_powers(B, cf, v).sum(axis=0)
+    rp, ci, vv = to_dev(A)
+    plan = m.mpk_plan_create(rp, ci, vv, max(k - 1, 1), m.mpk_plan_opts_default(jacobi=1, blocked=1))
+    X = torch.from_numpy(v).cuda()
+    for extra in (0, m.MPK_UNBLOCKED):
+        Y = torch.full_like(X, float("nan"))
+        m.mpk_apply(plan, m.Coeffs.from_triples(cf, [1.0] * k), X, Y,
+                    flags=m.MPK_JACOBI | m.MPK_FINAL_ONLY | extra)
+        assert m.mpk_plan_sync(plan) == m.MPK_OK
+        assert max_rel_err(Y.cpu().numpy(), want, den) <= 64 * k * U64
+
+
+@pytest.mark.parametrize("basis", ["f32", "f64"])
+def test_jacobi_sweeps_preconditioned_solve(m, basis):
+    """k Jacobi sweeps as the right preconditioner (Sec. 5.1): the solve reaches 1e-8 in fewer
+    Krylov columns than with the diagonal scaling alone, and agrees with the oracle's GMRES
+    preconditioned by the sweeps themselves."""
+    from oracle import poly
+    A = SOLVE_MATS["diff7_14"]()
+    b = mi.uniform_vectors(A.n, 4)[0]
+    plan = _plan(m, A)
+    bs = m.MPK_F32 if basis == "f32" else m.MPK_F64
+    _, one = _solve(m, plan, b, basis=bs, s=8, restart=48, tol=1e-8, jacobi=1)
+    for k in (2, 4):
+        x, info = _solve(m, plan, b, basis=bs, s=8, restart=48, tol=1e-8, jacobi=k)
+        assert info["status_code"] == m.MPK_OK, info
+        assert info["poly_degree"] == k - 1
+        rr = np.linalg.norm(b - sstep.spmv(A, x)) / np.linalg.norm(b)
+        assert rr <= 1e-8, rr
+        assert info["iters"] < one["iters"], (k, info["iters"], one["iters"])
+        ref = poly.jacobi_sweeps_gmres(A, b, k, m=48, tol=1e-10)
+        assert ref["converged"]
+        M = sp.csr_matrix((A.val, A.col, A.row_ptr), shape=(A.n, A.n)).toarray()
+        kappa = np.linalg.cond(M)
+        assert np.linalg.norm(x - ref["x"]) <= kappa * 2e-8 * np.linalg.norm(ref["x"])
+
+
+def test_jacobi_sweeps_blocked_equals_unblocked_and_argument_errors(m):
+    A = mi.diffusion7_lognormal(10)
+    b = mi.uniform_vectors(A.n, 2)[0]
+    plan = _plan(m, A, l2_budget_bytes=50_000, blocked=1)
+    x1, i1 = _solve(m, plan, b, s=8, restart=48, tol=1e-8, jacobi=6)
+    x2, i2 = _solve(m, plan, b, s=8, restart=48, tol=1e-8, jacobi=6, mpk_flags=m.MPK_UNBLOCKED)
+    assert i1["status_code"] == m.MPK_OK and i1["iters"] == i2["iters"] and np.array_equal(x1, x2)
+    for kw in ({"jacobi": 3, "poly_degree": 8}, {"jacobi": 65}, {"jacobi": -1}):
+        _, info = _solve(m, plan, b, s=8, restart=48, tol=1e-8, **kw)
+        assert info["status_code"] == m.MPK_ERR_ARG, kw
