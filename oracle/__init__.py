@@ -10,6 +10,8 @@ leg of ``bench.py`` may import this package.  It shares no code with the GPU lib
 * ``sstep.py``: textbook GMRES and s-step GMRES (Alg. 3), CholQR2, Leja ordering, Chebyshev
   coefficients, FP64 iterative refinement, in NumPy.
 * ``poly.py``: the GMRES polynomial preconditioner (Sec. 5.2) and right-preconditioned GMRES.
+* ``gs2.py``: two-stage Gauss-Seidel (GS2) preconditioning, the MPK of the GS2-preconditioned
+  operator (powers made of sub-powers) and s-step GMRES with it.
 """
 from __future__ import annotations
 

@@ -122,10 +122,13 @@ def ritz_values(H, k):
     return np.real(np.linalg.eigvals(H[:k, :k]))
 
 
-def gmres(A, b, x0=None, m=30, tol=1e-8, max_restarts=1000, cgs=False):
+def gmres(A, b, x0=None, m=30, tol=1e-8, max_restarts=1000, cgs=False, precond=None):
     """Restarted GMRES(m), Alg. 3(a)+(b): Arnoldi with modified (or classical) Gram-Schmidt,
     Givens rotations, residual check after each column.  Stops when the estimated residual
-    norm is <= tol * ||b||.  Returns dict(x, iters, hist, H_first, k_first, converged)."""
+    norm is <= tol * ||b||.  ``precond`` (a function v -> P^-1 v) makes it right-preconditioned:
+    the Arnoldi operator is A P^-1 and the correction is P^-1 (Q y).
+    Returns dict(x, iters, hist, H_first, k_first, converged)."""
+    M = precond if precond is not None else (lambda v: v)
     n = b.shape[0]
     x = np.zeros(n) if x0 is None else x0.astype(np.float64).copy()
     nb = np.linalg.norm(b)
@@ -149,7 +152,7 @@ def gmres(A, b, x0=None, m=30, tol=1e-8, max_restarts=1000, cgs=False):
         Q[:, 0] = r / beta
         k = 0
         for j in range(m):
-            w = spmv(A, Q[:, j])
+            w = spmv(A, M(Q[:, j]))
             if cgs:
                 h = Q[:, : j + 1].T @ w
                 w = w - Q[:, : j + 1] @ h
@@ -179,12 +182,12 @@ def gmres(A, b, x0=None, m=30, tol=1e-8, max_restarts=1000, cgs=False):
         if cycle == 0:
             H_first, k_first = Harn, k
         y = np.linalg.solve(np.triu(H[:k, :k]), g[:k])
-        x = x + Q[:, :k] @ y
+        x = x + M(Q[:, :k] @ y)
     return dict(x=x, iters=iters, hist=hist, H_first=H_first, k_first=k_first, converged=False)
 
 
 def sstep_gmres(A, b, x0=None, s=4, m=48, tol=1e-8, max_restarts=1000, shifts=None,
-                bcgs_passes=1, basis="newton"):
+                bcgs_passes=1, basis="newton", precond=None):
     """Restarted s-step GMRES, Alg. 3(a)+(c).
 
     Per block of s columns starting at basis column j: the MPK builds
@@ -197,7 +200,10 @@ def sstep_gmres(A, b, x0=None, s=4, m=48, tol=1e-8, max_restarts=1000, shifts=No
     column; then Givens rotations update the least-squares residual.
 
     Without ``shifts`` the first cycle runs plain GMRES(m) and its Ritz values give the
-    shifts (Sec. 4).  Returns dict(x, iters, hist, shifts, converged, block_hist)."""
+    shifts (Sec. 4).  ``precond`` (v -> P^-1 v) makes it right-preconditioned: the basis is
+    that of A P^-1, y_k = (A P^-1 - theta_k I) y_{k-1}, and x += P^-1 (Q y).
+    Returns dict(x, iters, hist, shifts, converged, block_hist)."""
+    M = precond if precond is not None else (lambda v: v)
     n = b.shape[0]
     x = np.zeros(n) if x0 is None else x0.astype(np.float64).copy()
     nb = np.linalg.norm(b)
@@ -206,7 +212,7 @@ def sstep_gmres(A, b, x0=None, s=4, m=48, tol=1e-8, max_restarts=1000, shifts=No
     iters = 0
     cycle0 = 0
     if basis == "newton" and shifts is None:
-        r0 = gmres(A, b, x, m=m, tol=tol, max_restarts=1)
+        r0 = gmres(A, b, x, m=m, tol=tol, max_restarts=1, precond=precond)
         x = r0["x"]
         iters += r0["iters"]
         hist.extend(r0["hist"][1:])
@@ -239,7 +245,13 @@ def sstep_gmres(A, b, x0=None, s=4, m=48, tol=1e-8, max_restarts=1000, shifts=No
         j = 0
         while j < m and not done:
             S = min(s, m - j)
-            V = _mpk(A, S, newton_coeffs(theta[:S]), Q[:, j])
+            if precond is None:
+                V = _mpk(A, S, newton_coeffs(theta[:S]), Q[:, j])
+            else:
+                V = np.zeros((S + 1, n))
+                V[0] = Q[:, j]
+                for i in range(S):
+                    V[i + 1] = spmv(A, M(V[i])) - theta[i] * V[i]
             W = V[1:].T.copy()
             C = np.zeros((j + 1, S))
             for _ in range(bcgs_passes):
@@ -286,7 +298,7 @@ def sstep_gmres(A, b, x0=None, s=4, m=48, tol=1e-8, max_restarts=1000, shifts=No
             block_hist.append(abs(g[k]) / nb)
             j += S
         y = np.linalg.solve(np.triu(H[:k, :k]), g[:k])
-        x = x + Q[:, :k] @ y
+        x = x + M(Q[:, :k] @ y)
     r = b - spmv(A, x)
     return dict(x=x, iters=iters, hist=hist, shifts=theta,
                 converged=bool(np.linalg.norm(r) <= tol * nb), block_hist=block_hist)
