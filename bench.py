@@ -179,19 +179,20 @@ def run_reference(args):
 
 
 def solver_leg(m, torch, dev, n_edge=64, solves=5, bases=("f32", "f64"), warm=True, poly_degree=0,
-               jacobi=0):
+               jacobi=0, gs2=0, gs2_gamma=1):
     """s-step GMRES(s=8, restart 48) to rel. residual 1e-8 on the log-normal diffusion matrix
     (7-point, sigma = 1, rows randomly permuted) at n_edge^3, FP32 basis + FP64 refinement vs an
     FP64 basis: solves/s and per-solve latency (p50/p99) over `solves` solves each.  poly_degree:
     GMRES-polynomial preconditioning (Sec. 5.2); jacobi: right Jacobi scaling fused into the
-    MPK (Sec. 5.1)."""
+    MPK (Sec. 5.1); gs2: two-stage Gauss-Seidel with gs2_gamma inner iterations as MPK
+    sub-powers (Sec. 5, Alg. GS2)."""
     A = mi.diffusion7_lognormal(n_edge)
     b = mi.uniform_vectors(A.n, 4)[0]
     rp = torch.from_numpy(A.row_ptr).to(dev)
     ci = torch.from_numpy(A.col).to(dev)
     vv = torch.from_numpy(A.val).to(dev)
     plan = m.mpk_plan_create(rp, ci, vv, 8, m.mpk_plan_opts_default(keep_f64=1, keep_f32=1,
-                                                                    jacobi=jacobi))
+                                                                    jacobi=1 if (jacobi or gs2) else 0))
     B = torch.from_numpy(b).to(dev)
     out = {"workload": "7-point log-normal diffusion %d^3 (sigma 1, rows permuted seed 1), b ~ U[-1,1) "
                        "seed 4, s=8, restart 48, tol 1e-8" % n_edge, "n": A.n, "nnz": A.nnz}
@@ -200,7 +201,8 @@ def solver_leg(m, torch, dev, n_edge=64, solves=5, bases=("f32", "f64"), warm=Tr
         for _ in range(solves + (1 if warm else 0)):
             X = torch.zeros_like(B)
             o = m.mpk_gmres_opts_default(s=8, restart=48, tol=1e-8, poly_degree=poly_degree,
-                                         jacobi=jacobi, basis=m.MPK_F32 if basis == "f32" else m.MPK_F64)
+                                         jacobi=jacobi, gs2=gs2, gs2_gamma=gs2_gamma,
+                                         basis=m.MPK_F32 if basis == "f32" else m.MPK_F64)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             info = m.sstep_gmres_solve(plan, B, X, o, check=False)
@@ -214,6 +216,39 @@ def solver_leg(m, torch, dev, n_edge=64, solves=5, bases=("f32", "f64"), warm=Tr
         out[basis] = {"solves_per_s": 1e3 * len(lat) / sum(lat), "p50_ms": float(np.percentile(lat, 50)),
                       "p99_ms": float(np.percentile(lat, 99)), "iters": iters[-1],
                       "rel_residual": max(rr), "converged": ok}
+    return out
+
+
+def gs2_mpk_leg(m, torch, dev, A, rp, ci, vv, p=P_MAIN, gammas=(1, 2), reps=20):
+    """MPK of the GS2-preconditioned operator (Sec. 5, Alg. GS2(b)) on the 27-point benchmark
+    matrix, level-order I/O: each power is gamma inner stages on the strictly lower part plus
+    the product with A, all blocked as sub-powers in one launch, against the same steps as
+    separate launches.  Flops per power: 2 nnz (product) + gamma * 2 nnz_L (inner stages)."""
+    n, nnz = A.n, A.nnz
+    nnz_l = int(np.sum(A.col < np.repeat(np.arange(n, dtype=np.int64), np.diff(A.row_ptr))))
+    out = {"workload": "27-point 160^3 (seed 2), GS2 from zero, Newton p=%d (Leja on [0,2]), "
+                       "level-order I/O" % p, "nnz_lower": nnz_l}
+    theta = mi.leja_points_interval(0.0, 2.0, p)
+    cf = m.mpk_coeffs_newton(theta)
+    for dt, name in ((torch.float64, "f64"), (torch.float32, "f32")):
+        vals = vv if dt == torch.float64 else vv.float()
+        # blocking depth in sub-powers: every stage of every power in one blocked launch
+        plan = m.mpk_plan_create(rp, ci, vals, p * (max(gammas) + 1), m.mpk_plan_opts_default(
+            assume_symmetric=1, blocked=1, jacobi=1))
+        Y = torch.zeros((p + 1) * n, dtype=dt, device=dev)
+        Y[:n] = 1.0
+        res = {}
+        for g in gammas:
+            fl = m.MPK_GS2 | m.MPK_GS2_GAMMA(g) | m.MPK_PERMUTED_IO | m.MPK_Y0_IS_X
+            tb = time_stream(lambda: m.mpk_apply(plan, cf, None, Y, flags=fl), reps, torch)
+            tu = time_stream(lambda: m.mpk_apply(plan, cf, None, Y, flags=fl | m.MPK_UNBLOCKED), reps, torch)
+            flop = p * (2.0 * nnz + g * 2.0 * nnz_l)
+            res["gamma%d" % g] = {"blocked_ms": tb, "unblocked_ms": tu, "speedup": tu / tb,
+                                  "blocked_gflops": flop / tb / 1e6, "unblocked_gflops": flop / tu / 1e6,
+                                  "matrix_passes": p * (g + 1)}
+        assert m.mpk_plan_sync(plan) == m.MPK_OK
+        out[name] = res
+        del plan
     return out
 
 
@@ -514,6 +549,9 @@ def main():
     assert m.mpk_plan_sync(plan32) == m.MPK_OK
     del plan32
 
+    # ---- GS2-preconditioned MPK (sub-powers) blocked vs one launch per sub-power
+    gs2_mpk = gs2_mpk_leg(m, torch, dev, A, rp, ci, vv, reps=reps)
+
     # ---- solver and serving legs (solves/s and latency at rel. residual 1e-8)
     solver = serving = None
     if not args.no_solver:
@@ -524,7 +562,10 @@ def main():
                   "n64_poly32": solver_leg(m, torch, dev, n_edge=64, solves=5, poly_degree=32),
                   # right Jacobi scaling fused into the MPK (Sec. 5.1), 64^3 and full size
                   "n64_jacobi": solver_leg(m, torch, dev, n_edge=64, solves=5, jacobi=1),
-                  "n256_jacobi": solver_leg(m, torch, dev, n_edge=256, solves=1, warm=False, jacobi=1)}
+                  "n256_jacobi": solver_leg(m, torch, dev, n_edge=256, solves=1, warm=False, jacobi=1),
+                  # two-stage Gauss-Seidel (gamma = 1) as MPK sub-powers (Sec. 5, Alg. GS2)
+                  "n64_gs2": solver_leg(m, torch, dev, n_edge=64, solves=5, gs2=1, gs2_gamma=1),
+                  "n256_gs2": solver_leg(m, torch, dev, n_edge=256, solves=1, warm=False, gs2=1, gs2_gamma=1)}
         serving = serving_leg(m)
     block = None
     if not args.no_block:
@@ -586,7 +627,7 @@ def main():
         "speedup_vs_pxspmv": sweep["p%d" % P_MAIN]["speedup"],
         "sweep": sweep, "kernel_only": kern, "fp32": fp32, "plan_ms": plan_ms,
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "solver": solver, "serving": serving,
-        "block_mpk": block,
+        "block_mpk": block, "gs2_mpk": gs2_mpk,
         "gpu_launches": launches_per_step * args.steps, "clocks": clk,
     }
     if rank == 0:

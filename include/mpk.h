@@ -111,7 +111,9 @@ typedef struct {
                                  MPK_JACOBI: a second copy of the SELL values per kept
                                  precision, b_ij = a_ij / a_jj (computed in FP64), plus
                                  D^-1 in FP64.  A column whose diagonal entry is missing or
-                                 zero is not scaled (d_j^-1 := 1).  Default 0 */
+                                 zero is not scaled (d_j^-1 := 1).  Also builds the bit mask
+                                 of strictly lower entries (in the caller's row order) that
+                                 MPK_GS2 needs: one uint32 per 32 stored entries.  Default 0 */
 } mpk_plan_opts;
 
 typedef struct mpk_plan_s *mpk_plan_t;
@@ -156,6 +158,23 @@ typedef struct {
 #define MPK_JACOBI        0x80u  /* the powers are those of A D^-1 instead of A (right
                                     Jacobi preconditioning, Sec. 5.1); needs a plan created
                                     with opts.jacobi = 1, else MPK_ERR_ARG */
+#define MPK_GS2           0x100u /* the powers are those of the GS2-preconditioned operator
+                                    A P^-1 (Sec. 5, Alg. GS2: one two-stage Gauss-Seidel
+                                    iteration from z^0 = 0 with gamma inner Jacobi-Richardson
+                                    iterations; L, D, U split in the caller's row order, a
+                                    zero or missing diagonal entry read as 1):
+                                      y_k = a_k A P^-1 y_{k-1} + b_k y_{k-1} + c_k y_{k-2}.
+                                    Each power runs as gamma + 1 sub-powers over the matrix
+                                    (Alg. GS2(b): the gamma inner stages on the Jacobi-scaled
+                                    strictly lower part, then the product with A D^-1), which
+                                    the blocked kernel schedules like powers, so L and U are
+                                    reused from cache across the stages.  Add
+                                    MPK_GS2_GAMMA(gamma), gamma in 0..15 (0 = Jacobi).  Needs a
+                                    plan created with opts.jacobi = 1 and n_rhs = 1
+                                    (MPK_ERR_ARG / MPK_ERR_UNIMPLEMENTED otherwise); excludes
+                                    MPK_JACOBI; the CTA-task kernel (opts.kernel = 1) runs it
+                                    unblocked. */
+#define MPK_GS2_GAMMA(g)  ((((uint32_t)(g)) & 15u) << 12)
 #define MPK_DEBUG_DROP_FLAG 0x40000000u /* test aid: the blocked task (chunk 0, power 1)
                                     does not publish its flag, so the waits on it run out and
                                     the call reports MPK_ERR_TIMEOUT at mpk_plan_sync */
@@ -321,6 +340,16 @@ typedef struct {
                                The true residual b - A x is unchanged by right preconditioning,
                                so tol keeps its meaning.  Needs a plan created with
                                opts.jacobi = 1.  Default 0 */
+    int32_t gs2;            /* 1: right preconditioning by one two-stage Gauss-Seidel
+                               iteration from zero (Sec. 5, Alg. GS2) with gs2_gamma inner
+                               Jacobi-Richardson iterations: the s-step basis is that of
+                               A P^-1 (MPK_GS2, every power gs2_gamma + 1 sub-powers, blocked
+                               like powers), the first cycle's Ritz values are those of
+                               A P^-1, and each correction u is added as x += P^-1 u,
+                               evaluated in FP64.  Needs a plan created with opts.jacobi = 1;
+                               excludes jacobi and poly_degree.  Default 0 */
+    int32_t gs2_gamma;      /* inner iterations of GS2, 0..15 (default 1, as in the paper's
+                               GS2 experiments) */
 } mpk_gmres_opts;
 
 typedef struct {

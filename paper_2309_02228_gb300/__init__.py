@@ -36,6 +36,13 @@ MPK_UNBLOCKED = 0x08
 MPK_Y0_IS_X = 0x10
 MPK_RHS_INTERLEAVED = 0x20
 MPK_JACOBI = 0x80
+MPK_GS2 = 0x100
+
+
+def MPK_GS2_GAMMA(gamma):
+    """Inner-iteration count of MPK_GS2 in the flag word (0..15)."""
+    return (int(gamma) & 15) << 12
+
 MPK_DEBUG_DROP_FLAG = 0x40000000
 MPK_NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -90,7 +97,7 @@ class mpk_gmres_opts(ctypes.Structure):
                 ("basis", ctypes.c_int), ("bcgs_passes", ctypes.c_int32),
                 ("shifts", ctypes.c_void_p), ("mpk_flags", ctypes.c_uint32),
                 ("poly_degree", ctypes.c_int32), ("poly_f64", ctypes.c_int32),
-                ("jacobi", ctypes.c_int32)]
+                ("jacobi", ctypes.c_int32), ("gs2", ctypes.c_int32), ("gs2_gamma", ctypes.c_int32)]
 
 
 class mpk_gmres_info(ctypes.Structure):

@@ -28,6 +28,8 @@ struct VecSet {
     int final_only;
     int use_gamma;
     int p_total;          // last absolute power of the whole call
+    int gs2_steps;        // MPK_GS2: gamma + 1 steps per power (0: plain powers)
+    void *h[2];           // MPK_GS2: ring of the inner iterates h_j (h_j in h[j & 1])
 };
 
 __device__ __forceinline__ void *ring_of(const VecSet &v, int k) {
@@ -374,6 +376,88 @@ __device__ __forceinline__ void slice_power(const SellView &A, int64_t s, const 
         row_sum<T, NR, SM, SV, BGMAX>(colp + lane, valp + lane, L, row, y1, n_rhs, q0, acc);
         row_finish<T, NR>(acc, row, n_rhs, q0, V, k, cf);
     }
+}
+
+// ------------------------------------------------------------------------------------------
+// Two-stage Gauss-Seidel (GS2, Sec. 5, Alg. GS2) as sub-powers of the MPK.  With B = A D~^-1
+// (the Jacobi-scaled values; D~ the diagonal, zero or missing entries read as 1) and L_B its
+// strictly lower part in the caller's row order (bit `lane` of lmask[slice_ptr[s] + j]), one
+// GS2 iteration from zero is P^-1 v = D~^-1 h_gamma with
+//     h_0 = v,   h_j = v - L_B h_{j-1}   (j = 1..gamma),
+// Alg. GS2's g_j = g_0 - D^-1 L g_{j-1} multiplied through by D~ (h_j = D~ g_j).  Power k of
+// the preconditioned operator is then gamma + 1 steps over the matrix:
+//     step j = 1..gamma:   h_j = y_{k-1} - L_B h_{j-1}            (h_0 = y_{k-1})
+//     step gamma + 1:      y_k = a_k B h_gamma + b_k y_{k-1} + c_k y_{k-2}
+// at absolute step t = (k - 1)(gamma + 1) + j.  The h_j live in a ring of two vectors: step t
+// starts at a row only after step t - 1 has finished at every row it reads and at the row
+// itself, so the step that last read the slot being overwritten (t - 1) is done there.
+// Row sums run over the stored entries in ascending order (entries outside L_B are skipped
+// by a select, FP64 keeps even / odd partial sums by entry position), so the blocked and
+// unblocked schedules give identical values.
+// ------------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void slice_gs2_step(const SellView &A, const uint32_t *lmask, int64_t s,
+                                               int lane, const VecSet &V, int t, const Coefs &cf) {
+    const int ST = V.gs2_steps;
+    const int k = (t - 1) / ST + 1;
+    const int j = t - (k - 1) * ST;
+    const bool full = j == ST;
+    const int32_t r0 = __ldg(A.slice_row + s), r1 = __ldg(A.slice_row + s + 1);
+    const int32_t row = r0 + lane;
+    const bool valid = row < r1;
+    const int32_t L = valid ? __ldg(A.slice_len + s) : 0;
+    const long long sp = __ldg(A.slice_ptr + s);
+    const long long o = 32ll * sp + lane;
+    const T *yk1 = vec_ro<T>(V, k - 1);
+    // ring slots by select, not by an indexed load (keeps the struct out of local memory)
+    const T *in = j == 1 ? yk1 : reinterpret_cast<const T *>(((j - 1) & 1) ? V.h[1] : V.h[0]);
+    const T *gval = reinterpret_cast<const T *>(A.val);
+    constexpr bool TWO = sizeof(T) == 8;
+    constexpr int BG = 8;
+    T a0 = 0, a1 = 0;
+    for (int32_t e = 0; e < L; e += BG) {
+        int32_t cc[BG];
+        T vv[BG];
+#pragma unroll
+        for (int u = 0; u < BG; u++) {
+            const bool in_ = e + u < L;
+            int32_t c = in_ ? __ldg(A.col + o + 32 * (e + u)) : -1;
+            if (!full && c >= 0 && !((__ldg(lmask + sp + e + u) >> lane) & 1u)) c = -1;
+            cc[u] = c;
+            vv[u] = in_ ? __ldg(gval + o + 32 * (e + u)) : (T)0;
+        }
+        T xx[BG];
+#pragma unroll
+        for (int u = 0; u < BG; u++) xx[u] = in[cc[u] >= 0 ? cc[u] : row];
+#pragma unroll
+        for (int u = 0; u < BG; u++) {
+            if (TWO && (u & 1)) {
+                const T f = fma(vv[u], xx[u], a1);
+                a1 = cc[u] >= 0 ? f : a1;
+            } else {
+                const T f = fma(vv[u], xx[u], a0);
+                a0 = cc[u] >= 0 ? f : a0;
+            }
+        }
+    }
+    if (!valid) return;
+    if (TWO) a0 += a1;
+    if (full) {
+        T acc[1] = {a0};
+        row_finish<T, 1>(acc, row, 1, 0, V, k, cf);
+    } else {
+        reinterpret_cast<T *>((j & 1) ? V.h[1] : V.h[0])[row] = yk1[row] - a0;
+    }
+}
+
+// Unblocked GS2 step t (one launch per step), one warp per slice.
+template <typename T>
+__global__ void __launch_bounds__(256) mpk_gs2_kernel(SellView A, const uint32_t *lmask, int64_t n_slices,
+                                                      VecSet V, int t, Coefs cf) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t s = w0; s < n_slices; s += nw) slice_gs2_step<T>(A, lmask, s, lane, V, t, cf);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -791,6 +875,7 @@ struct WaveArgs {
     uint64_t timeout_ns;
     uint32_t debug_drop;              // 1: task (chunk 0, power 1) does not publish
     uint32_t dynamic;                 // 1: tickets from the control block's dispenser
+    const uint32_t *lmask;            // MPK_GS2: strictly lower entries (see slice_gs2_step)
     uint32_t *kep;                    // device: earlier launches that ran each local power k;
                                       // the last CTA out adds this launch (powers 1..seg), so
                                       // a captured graph can replay the launch
@@ -815,8 +900,9 @@ template <typename T, int NR> constexpr int wave_min_blocks() {
     return (NR >= 4 * (16 / (int)sizeof(T))) ? 6 : (sizeof(T) == 4 ? (NR <= 2 ? 6 : 4) : (NR == 1 ? 5 : 4));
 }
 
-template <typename T, int NR, bool PAIRS>
-__global__ void __launch_bounds__(WAVE_BLOCK, (PAIRS ? 4 : wave_min_blocks<T, NR>())) mpk_wave_kernel(
+// GS2: every local power is one GS2 step (absolute step k0 + local index), see slice_gs2_step
+template <typename T, int NR, bool PAIRS, bool GS2 = false>
+__global__ void __launch_bounds__(WAVE_BLOCK, ((PAIRS || GS2) ? 4 : wave_min_blocks<T, NR>())) mpk_wave_kernel(
     SellView A, int n_rhs, VecSet V, Coefs cf, WaveArgs W) {
     constexpr int BGMAX = 8;
     __shared__ int32_t s_wm[WAVE_BLOCK / 32][MPK_MAX_P + 1];
@@ -890,12 +976,16 @@ __global__ void __launch_bounds__(WAVE_BLOCK, (PAIRS ? 4 : wave_min_blocks<T, NR
         const int k = W.k0 + kl;
         const int32_t s1 = __ldg(W.chunk_slice + c + 1);
         int32_t s = __ldg(W.chunk_slice + c);
-        if constexpr (NR == 1 && PAIRS) {
-            for (; s + 1 < s1; s += 2) slice_pair_power<T>(A, s, s + 1, lane, V, k, cf);
-        }
-        for (; s < s1; s++) {
-            const long long gofs = 32ll * __ldg(A.slice_ptr + s);
-            slice_power<T, NR, false, false, BGMAX>(A, s, A.col + gofs, gval + gofs, lane, n_rhs, V, k, cf);
+        if constexpr (GS2) {
+            for (; s < s1; s++) slice_gs2_step<T>(A, W.lmask, s, lane, V, k, cf);
+        } else {
+            if constexpr (NR == 1 && PAIRS) {
+                for (; s + 1 < s1; s += 2) slice_pair_power<T>(A, s, s + 1, lane, V, k, cf);
+            }
+            for (; s < s1; s++) {
+                const long long gofs = 32ll * __ldg(A.slice_ptr + s);
+                slice_power<T, NR, false, false, BGMAX>(A, s, A.col + gofs, gval + gofs, lane, n_rhs, V, k, cf);
+            }
         }
         // publish: the warp barrier orders every lane's results before lane 0's release add
         __syncwarp();
@@ -1013,7 +1103,8 @@ mpk_status launch_tasks(mpk_plan_s *P, const SellView &A, int n_rhs, const VecSe
 
 template <typename T, int NR>
 mpk_status launch_wave(mpk_plan_s *P, const SellView &A, int n_rhs, const VecSet &V,
-                       const Coefs &cf, Schedule *sch, int k0, int seg, uint32_t flags, cudaStream_t s) {
+                       const Coefs &cf, Schedule *sch, int k0, int seg, uint32_t flags, cudaStream_t s,
+                       bool gs2 = false) {
     WaveArgs W;
     memset(&W, 0, sizeof(W));
     W.chunk_slice = P->chunk_slice.as<int32_t>();
@@ -1031,7 +1122,10 @@ mpk_status launch_wave(mpk_plan_s *P, const SellView &A, int n_rhs, const VecSet
     auto kern = mpk_wave_kernel<T, NR, false>;
     if constexpr (NR == 1) {
         if (P->short_rows) kern = mpk_wave_kernel<T, 1, true>;
+        if (gs2) kern = mpk_wave_kernel<T, 1, false, true>;
     }
+    if (gs2 && NR != 1) return MPK_ERR_UNIMPLEMENTED;
+    W.lmask = P->s_lmask.as<uint32_t>();
     int occ = 0;
     MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, WAVE_BLOCK, 0));
     if (occ < 1) return MPK_ERR_UNIMPLEMENTED;
@@ -1081,6 +1175,30 @@ mpk_status launch_powers(mpk_plan_s *P, const SellView &A, int n_rhs, const VecS
         if (P->wave) MPK_TRY((launch_wave<T, NR>(P, A, n_rhs, V, cf, sch, k0, seg, flags, s)));
         else MPK_TRY((launch_tasks<T, NR>(P, A, n_rhs, V, cf, sch, k0, flags, s)));
         k0 += seg;
+    }
+    return MPK_OK;
+}
+
+// MPK_GS2: p powers of gamma + 1 steps each; blocked in segments of at most p_blk steps (a
+// segment may end inside a power: the step index is absolute)
+template <typename T>
+mpk_status launch_gs2(mpk_plan_s *P, const SellView &A, const VecSet &V, const Coefs &cf, int p,
+                      bool blocked, uint32_t flags, cudaStream_t s) {
+    const int total = p * V.gs2_steps;
+    if (!blocked || !P->wave) {
+        const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(std::max<int64_t>(P->n_slices, 1), 8), 1 << 30);
+        for (int t = 1; t <= total; t++)
+            mpk_gs2_kernel<T><<<grid, 256, 0, s>>>(A, P->s_lmask.as<uint32_t>(), P->n_slices, V, t, cf);
+        MPK_CUDA(cudaGetLastError());
+        return MPK_OK;
+    }
+    int t0 = 0;
+    while (t0 < total) {
+        const int seg = std::min(P->p_blk, total - t0);
+        Schedule *sch = nullptr;
+        MPK_TRY(mpk_get_schedule(P, seg, &sch, s));
+        MPK_TRY((launch_wave<T, 1>(P, A, 1, V, cf, sch, t0, seg, flags, s, true)));
+        t0 += seg;
     }
     return MPK_OK;
 }
@@ -1240,6 +1358,10 @@ mpk_status mpk_apply_internal(mpk_plan_s *P, const mpk_coeffs *co, mpk_dtype dty
     if (dtype == MPK_F32 && !P->has32) return MPK_ERR_ARG;
     const bool jacobi = (flags & MPK_JACOBI) != 0;
     if (jacobi && !P->jacobi) return MPK_ERR_ARG;
+    const bool gs2 = (flags & MPK_GS2) != 0;
+    const int gs2_gamma = (int)((flags >> 12) & 15u);
+    if (gs2 && (!P->jacobi || jacobi)) return MPK_ERR_ARG;
+    if (gs2 && n_rhs != 1) return MPK_ERR_UNIMPLEMENTED;
     const bool interleaved = (flags & MPK_RHS_INTERLEAVED) != 0;
     const bool permuted = (flags & MPK_PERMUTED_IO) != 0;
     const bool final_only = (flags & MPK_FINAL_ONLY) != 0;
@@ -1296,6 +1418,12 @@ mpk_status mpk_apply_internal(mpk_plan_s *P, const mpk_coeffs *co, mpk_dtype dty
     V.final_only = final_only ? 1 : 0;
     V.use_gamma = use_gamma ? 1 : 0;
     V.p_total = p;
+    if (gs2) {
+        V.gs2_steps = gs2_gamma + 1;
+        MPK_TRY(P->ws_h.ensure((size_t)2 * n * es));
+        V.h[0] = P->ws_h.p;
+        V.h[1] = P->ws_h.as<char>() + (size_t)n * es;
+    }
     const unsigned g = grid_n(n);
 
     if (direct) {
@@ -1341,11 +1469,15 @@ mpk_status mpk_apply_internal(mpk_plan_s *P, const mpk_coeffs *co, mpk_dtype dty
     A.slice_row = P->slice_row.as<int32_t>();
     A.slice_len = P->slice_len.as<int32_t>();
     A.col = P->s_col.as<int32_t>();
-    // MPK_JACOBI: the same kernels on the values of A D^-1 (Sec. 5.1)
-    A.val = dtype == MPK_F64 ? (jacobi ? P->s_jval64.p : P->s_val64.p)
-                             : (jacobi ? P->s_jval32.p : P->s_val32.p);
+    // MPK_JACOBI: the same kernels on the values of A D^-1 (Sec. 5.1); MPK_GS2 works on them too
+    const bool scaled = jacobi || gs2;
+    A.val = dtype == MPK_F64 ? (scaled ? P->s_jval64.p : P->s_val64.p)
+                             : (scaled ? P->s_jval32.p : P->s_val32.p);
 
     auto run = [&](bool blk) -> mpk_status {
+        if (gs2)
+            return dtype == MPK_F64 ? launch_gs2<double>(P, A, V, cf, p, blk, flags, s)
+                                    : launch_gs2<float>(P, A, V, cf, p, blk, flags, s);
         return dtype == MPK_F64 ? dispatch_nr<double>(P, A, n_rhs, V, cf, p, blk, flags, s)
                                 : dispatch_nr<float>(P, A, n_rhs, V, cf, p, blk, flags, s);
     };
@@ -1355,14 +1487,15 @@ mpk_status mpk_apply_internal(mpk_plan_s *P, const mpk_coeffs *co, mpk_dtype dty
         // the matrix does not fit in L2 and there are powers to reuse it for; then both
         // kernels are timed on this call's own data (their results are bit-identical, so the
         // second run just rewrites the same values) and the faster one is kept
-        const int key = (int)dtype * (1 << 24) + p * (1 << 12) + n_rhs;
+        const int key = (gs2 ? (gs2_gamma + 1) << 25 : 0) + (int)dtype * (1 << 24) + p * (1 << 12) + n_rhs;
         auto it = P->auto_blocked.find(key);
         if (it != P->auto_blocked.end()) {
             blocked = it->second;
         } else {
             const int64_t w = dtype == MPK_F64 ? 8 : 4;
             const int64_t bytes = P->sell_nnz * (4 + w) + 2 * n * n_rhs * w;
-            if (p < 2 || bytes <= P->l2_bytes) {
+            const int steps = gs2 ? p * (gs2_gamma + 1) : p;   // passes over the matrix
+            if (steps < 2 || bytes <= P->l2_bytes) {
                 blocked = false;
             } else {
                 cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -1407,6 +1540,38 @@ mpk_status mpk_apply_internal(mpk_plan_s *P, const mpk_coeffs *co, mpk_dtype dty
         MPK_CUDA(cudaMemcpyAsync(Y, Yd, (size_t)nout_blocks * ublk * es, cudaMemcpyDeviceToHost, s));
         MPK_CUDA(cudaStreamSynchronize(s));
     }
+    return MPK_OK;
+}
+
+mpk_status mpk_gs2_inner(mpk_plan_s *P, mpk_dtype dtype, int gamma, const void *v, void *out,
+                         void *tmp, cudaStream_t s) {
+    if (!P || !P->jacobi || gamma < 1 || gamma > 15) return MPK_ERR_ARG;
+    if (P->n == 0) return MPK_OK;
+    if ((dtype == MPK_F64 && !P->has64) || (dtype == MPK_F32 && !P->has32)) return MPK_ERR_ARG;
+    VecSet V;
+    memset(&V, 0, sizeof(V));
+    V.x = v;
+    V.final_only = 1;
+    V.p_total = 1;
+    V.gs2_steps = gamma + 1;
+    V.h[gamma & 1] = out;          // h_gamma lands in out
+    V.h[(gamma - 1) & 1] = tmp;
+    SellView A;
+    A.slice_ptr = P->slice_ptr.as<long long>();
+    A.slice_row = P->slice_row.as<int32_t>();
+    A.slice_len = P->slice_len.as<int32_t>();
+    A.col = P->s_col.as<int32_t>();
+    A.val = dtype == MPK_F64 ? P->s_jval64.p : P->s_jval32.p;
+    Coefs cf;
+    memset(&cf, 0, sizeof(cf));
+    const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(std::max<int64_t>(P->n_slices, 1), 8), 1 << 30);
+    for (int t = 1; t <= gamma; t++) {
+        if (dtype == MPK_F64)
+            mpk_gs2_kernel<double><<<grid, 256, 0, s>>>(A, P->s_lmask.as<uint32_t>(), P->n_slices, V, t, cf);
+        else
+            mpk_gs2_kernel<float><<<grid, 256, 0, s>>>(A, P->s_lmask.as<uint32_t>(), P->n_slices, V, t, cf);
+    }
+    MPK_CUDA(cudaGetLastError());
     return MPK_OK;
 }
 

@@ -709,8 +709,9 @@ struct Solver {
         MPK_TRY(gpart2.alloc_on((size_t)upd_grid * SMAX * SMAX * sizeof(double) + 64, st));
         MPK_TRY(cstate.alloc_on(sizeof(CycleState), st));
         MPK_TRY(dth.alloc_on(SMAX * sizeof(double), st));
-        if (uses_poly()) MPK_TRY(ptmp.alloc_on((size_t)2 * ldv * sizeof(T), st));
-        if (uses_poly() && poly64()) MPK_TRY(ptmp64.alloc_on((size_t)2 * ldv * sizeof(double), st));
+        if (uses_poly() || o.gs2) MPK_TRY(ptmp.alloc_on((size_t)2 * ldv * sizeof(T), st));
+        if (o.gs2) MPK_TRY(ptmp64.alloc_on((size_t)3 * ldv * sizeof(double), st));
+        else if (uses_poly() && poly64()) MPK_TRY(ptmp64.alloc_on((size_t)2 * ldv * sizeof(double), st));
         MPK_TRY(vec.alloc_on((size_t)3 * ldv * sizeof(double) + 64 * sizeof(double), st));
         bp = vec.as<double>();
         xp = bp + ldv;
@@ -811,9 +812,13 @@ struct Solver {
     }
     // a polynomial preconditioner: the GMRES polynomial, or k >= 2 Jacobi sweeps
     bool uses_poly() const { return o.poly_degree > 0 || o.jacobi >= 2; }
-    // right Jacobi scaling: every operator application is one of A D^-1
-    uint32_t jac_flag() const { return o.jacobi ? MPK_JACOBI : 0u; }
-    const double *dinv() const { return o.jacobi ? P->dinv64.as<double>() : nullptr; }
+    // right Jacobi scaling: every operator application is one of A D^-1; GS2: of A P^-1 with
+    // P^-1 one two-stage Gauss-Seidel iteration (sub-powers of the MPK)
+    uint32_t jac_flag() const {
+        if (o.gs2) return MPK_GS2 | MPK_GS2_GAMMA(o.gs2_gamma);
+        return o.jacobi ? MPK_JACOBI : 0u;
+    }
+    const double *dinv() const { return (o.jacobi || o.gs2) ? P->dinv64.as<double>() : nullptr; }
     // the polynomial runs with the FP64 matrix values although the basis is FP32
     bool poly64() const { return sizeof(T) == 4 && o.poly_f64 != 0; }
 
@@ -902,6 +907,15 @@ struct Solver {
                     MPK_TRY(apply_poly_u<T>(t0, t1));
                     add_f64_kernel<T><<<grid_rows(n), 256, 0, st>>>(t1, n, dinv(), xp);
                 }
+            } else if (o.gs2 && o.gs2_gamma >= 1) {
+                // x += P^-1 V y = D~^-1 h_gamma(V y), the GS2 stages in FP64
+                T *t0 = ptmp.as<T>();
+                double *d0 = ptmp64.as<double>(), *d1 = d0 + ldv, *d2 = d1 + ldv;
+                vy_kernel<T><<<grid_rows(n, 8), 256, 0, st>>>(V.as<T>(), ldv, k, cst->y, n, t0);
+                cvt_kernel<T, double><<<grid_rows(n), 256, 0, st>>>(t0, n, d0);
+                MPK_CUDA(cudaGetLastError());
+                MPK_TRY(mpk_gs2_inner(P, MPK_F64, o.gs2_gamma, d0, d1, d2, st));
+                add_f64_kernel<double><<<grid_rows(n), 256, 0, st>>>(d1, n, dinv(), xp);
             } else {
                 xupdate_kernel<T><<<grid_rows(n, 8), 256, 0, st>>>(V.as<T>(), ldv, k, cst->y, n, dinv(), xp);
             }
@@ -1154,6 +1168,8 @@ extern "C" mpk_status mpk_gmres_opts_default(mpk_gmres_opts *o) {
     o->poly_degree = 0;
     o->poly_f64 = 1;
     o->jacobi = 0;
+    o->gs2 = 0;
+    o->gs2_gamma = 1;
     return MPK_OK;
 }
 
@@ -1167,14 +1183,15 @@ extern "C" mpk_status sstep_gmres_solve(mpk_plan_t A, const double *b, double *x
     if (o.s < 1 || o.s > SMAX || o.restart < o.s || o.restart > MMAX || !(o.tol > 0) ||
         o.bcgs_passes < 1 || o.bcgs_passes > 2 || o.max_outer < 0 || o.poly_degree < 0 ||
         o.poly_degree > MPK_MAX_P || o.jacobi < 0 || o.jacobi > MPK_MAX_P + 1 ||
-        (o.jacobi >= 2 && o.poly_degree > 0))
+        (o.jacobi >= 2 && o.poly_degree > 0) || o.gs2 < 0 || o.gs2 > 1 || o.gs2_gamma < 0 ||
+        o.gs2_gamma > 15 || (o.gs2 && (o.jacobi || o.poly_degree > 0)))
         return MPK_ERR_ARG;
     if (!A->has64) return MPK_ERR_ARG;                       // FP64 residual needs FP64 values
     if (o.basis == MPK_F32 && !A->has32) return MPK_ERR_ARG;
     if ((o.poly_degree > 0 || o.jacobi >= 2) && o.basis == MPK_F32 && !o.poly_f64 && !A->has32)
         return MPK_ERR_ARG;
     if (o.s > A->p_max) return MPK_ERR_ARG;
-    if (o.jacobi && !A->jacobi) return MPK_ERR_ARG;          // the plan keeps no A D^-1
+    if ((o.jacobi || o.gs2) && !A->jacobi) return MPK_ERR_ARG;   // the plan keeps no A D^-1
     auto t0 = std::chrono::steady_clock::now();
     mpk_status st;
     mpk_gmres_info inf{};

@@ -125,6 +125,9 @@ struct mpk_plan_s {
     // D^-1 in level order (FP64; 1 where the diagonal entry is missing or zero)
     bool jacobi = false;
     DevBuf s_jval64, s_jval32, dinv64;
+    // two-stage Gauss-Seidel sub-powers (MPK_GS2, built with opts.jacobi): bit lane of word
+    // slice_ptr[s] + j marks a strictly lower entry in the caller's row order
+    DevBuf s_lmask;
 
     // blocked tasks: chunk c = slices [chunk_slice[c], chunk_slice[c+1]) inside one group
     DevBuf chunk_slice, chunk_row, chunk_entry, dep_lo, dep_hi;
@@ -161,8 +164,8 @@ struct mpk_plan_s {
     int blocked_block = 256;
     std::map<int, std::unique_ptr<Schedule>> schedules;
 
-    // workspace for permuted / interleaved vectors
-    DevBuf ws_x, ws_y, ws_host;
+    // workspace for permuted / interleaved vectors; ws_h: the GS2 inner iterates (2 vectors)
+    DevBuf ws_x, ws_y, ws_host, ws_h;
     uint32_t latched_error = 0;
 };
 
@@ -181,6 +184,11 @@ mpk_status mpk_build_blocks(mpk_plan_s *P, cudaStream_t s);
 // Row-sum kernels shared by the MPK and the solver (apply.cu)
 mpk_status mpk_launch_residual(mpk_plan_s *P, const double *x, const double *b, double *r,
                                cudaStream_t s);
+// h_gamma of one GS2 application from zero to v (level order, one vector, precision dtype):
+// h_0 = v, h_j = v - L_B h_{j-1}; the preconditioned vector is D~^-1 h_gamma.  out and tmp
+// are n-vectors; gamma >= 1.
+mpk_status mpk_gs2_inner(mpk_plan_s *P, mpk_dtype dtype, int gamma, const void *v, void *out,
+                         void *tmp, cudaStream_t s);
 mpk_status mpk_apply_internal(mpk_plan_s *P, const mpk_coeffs *co, mpk_dtype dtype,
                               const void *X, int64_t ldx, void *Y, int64_t ldy, int32_t n_rhs,
                               uint32_t flags, cudaStream_t stream);

@@ -680,6 +680,31 @@ __global__ void jacobi_scale_kernel(const int32_t *s_col, const double *s64, con
     }
 }
 
+// Strictly lower entries of the caller's row order, for the two-stage Gauss-Seidel sub-powers
+// (Sec. 5, Alg. GS2): bit `lane` of word slice_ptr[s] + j is set when lane's entry j of slice
+// s is stored (column >= 0), its row is inside the slice, and the column's original index is
+// below the row's (perm maps level order to the original order).  One warp per slice.
+__global__ void gs2_lower_mask_kernel(const int32_t *s_col, const long long *slice_ptr,
+                                      const int32_t *slice_row, const int32_t *slice_len,
+                                      int64_t n_slices, const int32_t *perm, uint32_t *lmask) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t sl = w0; sl < n_slices; sl += nw) {
+        const int32_t row = slice_row[sl] + lane;
+        const bool in = row < slice_row[sl + 1];
+        const int32_t orow = in ? perm[row] : 0;
+        const long long sp = slice_ptr[sl];
+        const int32_t L = slice_len[sl];
+        for (int32_t j = 0; j < L; j++) {
+            const int32_t c = s_col[32 * (sp + j) + lane];
+            const bool low = in && c >= 0 && perm[c] < orow;
+            const uint32_t m = __ballot_sync(0xffffffffu, low);
+            if (lane == 0) lmask[sp + j] = m;
+        }
+    }
+}
+
 __global__ void row_chunk_kernel(const int32_t *chunk_row, int64_t n_chunks, int32_t *row_chunk) {
     for (int64_t c = blockIdx.x; c < n_chunks; c += gridDim.x)
         for (int32_t r = chunk_row[c] + threadIdx.x; r < chunk_row[c + 1]; r += blockDim.x)
@@ -1093,9 +1118,17 @@ static mpk_status plan_create_impl(const mpk_csr *A, int32_t p_max, const mpk_pl
         MPK_TRY(P->dinv64.alloc(std::max<int64_t>(n, 1) * 8));
         if (P->has64) MPK_TRY(P->s_jval64.alloc(std::max<int64_t>(P->sell_nnz, 1) * 8));
         if (P->has32) MPK_TRY(P->s_jval32.alloc(std::max<int64_t>(P->sell_nnz, 1) * 4));
+        MPK_TRY(P->s_lmask.alloc(std::max<int64_t>(P->sell_nnz / 32, 1) * 4));
     }
     mpk_status st = mpk_build_blocks(P, s);
     if (st != MPK_OK) return st;
+    if (P->jacobi && P->n_slices > 0) {   // needs the SELL columns filled above
+        gs2_lower_mask_kernel<<<grid_for((int64_t)P->n_slices * 32), 256, 0, s>>>(
+            P->s_col.as<int32_t>(), P->slice_ptr.as<long long>(), P->slice_row.as<int32_t>(),
+            P->slice_len.as<int32_t>(), P->n_slices, P->perm.as<int32_t>(),
+            P->s_lmask.as<uint32_t>());
+        MPK_CUDA(cudaGetLastError());
+    }
 
     // ---- blocked-task dependency ranges and flags
     MPK_TRY(P->dep_lo.alloc((P->n_chunks + 1) * 4));
@@ -1244,7 +1277,7 @@ extern "C" mpk_status mpk_plan_stats(mpk_plan_t P, mpk_plan_info *st) {
     for (const DevBuf *d : {&P->perm, &P->iperm, &P->level, &P->level_ptr, &P->group_ptr, &P->rp,
                             &P->ci, &P->val64, &P->val32, &P->entry_map, &P->slice_row,
                             &P->slice_ptr, &P->slice_len, &P->s_col, &P->s_val64, &P->s_val32,
-                            &P->s_jval64, &P->s_jval32, &P->dinv64, &P->chunk_slice, &P->chunk_row, &P->chunk_entry, &P->dep_lo, &P->dep_hi, &P->flags,
+                            &P->s_jval64, &P->s_jval32, &P->dinv64, &P->s_lmask, &P->chunk_slice, &P->chunk_row, &P->chunk_entry, &P->dep_lo, &P->dep_hi, &P->flags,
                             &P->ctrl, &P->ws_x, &P->ws_y})
         b += d->bytes;
     st->device_bytes = (int64_t)b;

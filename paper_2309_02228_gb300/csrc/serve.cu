@@ -90,8 +90,10 @@ struct mpk_server_s {
         const int64_t m = o.gmres.restart;
         const int64_t wb = o.gmres.basis == MPK_F64 ? 8 : 4;
         const int64_t csr_in = 12 * nnz + 4 * (n + 1);
-        // Jacobi scaling adds a second SELL value copy per precision and D^-1
-        const int64_t jac = o.gmres.jacobi ? 2 * (8 + 4) * nnz + 8 * n : 0;
+        // Jacobi scaling adds a second SELL value copy per precision and D^-1; GS2 also the
+        // lower-entry mask, two inner-iterate vectors and three FP64 correction vectors
+        const bool scaled = o.gmres.jacobi || o.gmres.gs2;
+        const int64_t jac = (scaled ? 2 * (8 + 4) * nnz + 8 * n : 0) + (o.gmres.gs2 ? nnz / 8 + 48 * n : 0);
         const int64_t plan = 2 * (12 * nnz) + 2 * 8 * nnz + 64 * n + (8 << 20) + jac;
         const int64_t solver = (m + 1) * wb * ((n + 31) / 32 * 32) + 24 * n + (16 << 20);
         return csr_in + plan + solver;
@@ -117,7 +119,7 @@ struct mpk_server_s {
         mpk_plan_opts_default(&po);
         po.keep_f64 = 1;
         po.keep_f32 = o.gmres.basis == MPK_F32 ? 1 : 0;
-        po.jacobi = o.gmres.jacobi ? 1 : 0;
+        po.jacobi = (o.gmres.jacobi || o.gmres.gs2) ? 1 : 0;
         mpk_csr A{r.n, r.nnz, drp, dci, dval, MPK_F64};
         MPK_TRY(mpk_plan_create(&A, std::max(o.gmres.s, 1), &po, s, out));
         mpk_plan_info pi;
