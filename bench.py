@@ -185,7 +185,7 @@ def solver_leg(m, torch, dev, n_edge=64, solves=5, bases=("f32", "f64"), warm=Tr
     FP64 basis: solves/s and per-solve latency (p50/p99) over `solves` solves each.  poly_degree:
     GMRES-polynomial preconditioning (Sec. 5.2); jacobi: right Jacobi scaling fused into the
     MPK (Sec. 5.1); gs2: two-stage Gauss-Seidel with gs2_gamma inner iterations as MPK
-    sub-powers (Sec. 5, Alg. GS2)."""
+    sub-powers (Sec. 5.1, Alg. GS2)."""
     A = mi.diffusion7_lognormal(n_edge)
     b = mi.uniform_vectors(A.n, 4)[0]
     rp = torch.from_numpy(A.row_ptr).to(dev)
@@ -220,7 +220,7 @@ def solver_leg(m, torch, dev, n_edge=64, solves=5, bases=("f32", "f64"), warm=Tr
 
 
 def gs2_mpk_leg(m, torch, dev, A, rp, ci, vv, p=P_MAIN, gammas=(1, 2), reps=20):
-    """MPK of the GS2-preconditioned operator (Sec. 5, Alg. GS2(b)) on the 27-point benchmark
+    """MPK of the GS2-preconditioned operator (Sec. 5.1, Alg. GS2(b)) on the 27-point benchmark
     matrix, level-order I/O: each power is gamma inner stages on the strictly lower part plus
     the product with A, all blocked as sub-powers in one launch, against the same steps as
     separate launches.  Flops per power: 2 nnz (product) + gamma * 2 nnz_L (inner stages)."""
@@ -563,7 +563,7 @@ def main():
                   # right Jacobi scaling fused into the MPK (Sec. 5.1), 64^3 and full size
                   "n64_jacobi": solver_leg(m, torch, dev, n_edge=64, solves=5, jacobi=1),
                   "n256_jacobi": solver_leg(m, torch, dev, n_edge=256, solves=1, warm=False, jacobi=1),
-                  # two-stage Gauss-Seidel (gamma = 1) as MPK sub-powers (Sec. 5, Alg. GS2)
+                  # two-stage Gauss-Seidel (gamma = 1) as MPK sub-powers (Sec. 5.1, Alg. GS2)
                   "n64_gs2": solver_leg(m, torch, dev, n_edge=64, solves=5, gs2=1, gs2_gamma=1),
                   "n256_gs2": solver_leg(m, torch, dev, n_edge=256, solves=1, warm=False, gs2=1, gs2_gamma=1)}
         serving = serving_leg(m)

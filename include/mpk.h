@@ -159,7 +159,7 @@ typedef struct {
                                     Jacobi preconditioning, Sec. 5.1); needs a plan created
                                     with opts.jacobi = 1, else MPK_ERR_ARG */
 #define MPK_GS2           0x100u /* the powers are those of the GS2-preconditioned operator
-                                    A P^-1 (Sec. 5, Alg. GS2: one two-stage Gauss-Seidel
+                                    A P^-1 (Sec. 5.1, Alg. GS2: one two-stage Gauss-Seidel
                                     iteration from z^0 = 0 with gamma inner Jacobi-Richardson
                                     iterations; L, D, U split in the caller's row order, a
                                     zero or missing diagonal entry read as 1):
@@ -341,7 +341,7 @@ typedef struct {
                                so tol keeps its meaning.  Needs a plan created with
                                opts.jacobi = 1.  Default 0 */
     int32_t gs2;            /* 1: right preconditioning by one two-stage Gauss-Seidel
-                               iteration from zero (Sec. 5, Alg. GS2) with gs2_gamma inner
+                               iteration from zero (Sec. 5.1, Alg. GS2) with gs2_gamma inner
                                Jacobi-Richardson iterations: the s-step basis is that of
                                A P^-1 (MPK_GS2, every power gs2_gamma + 1 sub-powers, blocked
                                like powers), the first cycle's Ritz values are those of

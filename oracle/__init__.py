@@ -12,6 +12,8 @@ leg of ``bench.py`` may import this package.  It shares no code with the GPU lib
 * ``poly.py``: the GMRES polynomial preconditioner (Sec. 5.2) and right-preconditioned GMRES.
 * ``gs2.py``: two-stage Gauss-Seidel (GS2) preconditioning, the MPK of the GS2-preconditioned
   operator (powers made of sub-powers) and s-step GMRES with it.
+* ``cg.py``: textbook CG, s-step CG (Newton basis, Gram matrix, coordinate recurrences) and
+  FP64 refinement around it.
 """
 from __future__ import annotations
 

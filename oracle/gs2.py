@@ -2,7 +2,7 @@
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).  Slow and plain on purpose.
 
-Sec. 5 (the GS2 subsection, Alg. GS2): a Gauss-Seidel iteration (L + D) z^{k+1} = v - U z^k
+Sec. 5.1 (the GS2 part, Alg. GS2): a Gauss-Seidel iteration (L + D) z^{k+1} = v - U z^k
 whose triangular solve is replaced by gamma inner Jacobi-Richardson iterations:
     g_0 = D^-1 (v - U z^k);   g_j = g_0 - D^-1 L g_{j-1}  (j = 1..gamma);   z^{k+1} = z^k + g_gamma.
 As a preconditioner the paper uses one outer iteration from z^0 = 0, so P^-1 v = g_gamma.
@@ -91,7 +91,7 @@ def gs2_mpk(A, p, coeffs, x, gamma):
 
 
 def gs2_gmres(A, b, gamma, s=8, m=48, tol=1e-8, max_restarts=1000, shifts=None):
-    """Right-preconditioned s-step GMRES with P^-1 = one GS2 iteration from zero (Sec. 5, GS2
+    """Right-preconditioned s-step GMRES with P^-1 = one GS2 iteration from zero (Sec. 5.1, GS2
     subsection): the Newton basis of A P^-1, x = x0 + P^-1 (V y); the GMRES residual is the
     true residual b - A x.  Returns the dict of ``sstep.sstep_gmres``."""
     split = split_ldu(A)

@@ -379,7 +379,7 @@ __device__ __forceinline__ void slice_power(const SellView &A, int64_t s, const 
 }
 
 // ------------------------------------------------------------------------------------------
-// Two-stage Gauss-Seidel (GS2, Sec. 5, Alg. GS2) as sub-powers of the MPK.  With B = A D~^-1
+// Two-stage Gauss-Seidel (GS2, Sec. 5.1, Alg. GS2) as sub-powers of the MPK.  With B = A D~^-1
 // (the Jacobi-scaled values; D~ the diagonal, zero or missing entries read as 1) and L_B its
 // strictly lower part in the caller's row order (bit `lane` of lmask[slice_ptr[s] + j]), one
 // GS2 iteration from zero is P^-1 v = D~^-1 h_gamma with

@@ -681,7 +681,7 @@ __global__ void jacobi_scale_kernel(const int32_t *s_col, const double *s64, con
 }
 
 // Strictly lower entries of the caller's row order, for the two-stage Gauss-Seidel sub-powers
-// (Sec. 5, Alg. GS2): bit `lane` of word slice_ptr[s] + j is set when lane's entry j of slice
+// (Sec. 5.1, Alg. GS2): bit `lane` of word slice_ptr[s] + j is set when lane's entry j of slice
 // s is stored (column >= 0), its row is inside the slice, and the column's original index is
 // below the row's (perm maps level order to the original order).  One warp per slice.
 __global__ void gs2_lower_mask_kernel(const int32_t *s_col, const long long *slice_ptr,

@@ -1,4 +1,4 @@
-"""GPU parity for two-stage Gauss-Seidel (GS2) preconditioning as MPK sub-powers (Sec. 5, GS2
+"""GPU parity for two-stage Gauss-Seidel (GS2) preconditioning as MPK sub-powers (Sec. 5.1, GS2
 subsection, Alg. GS2(a) and (b)).
 
 * mpk_apply(..., MPK_GS2 | MPK_GS2_GAMMA(gamma)) against the oracle's MPK of the

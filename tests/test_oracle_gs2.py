@@ -1,5 +1,5 @@
 """Pins for the oracle's two-stage Gauss-Seidel (GS2) preconditioner and the MPK of the
-GS2-preconditioned operator (Sec. 5, GS2 subsection, Alg. GS2).
+GS2-preconditioned operator (Sec. 5.1, GS2 part, Alg. GS2).
 
 Each pin comes from outside the oracle's own loops:
 * gamma = 0 is the diagonal scaling D^-1 v (division by the dense diagonal);
