@@ -219,6 +219,40 @@ def solver_leg(m, torch, dev, n_edge=64, solves=5, bases=("f32", "f64"), warm=Tr
     return out
 
 
+def cg_leg(m, torch, dev, n_edge=64, solves=5, bases=("f32", "f64"), warm=True, s=8):
+    """s-step CG (s = 8, Ritz shifts from a setup phase) to rel. residual 1e-8 on the same SPD
+    log-normal diffusion matrix as the GMRES leg, FP32 basis + FP64 refinement vs an FP64 basis:
+    solves/s, latency, CG steps and the time split (MPK / Gram / rest)."""
+    A = mi.diffusion7_lognormal(n_edge)
+    b = mi.uniform_vectors(A.n, 4)[0]
+    rp = torch.from_numpy(A.row_ptr).to(dev)
+    ci = torch.from_numpy(A.col).to(dev)
+    vv = torch.from_numpy(A.val).to(dev)
+    plan = m.mpk_plan_create(rp, ci, vv, s, m.mpk_plan_opts_default(keep_f64=1, keep_f32=1))
+    B = torch.from_numpy(b).to(dev)
+    out = {"workload": "7-point log-normal diffusion %d^3 (sigma 1, rows permuted seed 1), b ~ U[-1,1) "
+                       "seed 4, s-step CG s=%d, tol 1e-8" % (n_edge, s), "n": A.n, "nnz": A.nnz}
+    for basis in bases:
+        lat, info = [], None
+        ok = True
+        for _ in range(solves + (1 if warm else 0)):
+            X = torch.zeros_like(B)
+            o = m.mpk_cg_opts_default(s=s, tol=1e-8, basis=m.MPK_F32 if basis == "f32" else m.MPK_F64)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = m.sstep_cg_solve(plan, B, X, o, check=False)
+            torch.cuda.synchronize()
+            lat.append(1e3 * (time.perf_counter() - t0))
+            ok = ok and info["status_code"] == m.MPK_OK
+        if warm and len(lat) > 1:
+            lat = lat[1:]
+        out[basis] = {"solves_per_s": 1e3 * len(lat) / sum(lat), "p50_ms": float(np.percentile(lat, 50)),
+                      "p99_ms": float(np.percentile(lat, 99)), "iters": info["iters"],
+                      "rel_residual": info["rel_residual"], "converged": ok,
+                      "ms_mpk": info["ms_mpk"], "ms_gram": info["ms_gram"], "ms_other": info["ms_other"]}
+    return out
+
+
 def gs2_mpk_leg(m, torch, dev, A, rp, ci, vv, p=P_MAIN, gammas=(1, 2), reps=20):
     """MPK of the GS2-preconditioned operator (Sec. 5.1, Alg. GS2(b)) on the 27-point benchmark
     matrix, level-order I/O: each power is gamma inner stages on the strictly lower part plus
@@ -565,7 +599,10 @@ def main():
                   "n256_jacobi": solver_leg(m, torch, dev, n_edge=256, solves=1, warm=False, jacobi=1),
                   # two-stage Gauss-Seidel (gamma = 1) as MPK sub-powers (Sec. 5.1, Alg. GS2)
                   "n64_gs2": solver_leg(m, torch, dev, n_edge=64, solves=5, gs2=1, gs2_gamma=1),
-                  "n256_gs2": solver_leg(m, torch, dev, n_edge=256, solves=1, warm=False, gs2=1, gs2_gamma=1)}
+                  "n256_gs2": solver_leg(m, torch, dev, n_edge=256, solves=1, warm=False, gs2=1, gs2_gamma=1),
+                  # s-step CG on the same SPD matrices (the short-recurrence method, Sec. 4 / Sec. 7)
+                  "n64_cg": cg_leg(m, torch, dev, n_edge=64, solves=5),
+                  "n256_cg": cg_leg(m, torch, dev, n_edge=256, solves=1, warm=False)}
         serving = serving_leg(m)
     block = None
     if not args.no_block:

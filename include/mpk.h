@@ -383,6 +383,60 @@ mpk_status sstep_gmres_solve(mpk_plan_t A, const double *b, double *x, const mpk
                              mpk_gmres_info *info, cudaStream_t stream);
 
 /* ------------------------------------------------------------------------------------------
+ * s-step CG with FP64 iterative refinement.  The paper names s-step CG as the short-recurrence
+ * method whose solver speedup should approach the MPK's, its orthogonalisation being minimal
+ * (Sec. 4, discussion of the s-step GMRES results; Sec. 7); the steps are the standard
+ * communication-avoiding CG: per outer iteration one MPK of s powers on p and one of s - 1
+ * powers on r (Newton basis) give Y = [p, .., rho_s(A) p, r, .., rho_{s-1}(A) r]; one FP64
+ * Gram matrix G = Y^T Y; s CG steps on coordinate vectors of length 2s + 1 with the change of
+ * basis B (A Y = Y B); then x += Y x', r = Y r', p = Y p'.
+ * ---------------------------------------------------------------------------------------- */
+typedef struct {
+    int32_t s;              /* CG steps per outer iteration = powers of the p basis (1..15,
+                               default 8) */
+    double tol;             /* stop when ||b - A x||_2 <= tol ||b||_2 (FP64; default 1e-8) */
+    double inner_tol;       /* inner solve tolerance relative to its rhs (default 1e-5) */
+    int32_t max_outer;      /* refinement steps (default 1000); the solve also stops
+                               (MPK_ERR_NOT_CONVERGED) after 50 steps without a new best true
+                               residual */
+    int32_t max_iters;      /* CG steps in total (default 100000) */
+    mpk_dtype basis;        /* MPK_F32 (default): FP32 matrix values, basis and coordinate
+                               recovery, FP64 Gram matrix, coefficients, x and true residual;
+                               MPK_F64: everything in FP64 */
+    const double *shifts;   /* host, s Newton shifts, or NULL: the first refinement step is a
+                               setup phase of 4 s plain CG steps whose Ritz values (eigenvalues
+                               of the Lanczos tridiagonal of its coefficients) are Leja-ordered */
+    uint32_t mpk_flags;     /* extra mpk_apply flags for the basis MPKs: MPK_UNBLOCKED runs
+                               back-to-back SpMVs (the baseline) */
+} mpk_cg_opts;
+
+typedef struct {
+    int32_t iters;          /* CG steps in total (setup phase included) */
+    int32_t outer;          /* refinement steps taken */
+    int32_t status;         /* mpk_status of the solve */
+    int32_t s_used;         /* s at exit (halved after a breakdown) */
+    double rel_residual;    /* true ||b - A x|| / ||b|| in FP64 at exit */
+    double shifts[16];      /* shifts used (first s entries) */
+    double ms_total, ms_mpk, ms_gram, ms_other;   /* CUDA-event timings per phase */
+} mpk_cg_info;
+
+mpk_status mpk_cg_opts_default(mpk_cg_opts *o);
+
+/* Solve A x = b for a symmetric positive definite A.  A: a plan holding FP64 values (for the
+ * residual), FP32 values too when basis = MPK_F32, and p_max >= s.  b, x: DEVICE FP64 vectors
+ * of length n in the original order; x holds the initial guess on entry and the solution on
+ * exit; info (host) may be NULL.  Each refinement step computes r = b - A x in FP64 and runs
+ * s-step CG on A d = r in the basis precision until its recurrence residual is below
+ * inner_tol ||r|| (tol ||b|| with an FP64 basis), adding the correction to x as it goes.
+ * A non-positive p^T A p in the coordinate recurrence (an indefinite A, or a numerically
+ * singular basis) ends that outer iteration at its last good step and halves s; at s = 1 the
+ * solve returns MPK_ERR_BREAKDOWN.  Synchronous on stream (the host reads a few status words
+ * per outer iteration).  Returns MPK_OK, MPK_ERR_NOT_CONVERGED (x holds the last iterate),
+ * MPK_ERR_BREAKDOWN, or an argument / CUDA error. */
+mpk_status sstep_cg_solve(mpk_plan_t A, const double *b, double *x, const mpk_cg_opts *o,
+                          mpk_cg_info *info, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------------------------
  * Serving: a continuously batched stream of s-step GMRES solves on one GPU.
  * ---------------------------------------------------------------------------------------- */
 typedef struct {

@@ -109,6 +109,20 @@ class mpk_gmres_info(ctypes.Structure):
                 ("poly_interval", ctypes.c_double * 2)]
 
 
+class mpk_cg_opts(ctypes.Structure):
+    _fields_ = [("s", ctypes.c_int32), ("tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
+                ("max_outer", ctypes.c_int32), ("max_iters", ctypes.c_int32), ("basis", ctypes.c_int),
+                ("shifts", ctypes.c_void_p), ("mpk_flags", ctypes.c_uint32)]
+
+
+class mpk_cg_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("outer", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("s_used", ctypes.c_int32), ("rel_residual", ctypes.c_double),
+                ("shifts", ctypes.c_double * 16), ("ms_total", ctypes.c_double),
+                ("ms_mpk", ctypes.c_double), ("ms_gram", ctypes.c_double),
+                ("ms_other", ctypes.c_double)]
+
+
 class mpk_server_opts(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_active", ctypes.c_int32),
                 ("n_streams", ctypes.c_int32), ("gmres", mpk_gmres_opts)]
@@ -148,6 +162,8 @@ _SIGS = [
     ("mpk_leja_order", ctypes.c_int, [_P, _I32, _I32, _P]),
     ("mpk_gmres_opts_default", ctypes.c_int, [ctypes.POINTER(mpk_gmres_opts)]),
     ("sstep_gmres_solve", ctypes.c_int, [_P, _P, _P, ctypes.POINTER(mpk_gmres_opts), ctypes.POINTER(mpk_gmres_info), _P]),
+    ("mpk_cg_opts_default", ctypes.c_int, [ctypes.POINTER(mpk_cg_opts)]),
+    ("sstep_cg_solve", ctypes.c_int, [_P, _P, _P, ctypes.POINTER(mpk_cg_opts), ctypes.POINTER(mpk_cg_info), _P]),
     ("mpk_server_opts_default", ctypes.c_int, [ctypes.POINTER(mpk_server_opts)]),
     ("mpk_server_create", ctypes.c_int, [ctypes.POINTER(mpk_server_opts), ctypes.POINTER(_P)]),
     ("mpk_server_submit", ctypes.c_int, [_P, _I64, _I64, _P, _P, _P, _P, _P, ctypes.POINTER(_I64)]),
@@ -413,6 +429,40 @@ def sstep_gmres_solve(plan, b, x, opts=None, shifts=None, stream=None, check=Tru
     d["status_code"] = int(st)
     if check:
         _check(st, "sstep_gmres_solve")
+    del keep
+    return d
+
+
+# ---------------------------------------------------------------------------------------------
+# s-step CG
+# ---------------------------------------------------------------------------------------------
+def mpk_cg_opts_default(**overrides) -> mpk_cg_opts:
+    o = mpk_cg_opts()
+    _check(lib().mpk_cg_opts_default(ctypes.byref(o)), "mpk_cg_opts_default")
+    names = {f for f, _ in o._fields_}
+    for k, v in overrides.items():
+        if k not in names:
+            raise TypeError("mpk_cg_opts has no field %r" % k)
+        setattr(o, k, v)
+    return o
+
+
+def sstep_cg_solve(plan, b, x, opts=None, shifts=None, stream=None, check=True):
+    """Solve A x = b for an SPD A by s-step CG (b, x: CUDA float64 tensors in the original
+    order).  Returns the info struct as a dict; raises on an error status unless check=False."""
+    o = opts if opts is not None else mpk_cg_opts_default()
+    keep = None
+    if shifts is not None:
+        keep = np.ascontiguousarray(shifts, dtype=np.float64)
+        o.shifts = keep.ctypes.data
+    info = mpk_cg_info()
+    st = lib().sstep_cg_solve(plan.handle, _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(info),
+                              _stream_ptr(stream))
+    d = {f: getattr(info, f) for f, _ in info._fields_ if f != "shifts"}
+    d["shifts"] = np.array(info.shifts[: o.s])
+    d["status_code"] = int(st)
+    if check:
+        _check(st, "sstep_cg_solve")
     del keep
     return d
 

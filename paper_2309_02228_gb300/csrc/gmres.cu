@@ -1149,6 +1149,378 @@ struct Solver {
     }
 };
 
+// ==========================================================================================
+// s-step CG (the short-recurrence method the paper names for the MPK, Sec. 4 and Sec. 7): per
+// outer iteration one MPK of s powers on p and one of s - 1 powers on r (Newton basis) give
+// Y = [p, .., rho_s(A) p, r, .., rho_{s-1}(A) r] (M = 2s + 1 columns of ldv), the Gram matrix
+// G = Y^T Y in FP64, s CG steps on coordinate vectors of length M, and the recovery
+// x += Y x', p = Y p', r = Y r'.  The MPK dominates; the only tall-skinny product left is one
+// Gram matrix per s steps (the reason the paper expects the MPK speedup to carry over).
+// ==========================================================================================
+constexpr int CG_SMAX = 15;                   // M = 2s + 1 <= 31: one warp owns the coordinates
+constexpr int CG_MMAX = 2 * CG_SMAX + 1;
+constexpr int CG_SETUP_MAX = 4 * CG_SMAX;     // setup-phase steps recorded for the Ritz values
+
+struct CgState {                              // device memory, one per solve
+    double xc[CG_MMAX], rc[CG_MMAX], pc[CG_MMAX];
+    double rr;                                // r'^T G r' after the last step taken
+    double alpha[CG_SETUP_MAX], beta[CG_SETUP_MAX];
+    int32_t steps;                            // steps taken by the last outer iteration
+    int32_t done;                             // the recurrence residual reached the target
+    int32_t breakdown;                        // p'^T G B p' <= 0 met (steps counts good ones)
+    int32_t n_setup;                          // setup-phase coefficients recorded
+};
+
+// The CG steps of one outer iteration on coordinate vectors; one warp, lane a owns component
+// a < M.  With B the change of basis (theta_j on the diagonal and a one below it inside each
+// block, nothing in the last column of a block):
+//   alpha = r'G r' / p'G B p',  x' += alpha p',  r' -= alpha B p',
+//   beta = r'G r' (new) / r'G r' (old),  p' = r' + beta p'.
+// Starts from p' = e_0, r' = e_{s+1}, x' = 0 (Y's first columns are p and r).  Dot products
+// are FP64 shuffle trees in a fixed order.  Stops after s steps, at `max_steps`, when
+// sqrt(r'G r') <= target, or at a non-positive p'G B p' (breakdown: that step is not taken).
+// record: append alpha_j, beta_j to the setup-phase coefficients (Lanczos tridiagonal).
+__global__ void __launch_bounds__(32) cg_coord_kernel(CgState *cs, const double *G, int M, int s,
+                                                      const double *theta, double target,
+                                                      int max_steps, int record) {
+    __shared__ double sG[CG_MMAX * CG_MMAX];
+    __shared__ double sv[CG_MMAX];
+    const int a = threadIdx.x;
+    for (int i = a; i < M * M; i += 32) sG[i] = G[i];
+    const bool inP = a <= s;
+    const int jl = inP ? a : a - s - 1;           // position inside the block
+    const int blen = inP ? s + 1 : s;             // block length
+    const double th = (a < M && jl < blen - 1) ? theta[jl] : 0.0;
+    const bool sub = a < M && jl >= 1;
+    double pc = a == 0 ? 1.0 : 0.0, rc = a == s + 1 ? 1.0 : 0.0, xc = 0.0;
+    __syncwarp();
+    auto gmul = [&](double v) -> double {         // (G v)_a
+        if (a < M) sv[a] = v;
+        __syncwarp();
+        double out = 0.0;
+        if (a < M)
+            for (int c = 0; c < M; c++) out = fma(sG[a + c * M], sv[c], out);
+        __syncwarp();
+        return out;
+    };
+    auto wsum = [&](double v) -> double {
+        v = a < M ? v : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        return v;
+    };
+    auto bmul = [&](double v) -> double {         // (B v)_a
+        const double up = __shfl_up_sync(0xffffffffu, v, 1);
+        return sub ? fma(th, v, up) : th * v;
+    };
+    double rr = wsum(rc * gmul(rc));
+    int steps = 0, done = 0, bd = 0;
+    int nrec = cs->n_setup;
+    for (int j = 0; j < s && steps < max_steps; j++) {
+        const double bp = bmul(pc);
+        const double den = wsum(pc * gmul(bp));
+        if (!(den > 0.0)) {
+            bd = 1;
+            break;
+        }
+        const double alpha = rr / den;
+        xc = fma(alpha, pc, xc);
+        rc = fma(-alpha, bp, rc);
+        const double rrn = wsum(rc * gmul(rc));
+        const double beta = rrn / rr;
+        pc = fma(beta, pc, rc);
+        rr = rrn;
+        steps++;
+        if (record && nrec < CG_SETUP_MAX) {
+            if (a == 0) {
+                cs->alpha[nrec] = alpha;
+                cs->beta[nrec] = beta;
+            }
+            nrec++;
+        }
+        if (sqrt(fmax(rr, 0.0)) <= target) {
+            done = 1;
+            break;
+        }
+    }
+    if (a < M) {
+        cs->xc[a] = xc;
+        cs->rc[a] = rc;
+        cs->pc[a] = pc;
+    }
+    __syncwarp();
+    if (a == 0) {
+        cs->rr = rr;
+        cs->steps = steps;
+        cs->done = done;
+        cs->breakdown = bd;
+        cs->n_setup = nrec;
+    }
+}
+
+// x += scale * Y x' (in the basis precision, added to the FP64 x); p = Y p' and r = Y r' in
+// place (Y columns 0 and s + 1).  A thread reads a row of Y before it writes that row.
+template <typename T>
+__global__ void __launch_bounds__(256) cg_recover_kernel(T *Y, int64_t ldv, int M, int s, const CgState *cs,
+                                                         int64_t n, double scale, double *x) {
+    __shared__ T cx[CG_MMAX], cp[CG_MMAX], cr[CG_MMAX];
+    if (threadIdx.x < M) {
+        cx[threadIdx.x] = (T)cs->xc[threadIdx.x];
+        cp[threadIdx.x] = (T)cs->pc[threadIdx.x];
+        cr[threadIdx.x] = (T)cs->rc[threadIdx.x];
+    }
+    __syncthreads();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        T dx = 0, pn = 0, rn = 0;
+        for (int a = 0; a < M; a++) {
+            const T y = Y[i + a * ldv];
+            dx = fma(cx[a], y, dx);
+            pn = fma(cp[a], y, pn);
+            rn = fma(cr[a], y, rn);
+        }
+        x[i] += scale * (double)dx;
+        Y[i] = pn;
+        Y[i + (int64_t)(s + 1) * ldv] = rn;
+    }
+}
+
+// p = r = (T)(r64 / scale): the first columns of both blocks
+template <typename T>
+__global__ void cg_start_kernel(const double *r, int64_t n, double inv, T *p, T *q) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const T v = (T)(r[i] * inv);
+        p[i] = v;
+        q[i] = v;
+    }
+}
+
+template <typename T>
+struct CgSolver {
+    mpk_plan_s *P;
+    cudaStream_t st;
+    mpk_cg_opts o;
+    int64_t n, ldv;
+    int M;
+    DevBuf Y, part, G, cstate, vec, dth;
+    double *bp, *xp, *rp, *nrm;
+    CgState *cs;
+    int gram_grid;
+    Timer t_mpk, t_gram, t_other;
+    std::vector<double> theta;
+    int s_cur;
+    mpk_cg_info info{};
+
+    CgSolver(mpk_plan_s *p, cudaStream_t s_) : P(p), st(s_), t_mpk(s_), t_gram(s_), t_other(s_) {}
+
+    mpk_status alloc() {
+        n = P->n;
+        ldv = (n + 31) / 32 * 32;
+        M = 2 * o.s + 1;
+        MPK_TRY(Y.alloc_on((size_t)M * ldv * sizeof(T), st));
+        gram_grid = 8 * P->n_sm;
+        MPK_TRY(part.alloc_on((size_t)gram_grid * CG_MMAX * SMAX * sizeof(double) + 4096, st));
+        MPK_TRY(G.alloc_on((size_t)CG_MMAX * CG_MMAX * sizeof(double), st));
+        MPK_TRY(cstate.alloc_on(sizeof(CgState), st));
+        MPK_TRY(dth.alloc_on(CG_SMAX * sizeof(double), st));
+        MPK_TRY(vec.alloc_on((size_t)3 * ldv * sizeof(double) + 64 * sizeof(double), st));
+        bp = vec.as<double>();
+        xp = bp + ldv;
+        rp = xp + ldv;
+        nrm = rp + ldv;
+        cs = cstate.as<CgState>();
+        MPK_CUDA(cudaMemsetAsync(cstate.p, 0, sizeof(CgState), st));
+        return MPK_OK;
+    }
+    T *col(int a) { return Y.as<T>() + (int64_t)a * ldv; }
+    void flush_timers() {
+        t_mpk.flush();
+        t_gram.flush();
+        t_other.flush();
+    }
+    mpk_status norm2(const double *v, double *out) {
+        const unsigned g = grid_rows(n);
+        sumsq_partial_kernel<double><<<g, RED_BLOCK, 0, st>>>(v, n, part.as<double>());
+        reduce_partials_kernel<<<redp_grid(1), 32 * REDP_WARPS, 0, st>>>(part.as<double>(), g, 1, 1, out, 1);
+        MPK_CUDA(cudaGetLastError());
+        return MPK_OK;
+    }
+    // G (Mc x Mc, column-major) = Y^T Y over the first Mc columns, in column blocks of <= 16
+    mpk_status gram(int Mc) {
+        const int g = (int)std::min<int64_t>(gram_grid, ceil_div(n, GRAM_RANGE));
+        double *Gd = G.as<double>();
+        for (int c0 = 0; c0 < Mc; c0 += SMAX) {
+            const int S = std::min(SMAX, Mc - c0);
+            if (S <= 4) gram_kernel<T, 4><<<g, 256, 0, st>>>(col(0), ldv, Mc, col(c0), ldv, S, n, part.as<double>());
+            else if (S <= 8) gram_kernel<T, 8><<<g, 256, 0, st>>>(col(0), ldv, Mc, col(c0), ldv, S, n, part.as<double>());
+            else gram_kernel<T, 16><<<g, 256, 0, st>>>(col(0), ldv, Mc, col(c0), ldv, S, n, part.as<double>());
+            reduce_partials_kernel<<<redp_grid(Mc * S), 32 * REDP_WARPS, 0, st>>>(part.as<double>(), g, Mc * S,
+                                                                               (int64_t)Mc * S, Gd + (int64_t)c0 * Mc, 0);
+        }
+        MPK_CUDA(cudaGetLastError());
+        return MPK_OK;
+    }
+    mpk_status basis(T *v0, int p) {
+        if (p < 1) return MPK_OK;
+        std::vector<double> a(p, 1.0), b(p, 0.0), c(p, 0.0);
+        for (int k = 0; k < p; k++) b[k] = -theta_use[k];
+        mpk_coeffs co{p, a.data(), b.data(), c.data(), nullptr};
+        const uint32_t fl = MPK_PERMUTED_IO | MPK_Y0_IS_X | (o.mpk_flags & MPK_UNBLOCKED);
+        return mpk_apply_internal(P, &co, sizeof(T) == 8 ? MPK_F64 : MPK_F32, nullptr, ldv, v0, ldv, 1, fl, st);
+    }
+    std::vector<double> theta_use;
+
+    // One inner solve of A d = r (r in rp, norm hr) by s-step CG with sc steps per outer
+    // iteration; the correction is added to xp as it goes.  Returns the steps taken.
+    mpk_status inner(int sc, const std::vector<double> &th, double hr, double tol_abs, int max_steps,
+                     bool record, int *steps_out, bool *bd_out) {
+        const int Mc = 2 * sc + 1;
+        theta_use = th;
+        *bd_out = false;
+        *steps_out = 0;
+        cg_start_kernel<T><<<grid_rows(n), 256, 0, st>>>(rp, n, 1.0 / hr, col(0), col(sc + 1));
+        MPK_CUDA(cudaGetLastError());
+        MPK_CUDA(cudaMemcpyAsync(dth.p, th.data(), sc * sizeof(double), cudaMemcpyHostToDevice, st));
+        int steps = 0;
+        while (steps < max_steps) {
+            t_mpk.start();
+            MPK_TRY(basis(col(0), sc));
+            MPK_TRY(basis(col(sc + 1), sc - 1));
+            t_mpk.stop();
+            t_gram.start();
+            MPK_TRY(gram(Mc));
+            t_gram.stop();
+            t_other.start();
+            cg_coord_kernel<<<1, 32, 0, st>>>(cs, G.as<double>(), Mc, sc, dth.as<double>(), tol_abs / hr,
+                                              max_steps - steps, record ? 1 : 0);
+            cg_recover_kernel<T><<<grid_rows(n, 8), 256, 0, st>>>(Y.as<T>(), ldv, Mc, sc, cs, n, hr, xp);
+            MPK_CUDA(cudaGetLastError());
+            int hs[3];
+            MPK_CUDA(cudaMemcpyAsync(hs, &cs->steps, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
+            t_other.stop();
+            MPK_CUDA(cudaStreamSynchronize(st));
+            flush_timers();
+            steps += hs[0];
+            if (hs[2]) {
+                *bd_out = true;
+                break;
+            }
+            if (hs[1] || hs[0] == 0) break;
+        }
+        *steps_out = steps;
+        return MPK_OK;
+    }
+
+    // Ritz values of the setup phase: eigenvalues of the Lanczos tridiagonal of its k steps
+    mpk_status setup_shifts() {
+        int k = 0;
+        MPK_CUDA(cudaMemcpyAsync(&k, &cs->n_setup, sizeof(int), cudaMemcpyDeviceToHost, st));
+        MPK_CUDA(cudaStreamSynchronize(st));
+        k = std::min(k, CG_SETUP_MAX);
+        if (k < 1) return MPK_ERR_BREAKDOWN;
+        std::vector<double> al(k), be(k);
+        MPK_CUDA(cudaMemcpyAsync(al.data(), cs->alpha, k * sizeof(double), cudaMemcpyDeviceToHost, st));
+        MPK_CUDA(cudaMemcpyAsync(be.data(), cs->beta, k * sizeof(double), cudaMemcpyDeviceToHost, st));
+        MPK_CUDA(cudaStreamSynchronize(st));
+        std::vector<double> T_((size_t)k * k, 0.0), ev;
+        for (int j = 0; j < k; j++) {
+            T_[j + j * k] = 1.0 / al[j] + (j > 0 ? be[j - 1] / al[j - 1] : 0.0);
+            if (j + 1 < k) {
+                const double e = std::sqrt(std::max(be[j], 0.0)) / al[j];
+                T_[j + (j + 1) * k] = e;
+                T_[(j + 1) + j * k] = e;
+            }
+        }
+        Solver<double>::jacobi_eigenvalues(T_, k, ev);
+        s_cur = std::min(s_cur, k);
+        theta.assign(o.s, 0.0);
+        MPK_TRY(mpk_leja_order(ev.data(), k, s_cur, theta.data()));
+        return MPK_OK;
+    }
+
+    mpk_status run(const double *b, double *x) {
+        MPK_TRY(alloc());
+        const unsigned g = grid_rows(n);
+        const int32_t *perm = P->perm.as<int32_t>();
+        gather_f64_kernel<<<g, 256, 0, st>>>(b, perm, n, bp);
+        gather_f64_kernel<<<g, 256, 0, st>>>(x, perm, n, xp);
+        MPK_CUDA(cudaGetLastError());
+        norm2(bp, nrm + 1);
+        double hb = 0.0;
+        MPK_CUDA(cudaMemcpyAsync(&hb, nrm + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+        MPK_CUDA(cudaStreamSynchronize(st));
+        s_cur = o.s;
+        bool have_shifts = o.shifts != nullptr;
+        if (have_shifts) theta.assign(o.shifts, o.shifts + o.s);
+        mpk_status result = MPK_ERR_NOT_CONVERGED;
+        double relres = 1.0, best_rel = 1e300;
+        int since_best = 0;
+        for (int outer = 0; outer <= o.max_outer; outer++) {
+            t_other.start();
+            MPK_TRY(mpk_launch_residual(P, xp, bp, rp, st));
+            norm2(rp, nrm + 2);
+            double hr = 0.0;
+            MPK_CUDA(cudaMemcpyAsync(&hr, nrm + 2, sizeof(double), cudaMemcpyDeviceToHost, st));
+            t_other.stop();
+            MPK_CUDA(cudaStreamSynchronize(st));
+            flush_timers();
+            relres = hb > 0 ? hr / hb : 0.0;
+            info.outer = outer;
+            if (relres <= o.tol || hb == 0.0) {
+                result = MPK_OK;
+                break;
+            }
+            if (outer == o.max_outer || info.iters >= o.max_iters || !std::isfinite(hr)) break;
+            if (relres < 0.999 * best_rel) {
+                best_rel = relres;
+                since_best = 0;
+            } else if (++since_best >= 50) {
+                break;
+            }
+            double tol_abs = std::max(o.inner_tol * hr, 0.5 * o.tol * hb);
+            if (sizeof(T) == 8) tol_abs = 0.5 * o.tol * hb;
+            const int left = o.max_iters - info.iters;
+            int k = 0;
+            bool bd = false;
+            if (!have_shifts) {
+                // setup phase: plain CG (s = 1, no shift), its coefficients recorded
+                MPK_TRY(inner(1, std::vector<double>(1, 0.0), hr, tol_abs, std::min(4 * o.s, left), true, &k, &bd));
+                if (bd) {
+                    result = MPK_ERR_BREAKDOWN;
+                    info.iters += k;
+                    break;
+                }
+                MPK_TRY(setup_shifts());
+                have_shifts = true;
+            } else {
+                std::vector<double> th(theta.begin(), theta.begin() + s_cur);
+                MPK_TRY(inner(s_cur, th, hr, tol_abs, left, false, &k, &bd));
+                if (bd) {
+                    if (s_cur == 1) {
+                        info.iters += k;
+                        result = MPK_ERR_BREAKDOWN;
+                        break;
+                    }
+                    s_cur = std::max(1, s_cur / 2);
+                }
+            }
+            info.iters += k;
+            if (k == 0 && !bd) break;
+        }
+        scatter_f64_kernel<<<g, 256, 0, st>>>(xp, perm, n, x);
+        MPK_CUDA(cudaGetLastError());
+        MPK_CUDA(cudaStreamSynchronize(st));
+        flush_timers();
+        info.rel_residual = relres;
+        info.status = result;
+        info.s_used = s_cur;
+        for (size_t i = 0; i < theta.size() && i < 16; i++) info.shifts[i] = theta[i];
+        info.ms_mpk = t_mpk.total;
+        info.ms_gram = t_gram.total;
+        info.ms_other = t_other.total;
+        return result;
+    }
+};
+
 }  // namespace
 
 extern "C" mpk_status mpk_gmres_opts_default(mpk_gmres_opts *o) {
@@ -1209,6 +1581,55 @@ extern "C" mpk_status sstep_gmres_solve(mpk_plan_t A, const double *b, double *x
     auto t1 = std::chrono::steady_clock::now();
     inf.ms_total = std::chrono::duration<double, std::milli>(t1 - t0).count();
     inf.status = st;
+    if (info) *info = inf;
+    return st;
+}
+
+extern "C" mpk_status mpk_cg_opts_default(mpk_cg_opts *o) {
+    if (!o) return MPK_ERR_ARG;
+    memset(o, 0, sizeof(*o));
+    o->s = 8;
+    o->tol = 1e-8;
+    o->inner_tol = 1e-5;
+    o->max_outer = 1000;
+    o->max_iters = 100000;
+    o->basis = MPK_F32;
+    o->shifts = nullptr;
+    o->mpk_flags = 0;
+    return MPK_OK;
+}
+
+extern "C" mpk_status sstep_cg_solve(mpk_plan_t A, const double *b, double *x, const mpk_cg_opts *opts,
+                                     mpk_cg_info *info, cudaStream_t stream) {
+    if (!A || !b || !x) return MPK_ERR_ARG;
+    mpk_cg_opts o;
+    if (opts) o = *opts;
+    else mpk_cg_opts_default(&o);
+    if (o.s < 1 || o.s > CG_SMAX || !(o.tol > 0) || !(o.inner_tol > 0) || o.max_outer < 0 ||
+        o.max_iters < 0 || (o.basis != MPK_F32 && o.basis != MPK_F64))
+        return MPK_ERR_ARG;
+    if (!A->has64) return MPK_ERR_ARG;                       // FP64 residual needs FP64 values
+    if (o.basis == MPK_F32 && !A->has32) return MPK_ERR_ARG;
+    if (o.s > A->p_max) return MPK_ERR_ARG;
+    if (o.shifts)
+        for (int i = 0; i < o.s; i++)
+            if (!std::isfinite(o.shifts[i])) return MPK_ERR_ARG;
+    auto t0 = std::chrono::steady_clock::now();
+    mpk_status st;
+    mpk_cg_info inf{};
+    if (o.basis == MPK_F64) {
+        CgSolver<double> S(A, stream);
+        S.o = o;
+        st = S.run(b, x);
+        inf = S.info;
+    } else {
+        CgSolver<float> S(A, stream);
+        S.o = o;
+        st = S.run(b, x);
+        inf = S.info;
+    }
+    inf.status = st;
+    inf.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (info) *info = inf;
     return st;
 }
