@@ -28,7 +28,11 @@ Readings (listed with the design notes):
 * convergence: the recurrence residual norm sqrt(r'^T G r') is checked after every inner step;
   an outer iteration may stop early, and then recovers x, r, p from the steps taken;
 * breakdown: p'^T G B p' <= 0 (A not positive definite, or a numerically singular basis);
-* refinement: outer FP64 loop r = b - A x, inner s-step CG on A d = r to inner_tol, x += d.
+* refinement: outer FP64 loop r = b - A x, inner s-step CG on A d = r to inner_tol, x += d;
+* residual replacement (``replace`` = k > 0, van der Vorst and Ye; Carson and Demmel for s-step
+  methods): at the start of every k-th outer iteration after the first, r is recomputed as
+  b - A x (p is kept), which bounds the drift of the recurrence residual in a low-precision
+  basis; the inner solve then runs to the overall tolerance.
 """
 from __future__ import annotations
 
@@ -124,9 +128,10 @@ def _basis(A, v, theta, k):
     return np.array(cols).T
 
 
-def cacg(A, b, s, theta, x0=None, tol=1e-8, max_iters=100000, stop_abs=None):
+def cacg(A, b, s, theta, x0=None, tol=1e-8, max_iters=100000, stop_abs=None, replace=0):
     """s-step CG (module docstring) from x0.  Stops when the recurrence residual norm is
-    <= max(tol * ||b||, stop_abs).  Returns dict(x, iters, outer, hist, converged) with hist
+    <= max(tol * ||b||, stop_abs).  replace = k > 0: r = b - A x at the start of every k-th
+    outer iteration after the first.  Returns dict(x, iters, outer, hist, converged) with hist
     the recurrence residual norms / ||b|| after every inner step."""
     n = A.n
     x = np.zeros(n) if x0 is None else np.asarray(x0, dtype=np.float64).copy()
@@ -141,6 +146,8 @@ def cacg(A, b, s, theta, x0=None, tol=1e-8, max_iters=100000, stop_abs=None):
     if np.linalg.norm(r) <= target:
         return dict(x=x, iters=0, outer=0, hist=hist, converged=True)
     while iters < max_iters:
+        if replace > 0 and outer > 0 and outer % replace == 0:
+            r = b - _sstep.spmv(A, x)
         Y = np.hstack([_basis(A, p, theta, s), _basis(A, r, theta, s - 1)])
         G = Y.T @ Y
         pc = np.zeros(2 * s + 1)
@@ -177,10 +184,11 @@ def cacg(A, b, s, theta, x0=None, tol=1e-8, max_iters=100000, stop_abs=None):
 
 
 def refine_cg(A, b, s, theta=None, tol=1e-8, inner_tol=1e-5, max_outer=200, round_inner=None,
-              max_iters=100000):
+              max_iters=100000, replace=0):
     """FP64 iterative refinement around s-step CG: r = b - A x (FP64); s-step CG on A d = r to
-    inner_tol relative to ||r|| (``round_inner`` rounds the inner right-hand side and the
-    correction, emulating a lower-precision inner solve); x += d; until ||r|| <= tol ||b||.
+    inner_tol relative to ||r|| (to 0.5 tol ||b|| with residual replacement every ``replace``
+    outer iterations; ``round_inner`` rounds the inner right-hand side and the correction,
+    emulating a lower-precision inner solve); x += d; until ||r|| <= tol ||b||.
     Without ``theta`` a setup phase of 4 s plain CG steps from x = 0 comes first; its Ritz
     values give the shifts.  Returns dict(x, outer, iters, relres, shifts)."""
     x = np.zeros(A.n)
@@ -201,8 +209,12 @@ def refine_cg(A, b, s, theta=None, tol=1e-8, inner_tol=1e-5, max_outer=200, roun
         if relres[-1] <= tol:
             return dict(x=x, outer=k, iters=iters, relres=relres, converged=True, shifts=th)
         rin = r if round_inner is None else r.astype(round_inner).astype(np.float64)
-        out = cacg(A, rin, s, th, tol=inner_tol, max_iters=max_iters - iters,
-                   stop_abs=tol * nb)
+        if replace > 0:
+            out = cacg(A, rin, s, th, tol=0.0, max_iters=max_iters - iters, stop_abs=0.5 * tol * nb,
+                       replace=replace)
+        else:
+            out = cacg(A, rin, s, th, tol=inner_tol, max_iters=max_iters - iters,
+                       stop_abs=tol * nb)
         iters += out["iters"]
         d = out["x"] if round_inner is None else out["x"].astype(round_inner).astype(np.float64)
         x = x + d

@@ -94,6 +94,22 @@ def test_sstep_iterates_equal_cg(s, basis):
         assert abs(got["hist"][k] - ref["hist"][k]) <= 1e-7 * ref["hist"][0], k
 
 
+@pytest.mark.parametrize("replace", [1, 2])
+def test_residual_replacement_keeps_the_cg_iterates(replace):
+    # in FP64 a replaced residual differs from the recurrence one by rounding only, so the
+    # iterates stay those of CG
+    A = mi.diffusion7_lognormal(8)
+    b = mi.uniform_vectors(A.n, 3)[0]
+    s = 4
+    th = ocg.cg_shifts(A, s)
+    ref = ocg.cg(A, b, tol=0.0, max_iters=5 * s)
+    got = ocg.cacg(A, b, s, th, tol=0.0, max_iters=5 * s, replace=replace)
+    assert np.linalg.norm(got["x"] - ref["x"]) <= 1e-8 * np.linalg.norm(ref["x"])
+    out = ocg.refine_cg(A, b, 8, tol=1e-8, replace=replace)
+    assert out["converged"] and out["outer"] <= 2
+    assert np.linalg.norm(b - sstep.spmv(A, out["x"])) <= 1e-8 * np.linalg.norm(b)
+
+
 @pytest.mark.parametrize("name", sorted(SPD))
 def test_sstep_cg_and_refinement_reach_1e8(name):
     A = SPD[name]()
