@@ -248,7 +248,8 @@ def cg_leg(m, torch, dev, n_edge=64, solves=5, bases=("f32", "f64"), warm=True, 
             lat = lat[1:]
         out[basis] = {"solves_per_s": 1e3 * len(lat) / sum(lat), "p50_ms": float(np.percentile(lat, 50)),
                       "p99_ms": float(np.percentile(lat, 99)), "iters": info["iters"],
-                      "rel_residual": info["rel_residual"], "converged": ok,
+                      "rel_residual": info["rel_residual"], "converged": ok, "refinement_steps": info["outer"],
+                      "s_used": info["s_used"],
                       "ms_mpk": info["ms_mpk"], "ms_gram": info["ms_gram"], "ms_other": info["ms_other"]}
     return out
 
@@ -452,6 +453,9 @@ def main():
     ap.add_argument("--profile-solver", action="store_true",
                     help="profiling run of the solver: two s-step GMRES solves (FP32 basis) on the "
                          "log-normal diffusion matrix at --profile-n")
+    ap.add_argument("--profile-cg", action="store_true",
+                    help="profiling run of s-step CG: --profile-reps solves (FP32 basis) on the "
+                         "log-normal diffusion matrix at --profile-n")
     ap.add_argument("--profile-cs", type=int, default=0, help="chunk_slices (0: plan default)")
     ap.add_argument("--profile-slack", type=int, default=0, help="slack_tasks (0: plan default)")
     args = ap.parse_args()
@@ -476,6 +480,11 @@ def main():
         out = solver_leg(m, torch, torch.device("cuda", local), n_edge=args.profile_n,
                          solves=args.profile_reps, bases=("f32",))
         print(json.dumps({"profile": "solver", "result": out}))
+        return 0 if out["f32"]["converged"] else 1
+    if args.profile_cg:
+        out = cg_leg(m, torch, torch.device("cuda", local), n_edge=args.profile_n,
+                     solves=args.profile_reps, bases=("f32",), warm=False)
+        print(json.dumps({"profile": "cg", "result": out}))
         return 0 if out["f32"]["converged"] else 1
     if args.profile:
         return run_profile(args, m, torch, local)

@@ -408,6 +408,14 @@ typedef struct {
                                of the Lanczos tridiagonal of its coefficients) are Leja-ordered */
     uint32_t mpk_flags;     /* extra mpk_apply flags for the basis MPKs: MPK_UNBLOCKED runs
                                back-to-back SpMVs (the baseline) */
+    int32_t replace;        /* residual replacement period k (default 1; 0 = off): at the start
+                               of every k-th outer iteration after the first, the basis
+                               r-column is replaced by the FP64 true residual b - A x (rounded
+                               to the basis precision; p is kept), one FP64 SpMV per k outer
+                               iterations (van der Vorst and Ye; Carson and Demmel for s-step
+                               methods).  It bounds the drift of the recurrence residual in an
+                               FP32 basis, so the inner solve runs to 0.5 tol ||b|| directly
+                               instead of inner_tol and the CG iterates are not restarted */
 } mpk_cg_opts;
 
 typedef struct {
@@ -427,7 +435,8 @@ mpk_status mpk_cg_opts_default(mpk_cg_opts *o);
  * of length n in the original order; x holds the initial guess on entry and the solution on
  * exit; info (host) may be NULL.  Each refinement step computes r = b - A x in FP64 and runs
  * s-step CG on A d = r in the basis precision until its recurrence residual is below
- * inner_tol ||r|| (tol ||b|| with an FP64 basis), adding the correction to x as it goes.
+ * inner_tol ||r|| (0.5 tol ||b|| with an FP64 basis or residual replacement), adding the
+ * correction to x as it goes.
  * A non-positive p^T A p in the coordinate recurrence (an indefinite A, or a numerically
  * singular basis) ends that outer iteration at its last good step and halves s; at s = 1 the
  * solve returns MPK_ERR_BREAKDOWN.  Synchronous on stream (the host reads a few status words

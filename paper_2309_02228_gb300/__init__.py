@@ -112,7 +112,7 @@ class mpk_gmres_info(ctypes.Structure):
 class mpk_cg_opts(ctypes.Structure):
     _fields_ = [("s", ctypes.c_int32), ("tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
                 ("max_outer", ctypes.c_int32), ("max_iters", ctypes.c_int32), ("basis", ctypes.c_int),
-                ("shifts", ctypes.c_void_p), ("mpk_flags", ctypes.c_uint32)]
+                ("shifts", ctypes.c_void_p), ("mpk_flags", ctypes.c_uint32), ("replace", ctypes.c_int32)]
 
 
 class mpk_cg_info(ctypes.Structure):

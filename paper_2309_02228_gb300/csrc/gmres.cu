@@ -1284,6 +1284,13 @@ __global__ void __launch_bounds__(256) cg_recover_kernel(T *Y, int64_t ldv, int 
     }
 }
 
+// q = (T)(r64 * inv): residual replacement of the r column
+template <typename T>
+__global__ void cg_replace_kernel(const double *r, int64_t n, double inv, T *q) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        q[i] = (T)(r[i] * inv);
+}
+
 // p = r = (T)(r64 / scale): the first columns of both blocks
 template <typename T>
 __global__ void cg_start_kernel(const double *r, int64_t n, double inv, T *p, T *q) {
@@ -1381,7 +1388,16 @@ struct CgSolver {
         MPK_CUDA(cudaGetLastError());
         MPK_CUDA(cudaMemcpyAsync(dth.p, th.data(), sc * sizeof(double), cudaMemcpyHostToDevice, st));
         int steps = 0;
-        while (steps < max_steps) {
+        for (int it = 0; steps < max_steps; it++) {
+            if (o.replace > 0 && it > 0 && it % o.replace == 0) {
+                // residual replacement: r = (b - A x) / hr in FP64 (x holds the start plus the
+                // correction so far, so this is the inner residual), p kept
+                t_other.start();
+                MPK_TRY(mpk_launch_residual(P, xp, bp, rp, st));
+                cg_replace_kernel<T><<<grid_rows(n), 256, 0, st>>>(rp, n, 1.0 / hr, col(sc + 1));
+                MPK_CUDA(cudaGetLastError());
+                t_other.stop();
+            }
             t_mpk.start();
             MPK_TRY(basis(col(0), sc));
             MPK_TRY(basis(col(sc + 1), sc - 1));
@@ -1477,7 +1493,7 @@ struct CgSolver {
                 break;
             }
             double tol_abs = std::max(o.inner_tol * hr, 0.5 * o.tol * hb);
-            if (sizeof(T) == 8) tol_abs = 0.5 * o.tol * hb;
+            if (sizeof(T) == 8 || o.replace > 0) tol_abs = 0.5 * o.tol * hb;
             const int left = o.max_iters - info.iters;
             int k = 0;
             bool bd = false;
@@ -1596,6 +1612,7 @@ extern "C" mpk_status mpk_cg_opts_default(mpk_cg_opts *o) {
     o->basis = MPK_F32;
     o->shifts = nullptr;
     o->mpk_flags = 0;
+    o->replace = 1;
     return MPK_OK;
 }
 
@@ -1606,7 +1623,7 @@ extern "C" mpk_status sstep_cg_solve(mpk_plan_t A, const double *b, double *x, c
     if (opts) o = *opts;
     else mpk_cg_opts_default(&o);
     if (o.s < 1 || o.s > CG_SMAX || !(o.tol > 0) || !(o.inner_tol > 0) || o.max_outer < 0 ||
-        o.max_iters < 0 || (o.basis != MPK_F32 && o.basis != MPK_F64))
+        o.max_iters < 0 || (o.basis != MPK_F32 && o.basis != MPK_F64) || o.replace < 0)
         return MPK_ERR_ARG;
     if (!A->has64) return MPK_ERR_ARG;                       // FP64 residual needs FP64 values
     if (o.basis == MPK_F32 && !A->has32) return MPK_ERR_ARG;

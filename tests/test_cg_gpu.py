@@ -6,6 +6,8 @@ names for the MPK, Sec. 4 and Sec. 7), through the C ABI.
   within kappa * 2e-8, in FP32 and FP64 bases, from zero and from a nonzero initial guess;
 * the shifts of the setup phase equal the oracle's Ritz values of the same CG steps;
 * with given shifts and an FP64 basis the number of CG steps matches the oracle's;
+* residual replacement (the default) needs fewer CG steps in an FP32 basis than refinement
+  alone;
 * the blocked and unblocked MPK give identical solves;
 * a negative definite matrix reports MPK_ERR_BREAKDOWN, the step limit MPK_ERR_NOT_CONVERGED,
   and invalid options MPK_ERR_ARG."""
@@ -108,10 +110,22 @@ def test_cg_steps_match_the_oracle_with_given_shifts(m, s):
     plan = _plan(m, A)
     x, info = _solve(m, plan, b, shifts=th, basis=m.MPK_F64, s=s, tol=1e-8)
     assert info["status_code"] == m.MPK_OK, info
-    ref = ocg.refine_cg(A, b, s, theta=th, tol=1e-8, inner_tol=1e-8)
+    ref = ocg.refine_cg(A, b, s, theta=th, tol=1e-8, inner_tol=1e-8, replace=1)
     assert ref["converged"]
     assert abs(info["iters"] - ref["iters"]) <= max(2, s), (info["iters"], ref["iters"])
     assert np.allclose(info["shifts"], th, rtol=0, atol=0)
+
+
+def test_cg_residual_replacement_saves_steps_in_fp32(m):
+    A = mi.diffusion7_lognormal(20)
+    b = mi.uniform_vectors(A.n, 4)[0]
+    plan = _plan(m, A)
+    xr, ir = _solve(m, plan, b, basis=m.MPK_F32, s=8, tol=1e-8, replace=1)
+    xn, inn = _solve(m, plan, b, basis=m.MPK_F32, s=8, tol=1e-8, replace=0)
+    for x, info in ((xr, ir), (xn, inn)):
+        assert info["status_code"] == m.MPK_OK, info
+        assert np.linalg.norm(b - sstep.spmv(A, x)) <= 1e-8 * np.linalg.norm(b)
+    assert ir["iters"] < inn["iters"], (ir, inn)
 
 
 def test_cg_blocked_equals_unblocked(m):
@@ -136,7 +150,7 @@ def test_cg_breakdown_and_limits(m):
     _, info = _solve(m, plan2, b, s=4, tol=1e-8, max_iters=10)
     assert info["status_code"] == m.MPK_ERR_NOT_CONVERGED, info
     assert info["iters"] <= 10
-    for kw in ({"s": 0}, {"s": 16}, {"tol": 0.0}, {"basis": 7}):
+    for kw in ({"s": 0}, {"s": 16}, {"tol": 0.0}, {"basis": 7}, {"replace": -1}):
         _, info = _solve(m, plan2, b, **kw)
         assert info["status_code"] == m.MPK_ERR_ARG, kw
     small = _plan(m, A, p=4)
