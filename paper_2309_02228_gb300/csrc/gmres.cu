@@ -1176,33 +1176,56 @@ struct CgState {                              // device memory, one per solve
 // block, nothing in the last column of a block):
 //   alpha = r'G r' / p'G B p',  x' += alpha p',  r' -= alpha B p',
 //   beta = r'G r' (new) / r'G r' (old),  p' = r' + beta p'.
+// G B is formed once (column c is theta_c G e_c + G e_{c+1}), and G r' is carried along by
+// G r' -= alpha (G B p'), so each step costs one FP64 matrix-vector product (G B p').
 // Starts from p' = e_0, r' = e_{s+1}, x' = 0 (Y's first columns are p and r).  Dot products
 // are FP64 shuffle trees in a fixed order.  Stops after s steps, at `max_steps`, when
 // sqrt(r'G r') <= target, or at a non-positive p'G B p' (breakdown: that step is not taken).
 // record: append alpha_j, beta_j to the setup-phase coefficients (Lanczos tridiagonal).
 __global__ void __launch_bounds__(32) cg_coord_kernel(CgState *cs, const double *G, int M, int s,
                                                       const double *theta, double target,
-                                                      int max_steps, int record) {
-    __shared__ double sG[CG_MMAX * CG_MMAX];
+                                                      int max_steps, int record, int bs) {
+    __shared__ double sGB[CG_MMAX * CG_MMAX];
     __shared__ double sv[CG_MMAX];
     const int a = threadIdx.x;
-    for (int i = a; i < M * M; i += 32) sG[i] = G[i];
+    // diagonal of B in column c and whether B has a one below it (c not last in its block)
+    auto bdiag = [&](int c) -> double {
+        const int j = c <= s ? c : c - s - 1;
+        const int len = c <= s ? s + 1 : s;
+        return j < len - 1 ? theta[j] : 0.0;
+    };
+    auto bsub = [&](int c) -> bool {
+        const int j = c <= s ? c : c - s - 1;
+        const int len = c <= s ? s + 1 : s;
+        return j < len - 1;
+    };
+    // G: the upper triangle packed by bs x bs blocks (gram_sym_kernel); read it symmetrically
+    const int nbk = (M + bs - 1) / bs;
+    auto g = [&](int r, int c) -> double {
+        if (r > c) {
+            const int t_ = r;
+            r = c;
+            c = t_;
+        }
+        const int ab = r / bs, bb = c / bs;
+        const int pb = ab * nbk - ab * (ab - 1) / 2 + (bb - ab);
+        return G[pb * bs * bs + (r - ab * bs) * bs + (c - bb * bs)];
+    };
+    double gr = 0.0;                               // (G r')_a, r' = e_{s+1}
+    if (a < M) {
+        for (int c = 0; c < M; c++) {
+            double v = bdiag(c) * g(a, c);
+            if (bsub(c)) v += g(a, c + 1);
+            sGB[a + c * M] = v;
+        }
+        gr = g(a, s + 1);
+    }
     const bool inP = a <= s;
     const int jl = inP ? a : a - s - 1;           // position inside the block
-    const int blen = inP ? s + 1 : s;             // block length
-    const double th = (a < M && jl < blen - 1) ? theta[jl] : 0.0;
     const bool sub = a < M && jl >= 1;
+    const double th = a < M ? bdiag(a) : 0.0;
     double pc = a == 0 ? 1.0 : 0.0, rc = a == s + 1 ? 1.0 : 0.0, xc = 0.0;
     __syncwarp();
-    auto gmul = [&](double v) -> double {         // (G v)_a
-        if (a < M) sv[a] = v;
-        __syncwarp();
-        double out = 0.0;
-        if (a < M)
-            for (int c = 0; c < M; c++) out = fma(sG[a + c * M], sv[c], out);
-        __syncwarp();
-        return out;
-    };
     auto wsum = [&](double v) -> double {
         v = a < M ? v : 0.0;
 #pragma unroll
@@ -1213,12 +1236,26 @@ __global__ void __launch_bounds__(32) cg_coord_kernel(CgState *cs, const double 
         const double up = __shfl_up_sync(0xffffffffu, v, 1);
         return sub ? fma(th, v, up) : th * v;
     };
-    double rr = wsum(rc * gmul(rc));
+    double rr = wsum(rc * gr);
     int steps = 0, done = 0, bd = 0;
     int nrec = cs->n_setup;
     for (int j = 0; j < s && steps < max_steps; j++) {
+        // v1 = (G B p')_a, two partial sums to halve the dependent chain
+        if (a < M) sv[a] = pc;
+        __syncwarp();
+        double v1 = 0.0, v2 = 0.0;
+        if (a < M) {
+            int c = 0;
+            for (; c + 1 < M; c += 2) {
+                v1 = fma(sGB[a + c * M], sv[c], v1);
+                v2 = fma(sGB[a + (c + 1) * M], sv[c + 1], v2);
+            }
+            if (c < M) v1 = fma(sGB[a + c * M], sv[c], v1);
+        }
+        __syncwarp();
+        v1 += v2;
         const double bp = bmul(pc);
-        const double den = wsum(pc * gmul(bp));
+        const double den = wsum(pc * v1);
         if (!(den > 0.0)) {
             bd = 1;
             break;
@@ -1226,7 +1263,8 @@ __global__ void __launch_bounds__(32) cg_coord_kernel(CgState *cs, const double 
         const double alpha = rr / den;
         xc = fma(alpha, pc, xc);
         rc = fma(-alpha, bp, rc);
-        const double rrn = wsum(rc * gmul(rc));
+        gr = fma(-alpha, v1, gr);
+        const double rrn = wsum(rc * gr);
         const double beta = rrn / rr;
         pc = fma(beta, pc, rc);
         rr = rrn;
@@ -1255,6 +1293,114 @@ __global__ void __launch_bounds__(32) cg_coord_kernel(CgState *cs, const double 
         cs->done = done;
         cs->breakdown = bd;
         cs->n_setup = nrec;
+    }
+}
+
+// Symmetric Gram of the CG basis: the upper triangle of G = Y^T Y (Y: n x M, M <= 31), stored
+// packed by BS x BS blocks: block pair pb = (ab, bb), ab <= bb, enumerated row by row, entry
+// (i, j) of the block at pb * BS^2 + i * BS + j.  A CTA stages 128-row tiles of Y in shared
+// memory; thread t owns block pair t % NBP and the rows g, g + RG, ... of each tile
+// (g = t / NBP, RG = 256 / NBP row groups).  Products are summed in the basis precision over
+// up to 32 tiles, then added to FP64 totals; the CTA sums its row groups in order (in the
+// shared memory the tiles used) and writes one FP64 partial per entry, which
+// reduce_partials_kernel sums over the CTAs in a fixed order.  BS = 4 for FP32 (loads of 8
+// values per 16 FMAs), 2 for FP64 (fewer wasted products on the slow FP64 pipe).
+constexpr int GSYM_TR = 128;
+constexpr int GSYM_MP = 32;                   // M padded (<= 32 columns)
+template <typename T> constexpr int gsym_bs() { return sizeof(T) == 4 ? 4 : 2; }
+static inline int gsym_nbp(int M, int bs) {
+    const int nb = (M + bs - 1) / bs;
+    return nb * (nb + 1) / 2;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) gram_sym_kernel(const T *Y, int64_t ldv, int M, int64_t n,
+                                                       double *part) {
+    constexpr int BS = gsym_bs<T>();
+    // tiles of Y during the sweep, then the row groups' FP64 totals (RG * NBP * BS^2 <= 256 * BS^2)
+    constexpr int SH_BYTES = (GSYM_MP * GSYM_TR * (int)sizeof(T)) > (256 * BS * BS * 8)
+                                 ? (GSYM_MP * GSYM_TR * (int)sizeof(T)) : (256 * BS * BS * 8);
+    __shared__ __align__(16) unsigned char sh_raw[SH_BYTES];
+    T *sY = reinterpret_cast<T *>(sh_raw);
+    const int nb = (M + BS - 1) / BS;
+    const int Mp = nb * BS;
+    const int NBP = nb * (nb + 1) / 2;
+    const int RG = (int)blockDim.x / NBP;
+    const int t = threadIdx.x;
+    const bool act = t < NBP * RG;
+    const int pb = t % NBP, g = t / NBP;
+    int ab = 0, rem = pb;
+    while (rem >= nb - ab) {
+        rem -= nb - ab;
+        ab++;
+    }
+    const int bb = ab + rem;
+    double acc[BS * BS];
+    T tacc[BS * BS];
+#pragma unroll
+    for (int k = 0; k < BS * BS; k++) {
+        acc[k] = 0.0;
+        tacc[k] = (T)0;
+    }
+    int since = 0;
+    // thread t stages row t % 128 of columns t / 128, t / 128 + 2, ... of a tile: the next
+    // tile's loads are issued into registers before the current tile is computed
+    constexpr int PF = GSYM_MP * GSYM_TR / 256;      // 16 staged values per thread
+    const int pr = t % GSYM_TR, pc0 = t / GSYM_TR;
+    T pre[PF];
+    auto prefetch = [&](int64_t tile) {
+        const int64_t r = tile * GSYM_TR + pr;
+#pragma unroll
+        for (int j = 0; j < PF; j++) {
+            const int c = pc0 + 2 * j;
+            pre[j] = (c < M && r < n) ? __ldg(Y + r + (int64_t)c * ldv) : (T)0;
+        }
+    };
+    if ((int64_t)blockIdx.x * GSYM_TR < n) prefetch(blockIdx.x);
+    for (int64_t tile = blockIdx.x; tile * GSYM_TR < n; tile += gridDim.x) {
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < PF; j++) {
+            const int c = pc0 + 2 * j;
+            if (c < Mp) sY[c * GSYM_TR + pr] = pre[j];
+        }
+        __syncthreads();
+        if ((tile + gridDim.x) * GSYM_TR < n) prefetch(tile + gridDim.x);
+        if (act) {
+            for (int r = g; r < GSYM_TR; r += RG) {
+                T xa[BS], xb[BS];
+#pragma unroll
+                for (int i = 0; i < BS; i++) {
+                    xa[i] = sY[(ab * BS + i) * GSYM_TR + r];
+                    xb[i] = sY[(bb * BS + i) * GSYM_TR + r];
+                }
+#pragma unroll
+                for (int i = 0; i < BS; i++)
+#pragma unroll
+                    for (int j = 0; j < BS; j++) tacc[i * BS + j] = fma(xa[i], xb[j], tacc[i * BS + j]);
+            }
+            if (++since == 32) {
+#pragma unroll
+                for (int k = 0; k < BS * BS; k++) {
+                    acc[k] += (double)tacc[k];
+                    tacc[k] = (T)0;
+                }
+                since = 0;
+            }
+        }
+    }
+    const int m = NBP * BS * BS;
+    double *red = reinterpret_cast<double *>(sh_raw);
+    __syncthreads();
+    if (act) {
+#pragma unroll
+        for (int k = 0; k < BS * BS; k++) red[g * m + pb * BS * BS + k] = acc[k] + (double)tacc[k];
+    }
+    __syncthreads();
+    for (int e = t; e < m; e += blockDim.x) {
+        double v = 0.0;
+        for (int q = 0; q < RG; q++) v += red[q * m + e];
+        part[(int64_t)blockIdx.x * m + e] = v;
     }
 }
 
@@ -1325,8 +1471,9 @@ struct CgSolver {
         M = 2 * o.s + 1;
         MPK_TRY(Y.alloc_on((size_t)M * ldv * sizeof(T), st));
         gram_grid = 8 * P->n_sm;
-        MPK_TRY(part.alloc_on((size_t)gram_grid * CG_MMAX * SMAX * sizeof(double) + 4096, st));
-        MPK_TRY(G.alloc_on((size_t)CG_MMAX * CG_MMAX * sizeof(double), st));
+        // symmetric Gram partials: (CTA, row group) x packed entries <= CTAs x 256 threads x BS^2
+        MPK_TRY(part.alloc_on((size_t)(2 * P->n_sm) * 256 * BS * BS * sizeof(double) + 4096, st));
+        MPK_TRY(G.alloc_on((size_t)GSYM_MP * GSYM_MP * sizeof(double), st));
         MPK_TRY(cstate.alloc_on(sizeof(CgState), st));
         MPK_TRY(dth.alloc_on(CG_SMAX * sizeof(double), st));
         MPK_TRY(vec.alloc_on((size_t)3 * ldv * sizeof(double) + 64 * sizeof(double), st));
@@ -1351,18 +1498,15 @@ struct CgSolver {
         MPK_CUDA(cudaGetLastError());
         return MPK_OK;
     }
-    // G (Mc x Mc, column-major) = Y^T Y over the first Mc columns, in column blocks of <= 16
+    // G = Y^T Y over the first Mc columns: upper triangle packed by blocks (gram_sym_kernel)
+    static constexpr int BS = gsym_bs<T>();
+    int gsym_grid() const { return (int)std::min<int64_t>(2 * P->n_sm, std::max<int64_t>(1, ceil_div(n, GSYM_TR))); }
     mpk_status gram(int Mc) {
-        const int g = (int)std::min<int64_t>(gram_grid, ceil_div(n, GRAM_RANGE));
-        double *Gd = G.as<double>();
-        for (int c0 = 0; c0 < Mc; c0 += SMAX) {
-            const int S = std::min(SMAX, Mc - c0);
-            if (S <= 4) gram_kernel<T, 4><<<g, 256, 0, st>>>(col(0), ldv, Mc, col(c0), ldv, S, n, part.as<double>());
-            else if (S <= 8) gram_kernel<T, 8><<<g, 256, 0, st>>>(col(0), ldv, Mc, col(c0), ldv, S, n, part.as<double>());
-            else gram_kernel<T, 16><<<g, 256, 0, st>>>(col(0), ldv, Mc, col(c0), ldv, S, n, part.as<double>());
-            reduce_partials_kernel<<<redp_grid(Mc * S), 32 * REDP_WARPS, 0, st>>>(part.as<double>(), g, Mc * S,
-                                                                               (int64_t)Mc * S, Gd + (int64_t)c0 * Mc, 0);
-        }
+        const int g = gsym_grid();
+        const int m = gsym_nbp(Mc, BS) * BS * BS;
+        gram_sym_kernel<T><<<g, 256, 0, st>>>(Y.as<T>(), ldv, Mc, n, part.as<double>());
+        reduce_partials_kernel<<<redp_grid(m), 32 * REDP_WARPS, 0, st>>>(part.as<double>(), g, m, (int64_t)m,
+                                                                       G.as<double>(), 0);
         MPK_CUDA(cudaGetLastError());
         return MPK_OK;
     }
@@ -1407,7 +1551,7 @@ struct CgSolver {
             t_gram.stop();
             t_other.start();
             cg_coord_kernel<<<1, 32, 0, st>>>(cs, G.as<double>(), Mc, sc, dth.as<double>(), tol_abs / hr,
-                                              max_steps - steps, record ? 1 : 0);
+                                              max_steps - steps, record ? 1 : 0, BS);
             cg_recover_kernel<T><<<grid_rows(n, 8), 256, 0, st>>>(Y.as<T>(), ldv, Mc, sc, cs, n, hr, xp);
             MPK_CUDA(cudaGetLastError());
             int hs[3];
