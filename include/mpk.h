@@ -98,7 +98,11 @@ typedef struct {
     int32_t kernel;           /* blocked kernel: 0 = warp tasks (default: every warp takes
                                  tasks from a ticket dispenser and waits on per-block
                                  completion counters), 1 = CTA tasks fed by a control warp,
-                                 2 = warp tasks in static round robin */
+                                 2 = warp tasks in static round robin, 3 = ready-first warp
+                                 tasks (no schedule: a warp claims, highest power first, the
+                                 next chunk of a power whose dependencies are complete, else
+                                 the next chunk of power 1; claimed tasks never wait; chunks
+                                 are dealt to interleaved shards, each with its own cursors) */
     int32_t blocked;          /* mpk_apply without MPK_UNBLOCKED: 1 = always the blocked
                                  kernel, 0 = never, -1 = automatic (default): p >= 2 and a
                                  matrix larger than the L2 cache, and then whichever kernel
@@ -114,6 +118,9 @@ typedef struct {
                                  zero is not scaled (d_j^-1 := 1).  Also builds the bit mask
                                  of strictly lower entries (in the caller's row order) that
                                  MPK_GS2 needs: one uint32 per 32 stored entries.  Default 0 */
+    int32_t shard_warps;      /* kernel = 3: warps per shard of the ready-first hand-out
+                                 (default 4; fewer shards share cursors more, more shards widen
+                                 the window between powers) */
 } mpk_plan_opts;
 
 typedef struct mpk_plan_s *mpk_plan_t;

@@ -70,7 +70,7 @@ class mpk_plan_opts(ctypes.Structure):
                 ("schedule", ctypes.c_int32), ("slack_tasks", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("stage", ctypes.c_int32),
                 ("kernel", ctypes.c_int32), ("blocked", ctypes.c_int32),
-                ("jacobi", ctypes.c_int32)]
+                ("jacobi", ctypes.c_int32), ("shard_warps", ctypes.c_int32)]
 
 
 class mpk_plan_info(ctypes.Structure):

@@ -30,6 +30,11 @@ struct VecSet {
     int p_total;          // last absolute power of the whole call
     int gs2_steps;        // MPK_GS2: gamma + 1 steps per power (0: plain powers)
     void *h[2];           // MPK_GS2: ring of the inner iterates h_j (h_j in h[j & 1])
+    void *orig;           // one right-hand side, all powers, original order requested: y_k is
+                          // also stored at orig + k * orig_ld + operm[row] by the kernel that
+                          // computes it (no separate un-staging pass); null otherwise
+    int64_t orig_ld;
+    const int32_t *operm; // level order -> original row
 };
 
 __device__ __forceinline__ void *ring_of(const VecSet &v, int k) {
@@ -217,6 +222,9 @@ __device__ __forceinline__ void row_finish(const T (&acc)[NR], int32_t row, int 
     }
 #pragma unroll
     for (int q = 0; q < NR; q++) yk[o + q] = res[q];
+    if constexpr (NR == 1) {
+        if (V.orig) reinterpret_cast<T *>(V.orig)[(int64_t)k * V.orig_ld + __ldg(V.operm + row)] = res[0];
+    }
     if (V.use_gamma) {
         T *acc_out = reinterpret_cast<T *>(V.final_out);
         const T gk = (T)cf.g[k];
@@ -876,6 +884,13 @@ struct WaveArgs {
     uint32_t debug_drop;              // 1: task (chunk 0, power 1) does not publish
     uint32_t dynamic;                 // 1: tickets from the control block's dispenser
     const uint32_t *lmask;            // MPK_GS2: strictly lower entries (see slice_gs2_step)
+    uint32_t *cursor;                 // ready-first: per (local power k, shard s) at k * n_shards
+                                      // + s, the next position j not yet handed out (chunk
+                                      // s + j * n_shards)
+    const int32_t *chunk_blk;         // ready-first: counter block of each chunk
+    const int32_t *wait_blk;          // ready-first: last block a chunk's task depends on
+    int32_t n_chunks;
+    int32_t n_shards;                 // ready-first: chunk c belongs to shard c % n_shards
     uint32_t *kep;                    // device: earlier launches that ran each local power k;
                                       // the last CTA out adds this launch (powers 1..seg), so
                                       // a captured graph can replay the launch
@@ -1009,6 +1024,170 @@ __global__ void __launch_bounds__(WAVE_BLOCK, ((PAIRS || GS2) ? 4 : wave_min_blo
 }
 
 // ------------------------------------------------------------------------------------------
+// Ready-first warp tasks (opts.kernel = 3).  The tasks are the warp-task kernel's (chunk c,
+// local power k), but none is scheduled ahead.  Chunks are dealt to n_shards interleaved
+// shards (chunk c to shard c % n_shards, every shard served by the same number of warps, at
+// least one); every (power, shard) keeps a cursor, its next chunk not yet handed out.  A warp
+// takes, highest power first, its shard's cursor chunk of a power whose dependencies are
+// already complete (power k - 1 has finished every counter block up to the one holding
+// max(dep_hi(c), c)), claiming it by compare-and-swap; when no higher power is ready it takes
+// its shard's next chunk of power 1, which depends on nothing.  So a claimed task never waits,
+// each power advances as soon as its inputs exist (the window between consecutive powers is
+// about a level plus two rows of shards, which can stay in L2), and every shard's warps can
+// always claim the lowest ready task of their shard, so the launch always progresses.  (With
+// a single cursor per power every warp raced for the same chunk and the hand-out serialised,
+// measured: one task per L2 round trip.)  Completion is published as in the warp-task kernel
+// (same counters, same launch accounting) and the row function is the same, so results are
+// bit-identical to every other kernel.  A warp that finds nothing ready backs off; that wait
+// is bounded (timeout: error latched, every warp stops).
+// ------------------------------------------------------------------------------------------
+template <typename T, int NR, bool PAIRS, bool GS2 = false>
+__global__ void __launch_bounds__(WAVE_BLOCK, ((PAIRS || GS2) ? 4 : wave_min_blocks<T, NR>())) mpk_ready_kernel(
+    SellView A, int n_rhs, VecSet V, Coefs cf, WaveArgs W) {
+    constexpr int BGMAX = 8;
+    __shared__ int32_t s_wm[WAVE_BLOCK / 32][MPK_MAX_P + 1];
+    __shared__ uint32_t s_mult[MPK_MAX_P + 1];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    for (int i = lane; i <= MPK_MAX_P; i += 32) s_wm[wib][i] = 0;
+    // counters of local power k read kep[k] + 1 times the block size when this launch is done
+    if (threadIdx.x <= MPK_MAX_P)
+        s_mult[threadIdx.x] = (threadIdx.x <= W.seg ? *(volatile uint32_t *)(W.kep + threadIdx.x) : 0u) + 1u;
+    __syncthreads();
+    const T *gval = reinterpret_cast<const T *>(A.val);
+    const uint32_t S = (uint32_t)W.n_shards;
+    const uint32_t shard = (uint32_t)(blockIdx.x * (WAVE_BLOCK / 32) + wib) % S;
+    // positions j of this shard: chunks shard + j * S < n_chunks
+    const uint32_t nch = (uint32_t)W.n_chunks > shard ? ((uint32_t)W.n_chunks - shard + S - 1) / S : 0u;
+    uint32_t *cur = W.cursor + shard;   // power k's cursor at cur[k * S]
+    bool idle = false;
+    uint64_t t_idle = 0;
+    for (;;) {
+        // ---- claim a ready task: peek every cursor of the shard at once (lane k: power k)
+        int32_t c = -1;
+        int kl = 0;
+        uint32_t cv = 0xffffffffu;
+        if (lane >= 1 && lane <= W.seg) cv = ld_relaxed_u32(cur + (int64_t)lane * S);
+        bool higher_left = false;
+        for (int k = W.seg; k >= 2 && kl == 0; k--) {
+            uint32_t jk = __shfl_sync(0xffffffffu, cv, k);
+            for (int attempt = 0; attempt < 3 && jk < nch; attempt++) {
+                higher_left = true;
+                const uint32_t ck = shard + jk * S;
+                // is power k - 1 complete on every block up to wait_blk[ck]?  (no waiting)
+                const int32_t hb = __ldg(W.wait_blk + ck);
+                int32_t wm = s_wm[wib][k - 1];
+                const uint32_t *cp = W.cnt + (int64_t)(k - 1) * W.n_cblk;
+                const uint32_t mult = s_mult[k - 1];
+                bool ready = true;
+                while (wm <= hb) {
+                    const int32_t b = wm + lane;
+                    bool done = true;
+                    if (b <= hb) {
+                        const uint32_t v = ld_relaxed_u32(cp + b);
+                        done = (int32_t)(v - mult * (uint32_t)__ldg(W.cblk_size + b)) >= 0;
+                    }
+                    const unsigned nd = __ballot_sync(0xffffffffu, !done);
+                    if (nd == 0) {
+                        wm = min(wm + 32, hb + 1);
+                        continue;
+                    }
+                    wm += __ffs(nd) - 1;
+                    ready = false;
+                    break;
+                }
+                if (lane == 0) s_wm[wib][k - 1] = wm;
+                __syncwarp();
+                if (!ready) break;
+                uint32_t old = 0;
+                if (lane == 0) old = atomicCAS(cur + (int64_t)k * S, jk, jk + 1u);
+                old = __shfl_sync(0xffffffffu, old, 0);
+                if (old == jk) {
+                    c = (int32_t)ck;
+                    kl = k;
+                    break;
+                }
+                jk = old;   // another warp of the shard took it: try the new cursor position
+            }
+        }
+        if (kl == 0) {
+            const uint32_t c1 = __shfl_sync(0xffffffffu, cv, 1);
+            if (c1 < nch) {
+                uint32_t got = 0;
+                if (lane == 0) got = atomicAdd(cur + S, 1u);
+                got = __shfl_sync(0xffffffffu, got, 0);
+                if (got < nch) {
+                    c = (int32_t)(shard + got * S);
+                    kl = 1;
+                }
+            }
+        }
+        if (kl == 0) {
+            const uint32_t c1 = __shfl_sync(0xffffffffu, cv, 1);
+            if (!higher_left && c1 >= nch) break;   // every task has been handed out
+            // nothing ready yet: back off, bounded
+            uint64_t now = 0;
+            uint32_t err = 0;
+            if (lane == 0) {
+                now = globaltimer_ns();
+                err = *(volatile uint32_t *)&W.ctrl->error;
+            }
+            now = __shfl_sync(0xffffffffu, now, 0);
+            err = __shfl_sync(0xffffffffu, err, 0);
+            if (err) break;
+            if (!idle) {
+                idle = true;
+                t_idle = now;
+            } else if (now - t_idle > W.timeout_ns) {
+                if (lane == 0 && atomicOr(&W.ctrl->error, 1u) == 0u) W.ctrl->err_task = 0xfffffffeu;
+                break;
+            }
+            __nanosleep(128);
+            continue;
+        }
+        idle = false;
+        if (kl > 1) fence_acq_rel_gpu();   // acquire: counters observed above before the vectors
+        // ---- the task: the warp-task kernel's body
+        const int k = W.k0 + kl;
+        const int32_t s1 = __ldg(W.chunk_slice + c + 1);
+        int32_t s = __ldg(W.chunk_slice + c);
+        if constexpr (GS2) {
+            for (; s < s1; s++) slice_gs2_step<T>(A, W.lmask, s, lane, V, k, cf);
+        } else {
+            if constexpr (NR == 1 && PAIRS) {
+                for (; s + 1 < s1; s += 2) slice_pair_power<T>(A, s, s + 1, lane, V, k, cf);
+            }
+            for (; s < s1; s++) {
+                const long long gofs = 32ll * __ldg(A.slice_ptr + s);
+                slice_power<T, NR, false, false, BGMAX>(A, s, A.col + gofs, gval + gofs, lane, n_rhs, V, k, cf);
+            }
+        }
+        __syncwarp();
+        if (lane == 0 && !(W.debug_drop && c == 0 && kl == 1))
+            red_release_add_u32(W.cnt + (int64_t)kl * W.n_cblk + __ldg(W.chunk_blk + c), 1u);
+    }
+    // every CTA gets here; the last one (every other CTA's warps have left the task loop)
+    // clears the cursors and counts this launch for every local power it ran (so a captured
+    // graph replays it)
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(&W.ctrl->done_ctas, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last) {
+        for (int64_t i = threadIdx.x; i < (int64_t)(W.seg + 1) * S; i += blockDim.x) W.cursor[i] = 0u;
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            W.ctrl->done_ctas = 0;
+            for (int k = 1; k <= W.seg; k++) W.kep[k] += 1u;
+            __threadfence();
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
 // Staging: user layout (original or level order, column-major or interleaved) <-> the
 // kernel's interleaved level-order layout.
 // ------------------------------------------------------------------------------------------
@@ -1119,13 +1298,18 @@ mpk_status launch_wave(mpk_plan_s *P, const SellView &A, int n_rhs, const VecSet
     W.timeout_ns = (uint64_t)P->opts.wait_timeout_us * 1000ull;
     W.debug_drop = (flags & MPK_DEBUG_DROP_FLAG) && k0 == 0 ? 1u : 0u;
     W.dynamic = P->wave_dynamic ? 1u : 0u;
-    auto kern = mpk_wave_kernel<T, NR, false>;
+    const bool rf = P->ready_first != 0;
+    auto kern = rf ? mpk_ready_kernel<T, NR, false> : mpk_wave_kernel<T, NR, false>;
     if constexpr (NR == 1) {
-        if (P->short_rows) kern = mpk_wave_kernel<T, 1, true>;
-        if (gs2) kern = mpk_wave_kernel<T, 1, false, true>;
+        if (P->short_rows) kern = rf ? mpk_ready_kernel<T, 1, true> : mpk_wave_kernel<T, 1, true>;
+        if (gs2) kern = rf ? mpk_ready_kernel<T, 1, false, true> : mpk_wave_kernel<T, 1, false, true>;
     }
     if (gs2 && NR != 1) return MPK_ERR_UNIMPLEMENTED;
     W.lmask = P->s_lmask.as<uint32_t>();
+    W.cursor = P->wave_cur.as<uint32_t>();
+    W.chunk_blk = P->chunk_blk_d.as<int32_t>();
+    W.wait_blk = P->wait_blk_d.as<int32_t>();
+    W.n_chunks = P->n_chunks;
     int occ = 0;
     MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, WAVE_BLOCK, 0));
     if (occ < 1) return MPK_ERR_UNIMPLEMENTED;
@@ -1134,6 +1318,12 @@ mpk_status launch_wave(mpk_plan_s *P, const SellView &A, int n_rhs, const VecSet
     const int64_t grid = std::min<int64_t>((int64_t)P->n_sm * per_sm, ceil_div(warps, WAVE_BLOCK / 32));
     W.kep = P->wave_kep.as<uint32_t>();
     W.seg = seg;
+    if (rf) {
+        // shards of the ready-first hand-out: each served by shard_warps warps (at least one)
+        const int64_t lw = grid * (WAVE_BLOCK / 32);
+        const int64_t wps = std::max<int32_t>(1, P->shard_warps);
+        W.n_shards = (int32_t)std::max<int64_t>(1, std::min<int64_t>(lw / wps, P->max_shards));
+    }
     // cooperative (all CTAs co-resident, which the ticket order relies on); launched through
     // cudaLaunchKernelEx so that stream capture can record it
     cudaLaunchConfig_t lc;
@@ -1461,6 +1651,14 @@ mpk_status mpk_apply_internal(mpk_plan_s *P, const mpk_coeffs *co, mpk_dtype dty
             V.x = P->ws_y.p;
             V.ybase = P->ws_y.p;
             V.bstride = blk;
+            if (n_rhs == 1 && perm) {
+                // one vector in the original order: the kernels store every power there too,
+                // and y_0 is the caller's x
+                V.orig = Yd;
+                V.orig_ld = ldy;
+                V.operm = perm;
+                MPK_CUDA(cudaMemcpyAsync(Yd, Xd, (size_t)n * es, cudaMemcpyDeviceToDevice, s));
+            }
         }
     }
 
@@ -1526,7 +1724,7 @@ mpk_status mpk_apply_internal(mpk_plan_s *P, const mpk_coeffs *co, mpk_dtype dty
     }
     if (!computed) MPK_TRY(run(blocked));
 
-    if (!direct) {
+    if (!direct && !V.orig) {
         // un-stage every output block into the user's layout / order (one launch)
         const void *src = final_only ? V.final_out : P->ws_y.p;
         const dim3 grid2(std::max(1u, g / (unsigned)nout_blocks), (unsigned)nout_blocks);
@@ -1594,6 +1792,7 @@ extern "C" mpk_status mpk_plan_sync(mpk_plan_t P, cudaStream_t s) {
         MPK_CUDA(cudaMemcpy(&P->ctrl.as<MpkCtrl>()->error, zero, 8, cudaMemcpyHostToDevice));
         if (P->wave_cnt.p) MPK_CUDA(cudaMemset(P->wave_cnt.p, 0, P->wave_cnt.bytes));
         if (P->wave_kep.p) MPK_CUDA(cudaMemset(P->wave_kep.p, 0, P->wave_kep.bytes));
+        if (P->wave_cur.p) MPK_CUDA(cudaMemset(P->wave_cur.p, 0, P->wave_cur.bytes));
         return MPK_ERR_TIMEOUT;
     }
     return MPK_OK;

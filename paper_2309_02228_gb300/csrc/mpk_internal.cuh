@@ -155,6 +155,12 @@ struct mpk_plan_s {
     std::vector<int32_t> h_dep_hi_blk;// dep_hi rounded up to the end of its block
     DevBuf cblk_size, wave_cnt;       // chunks per block; counters [(k) * n_cblk + b]
     DevBuf wave_kep;                  // uint32 per local power: launches that ran it
+    // ready-first hand-out (opts.kernel = 3): per local power the next chunk not yet handed
+    // out (reset by each launch's last CTA), and per chunk its counter block and the last
+    // block its task depends on
+    int ready_first = 0;
+    int32_t shard_warps = 4, max_shards = 1;   // warps per shard; cursor rows allocated
+    DevBuf wave_cur, chunk_blk_d, wait_blk_d;
     int64_t wave_slack = 0;
     // automatic blocked / unblocked choice per (precision, p, n_rhs) (opts.blocked = -1)
     std::map<int, bool> auto_blocked;

@@ -1175,6 +1175,12 @@ static mpk_status plan_create_impl(const mpk_csr *A, int32_t p_max, const mpk_pl
         MPK_CUDA(cudaMemsetAsync(P->wave_cnt.p, 0, P->wave_cnt.bytes, s));
         MPK_TRY(P->wave_kep.alloc((MPK_MAX_P + 1) * 4));
         MPK_CUDA(cudaMemsetAsync(P->wave_kep.p, 0, P->wave_kep.bytes, s));
+        // ready-first cursors: (local power, shard), at most one shard per resident warp
+        P->max_shards = P->n_sm * 64;
+        MPK_TRY(P->wave_cur.alloc((size_t)(MPK_MAX_P + 1) * P->max_shards * 4));
+        MPK_CUDA(cudaMemsetAsync(P->wave_cur.p, 0, P->wave_cur.bytes, s));
+        MPK_TRY(upload(P->chunk_blk_d, P->h_chunk_blk, s));
+        MPK_TRY(upload(P->wait_blk_d, P->h_wait_blk, s));
     }
     MPK_TRY(P->prefix.alloc((MPK_MAX_P + 2) * sizeof(unsigned long long)));
     MPK_CUDA(cudaMemsetAsync(P->prefix.p, 0, P->prefix.bytes, s));
@@ -1185,6 +1191,8 @@ static mpk_status plan_create_impl(const mpk_csr *A, int32_t p_max, const mpk_pl
     // lag-greedy slack: about the tasks in flight (two slots per resident CTA)
     P->sched_slack = o.slack_tasks > 0 ? o.slack_tasks : 2ll * P->n_sm * P->ctas_per_sm;
     P->wave = o.kernel == 1 ? 0 : 1;
+    P->ready_first = o.kernel == 3 ? 1 : 0;
+    P->shard_warps = o.shard_warps > 0 ? o.shard_warps : 4;
     P->short_rows = (P->n_slices > 0 && P->sell_nnz <= 12ll * 32 * P->n_slices) ? 1 : 0;
     P->wave_dynamic = o.kernel == 2 ? 0 : 1;
     // warp tasks: four tasks per resident warp (32 per SM) - measured best on the 27-point

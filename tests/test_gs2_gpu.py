@@ -4,8 +4,9 @@ subsection, Alg. GS2(a) and (b)).
 * mpk_apply(..., MPK_GS2 | MPK_GS2_GAMMA(gamma)) against the oracle's MPK of the
   GS2-preconditioned operator (oracle.gs2.gs2_mpk, which runs Alg. GS2 on A's own L, D, U), per
   entry within 64 * k * (gamma + 1) * u of the same recurrence run on absolute values
-  (|A| |P^-1|, |P^-1| the truncated Neumann series of |D^-1 L|); blocked (warp tasks, dynamic
-  and static tickets, segments that end inside a power) bit-identical to unblocked;
+  (|A| |P^-1|, |P^-1| the truncated Neumann series of |D^-1 L|); blocked (warp tasks with
+  dynamic, static and ready-first hand-out, segments that end inside a power) bit-identical to
+  unblocked;
   original-order and level-order I/O, final-only with polynomial sums, FP32 and FP64, zero and
   missing diagonal entries;
 * flag and plan errors are reported, not run;
@@ -106,7 +107,7 @@ def test_gs2_mpk_fp64_vs_oracle(m, name, gamma):
     den = _abs_den(A, cf, x, gamma)
     fl = _gs2_flags(m, gamma)
     rp, ci, vv = to_dev(A)
-    for budget, kern, pblk in ((20_000, 0, 0), (40_000, 2, 3), (1 << 30, 1, 0)):
+    for budget, kern, pblk in ((20_000, 0, 0), (40_000, 2, 3), (1 << 30, 1, 0), (20_000, 3, 3)):
         plan = m.mpk_plan_create(rp, ci, vv, p, m.mpk_plan_opts_default(
             l2_budget_bytes=budget, kernel=kern, blocked=1, jacobi=1, p_blk=pblk))
         got = _run(m, plan, A.n, cf, x, fl, torch.float64)

@@ -156,11 +156,13 @@ def test_mpk_fp64_vs_oracle(m, basis, name):
     den = abs_powers(A, cf, x)
     rp, ci, vv = to_dev(A)
     # kernel 0 = warp tasks with a ticket dispenser, 1 = CTA tasks, 2 = warp tasks in static
-    # round robin; slack 7 makes most warp tasks wait for their dependencies
+    # round robin, 3 = ready-first warp tasks; slack 7 makes most warp tasks wait for their
+    # dependencies
     for budget, cs, stage, sched, kern, slack in ((30_000, 1, -1, 1, 0, 0), (300_000, 2, 0, 1, 1, 0),
                                                   (1 << 30, 8, -1, 0, 0, 0), (100_000, 4, -1, 0, 2, 0),
                                                   (60_000, 1, -1, 1, 0, 7), (60_000, 2, -1, 1, 2, 7),
-                                                  (30_000, 1, -1, 1, 1, 0)):
+                                                  (30_000, 1, -1, 1, 1, 0), (30_000, 1, -1, 1, 3, 0),
+                                                  (1 << 30, 8, -1, 1, 3, 0)):
         plan = m.mpk_plan_create(rp, ci, vv, p, m.mpk_plan_opts_default(
             l2_budget_bytes=budget, chunk_slices=cs, stage=stage, schedule=sched, kernel=kern,
             slack_tasks=slack, blocked=1))
@@ -238,7 +240,7 @@ def test_block_mpk_n_rhs(m, n_rhs, interleaved):
             assert max_rel_err(got[k, :, q], ref[k], den[k]) <= 64 * k * U32
 
 
-@pytest.mark.parametrize("kern", [0, 1, 2])
+@pytest.mark.parametrize("kern", [0, 1, 2, 3])
 def test_final_only_gamma_and_segments(m, kern):
     import torch
     A = MATS["diff7_10"]
@@ -284,7 +286,7 @@ def test_host_io(m):
     assert np.array_equal(Yh.numpy().reshape(p + 1, -1), dev)
 
 
-@pytest.mark.parametrize("kern", [0, 1, 2])
+@pytest.mark.parametrize("kern", [0, 1, 2, 3])
 def test_timeout_is_reported_and_plan_recovers(m, kern):
     """A completion that nothing publishes: the waits on it run out (short bound), the call
     reports MPK_ERR_TIMEOUT, and the plan works again afterwards."""
@@ -343,7 +345,8 @@ def test_automatic_blocked_choice(m):
         torch.cuda.empty_cache()
 
 
-def test_graph_capture_replays_the_blocked_kernel(m):
+@pytest.mark.parametrize("kern", [0, 3])
+def test_graph_capture_replays_the_blocked_kernel(m, kern):
     """A blocked mpk_apply captured in a CUDA graph (after one ordinary call, which builds the
     schedule) replays correctly: the per-power launch counts the dependency waits compare
     against live in device memory, so each replay is a fresh launch.  Each replay's result
@@ -354,7 +357,7 @@ def test_graph_capture_replays_the_blocked_kernel(m):
     cf = BASES["newton"](p)
     rp, ci, vv = to_dev(A)
     plan = m.mpk_plan_create(rp, ci, vv, p, m.mpk_plan_opts_default(l2_budget_bytes=40_000, blocked=1,
-                                                                     slack_tasks=5))
+                                                                     slack_tasks=5, kernel=kern))
     X = torch.from_numpy(mi.uniform_vectors(A.n, 2)[0]).cuda()
     Y = torch.empty((p + 1) * A.n, dtype=torch.float64, device="cuda")
     m.mpk_apply(plan, cf, X, Y)
