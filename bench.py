@@ -55,11 +55,12 @@ def measured_peaks():
 # 2.07 GHz (the part's FP64 rate is 1.25 TFLOP/s nominal).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
-# DRAM bytes (read + write) of one blocked FP64 p = 4 launch of the headline matrix, from an ncu
-# capture (dram__bytes_read.sum + dram__bytes_write.sum) of the same kernel on the 27-point
-# 128^3 matrix (3.066 GB), scaled by stored SELL entries (109,664,800 / 56,041,696).  Valid
-# for the kernel as captured; set to None when the kernel changes until it is captured again.
-TRAFFIC_F64_P4_BYTES = 6.00e9
+# DRAM bytes (read + write) of one blocked FP64 p = 4 launch of the headline call (original
+# order in and out), from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# same kernel and call on the 27-point 128^3 matrix (3.026 + 0.253 GB), scaled by stored SELL
+# entries (109,664,800 / 56,041,696).  Valid for the kernel as captured; set to None when the
+# kernel changes until it is captured again.
+TRAFFIC_F64_P4_BYTES = 6.417e9
 
 
 class ClockSampler:
