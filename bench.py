@@ -126,6 +126,24 @@ def gen_workload():
     return A, x, theta
 
 
+def max_over_ranks(ms, world, device):
+    """The slowest rank's time per step (every rank runs its own replica; no data-path
+    exchange exists on one GPU's path): an all-reduce MAX over the process group, or ms
+    itself on one rank."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gflops(flop_per_rank, world, ms_step):
+    """Whole-job throughput: the GFLOP all ranks did in one step over the slowest rank's time."""
+    return world * flop_per_rank / (ms_step * 1e-3) / 1e9
+
+
 def cpu_baseline(A, x, theta, budget_s=10.0):
     """The oracle as it stands (plain FP64 CSR loops, static OpenMP rows) on the host cores:
     full 27-point matrix, p = 4 Newton, repeated until about budget_s seconds."""
@@ -383,7 +401,8 @@ def block_mpk_leg(m, torch, dev, hbm_peak, reps=20):
     """Block MPK as an AMG polynomial smoother: 27-point 128^3 matrix (seed 5) in FP32,
     Chebyshev basis p = 6 on [0.1, 52], n_rhs = 8, 16, 32 right-hand sides interleaved in level
     order (X ~ U[-1,1), seed 6).  Each variant is captured once in a CUDA graph and replayed;
-    modes: all p+1 powers out (basis) and the final polynomial sum_k y_k only (smoother).
+    modes: all p+1 powers out (basis) and the final polynomial sum_k y_k only (smoother); plans:
+    blocked, unblocked, the automatic choice, and the autotuner's options for the call shape.
     GFLOP/s = 2 nnz p n_rhs / t; effective GB/s = the algorithmic minimum bytes / t."""
     A = mi.stencil27(128, seed=5)
     n, nnz, p = A.n, A.nnz, 6
@@ -409,7 +428,13 @@ def block_mpk_leg(m, torch, dev, hbm_peak, reps=20):
             fl = m.MPK_PERMUTED_IO | m.MPK_RHS_INTERLEAVED | (m.MPK_FINAL_ONLY if final else 0)
             cc = cog if final else co
             bmin = M + 4 * n * n_rhs * (2 if final else p + 2)
-            for mode, plan in plans.items():
+            # the autotuner's choice for this call shape (plan options timed on this matrix)
+            best, tinfo = m.mpk_autotune(rp, ci, vv, cc, n_rhs=n_rhs, flags=fl,
+                                         base=m.mpk_plan_opts_default(assume_symmetric=1, p_blk=p), reps=3)
+            tuned = m.mpk_plan_create(rp, ci, vv, p, best)
+            modes = dict(plans)
+            modes["tuned"] = tuned
+            for mode, plan in modes.items():
                 call = lambda: m.mpk_apply(plan, cc, X, Y, n_rhs=n_rhs, flags=fl)
                 call()                                  # schedule, automatic choice
                 torch.cuda.synchronize()
@@ -423,6 +448,10 @@ def block_mpk_leg(m, torch, dev, hbm_peak, reps=20):
                 res["%s_%s" % ("final" if final else "basis", mode)] = {
                     "ms": ms, "gflops": 2.0 * nnz * p * n_rhs / ms / 1e6,
                     "eff_gbs": bmin / ms / 1e6, "eff_frac": bmin / ms / 1e6 / hbm_peak}
+            res["%s_tuned" % ("final" if final else "basis")].update(
+                {"candidate": tinfo["best_index"], "blocked": int(best.blocked), "kernel": int(best.kernel),
+                 "chunk_slices": int(best.chunk_slices), "l2_budget_bytes": int(best.l2_budget_bytes)})
+            del tuned
         out["n_rhs%d" % n_rhs] = res
         del X, Y
     del plans
@@ -544,15 +573,11 @@ def main():
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    ms_step = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        tt = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_step = float(tt.item())
+    ms_step = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, dev)
     status = m.mpk_plan_sync(plan)
     assert status == m.MPK_OK, m.status_name(status)
     flop = 2.0 * nnz * P_MAIN
-    value = world * flop / (ms_step * 1e-3) / 1e9
+    value = whole_job_gflops(flop, world, ms_step)
 
     # ---- the p x SpMV baseline through the same call, and the p sweep
     reps = max(5, min(args.steps, 50))

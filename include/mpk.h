@@ -299,6 +299,33 @@ mpk_status mpk_coeffs_newton(const double *theta, int32_t p, double *a, double *
 mpk_status mpk_leja_order(const double *values, int32_t n, int32_t count, double *out);
 
 /* ------------------------------------------------------------------------------------------
+ * Autotuner.  No counterpart in the paper, which sets its blocking depth p_opt and cache size C
+ * by hand per machine (Sec. 3, Sec. 4).  On this part the best plan options depend on the
+ * precision and the number of right-hand sides, so they are measured for one call shape.
+ * ---------------------------------------------------------------------------------------- */
+typedef struct {
+    int32_t n_trials;       /* candidates timed */
+    int32_t best_index;     /* position of the best in the candidate list (0 = the base) */
+    double best_ms;         /* median time per mpk_apply call with the best options */
+    double base_ms;         /* the same with the base options */
+} mpk_tune_info;
+
+/* Times mpk_apply(co, dtype, n_rhs, flags) on plans of A built with a fixed list of nine
+ * candidate options derived from `base` (NULL: mpk_plan_opts_default): the base itself; p back-to-back
+ * SpMVs (blocked = 0); the blocked warp-task kernel with chunks of 2, 4, 8 and 16 slices; the
+ * static round-robin kernel; level groups sized for a quarter of L2 and for all of it.  Each
+ * candidate runs two untimed calls and `reps` timed ones (CUDA events on `stream`, median).
+ * A: DEVICE CSR as for mpk_plan_create; p = co->p <= MPK_MAX_P; flags: any mpk_apply flags
+ * but MPK_HOST_IO, MPK_Y0_IS_X, MPK_UNBLOCKED and the debug flag (MPK_ERR_ARG).  The tuner
+ * allocates one plan at a time and device input (all ones) and output buffers of the call's
+ * shape, all freed before it returns; synchronous on `stream`.  *best receives the fastest
+ * candidate's options (pass them to mpk_plan_create); info (host) may be NULL.  Every
+ * candidate computes bit-identical results, so the choice affects only speed. */
+mpk_status mpk_autotune(const mpk_csr *A, int32_t p, const mpk_coeffs *co, mpk_dtype dtype,
+                        int32_t n_rhs, uint32_t flags, const mpk_plan_opts *base, int32_t reps,
+                        mpk_plan_opts *best, mpk_tune_info *info, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------------------------
  * s-step GMRES (Sec. 4, Alg. 3(a)+(c)) with FP64 iterative refinement.
  * ---------------------------------------------------------------------------------------- */
 typedef struct {

@@ -109,6 +109,11 @@ class mpk_gmres_info(ctypes.Structure):
                 ("poly_interval", ctypes.c_double * 2)]
 
 
+class mpk_tune_info(ctypes.Structure):
+    _fields_ = [("n_trials", ctypes.c_int32), ("best_index", ctypes.c_int32),
+                ("best_ms", ctypes.c_double), ("base_ms", ctypes.c_double)]
+
+
 class mpk_cg_opts(ctypes.Structure):
     _fields_ = [("s", ctypes.c_int32), ("tol", ctypes.c_double), ("inner_tol", ctypes.c_double),
                 ("max_outer", ctypes.c_int32), ("max_iters", ctypes.c_int32), ("basis", ctypes.c_int),
@@ -162,6 +167,9 @@ _SIGS = [
     ("mpk_leja_order", ctypes.c_int, [_P, _I32, _I32, _P]),
     ("mpk_gmres_opts_default", ctypes.c_int, [ctypes.POINTER(mpk_gmres_opts)]),
     ("sstep_gmres_solve", ctypes.c_int, [_P, _P, _P, ctypes.POINTER(mpk_gmres_opts), ctypes.POINTER(mpk_gmres_info), _P]),
+    ("mpk_autotune", ctypes.c_int, [ctypes.POINTER(mpk_csr), _I32, ctypes.POINTER(mpk_coeffs), ctypes.c_int,
+                                    _I32, _U32, ctypes.POINTER(mpk_plan_opts), _I32,
+                                    ctypes.POINTER(mpk_plan_opts), ctypes.POINTER(mpk_tune_info), _P]),
     ("mpk_cg_opts_default", ctypes.c_int, [ctypes.POINTER(mpk_cg_opts)]),
     ("sstep_cg_solve", ctypes.c_int, [_P, _P, _P, ctypes.POINTER(mpk_cg_opts), ctypes.POINTER(mpk_cg_info), _P]),
     ("mpk_server_opts_default", ctypes.c_int, [ctypes.POINTER(mpk_server_opts)]),
@@ -431,6 +439,29 @@ def sstep_gmres_solve(plan, b, x, opts=None, shifts=None, stream=None, check=Tru
         _check(st, "sstep_gmres_solve")
     del keep
     return d
+
+
+# ---------------------------------------------------------------------------------------------
+# Autotuner
+# ---------------------------------------------------------------------------------------------
+def mpk_autotune(row_ptr, col, val, coeffs, n_rhs=1, flags=0, dtype=None, base=None, reps=5,
+                 stream=None, check=True):
+    """Time the candidate plan options for mpk_apply(coeffs, n_rhs, flags) on this matrix (see
+    include/mpk.h); returns (best mpk_plan_opts, info dict)."""
+    if not isinstance(coeffs, Coeffs):
+        coeffs = Coeffs.from_triples(coeffs)
+    A = _csr_struct(row_ptr, col, val)
+    d = _dtype_code(val.dtype if dtype is None else dtype)
+    best = mpk_plan_opts()
+    info = mpk_tune_info()
+    st = lib().mpk_autotune(ctypes.byref(A), coeffs.p, ctypes.byref(coeffs.struct), d, int(n_rhs),
+                            int(flags), ctypes.byref(base) if base is not None else None, int(reps),
+                            ctypes.byref(best), ctypes.byref(info), _stream_ptr(stream))
+    out = {f: getattr(info, f) for f, _ in info._fields_}
+    out["status_code"] = int(st)
+    if check:
+        _check(st, "mpk_autotune")
+    return best, out
 
 
 # ---------------------------------------------------------------------------------------------

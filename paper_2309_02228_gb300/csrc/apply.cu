@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "mpk_internal.cuh"
@@ -105,15 +106,51 @@ template <typename T, int NR> struct RowBatch {
     static constexpr int B = ((sizeof(T) == 4 ? 32 : 16) / NR) > 0 ? ((sizeof(T) == 4 ? 32 : 16) / NR) : 1;
 };
 
+// NB consecutive entries j .. j+NB-1 of a row, all inside the slice length: column and value
+// loads first, then the gathers, then the FMAs (FP64: even entries into acc, odd into acc2;
+// j is even whenever a batch starts, so the parity is the entry's).  Padding entries
+// (column -1) gather the row's own element and are dropped by a select.
+template <typename T, int NR, int NB, bool TWO>
+__device__ __forceinline__ void row_batch_g(const int32_t *colp, const T *valp, int32_t j, int32_t row,
+                                            const T *y1, int n_rhs, int q0, T (&acc)[NR], T (&acc2)[NR]) {
+    int32_t cc[NB];
+    T vv[NB];
+    T xx[NB][NR];
+#pragma unroll
+    for (int u = 0; u < NB; u++) {
+        cc[u] = __ldg(colp + 32 * (j + u));
+        vv[u] = __ldg(valp + 32 * (j + u));
+    }
+#pragma unroll
+    for (int u = 0; u < NB; u++)
+        VecLoad<T, NR>::ld(y1 + (int64_t)(cc[u] >= 0 ? cc[u] : row) * n_rhs + q0, xx[u]);
+#pragma unroll
+    for (int u = 0; u < NB; u++)
+#pragma unroll
+        for (int q = 0; q < NR; q++) {
+            if (TWO && (u & 1)) {
+                const T f = fma(vv[u], xx[u][q], acc2[q]);
+                acc2[q] = cc[u] >= 0 ? f : acc2[q];
+            } else {
+                const T f = fma(vv[u], xx[u][q], acc[q]);
+                acc[q] = cc[u] >= 0 ? f : acc[q];
+            }
+        }
+}
+
 // Row sum of one row over its stored entries (stride 32 between consecutive entries of the
 // row, SELL-32), ascending column order, one FMA per entry.
 //
 // SM (a staged task): columns and values sit in shared memory, so only the vector gathers are
 // kept in registers - all gathers of a batch are issued before the first FMA, and the column
 // and value of each entry are read again from shared memory for the FMA.
-// Global: column and value loads of a batch first, then the gathers, then the FMAs.
-// Padding entries (column -1) gather the row's own element and are dropped by a select; a
-// partial last batch is predicated, never split into dependent single steps.
+// Global: full batches of BG entries (row_batch_g), then the remainder in batches of 4, 2 and
+// 1.  The slice length is the same for every lane, so those branches are uniform and no
+// multiply-add is issued past the end of the slice (on the FP64 pipe, the bound of the FP64
+// kernels, a predicated 8-wide tail cost 32 FMAs for a 27-entry row).  FP32 with one
+// right-hand side keeps one predicated whole-row batch instead (memory-bound: all loads in
+// flight).  Every variant visits entries and partial sums in the same order, so the values do
+// not depend on the variant.
 template <typename T, int NR, bool SM, bool SV, int BGMAX = 8>
 __device__ __forceinline__ void row_sum(const int32_t *colp, const T *valp, int32_t L, int32_t row,
                                         const T *y1, int n_rhs, int q0, T (&acc)[NR]) {
@@ -129,9 +166,57 @@ __device__ __forceinline__ void row_sum(const int32_t *colp, const T *valp, int3
         acc[q] = (T)0;
         acc2[q] = (T)0;
     }
-    for (int32_t j = 0; j < L; j += BT) {
-        T xx[BT][NR];
-        if (SM) {
+    // FP32 with one right-hand side is bound by memory: there a whole row's loads in flight at
+    // once (one predicated batch of BT entries, unrolled) beats skipping the tail's FMAs
+    constexpr bool WHOLE_ROW = sizeof(T) == 4 && NR == 1;
+    if constexpr (!SM && WHOLE_ROW) {
+        constexpr int BG = BT > BGMAX ? BGMAX : BT;
+        for (int32_t j = 0; j < L; j += BT) {
+#pragma unroll
+            for (int j2 = 0; j2 < BT; j2 += BG) {
+                int32_t cc[BG];
+                T vv[BG];
+                T xx[BG][NR];
+#pragma unroll
+                for (int u = 0; u < BG; u++) {
+                    const bool in = j + j2 + u < L;
+                    cc[u] = in ? __ldg(colp + 32 * (j + j2 + u)) : -1;
+                    vv[u] = in ? __ldg(valp + 32 * (j + j2 + u)) : (T)0;
+                }
+#pragma unroll
+                for (int u = 0; u < BG; u++)
+                    VecLoad<T, NR>::ld(y1 + (int64_t)(cc[u] >= 0 ? cc[u] : row) * n_rhs + q0, xx[u]);
+#pragma unroll
+                for (int u = 0; u < BG; u++)
+#pragma unroll
+                    for (int q = 0; q < NR; q++) {
+                        const T f = fma(vv[u], xx[u][q], acc[q]);
+                        acc[q] = cc[u] >= 0 ? f : acc[q];
+                    }
+            }
+        }
+    } else if constexpr (!SM) {
+        constexpr int BG = BT > BGMAX ? BGMAX : BT;   // register budget of the global path
+        int32_t j = 0;
+        for (; j + BG <= L; j += BG) row_batch_g<T, NR, BG, TWO>(colp, valp, j, row, y1, n_rhs, q0, acc, acc2);
+        if constexpr (BG > 4) {
+            if (L - j >= 4) {
+                row_batch_g<T, NR, 4, TWO>(colp, valp, j, row, y1, n_rhs, q0, acc, acc2);
+                j += 4;
+            }
+        }
+        if constexpr (BG > 2) {
+            if (L - j >= 2) {
+                row_batch_g<T, NR, 2, TWO>(colp, valp, j, row, y1, n_rhs, q0, acc, acc2);
+                j += 2;
+            }
+        }
+        if constexpr (BG > 1) {
+            if (L - j >= 1) row_batch_g<T, NR, 1, TWO>(colp, valp, j, row, y1, n_rhs, q0, acc, acc2);
+        }
+    } else {
+        for (int32_t j = 0; j < L; j += BT) {
+            T xx[BT][NR];
 #pragma unroll
             for (int u = 0; u < BT; u++) {
                 if (j + u < L) {
@@ -158,34 +243,6 @@ __device__ __forceinline__ void row_sum(const int32_t *colp, const T *valp, int3
                     }
                 }
             }
-        } else {
-            constexpr int BG = BT > BGMAX ? BGMAX : BT;   // register budget of the global path
-#pragma unroll
-            for (int j2 = 0; j2 < BT; j2 += BG) {
-                int32_t cc[BG];
-                T vv[BG];
-#pragma unroll
-                for (int u = 0; u < BG; u++) {
-                    const bool in = j + j2 + u < L;
-                    cc[u] = in ? __ldg(colp + 32 * (j + j2 + u)) : -1;
-                    vv[u] = in ? __ldg(valp + 32 * (j + j2 + u)) : (T)0;
-                }
-#pragma unroll
-                for (int u = 0; u < BG; u++)
-                    VecLoad<T, NR>::ld(y1 + (int64_t)(cc[u] >= 0 ? cc[u] : row) * n_rhs + q0, xx[j2 + u]);
-#pragma unroll
-                for (int u = 0; u < BG; u++)
-#pragma unroll
-                    for (int q = 0; q < NR; q++) {
-                        if (TWO && (u & 1)) {
-                            const T f = fma(vv[u], xx[j2 + u][q], acc2[q]);
-                            acc2[q] = cc[u] >= 0 ? f : acc2[q];
-                        } else {
-                            const T f = fma(vv[u], xx[j2 + u][q], acc[q]);
-                            acc[q] = cc[u] >= 0 ? f : acc[q];
-                        }
-                    }
-            }
         }
     }
     if (TWO) {
@@ -206,8 +263,15 @@ __device__ __forceinline__ void row_finish(const T (&acc)[NR], int32_t row, int 
     const T a = (T)cf.a[k], b = (T)cf.b[k], c = (T)cf.c[k];
     const int64_t o = (int64_t)row * n_rhs + q0;
     T res[NR];
+    // a = 1 (monomial and Newton bases): the product is exact, so skipping it changes nothing
+    // but saves one FP64 pipe operation per row, where that pipe is the bound
+    if (a == (T)1) {
 #pragma unroll
-    for (int q = 0; q < NR; q++) res[q] = a * acc[q];
+        for (int q = 0; q < NR; q++) res[q] = acc[q];
+    } else {
+#pragma unroll
+        for (int q = 0; q < NR; q++) res[q] = a * acc[q];
+    }
     if (b != (T)0) {
         T yv[NR];
         VecLoad<T, NR>::ld(y1 + o, yv);
@@ -423,22 +487,24 @@ __device__ __forceinline__ void slice_gs2_step(const SellView &A, const uint32_t
     constexpr bool TWO = sizeof(T) == 8;
     constexpr int BG = 8;
     T a0 = 0, a1 = 0;
-    for (int32_t e = 0; e < L; e += BG) {
-        int32_t cc[BG];
-        T vv[BG];
+    // NB entries e .. e+NB-1 (all inside the slice length): loads, gathers, then FMAs; an inner
+    // stage drops entries outside L_B (mask bit clear) like padding
+    auto batch = [&](auto nb_tag, int32_t e) {
+        constexpr int NB = decltype(nb_tag)::value;
+        int32_t cc[NB];
+        T vv[NB];
 #pragma unroll
-        for (int u = 0; u < BG; u++) {
-            const bool in_ = e + u < L;
-            int32_t c = in_ ? __ldg(A.col + o + 32 * (e + u)) : -1;
+        for (int u = 0; u < NB; u++) {
+            int32_t c = __ldg(A.col + o + 32 * (e + u));
             if (!full && c >= 0 && !((__ldg(lmask + sp + e + u) >> lane) & 1u)) c = -1;
             cc[u] = c;
-            vv[u] = in_ ? __ldg(gval + o + 32 * (e + u)) : (T)0;
+            vv[u] = __ldg(gval + o + 32 * (e + u));
         }
-        T xx[BG];
+        T xx[NB];
 #pragma unroll
-        for (int u = 0; u < BG; u++) xx[u] = in[cc[u] >= 0 ? cc[u] : row];
+        for (int u = 0; u < NB; u++) xx[u] = in[cc[u] >= 0 ? cc[u] : row];
 #pragma unroll
-        for (int u = 0; u < BG; u++) {
+        for (int u = 0; u < NB; u++) {
             if (TWO && (u & 1)) {
                 const T f = fma(vv[u], xx[u], a1);
                 a1 = cc[u] >= 0 ? f : a1;
@@ -447,7 +513,19 @@ __device__ __forceinline__ void slice_gs2_step(const SellView &A, const uint32_t
                 a0 = cc[u] >= 0 ? f : a0;
             }
         }
+    };
+    // full batches, then the remainder as 4, 2, 1 (batch starts stay even: entry parity kept)
+    int32_t e = 0;
+    for (; e + BG <= L; e += BG) batch(std::integral_constant<int, BG>{}, e);
+    if (L - e >= 4) {
+        batch(std::integral_constant<int, 4>{}, e);
+        e += 4;
     }
+    if (L - e >= 2) {
+        batch(std::integral_constant<int, 2>{}, e);
+        e += 2;
+    }
+    if (L - e >= 1) batch(std::integral_constant<int, 1>{}, e);
     if (!valid) return;
     if (TWO) a0 += a1;
     if (full) {
