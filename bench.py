@@ -57,10 +57,10 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 # DRAM bytes (read + write) of one blocked FP64 p = 4 launch of the headline call (original
 # order in and out), from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# same kernel and call on the 27-point 128^3 matrix (3.026 + 0.253 GB), scaled by stored SELL
+# same kernel and call on the 27-point 128^3 matrix (2.961 + 0.159 GB), scaled by stored SELL
 # entries (109,664,800 / 56,041,696).  Valid for the kernel as captured; set to None when the
 # kernel changes until it is captured again.
-TRAFFIC_F64_P4_BYTES = 6.417e9
+TRAFFIC_F64_P4_BYTES = 6.105e9
 
 
 class ClockSampler:
@@ -165,6 +165,14 @@ def cpu_baseline(A, x, theta, budget_s=10.0):
             "seconds": t_total}
 
 
+def headline_config(n, nnz):
+    """The headline workload, shared by both arms' JSON lines."""
+    return {"workload": "27-point 160^3 CSR FP64 (diag 26, off-diag -1-U[0,0.1) seed 2), "
+                        "Newton MPK p=4 with Leja shifts on [0,52], original-order I/O",
+            "n": n, "nnz": nnz, "p": P_MAIN, "parallelism": "replica per GPU",
+            "l2_policy": "inputs larger than L2 (1.33 GB matrix)"}
+
+
 def run_reference(args):
     """--impl reference: the CPU oracle timed on the host cores for the same metric."""
     rank = int(os.environ.get("RANK", "0"))
@@ -188,8 +196,7 @@ def run_reference(args):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
-           "config": {"workload": "27-point 160^3 CSR FP64, Newton MPK p=4 (Leja shifts on [0,52])",
-                      "n": A.n, "nnz": A.nnz, "p": P_MAIN},
+           "config": dict(headline_config(A.n, A.nnz), plan="oracle: plain CSR rows, OpenMP static"),
            "cpu_baseline": {"value": gf, "unit": "GFLOP/s", "kind": "oracle",
                             "cores": oracle.omp_threads(),
                             "sample": "full matrix, %d timed calls of p=4" % args.steps},
@@ -702,12 +709,9 @@ def main():
         "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "27-point 160^3 CSR FP64 (diag 26, off-diag -1-U[0,0.1) seed 2), "
-                               "Newton MPK p=4 with Leja shifts on [0,52], original-order I/O",
-                   "n": n, "nnz": nnz, "p": P_MAIN, "parallelism": "replica per GPU",
-                   "l2_policy": "inputs larger than L2 (1.33 GB matrix)",
-                   "plan": {k: pst[k] for k in ("n_levels", "n_groups", "n_chunks", "p_blk",
-                                                "l2_budget_bytes", "sell_nnz", "root")}},
+        "config": dict(headline_config(n, nnz),
+                       plan={k: pst[k] for k in ("n_levels", "n_groups", "n_chunks", "p_blk",
+                                                 "l2_budget_bytes", "sell_nnz", "root")}),
         "pxspmv_gflops": sweep["p%d" % P_MAIN]["pxspmv_gflops"],
         "speedup_vs_pxspmv": sweep["p%d" % P_MAIN]["speedup"],
         "sweep": sweep, "kernel_only": kern, "fp32": fp32, "plan_ms": plan_ms,

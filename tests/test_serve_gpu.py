@@ -1,7 +1,8 @@
 """GPU tests of the solve server (continuous batching under an HBM budget).
 
 Each request's solution is bitwise identical whether it runs alone or mixed with others
-(every reduction in the solve has a fixed order), every solution reaches the 1e-8 true
+(every reduction in the solve has a fixed order), also with GS2-preconditioned solves, every
+solution reaches the 1e-8 true
 residual, a request larger than the budget is refused, and a budget that fits one request at
 a time serialises admission."""
 import time
@@ -46,10 +47,17 @@ def _drain(srv, expect, timeout=120.0):
     return out
 
 
-def test_alone_vs_mixed_bitwise(m):
+@pytest.mark.parametrize("precond", ["none", "gs2"])
+def test_alone_vs_mixed_bitwise(m, precond):
     reqs = _requests(10)
-    opts = m.mpk_server_opts_default(max_active=1)
-    srv = m.Server(opts)
+
+    def opts(**kw):
+        o = m.mpk_server_opts_default(**kw)
+        if precond == "gs2":   # two-stage Gauss-Seidel sub-powers (Sec. 5.1) in every solve
+            o.gmres.gs2 = 1
+            o.gmres.gs2_gamma = 1
+        return o
+    srv = m.Server(opts(max_active=1))
     alone = []
     for A, b in reqs:
         rid, x = srv.submit(A.row_ptr, A.col, A.val, b)
@@ -57,7 +65,7 @@ def test_alone_vs_mixed_bitwise(m):
         assert res["status"] == m.MPK_OK, res
         alone.append(res["x"].copy())
     srv.close()
-    srv = m.Server(m.mpk_server_opts_default(max_active=4))
+    srv = m.Server(opts(max_active=4))
     ids = [srv.submit(A.row_ptr, A.col, A.val, b)[0] for A, b in reqs]
     got = _drain(srv, len(ids))
     srv.close()
