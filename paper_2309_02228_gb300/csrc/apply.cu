@@ -63,6 +63,15 @@ struct SellView {
     const void *val;
 };
 
+// The strictly lower entries (caller's row order) of the Jacobi-scaled matrix, packed per row
+// into slices with the same rows as the full ones (MPK_GS2 inner stages)
+struct LowerView {
+    const long long *slice_ptr;
+    const int32_t *slice_len;
+    const int32_t *col;
+    const void *val;
+};
+
 // ------------------------------------------------------------------------------------------
 // The row function: power k of rows [slice_row[s], slice_row[s+1]) for rhs block [q0, q0+NR).
 // Thread `lane` owns row slice_row[s] + lane.  The row sum runs over the stored entries in
@@ -453,8 +462,9 @@ __device__ __forceinline__ void slice_power(const SellView &A, int64_t s, const 
 // ------------------------------------------------------------------------------------------
 // Two-stage Gauss-Seidel (GS2, Sec. 5.1, Alg. GS2) as sub-powers of the MPK.  With B = A D~^-1
 // (the Jacobi-scaled values; D~ the diagonal, zero or missing entries read as 1) and L_B its
-// strictly lower part in the caller's row order (bit `lane` of lmask[slice_ptr[s] + j]), one
-// GS2 iteration from zero is P^-1 v = D~^-1 h_gamma with
+// strictly lower part in the caller's row order (packed per row into slices of their own,
+// LowerView: the split form A = L + D + U the paper's GS2 kernel streams), one GS2 iteration
+// from zero is P^-1 v = D~^-1 h_gamma with
 //     h_0 = v,   h_j = v - L_B h_{j-1}   (j = 1..gamma),
 // Alg. GS2's g_j = g_0 - D^-1 L g_{j-1} multiplied through by D~ (h_j = D~ g_j).  Power k of
 // the preconditioned operator is then gamma + 1 steps over the matrix:
@@ -463,12 +473,13 @@ __device__ __forceinline__ void slice_power(const SellView &A, int64_t s, const 
 // at absolute step t = (k - 1)(gamma + 1) + j.  The h_j live in a ring of two vectors: step t
 // starts at a row only after step t - 1 has finished at every row it reads and at the row
 // itself, so the step that last read the slot being overwritten (t - 1) is done there.
-// Row sums run over the stored entries in ascending order (entries outside L_B are skipped
-// by a select, FP64 keeps even / odd partial sums by entry position), so the blocked and
-// unblocked schedules give identical values.
+// An inner stage streams only the packed lower entries (about half the row), the product step
+// the full row.  Row sums run over the stored entries in ascending order (FP64 keeps even /
+// odd partial sums by entry position), so the blocked and unblocked schedules give identical
+// values.
 // ------------------------------------------------------------------------------------------
 template <typename T>
-__device__ __forceinline__ void slice_gs2_step(const SellView &A, const uint32_t *lmask, int64_t s,
+__device__ __forceinline__ void slice_gs2_step(const SellView &A, const LowerView &Lw, int64_t s,
                                                int lane, const VecSet &V, int t, const Coefs &cf) {
     const int ST = V.gs2_steps;
     const int k = (t - 1) / ST + 1;
@@ -477,28 +488,28 @@ __device__ __forceinline__ void slice_gs2_step(const SellView &A, const uint32_t
     const int32_t r0 = __ldg(A.slice_row + s), r1 = __ldg(A.slice_row + s + 1);
     const int32_t row = r0 + lane;
     const bool valid = row < r1;
-    const int32_t L = valid ? __ldg(A.slice_len + s) : 0;
-    const long long sp = __ldg(A.slice_ptr + s);
+    // the product step streams the full slice, an inner stage only the packed lower entries
+    const long long sp = full ? __ldg(A.slice_ptr + s) : __ldg(Lw.slice_ptr + s);
+    const int32_t L = valid ? (full ? __ldg(A.slice_len + s) : __ldg(Lw.slice_len + s)) : 0;
     const long long o = 32ll * sp + lane;
+    const int32_t *colp = (full ? A.col : Lw.col) + o;
+    const T *valp = reinterpret_cast<const T *>(full ? A.val : Lw.val) + o;
     const T *yk1 = vec_ro<T>(V, k - 1);
     // ring slots by select, not by an indexed load (keeps the struct out of local memory)
     const T *in = j == 1 ? yk1 : reinterpret_cast<const T *>(((j - 1) & 1) ? V.h[1] : V.h[0]);
-    const T *gval = reinterpret_cast<const T *>(A.val);
     constexpr bool TWO = sizeof(T) == 8;
     constexpr int BG = 8;
     T a0 = 0, a1 = 0;
-    // NB entries e .. e+NB-1 (all inside the slice length): loads, gathers, then FMAs; an inner
-    // stage drops entries outside L_B (mask bit clear) like padding
+    // NB entries e .. e+NB-1 (all inside the slice length): loads, gathers, then FMAs;
+    // padding (column -1) gathers the row's own element and is dropped by a select
     auto batch = [&](auto nb_tag, int32_t e) {
         constexpr int NB = decltype(nb_tag)::value;
         int32_t cc[NB];
         T vv[NB];
 #pragma unroll
         for (int u = 0; u < NB; u++) {
-            int32_t c = __ldg(A.col + o + 32 * (e + u));
-            if (!full && c >= 0 && !((__ldg(lmask + sp + e + u) >> lane) & 1u)) c = -1;
-            cc[u] = c;
-            vv[u] = __ldg(gval + o + 32 * (e + u));
+            cc[u] = __ldg(colp + 32 * (e + u));
+            vv[u] = __ldg(valp + 32 * (e + u));
         }
         T xx[NB];
 #pragma unroll
@@ -538,12 +549,12 @@ __device__ __forceinline__ void slice_gs2_step(const SellView &A, const uint32_t
 
 // Unblocked GS2 step t (one launch per step), one warp per slice.
 template <typename T>
-__global__ void __launch_bounds__(256) mpk_gs2_kernel(SellView A, const uint32_t *lmask, int64_t n_slices,
+__global__ void __launch_bounds__(256) mpk_gs2_kernel(SellView A, LowerView Lw, int64_t n_slices,
                                                       VecSet V, int t, Coefs cf) {
     const int lane = threadIdx.x & 31;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t s = w0; s < n_slices; s += nw) slice_gs2_step<T>(A, lmask, s, lane, V, t, cf);
+    for (int64_t s = w0; s < n_slices; s += nw) slice_gs2_step<T>(A, Lw, s, lane, V, t, cf);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -961,7 +972,7 @@ struct WaveArgs {
     uint64_t timeout_ns;
     uint32_t debug_drop;              // 1: task (chunk 0, power 1) does not publish
     uint32_t dynamic;                 // 1: tickets from the control block's dispenser
-    const uint32_t *lmask;            // MPK_GS2: strictly lower entries (see slice_gs2_step)
+    LowerView low;                    // MPK_GS2: packed strictly lower entries
     uint32_t *cursor;                 // ready-first: per (local power k, shard s) at k * n_shards
                                       // + s, the next position j not yet handed out (chunk
                                       // s + j * n_shards)
@@ -1070,7 +1081,7 @@ __global__ void __launch_bounds__(WAVE_BLOCK, ((PAIRS || GS2) ? 4 : wave_min_blo
         const int32_t s1 = __ldg(W.chunk_slice + c + 1);
         int32_t s = __ldg(W.chunk_slice + c);
         if constexpr (GS2) {
-            for (; s < s1; s++) slice_gs2_step<T>(A, W.lmask, s, lane, V, k, cf);
+            for (; s < s1; s++) slice_gs2_step<T>(A, W.low, s, lane, V, k, cf);
         } else {
             if constexpr (NR == 1 && PAIRS) {
                 for (; s + 1 < s1; s += 2) slice_pair_power<T>(A, s, s + 1, lane, V, k, cf);
@@ -1229,7 +1240,7 @@ __global__ void __launch_bounds__(WAVE_BLOCK, ((PAIRS || GS2) ? 4 : wave_min_blo
         const int32_t s1 = __ldg(W.chunk_slice + c + 1);
         int32_t s = __ldg(W.chunk_slice + c);
         if constexpr (GS2) {
-            for (; s < s1; s++) slice_gs2_step<T>(A, W.lmask, s, lane, V, k, cf);
+            for (; s < s1; s++) slice_gs2_step<T>(A, W.low, s, lane, V, k, cf);
         } else {
             if constexpr (NR == 1 && PAIRS) {
                 for (; s + 1 < s1; s += 2) slice_pair_power<T>(A, s, s + 1, lane, V, k, cf);
@@ -1294,6 +1305,15 @@ __global__ void scatter_out_kernel(const T *in, int64_t in_stride, const int32_t
             else dst[i + q * ldy] = v;
         }
     }
+}
+
+static LowerView lower_view(const mpk_plan_s *P, mpk_dtype dt) {
+    LowerView v;
+    v.slice_ptr = P->l_slice_ptr.as<long long>();
+    v.slice_len = P->l_slice_len.as<int32_t>();
+    v.col = P->l_col.as<int32_t>();
+    v.val = dt == MPK_F64 ? P->l_val64.p : P->l_val32.p;
+    return v;
 }
 
 static unsigned grid_n(int64_t n, int block = 256) {
@@ -1383,7 +1403,7 @@ mpk_status launch_wave(mpk_plan_s *P, const SellView &A, int n_rhs, const VecSet
         if (gs2) kern = rf ? mpk_ready_kernel<T, 1, false, true> : mpk_wave_kernel<T, 1, false, true>;
     }
     if (gs2 && NR != 1) return MPK_ERR_UNIMPLEMENTED;
-    W.lmask = P->s_lmask.as<uint32_t>();
+    W.low = lower_view(P, sizeof(T) == 8 ? MPK_F64 : MPK_F32);
     W.cursor = P->wave_cur.as<uint32_t>();
     W.chunk_blk = P->chunk_blk_d.as<int32_t>();
     W.wait_blk = P->wait_blk_d.as<int32_t>();
@@ -1456,7 +1476,7 @@ mpk_status launch_gs2(mpk_plan_s *P, const SellView &A, const VecSet &V, const C
     if (!blocked || !P->wave) {
         const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(std::max<int64_t>(P->n_slices, 1), 8), 1 << 30);
         for (int t = 1; t <= total; t++)
-            mpk_gs2_kernel<T><<<grid, 256, 0, s>>>(A, P->s_lmask.as<uint32_t>(), P->n_slices, V, t, cf);
+            mpk_gs2_kernel<T><<<grid, 256, 0, s>>>(A, lower_view(P, sizeof(T) == 8 ? MPK_F64 : MPK_F32), P->n_slices, V, t, cf);
         MPK_CUDA(cudaGetLastError());
         return MPK_OK;
     }
@@ -1843,9 +1863,9 @@ mpk_status mpk_gs2_inner(mpk_plan_s *P, mpk_dtype dtype, int gamma, const void *
     const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(std::max<int64_t>(P->n_slices, 1), 8), 1 << 30);
     for (int t = 1; t <= gamma; t++) {
         if (dtype == MPK_F64)
-            mpk_gs2_kernel<double><<<grid, 256, 0, s>>>(A, P->s_lmask.as<uint32_t>(), P->n_slices, V, t, cf);
+            mpk_gs2_kernel<double><<<grid, 256, 0, s>>>(A, lower_view(P, MPK_F64), P->n_slices, V, t, cf);
         else
-            mpk_gs2_kernel<float><<<grid, 256, 0, s>>>(A, P->s_lmask.as<uint32_t>(), P->n_slices, V, t, cf);
+            mpk_gs2_kernel<float><<<grid, 256, 0, s>>>(A, lower_view(P, MPK_F32), P->n_slices, V, t, cf);
     }
     MPK_CUDA(cudaGetLastError());
     return MPK_OK;

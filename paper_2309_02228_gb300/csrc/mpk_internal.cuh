@@ -128,6 +128,10 @@ struct mpk_plan_s {
     // two-stage Gauss-Seidel sub-powers (MPK_GS2, built with opts.jacobi): bit lane of word
     // slice_ptr[s] + j marks a strictly lower entry in the caller's row order
     DevBuf s_lmask;
+    // the strictly lower entries packed per row into slices of their own (same rows as the
+    // full slices; l_slice_ptr in units of 32 entries), with the Jacobi-scaled values
+    DevBuf l_slice_ptr, l_slice_len, l_col, l_val64, l_val32;
+    int64_t l_sell_nnz = 0;
 
     // blocked tasks: chunk c = slices [chunk_slice[c], chunk_slice[c+1]) inside one group
     DevBuf chunk_slice, chunk_row, chunk_entry, dep_lo, dep_hi;

@@ -705,6 +705,66 @@ __global__ void gs2_lower_mask_kernel(const int32_t *s_col, const long long *sli
     }
 }
 
+// The strictly lower entries of every row, packed in their stored order into slices of their
+// own (the GS2 inner stages read only them, Sec. 5.1): slice s keeps the rows of the full
+// slice; its length is the largest lower count among those rows.  One warp per slice.
+__global__ void gs2_lower_len_kernel(const int32_t *slice_row, const int32_t *slice_len,
+                                     const long long *slice_ptr, int64_t n_slices,
+                                     const uint32_t *lmask, int32_t *l_len) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t sl = w0; sl < n_slices; sl += nw) {
+        const long long sp = slice_ptr[sl];
+        int32_t cnt = 0;
+        for (int32_t j = 0; j < slice_len[sl]; j++) cnt += (lmask[sp + j] >> lane) & 1u;
+        for (int o = 16; o > 0; o >>= 1) cnt = max(cnt, __shfl_xor_sync(0xffffffffu, cnt, o));
+        if (lane == 0) l_len[sl] = cnt;
+    }
+}
+
+// Fill the packed lower slices: lane l of slice s copies its row's lower entries (columns and
+// the Jacobi-scaled values b_ij) in stored order to 32 * l_ptr[s] + 32 * j + l; the rest of the
+// slice length is padding (column -1, value 0).
+__global__ void gs2_lower_fill_kernel(const int32_t *slice_len, const long long *slice_ptr,
+                                      const long long *l_ptr, const int32_t *l_len, int64_t n_slices,
+                                      const uint32_t *lmask, const int32_t *s_col, const double *j64,
+                                      const float *j32, int32_t *l_col, double *l64, float *l32) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t sl = w0; sl < n_slices; sl += nw) {
+        const long long sp = slice_ptr[sl], lp = l_ptr[sl];
+        int32_t cnt = 0;
+        for (int32_t j = 0; j < slice_len[sl]; j++) {
+            if (!((lmask[sp + j] >> lane) & 1u)) continue;
+            const long long src = 32ll * (sp + j) + lane, dst = 32ll * (lp + cnt) + lane;
+            l_col[dst] = s_col[src];
+            if (l64) l64[dst] = j64[src];
+            if (l32) l32[dst] = j32[src];
+            cnt++;
+        }
+        for (; cnt < l_len[sl]; cnt++) {
+            const long long dst = 32ll * (lp + cnt) + lane;
+            l_col[dst] = -1;
+            if (l64) l64[dst] = 0.0;
+            if (l32) l32[dst] = 0.0f;
+        }
+    }
+}
+
+static mpk_status gs2_lower_fill(mpk_plan_s *P, cudaStream_t s) {
+    if (!P->l_col.p || P->n_slices == 0) return MPK_OK;
+    gs2_lower_fill_kernel<<<grid_for((int64_t)P->n_slices * 32), 256, 0, s>>>(
+        P->slice_len.as<int32_t>(), P->slice_ptr.as<long long>(), P->l_slice_ptr.as<long long>(),
+        P->l_slice_len.as<int32_t>(), P->n_slices, P->s_lmask.as<uint32_t>(), P->s_col.as<int32_t>(),
+        P->has64 ? P->s_jval64.as<double>() : nullptr, P->has32 ? P->s_jval32.as<float>() : nullptr,
+        P->l_col.as<int32_t>(), P->has64 ? P->l_val64.as<double>() : nullptr,
+        P->has32 ? P->l_val32.as<float>() : nullptr);
+    MPK_CUDA(cudaGetLastError());
+    return MPK_OK;
+}
+
 __global__ void row_chunk_kernel(const int32_t *chunk_row, int64_t n_chunks, int32_t *row_chunk) {
     for (int64_t c = blockIdx.x; c < n_chunks; c += gridDim.x)
         for (int32_t r = chunk_row[c] + threadIdx.x; r < chunk_row[c + 1]; r += blockDim.x)
@@ -1128,6 +1188,25 @@ static mpk_status plan_create_impl(const mpk_csr *A, int32_t p_max, const mpk_pl
             P->slice_len.as<int32_t>(), P->n_slices, P->perm.as<int32_t>(),
             P->s_lmask.as<uint32_t>());
         MPK_CUDA(cudaGetLastError());
+        // packed lower slices for the GS2 inner stages
+        DevBuf llen;
+        MPK_TRY(llen.alloc(P->n_slices * 4));
+        gs2_lower_len_kernel<<<grid_for((int64_t)P->n_slices * 32), 256, 0, s>>>(
+            P->slice_row.as<int32_t>(), P->slice_len.as<int32_t>(), P->slice_ptr.as<long long>(),
+            P->n_slices, P->s_lmask.as<uint32_t>(), llen.as<int32_t>());
+        MPK_CUDA(cudaGetLastError());
+        std::vector<int32_t> h_len(P->n_slices);
+        MPK_CUDA(cudaMemcpyAsync(h_len.data(), llen.p, P->n_slices * 4, cudaMemcpyDeviceToHost, s));
+        MPK_CUDA(cudaStreamSynchronize(s));
+        std::vector<long long> h_lp(P->n_slices + 1, 0);
+        for (int64_t i = 0; i < P->n_slices; i++) h_lp[i + 1] = h_lp[i] + h_len[i];
+        P->l_sell_nnz = 32ll * h_lp[P->n_slices];
+        MPK_TRY(upload(P->l_slice_ptr, h_lp, s));
+        MPK_TRY(upload(P->l_slice_len, h_len, s));
+        MPK_TRY(P->l_col.alloc(std::max<int64_t>(P->l_sell_nnz, 1) * 4));
+        if (P->has64) MPK_TRY(P->l_val64.alloc(std::max<int64_t>(P->l_sell_nnz, 1) * 8));
+        if (P->has32) MPK_TRY(P->l_val32.alloc(std::max<int64_t>(P->l_sell_nnz, 1) * 4));
+        MPK_TRY(gs2_lower_fill(P, s));
     }
 
     // ---- blocked-task dependency ranges and flags
@@ -1230,6 +1309,7 @@ mpk_status mpk_build_blocks(mpk_plan_s *P, cudaStream_t s) {
             P->dinv64.as<double>(), P->has64 ? P->s_jval64.as<double>() : nullptr,
             P->has32 ? P->s_jval32.as<float>() : nullptr);
         MPK_CUDA(cudaGetLastError());
+        MPK_TRY(gs2_lower_fill(P, s));   // value updates: refresh the packed lower slices
     }
     return MPK_OK;
 }
@@ -1285,7 +1365,7 @@ extern "C" mpk_status mpk_plan_stats(mpk_plan_t P, mpk_plan_info *st) {
     for (const DevBuf *d : {&P->perm, &P->iperm, &P->level, &P->level_ptr, &P->group_ptr, &P->rp,
                             &P->ci, &P->val64, &P->val32, &P->entry_map, &P->slice_row,
                             &P->slice_ptr, &P->slice_len, &P->s_col, &P->s_val64, &P->s_val32,
-                            &P->s_jval64, &P->s_jval32, &P->dinv64, &P->s_lmask, &P->chunk_slice, &P->chunk_row, &P->chunk_entry, &P->dep_lo, &P->dep_hi, &P->flags,
+                            &P->s_jval64, &P->s_jval32, &P->dinv64, &P->s_lmask, &P->l_slice_ptr, &P->l_slice_len, &P->l_col, &P->l_val64, &P->l_val32, &P->chunk_slice, &P->chunk_row, &P->chunk_entry, &P->dep_lo, &P->dep_hi, &P->flags,
                             &P->ctrl, &P->ws_x, &P->ws_y})
         b += d->bytes;
     st->device_bytes = (int64_t)b;
