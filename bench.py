@@ -374,20 +374,25 @@ def run_profile(args, m, torch, local):
     rp = torch.from_numpy(A.row_ptr).to(dev)
     ci = torch.from_numpy(A.col).to(dev)
     vv = torch.from_numpy(A.val).to(dev).to(dt)
-    opts = m.mpk_plan_opts_default(assume_symmetric=1, p_blk=p, blocked=1)
+    gs2 = args.profile_gs2 >= 0
+    # GS2: every sub-power of every power in one blocked launch
+    pmax = p * (args.profile_gs2 + 1) if gs2 else p
+    opts = m.mpk_plan_opts_default(assume_symmetric=1, p_blk=pmax, blocked=1, jacobi=1 if gs2 else 0)
     if args.profile_cs > 0:
         opts.chunk_slices = args.profile_cs
     if args.profile_slack > 0:
         opts.slack_tasks = args.profile_slack
     if args.profile_kernel >= 0:
         opts.kernel = args.profile_kernel
-    plan = m.mpk_plan_create(rp, ci, vv, p, opts)
+    plan = m.mpk_plan_create(rp, ci, vv, pmax, opts)
     perm = m.mpk_plan_perm(plan)["perm"].long()
     Y = torch.empty((p + 1) * A.n, dtype=dt, device=dev)
     X = torch.from_numpy(x).to(dev).to(dt)
     Y[:A.n] = X[perm]
     co = m.mpk_coeffs_newton(theta)
     fl = m.MPK_PERMUTED_IO | m.MPK_Y0_IS_X
+    if gs2:
+        fl |= m.MPK_GS2 | m.MPK_GS2_GAMMA(args.profile_gs2)
     for _ in range(args.profile_reps):
         if args.profile_orig:
             # the headline's call: original order in and out (gather, blocked kernel that also
@@ -498,6 +503,9 @@ def main():
     ap.add_argument("--profile-reps", type=int, default=3)
     ap.add_argument("--profile-kernel", type=int, default=-1,
                     help="blocked kernel of the profiling plan (plan option kernel; -1: default)")
+    ap.add_argument("--profile-gs2", type=int, default=-1,
+                    help="profiling run of the GS2-preconditioned MPK with this many inner stages "
+                         "(-1: plain MPK)")
     ap.add_argument("--profile-orig", action="store_true",
                     help="profiling run with original-order I/O (the headline's call)")
     ap.add_argument("--profile-solver", action="store_true",

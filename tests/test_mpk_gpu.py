@@ -373,3 +373,49 @@ def test_graph_capture_replays_the_blocked_kernel(m, kern):
         assert m.mpk_plan_sync(plan) == m.MPK_OK
         ref = _run(m, plan, A, cf, xs, flags=m.MPK_UNBLOCKED)
         assert np.array_equal(Y.cpu().numpy().reshape(p + 1, -1), ref)
+
+
+def test_maximum_power_count_and_rhs_block(m):
+    """p = 63 (MPK_MAX_P, Chebyshev basis so the powers stay bounded) through one blocked
+    launch of 63 local powers, bit-identical to 63 SpMVs and within the tolerance of the oracle;
+    n_rhs = 1024 (the largest block) in FP32, interleaved and column-major, against the oracle
+    column by column on a sample of right-hand sides."""
+    import torch
+    A = MATS["diff7_10"]
+    p = 63
+    cf = sstep.chebyshev_coeffs(0.0, 2.2 * float(np.abs(A.val).max()), p)
+    x = mi.uniform_vectors(A.n, 9)[0]
+    rp, ci, vv = to_dev(A)
+    plan = m.mpk_plan_create(rp, ci, vv, p, m.mpk_plan_opts_default(l2_budget_bytes=40_000, blocked=1))
+    assert m.mpk_plan_stats(plan)["p_blk"] == p
+    got = _run(m, plan, A, cf, x)
+    got_u = _run(m, plan, A, cf, x, flags=m.MPK_UNBLOCKED)
+    assert np.array_equal(got, got_u)
+    ref = oracle.mpk(A, p, cf, x)
+    den = abs_powers(A, cf, x)
+    for k in range(1, p + 1):
+        assert max_rel_err(got[k], ref[k], den[k]) <= 64 * k * U64, k
+    # the largest block of right-hand sides
+    B = mi.random_sparse(300, 0.02, 4, symmetric=True, diag=True)
+    B32 = mi.CSR(B.row_ptr, B.col, B.val.astype(np.float32).astype(np.float64))
+    nr, p2 = 1024, 2
+    cf2 = sstep.newton_coeffs([0.5, -0.25])
+    Xh = mi.uniform_vectors(B.n, 3, nr).astype(np.float32)            # nr x n
+    rpb, cib, vb = to_dev(B, np.float32)
+    plan2 = m.mpk_plan_create(rpb, cib, vb, p2, m.mpk_plan_opts_default(blocked=1))
+    cols = [0, 1, 511, 1023]
+    for fl, X, unpack in (
+            (m.MPK_RHS_INTERLEAVED, torch.from_numpy(np.ascontiguousarray(Xh.T)).cuda(),
+             lambda Y: Y.view(p2 + 1, B.n, nr).permute(0, 2, 1)),
+            (0, torch.from_numpy(np.ascontiguousarray(Xh)).cuda().view(-1),
+             lambda Y: Y.view(p2 + 1, nr, B.n))):
+        Y = torch.full(((p2 + 1) * B.n * nr,), float("nan"), dtype=torch.float32, device="cuda")
+        m.mpk_apply(plan2, cf2, X, Y, n_rhs=nr, flags=fl)
+        assert m.mpk_plan_sync(plan2) == m.MPK_OK
+        out = unpack(Y).double().cpu().numpy()          # (p+1, nr, n)
+        for q in cols:
+            xq = Xh[q].astype(np.float64)
+            ref2 = oracle.mpk(B32, p2, cf2, xq)
+            den2 = abs_powers(B32, cf2, xq)
+            for k in range(1, p2 + 1):
+                assert max_rel_err(out[k, q], ref2[k], den2[k]) <= 64 * k * 2.0 ** -24, (fl, q, k)
