@@ -115,9 +115,12 @@ typedef struct {
                                  MPK_JACOBI: a second copy of the SELL values per kept
                                  precision, b_ij = a_ij / a_jj (computed in FP64), plus
                                  D^-1 in FP64.  A column whose diagonal entry is missing or
-                                 zero is not scaled (d_j^-1 := 1).  Also builds the bit mask
-                                 of strictly lower entries (in the caller's row order) that
-                                 MPK_GS2 needs: one uint32 per 32 stored entries.  Default 0 */
+                                 zero is not scaled (d_j^-1 := 1).  Also builds what MPK_GS2
+                                 needs: a bit mask of the strictly lower entries (in the
+                                 caller's row order; one uint32 per 32 stored entries) and
+                                 those entries of A D^-1 packed per row into slices of their
+                                 own (columns and values, about half the matrix again).
+                                 Default 0 */
     int32_t shard_warps;      /* kernel = 3: warps per shard of the ready-first hand-out
                                  (default 4; fewer shards share cursors more, more shards widen
                                  the window between powers) */
@@ -173,9 +176,10 @@ typedef struct {
                                       y_k = a_k A P^-1 y_{k-1} + b_k y_{k-1} + c_k y_{k-2}.
                                     Each power runs as gamma + 1 sub-powers over the matrix
                                     (Alg. GS2(b): the gamma inner stages on the Jacobi-scaled
-                                    strictly lower part, then the product with A D^-1), which
-                                    the blocked kernel schedules like powers, so L and U are
-                                    reused from cache across the stages.  Add
+                                    strictly lower part, which they stream from its own packed
+                                    copy, then the product with A D^-1); the blocked kernel
+                                    schedules the sub-powers like powers, all in one launch.
+                                    Add
                                     MPK_GS2_GAMMA(gamma), gamma in 0..15 (0 = Jacobi).  Needs a
                                     plan created with opts.jacobi = 1 and n_rhs = 1
                                     (MPK_ERR_ARG / MPK_ERR_UNIMPLEMENTED otherwise); excludes
