@@ -56,11 +56,11 @@ def measured_peaks():
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 # DRAM bytes (read + write) of one blocked FP64 p = 4 launch of the headline call (original
-# order in and out), from an ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the
-# same kernel and call on the 27-point 128^3 matrix, scaled by stored SELL entries
-# (109,664,800 / 56,041,696).  Valid for the kernel as captured; None when the kernel has
-# changed since (streamed last-power loads) until it is captured again.
-TRAFFIC_F64_P4_BYTES = None
+# order in and out, 4-slice chunks), from an ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum) of the same kernel and call on the 27-point 128^3 matrix
+# (2.821 + 0.109 GB), scaled by stored SELL entries (109,664,800 / 56,041,696).  Valid for the
+# kernel as captured; set to None when the kernel changes until it is captured again.
+TRAFFIC_F64_P4_BYTES = 5.734e9
 
 
 class ClockSampler:
