@@ -424,10 +424,11 @@ mpk_status sstep_gmres_solve(mpk_plan_t A, const double *b, double *x, const mpk
  * s-step CG with FP64 iterative refinement.  The paper names s-step CG as the short-recurrence
  * method whose solver speedup should approach the MPK's, its orthogonalisation being minimal
  * (Sec. 4, discussion of the s-step GMRES results; Sec. 7); the steps are the standard
- * communication-avoiding CG: per outer iteration one MPK of s powers on p and one of s - 1
- * powers on r (Newton basis) give Y = [p, .., rho_s(A) p, r, .., rho_{s-1}(A) r]; one FP64
- * Gram matrix G = Y^T Y; s CG steps on coordinate vectors of length 2s + 1 with the change of
- * basis B (A Y = Y B); then x += Y x', r = Y r', p = Y p'.
+ * communication-avoiding CG: per outer iteration s Newton powers on p and s - 1 on r give
+ * Y = [p, .., rho_s(A) p, r, .., rho_{s-1}(A) r] (one two-rhs MPK call of s powers on the
+ * pair (p, r), so the matrix is read s times, not 2s - 1); one FP64 Gram matrix G = Y^T Y;
+ * s CG steps on coordinate vectors of length 2s + 1 with the change of basis B (A Y = Y B);
+ * then x += Y x', r = Y r', p = Y p'.
  * ---------------------------------------------------------------------------------------- */
 typedef struct {
     int32_t s;              /* CG steps per outer iteration = powers of the p basis (1..15,

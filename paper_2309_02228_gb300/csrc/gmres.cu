@@ -22,6 +22,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "mpk_internal.cuh"
@@ -1313,8 +1314,18 @@ static inline int gsym_nbp(int M, int bs) {
     return nb * (nb + 1) / 2;
 }
 
+// Basis storage of s-step CG: the two Krylov sequences P_k(A) p (k = 0..s) and P_k(A) r
+// (k = 0..s-1) sit as interleaved pairs, pair k = (P_k(A) p, P_k(A) r) at Y + 2 k ldv with
+// element i of the pair at offsets 2i and 2i + 1.  One two-rhs MPK call then builds both
+// sequences and reads the matrix once per power for both (two single-rhs calls read it
+// 2s - 1 times).  Basis column a (a <= s: P_a(A) p; a > s: P_{a-s-1}(A) r) has element i at
+// Y[cg_col_ofs(a, s, ldv) + 2 i].  Pair s also holds P_s(A) r, which the method does not use.
+__host__ __device__ __forceinline__ int64_t cg_col_ofs(int a, int s, int64_t ldv) {
+    return a <= s ? (int64_t)a * 2 * ldv : (int64_t)(a - s - 1) * 2 * ldv + 1;
+}
+
 template <typename T>
-__global__ void __launch_bounds__(256) gram_sym_kernel(const T *Y, int64_t ldv, int M, int64_t n,
+__global__ void __launch_bounds__(256) gram_sym_kernel(const T *Y, int64_t ldv, int M, int s, int64_t n,
                                                        double *part) {
     constexpr int BS = gsym_bs<T>();
     // tiles of Y during the sweep, then the row groups' FP64 totals (RG * NBP * BS^2 <= 256 * BS^2)
@@ -1353,7 +1364,7 @@ __global__ void __launch_bounds__(256) gram_sym_kernel(const T *Y, int64_t ldv, 
 #pragma unroll
         for (int j = 0; j < PF; j++) {
             const int c = pc0 + 2 * j;
-            pre[j] = (c < M && r < n) ? __ldg(Y + r + (int64_t)c * ldv) : (T)0;
+            pre[j] = (c < M && r < n) ? __ldg(Y + cg_col_ofs(c, s, ldv) + 2 * r) : (T)0;
         }
     };
     if ((int64_t)blockIdx.x * GSYM_TR < n) prefetch(blockIdx.x);
@@ -1405,7 +1416,7 @@ __global__ void __launch_bounds__(256) gram_sym_kernel(const T *Y, int64_t ldv, 
 }
 
 // x += scale * Y x' (in the basis precision, added to the FP64 x); p = Y p' and r = Y r' in
-// place (Y columns 0 and s + 1).  A thread reads a row of Y before it writes that row.
+// place (pair 0).  A thread reads a row of Y before it writes that row.
 template <typename T>
 __global__ void __launch_bounds__(256) cg_recover_kernel(T *Y, int64_t ldv, int M, int s, const CgState *cs,
                                                          int64_t n, double scale, double *x) {
@@ -1416,34 +1427,47 @@ __global__ void __launch_bounds__(256) cg_recover_kernel(T *Y, int64_t ldv, int 
         cr[threadIdx.x] = (T)cs->rc[threadIdx.x];
     }
     __syncthreads();
+    using T2 = typename std::conditional<sizeof(T) == 8, double2, float2>::type;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         T dx = 0, pn = 0, rn = 0;
-        for (int a = 0; a < M; a++) {
-            const T y = Y[i + a * ldv];
-            dx = fma(cx[a], y, dx);
-            pn = fma(cp[a], y, pn);
-            rn = fma(cr[a], y, rn);
+        // pair k: basis columns k (from p) and s + 1 + k (from r, k < s)
+        for (int k = 0; k <= s; k++) {
+            const T2 y = *reinterpret_cast<const T2 *>(Y + (int64_t)k * 2 * ldv + 2 * i);
+            dx = fma(cx[k], y.x, dx);
+            pn = fma(cp[k], y.x, pn);
+            rn = fma(cr[k], y.x, rn);
+            if (k < s) {
+                const int a = s + 1 + k;
+                dx = fma(cx[a], y.y, dx);
+                pn = fma(cp[a], y.y, pn);
+                rn = fma(cr[a], y.y, rn);
+            }
         }
         x[i] += scale * (double)dx;
-        Y[i] = pn;
-        Y[i + (int64_t)(s + 1) * ldv] = rn;
+        T2 o;
+        o.x = pn;
+        o.y = rn;
+        *reinterpret_cast<T2 *>(Y + 2 * i) = o;
     }
 }
 
-// q = (T)(r64 * inv): residual replacement of the r column
+// r column of pair 0 = (T)(r64 * inv): residual replacement
 template <typename T>
-__global__ void cg_replace_kernel(const double *r, int64_t n, double inv, T *q) {
+__global__ void cg_replace_kernel(const double *r, int64_t n, double inv, T *Y) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        q[i] = (T)(r[i] * inv);
+        Y[2 * i + 1] = (T)(r[i] * inv);
 }
 
-// p = r = (T)(r64 / scale): the first columns of both blocks
+// p = r = (T)(r64 / scale): both columns of pair 0
 template <typename T>
-__global__ void cg_start_kernel(const double *r, int64_t n, double inv, T *p, T *q) {
+__global__ void cg_start_kernel(const double *r, int64_t n, double inv, T *Y) {
+    using T2 = typename std::conditional<sizeof(T) == 8, double2, float2>::type;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const T v = (T)(r[i] * inv);
-        p[i] = v;
-        q[i] = v;
+        T2 o;
+        o.x = v;
+        o.y = v;
+        *reinterpret_cast<T2 *>(Y + 2 * i) = o;
     }
 }
 
@@ -1469,7 +1493,7 @@ struct CgSolver {
         n = P->n;
         ldv = (n + 31) / 32 * 32;
         M = 2 * o.s + 1;
-        MPK_TRY(Y.alloc_on((size_t)M * ldv * sizeof(T), st));
+        MPK_TRY(Y.alloc_on((size_t)(o.s + 1) * 2 * ldv * sizeof(T), st));   // s + 1 pairs
         gram_grid = 8 * P->n_sm;
         // symmetric Gram partials: (CTA, row group) x packed entries <= CTAs x 256 threads x BS^2
         MPK_TRY(part.alloc_on((size_t)(2 * P->n_sm) * 256 * BS * BS * sizeof(double) + 4096, st));
@@ -1485,7 +1509,6 @@ struct CgSolver {
         MPK_CUDA(cudaMemsetAsync(cstate.p, 0, sizeof(CgState), st));
         return MPK_OK;
     }
-    T *col(int a) { return Y.as<T>() + (int64_t)a * ldv; }
     void flush_timers() {
         t_mpk.flush();
         t_gram.flush();
@@ -1501,22 +1524,23 @@ struct CgSolver {
     // G = Y^T Y over the first Mc columns: upper triangle packed by blocks (gram_sym_kernel)
     static constexpr int BS = gsym_bs<T>();
     int gsym_grid() const { return (int)std::min<int64_t>(2 * P->n_sm, std::max<int64_t>(1, ceil_div(n, GSYM_TR))); }
-    mpk_status gram(int Mc) {
+    mpk_status gram(int sc) {
+        const int Mc = 2 * sc + 1;
         const int g = gsym_grid();
         const int m = gsym_nbp(Mc, BS) * BS * BS;
-        gram_sym_kernel<T><<<g, 256, 0, st>>>(Y.as<T>(), ldv, Mc, n, part.as<double>());
+        gram_sym_kernel<T><<<g, 256, 0, st>>>(Y.as<T>(), ldv, Mc, sc, n, part.as<double>());
         reduce_partials_kernel<<<redp_grid(m), 32 * REDP_WARPS, 0, st>>>(part.as<double>(), g, m, (int64_t)m,
                                                                        G.as<double>(), 0);
         MPK_CUDA(cudaGetLastError());
         return MPK_OK;
     }
-    mpk_status basis(T *v0, int p) {
-        if (p < 1) return MPK_OK;
+    // both Newton sequences, p powers each, as pairs 1..p (pair 0 holds p and r)
+    mpk_status basis(int p) {
         std::vector<double> a(p, 1.0), b(p, 0.0), c(p, 0.0);
         for (int k = 0; k < p; k++) b[k] = -theta_use[k];
         mpk_coeffs co{p, a.data(), b.data(), c.data(), nullptr};
-        const uint32_t fl = MPK_PERMUTED_IO | MPK_Y0_IS_X | (o.mpk_flags & MPK_UNBLOCKED);
-        return mpk_apply_internal(P, &co, sizeof(T) == 8 ? MPK_F64 : MPK_F32, nullptr, ldv, v0, ldv, 1, fl, st);
+        const uint32_t fl = MPK_PERMUTED_IO | MPK_Y0_IS_X | MPK_RHS_INTERLEAVED | (o.mpk_flags & MPK_UNBLOCKED);
+        return mpk_apply_internal(P, &co, sizeof(T) == 8 ? MPK_F64 : MPK_F32, nullptr, ldv, Y.p, ldv, 2, fl, st);
     }
     std::vector<double> theta_use;
 
@@ -1528,7 +1552,7 @@ struct CgSolver {
         theta_use = th;
         *bd_out = false;
         *steps_out = 0;
-        cg_start_kernel<T><<<grid_rows(n), 256, 0, st>>>(rp, n, 1.0 / hr, col(0), col(sc + 1));
+        cg_start_kernel<T><<<grid_rows(n), 256, 0, st>>>(rp, n, 1.0 / hr, Y.as<T>());
         MPK_CUDA(cudaGetLastError());
         MPK_CUDA(cudaMemcpyAsync(dth.p, th.data(), sc * sizeof(double), cudaMemcpyHostToDevice, st));
         int steps = 0;
@@ -1538,16 +1562,15 @@ struct CgSolver {
                 // correction so far, so this is the inner residual), p kept
                 t_other.start();
                 MPK_TRY(mpk_launch_residual(P, xp, bp, rp, st));
-                cg_replace_kernel<T><<<grid_rows(n), 256, 0, st>>>(rp, n, 1.0 / hr, col(sc + 1));
+                cg_replace_kernel<T><<<grid_rows(n), 256, 0, st>>>(rp, n, 1.0 / hr, Y.as<T>());
                 MPK_CUDA(cudaGetLastError());
                 t_other.stop();
             }
             t_mpk.start();
-            MPK_TRY(basis(col(0), sc));
-            MPK_TRY(basis(col(sc + 1), sc - 1));
+            MPK_TRY(basis(sc));
             t_mpk.stop();
             t_gram.start();
-            MPK_TRY(gram(Mc));
+            MPK_TRY(gram(sc));
             t_gram.stop();
             t_other.start();
             cg_coord_kernel<<<1, 32, 0, st>>>(cs, G.as<double>(), Mc, sc, dth.as<double>(), tol_abs / hr,
