@@ -1200,9 +1200,13 @@ __global__ void __launch_bounds__(32) cg_coord_kernel(CgState *cs, const double 
         const int len = c <= s ? s + 1 : s;
         return j < len - 1;
     };
-    // G: the upper triangle packed by bs x bs blocks (gram_sym_kernel); read it symmetrically
-    const int nbk = (M + bs - 1) / bs;
+    // G: the upper triangle over the basis storage's 2s + 2 columns in pair order (column
+    // 2k + q: slot q of pair k), packed by bs x bs blocks (gram_sym_kernel); basis column a is
+    // storage column a <= s ? 2a : 2(a - s - 1) + 1.  Read symmetrically.
+    const int nbk = (2 * (s + 1) + bs - 1) / bs;
     auto g = [&](int r, int c) -> double {
+        r = r <= s ? 2 * r : 2 * (r - s - 1) + 1;
+        c = c <= s ? 2 * c : 2 * (c - s - 1) + 1;
         if (r > c) {
             const int t_ = r;
             r = c;
@@ -1297,21 +1301,51 @@ __global__ void __launch_bounds__(32) cg_coord_kernel(CgState *cs, const double 
     }
 }
 
-// Symmetric Gram of the CG basis: the upper triangle of G = Y^T Y (Y: n x M, M <= 31), stored
-// packed by BS x BS blocks: block pair pb = (ab, bb), ab <= bb, enumerated row by row, entry
-// (i, j) of the block at pb * BS^2 + i * BS + j.  A CTA stages 128-row tiles of Y in shared
+// Symmetric Gram of the CG basis storage: the upper triangle of G = Y^T Y over its 2s + 2
+// columns in pair order (column 2k + q is slot q of pair k; P_s(A) r, column 2s + 1, is
+// summed too and not used), stored packed by BS x BS blocks: block pair pb = (ab, bb),
+// ab <= bb, enumerated row by row, entry (i, j) of the block at pb * BS^2 + i * BS + j.  A
+// block of columns is then whole pairs (FP32: two, FP64: one), read from the staged tile by
+// vector loads.  A CTA stages 128-row tiles of Y in shared
 // memory; thread t owns block pair t % NBP and the rows g, g + RG, ... of each tile
 // (g = t / NBP, RG = 256 / NBP row groups).  Products are summed in the basis precision over
 // up to 32 tiles, then added to FP64 totals; the CTA sums its row groups in order (in the
 // shared memory the tiles used) and writes one FP64 partial per entry, which
 // reduce_partials_kernel sums over the CTAs in a fixed order.  BS = 4 for FP32 (loads of 8
 // values per 16 FMAs), 2 for FP64 (fewer wasted products on the slow FP64 pipe).
+// Tiles arrive by 16-byte asynchronous copies (cp.async) into a ring of GSYM_STAGES shared
+// buffers, GSYM_STAGES - 1 tiles ahead of the one being summed: with one tile in flight per
+// CTA the kernel was bound by memory latency (about 1 TB/s on the FP32 basis).
 constexpr int GSYM_TR = 128;
+constexpr int GSYM_STAGES = 4;
 constexpr int GSYM_MP = 32;                   // M padded (<= 32 columns)
 template <typename T> constexpr int gsym_bs() { return sizeof(T) == 4 ? 4 : 2; }
 static inline int gsym_nbp(int M, int bs) {
     const int nb = (M + bs - 1) / bs;
     return nb * (nb + 1) / 2;
+}
+// shared elements of one pair's tile: 2 GSYM_TR values and 16 bytes of padding, so that the
+// pairs of a stage start in different banks and every copy stays 16-byte aligned
+template <typename T> constexpr int gsym_pstride() { return 2 * GSYM_TR + 16 / (int)sizeof(T); }
+// pairs of a stage for np stored pairs: whole column blocks (FP32: an even number of pairs;
+// the padding pair reads zeros)
+template <typename T> constexpr int gsym_pairs(int np) { return sizeof(T) == 4 ? (np + 1) / 2 * 2 : np; }
+// dynamic shared memory of gram_sym_kernel for np pairs: the stage ring, reused afterwards for
+// the row groups' FP64 totals (at most 256 BS^2 values)
+template <typename T> size_t gsym_smem_bytes(int np) {
+    constexpr int BS = sizeof(T) == 4 ? 4 : 2;
+    const size_t ring = (size_t)GSYM_STAGES * gsym_pairs<T>(np) * gsym_pstride<T>() * sizeof(T);
+    const size_t red = (size_t)256 * BS * BS * sizeof(double);
+    return ring > red ? ring : red;
+}
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 // Basis storage of s-step CG: the two Krylov sequences P_k(A) p (k = 0..s) and P_k(A) r
@@ -1325,16 +1359,20 @@ __host__ __device__ __forceinline__ int64_t cg_col_ofs(int a, int s, int64_t ldv
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) gram_sym_kernel(const T *Y, int64_t ldv, int M, int s, int64_t n,
+__global__ void __launch_bounds__(256) gram_sym_kernel(const T *Y, int64_t ldv, int s, int64_t n,
                                                        double *part) {
     constexpr int BS = gsym_bs<T>();
-    // tiles of Y during the sweep, then the row groups' FP64 totals (RG * NBP * BS^2 <= 256 * BS^2)
-    constexpr int SH_BYTES = (GSYM_MP * GSYM_TR * (int)sizeof(T)) > (256 * BS * BS * 8)
-                                 ? (GSYM_MP * GSYM_TR * (int)sizeof(T)) : (256 * BS * BS * 8);
-    __shared__ __align__(16) unsigned char sh_raw[SH_BYTES];
+    constexpr int PS = gsym_pstride<T>();
+    constexpr int CE = 16 / (int)sizeof(T);          // elements per 16-byte copy
+    constexpr int CH = 2 * GSYM_TR / CE;             // copies per pair and tile
+    using T2 = typename std::conditional<sizeof(T) == 8, double2, float2>::type;
+    extern __shared__ __align__(16) unsigned char sh_raw[];
     T *sY = reinterpret_cast<T *>(sh_raw);
+    const int np = s + 1;                            // stored pairs
+    const int npad = gsym_pairs<T>(np);              // pairs of a stage
+    const int stage = npad * PS;
+    const int M = 2 * np;                            // storage columns
     const int nb = (M + BS - 1) / BS;
-    const int Mp = nb * BS;
     const int NBP = nb * (nb + 1) / 2;
     const int RG = (int)blockDim.x / NBP;
     const int t = threadIdx.x;
@@ -1346,6 +1384,13 @@ __global__ void __launch_bounds__(256) gram_sym_kernel(const T *Y, int64_t ldv, 
         ab++;
     }
     const int bb = ab + rem;
+    // this thread's column blocks inside a stage: BS / 2 whole pairs each
+    const int oa = ab * (BS / 2) * PS, ob = bb * (BS / 2) * PS;
+    // padding pairs (never copied) read zeros
+    for (int i = t; i < GSYM_STAGES * (npad - np) * PS; i += blockDim.x) {
+        const int stg = i / ((npad - np) * PS), e = i % ((npad - np) * PS);
+        sY[stg * stage + np * PS + e] = (T)0;
+    }
     double acc[BS * BS];
     T tacc[BS * BS];
 #pragma unroll
@@ -1354,36 +1399,42 @@ __global__ void __launch_bounds__(256) gram_sym_kernel(const T *Y, int64_t ldv, 
         tacc[k] = (T)0;
     }
     int since = 0;
-    // thread t stages row t % 128 of columns t / 128, t / 128 + 2, ... of a tile: the next
-    // tile's loads are issued into registers before the current tile is computed
-    constexpr int PF = GSYM_MP * GSYM_TR / 256;      // 16 staged values per thread
-    const int pr = t % GSYM_TR, pc0 = t / GSYM_TR;
-    T pre[PF];
-    auto prefetch = [&](int64_t tile) {
-        const int64_t r = tile * GSYM_TR + pr;
-#pragma unroll
-        for (int j = 0; j < PF; j++) {
-            const int c = pc0 + 2 * j;
-            pre[j] = (c < M && r < n) ? __ldg(Y + cg_col_ofs(c, s, ldv) + 2 * r) : (T)0;
+    const int64_t ntiles = (n + GSYM_TR - 1) / GSYM_TR;
+    // copies of the rows of `tile` that exist (pair k: 2 rows' values per row, contiguous)
+    // into ring buffer stg; one commit group per call, empty past the last tile
+    auto issue = [&](int64_t tile, int stg) {
+        if (tile < ntiles) {
+            const int64_t r0 = tile * GSYM_TR;
+            const int vals = 2 * (int)(n - r0 < GSYM_TR ? n - r0 : GSYM_TR);
+            T *dst = sY + stg * stage;
+            for (int idx = t; idx < np * CH; idx += blockDim.x) {
+                const int k = idx / CH, e = (idx % CH) * CE;
+                if (e < vals) cp_async16(dst + k * PS + e, Y + (int64_t)k * 2 * ldv + 2 * r0 + e);
+            }
         }
+        cp_async_commit();
     };
-    if ((int64_t)blockIdx.x * GSYM_TR < n) prefetch(blockIdx.x);
-    for (int64_t tile = blockIdx.x; tile * GSYM_TR < n; tile += gridDim.x) {
-        __syncthreads();
 #pragma unroll
-        for (int j = 0; j < PF; j++) {
-            const int c = pc0 + 2 * j;
-            if (c < Mp) sY[c * GSYM_TR + pr] = pre[j];
-        }
+    for (int j = 0; j < GSYM_STAGES - 1; j++) issue((int64_t)blockIdx.x + (int64_t)j * gridDim.x, j);
+    int it = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, it++) {
+        // the buffer refilled here was summed in the previous iteration (barrier below)
+        issue(tile + (int64_t)(GSYM_STAGES - 1) * gridDim.x, (it + GSYM_STAGES - 1) % GSYM_STAGES);
+        cp_async_wait<GSYM_STAGES - 1>();
         __syncthreads();
-        if ((tile + gridDim.x) * GSYM_TR < n) prefetch(tile + gridDim.x);
+        const T *sb = sY + (it % GSYM_STAGES) * stage;
+        const int rows = (int)(n - tile * GSYM_TR < GSYM_TR ? n - tile * GSYM_TR : GSYM_TR);
         if (act) {
-            for (int r = g; r < GSYM_TR; r += RG) {
+            for (int r = g; r < rows; r += RG) {
                 T xa[BS], xb[BS];
 #pragma unroll
-                for (int i = 0; i < BS; i++) {
-                    xa[i] = sY[(ab * BS + i) * GSYM_TR + r];
-                    xb[i] = sY[(bb * BS + i) * GSYM_TR + r];
+                for (int h = 0; h < BS / 2; h++) {
+                    const T2 va = *reinterpret_cast<const T2 *>(sb + oa + h * PS + 2 * r);
+                    const T2 vb = *reinterpret_cast<const T2 *>(sb + ob + h * PS + 2 * r);
+                    xa[2 * h] = va.x;
+                    xa[2 * h + 1] = va.y;
+                    xb[2 * h] = vb.x;
+                    xb[2 * h + 1] = vb.y;
                 }
 #pragma unroll
                 for (int i = 0; i < BS; i++)
@@ -1399,10 +1450,12 @@ __global__ void __launch_bounds__(256) gram_sym_kernel(const T *Y, int64_t ldv, 
                 since = 0;
             }
         }
+        __syncthreads();
     }
+    cp_async_wait<0>();
+    __syncthreads();
     const int m = NBP * BS * BS;
     double *red = reinterpret_cast<double *>(sh_raw);
-    __syncthreads();
     if (act) {
 #pragma unroll
         for (int k = 0; k < BS * BS; k++) red[g * m + pb * BS * BS + k] = acc[k] + (double)tacc[k];
@@ -1498,6 +1551,8 @@ struct CgSolver {
         // symmetric Gram partials: (CTA, row group) x packed entries <= CTAs x 256 threads x BS^2
         MPK_TRY(part.alloc_on((size_t)(2 * P->n_sm) * 256 * BS * BS * sizeof(double) + 4096, st));
         MPK_TRY(G.alloc_on((size_t)GSYM_MP * GSYM_MP * sizeof(double), st));
+        MPK_CUDA(cudaFuncSetAttribute(gram_sym_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)gsym_smem_bytes<T>(o.s + 1)));
         MPK_TRY(cstate.alloc_on(sizeof(CgState), st));
         MPK_TRY(dth.alloc_on(CG_SMAX * sizeof(double), st));
         MPK_TRY(vec.alloc_on((size_t)3 * ldv * sizeof(double) + 64 * sizeof(double), st));
@@ -1521,14 +1576,14 @@ struct CgSolver {
         MPK_CUDA(cudaGetLastError());
         return MPK_OK;
     }
-    // G = Y^T Y over the first Mc columns: upper triangle packed by blocks (gram_sym_kernel)
+    // G = Y^T Y over the basis storage: upper triangle packed by blocks (gram_sym_kernel)
     static constexpr int BS = gsym_bs<T>();
     int gsym_grid() const { return (int)std::min<int64_t>(2 * P->n_sm, std::max<int64_t>(1, ceil_div(n, GSYM_TR))); }
+    // G over the basis storage's 2 sc + 2 columns (pair order)
     mpk_status gram(int sc) {
-        const int Mc = 2 * sc + 1;
         const int g = gsym_grid();
-        const int m = gsym_nbp(Mc, BS) * BS * BS;
-        gram_sym_kernel<T><<<g, 256, 0, st>>>(Y.as<T>(), ldv, Mc, sc, n, part.as<double>());
+        const int m = gsym_nbp(2 * sc + 2, BS) * BS * BS;
+        gram_sym_kernel<T><<<g, 256, gsym_smem_bytes<T>(sc + 1), st>>>(Y.as<T>(), ldv, sc, n, part.as<double>());
         reduce_partials_kernel<<<redp_grid(m), 32 * REDP_WARPS, 0, st>>>(part.as<double>(), g, m, (int64_t)m,
                                                                        G.as<double>(), 0);
         MPK_CUDA(cudaGetLastError());
