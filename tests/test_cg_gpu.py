@@ -9,6 +9,7 @@ names for the MPK, Sec. 4 and Sec. 7), through the C ABI.
 * residual replacement (the default) needs fewer CG steps in an FP32 basis than refinement
   alone;
 * the blocked and unblocked MPK give identical solves;
+* s = 15 (the largest basis, the Gram kernel's largest shared-memory ring) converges;
 * a negative definite matrix reports MPK_ERR_BREAKDOWN, the step limit MPK_ERR_NOT_CONVERGED,
   and invalid options MPK_ERR_ARG."""
 import numpy as np
@@ -100,6 +101,20 @@ def test_cg_setup_shifts_are_the_oracles_ritz_values(m):
     want = ocg.ritz_shifts(setup["alphas"], setup["betas"], s)
     got = info["shifts"]
     assert np.allclose(got, want, rtol=1e-6, atol=1e-6 * np.abs(want).max()), (got, want)
+
+
+@pytest.mark.parametrize("basis", ["f32", "f64"])
+def test_cg_largest_s(m, basis):
+    """s = 15, the largest basis (31 columns, 32 in the pair storage): its Gram kernel's stage
+    ring needs more than the default 48 KB of shared memory.  The solve reaches 1e-8."""
+    A = MATS["poisson2d_40"]()
+    b = mi.uniform_vectors(A.n, 7)[0]
+    plan = _plan(m, A, p=15)
+    bs = m.MPK_F32 if basis == "f32" else m.MPK_F64
+    x, info = _solve(m, plan, b, basis=bs, s=15, tol=1e-8)
+    assert info["status_code"] == m.MPK_OK, info
+    assert np.linalg.norm(b - sstep.spmv(A, x)) <= 1e-8 * np.linalg.norm(b)
+    assert 1 <= info["s_used"] <= 15
 
 
 @pytest.mark.parametrize("s", [1, 4, 8])
