@@ -88,21 +88,31 @@ typedef struct {
                                  advances once its dependencies were issued slack_tasks
                                  tickets earlier) */
     int32_t slack_tasks;      /* lag-greedy slack in tasks; 0 = the number of resident CTAs
-                                 (CTA tasks) or 128 per SM (warp tasks) */
+                                 (CTA tasks), 128 per SM (warp tasks) or three per resident
+                                 warp (lane tasks) */
     int32_t block_threads;    /* compute threads per CTA of the blocked kernel: 128 or 256
                                  (default); one control warp is added */
     int32_t stage;            /* CTA-task kernel only: stage each task's matrix block
                                  (columns and values) in shared memory with bulk asynchronous
                                  copies: -1 auto (on unless a 32-row slice exceeds a slot),
                                  0 off */
-    int32_t kernel;           /* blocked kernel: 0 = warp tasks (default: every warp takes
+    int32_t kernel;           /* blocked kernel: 0 = warp tasks (every warp takes
                                  tasks from a ticket dispenser and waits on per-block
                                  completion counters), 1 = CTA tasks fed by a control warp,
                                  2 = warp tasks in static round robin, 3 = ready-first warp
                                  tasks (no schedule: a warp claims, highest power first, the
                                  next chunk of a power whose dependencies are complete, else
                                  the next chunk of power 1; claimed tasks never wait; chunks
-                                 are dealt to interleaved shards, each with its own cursors) */
+                                 are dealt to interleaved shards, each with its own cursors),
+                                 4 = lane tasks (the default; single right-hand side, not
+                                 MPK_GS2; other calls run kernel 0): tasks of task_units
+                                 sub-slices of
+                                 32 / lanes_per_row rows, in lag-greedy order, dealt round
+                                 robin to the CTAs and inside a CTA to whichever warp is free
+                                 (a shared-memory counter: no global atomic per task), waiting
+                                 on per-block completion counters; lanes_per_row > 1 selects
+                                 this kernel for single right-hand sides whatever the value of
+                                 kernel */
     int32_t blocked;          /* mpk_apply without MPK_UNBLOCKED: 1 = always the blocked
                                  kernel, 0 = never, -1 = automatic (default): p >= 2 and a
                                  matrix larger than the L2 cache, and then whichever kernel
@@ -124,6 +134,21 @@ typedef struct {
     int32_t shard_warps;      /* kernel = 3: warps per shard of the ready-first hand-out
                                  (default 4; fewer shards share cursors more, more shards widen
                                  the window between powers) */
+    int32_t lanes_per_row;    /* single right-hand side (plain and MPK_JACOBI powers, blocked
+                                 and unblocked alike, so both still give identical values):
+                                 lanes of a warp that share one row, 1, 2, 4 or 8.  A warp then
+                                 covers a sub-slice of 32 / lanes_per_row rows of a SELL-32
+                                 slice; each lane sums the row's entries j = part,
+                                 part + lanes_per_row, ... (ascending) and the partial sums
+                                 are added by a fixed butterfly.  Fewer rows per warp shorten
+                                 the rows a task holds (0 = automatic: 1, which measured
+                                 fastest on the 27-point benchmark matrices in both
+                                 precisions) */
+    int32_t task_units;       /* kernel = 4: sub-slices per task (default 1) */
+    int32_t task_dispatch;    /* kernel = 4: 0 = tickets dealt round robin to the CTAs, inside
+                                 a CTA to whichever warp is free (default); 1 = one ticket
+                                 dispenser for the whole grid (a global atomic per task);
+                                 2 = static: warp w of W runs tickets w, w + W, w + 2W, ... */
 } mpk_plan_opts;
 
 typedef struct mpk_plan_s *mpk_plan_t;
@@ -316,8 +341,10 @@ typedef struct {
 
 /* Times mpk_apply(co, dtype, n_rhs, flags) on plans of A built with a fixed list of nine
  * candidate options derived from `base` (NULL: mpk_plan_opts_default): the base itself; p back-to-back
- * SpMVs (blocked = 0); the blocked warp-task kernel with chunks of 2, 4, 8 and 16 slices; the
- * static round-robin kernel; level groups sized for a quarter of L2 and for all of it.  Each
+ * SpMVs (blocked = 0); the lane-task kernel with a slack of two and of four tickets per
+ * resident warp, and with two slices per task; the warp-task kernel with chunks of 4 and 8
+ * slices; the lane-task kernel with level groups sized for a quarter of L2 and for all of it
+ * (lanes_per_row stays the base's).  Each
  * candidate runs two untimed calls and `reps` timed ones (CUDA events on `stream`, median).
  * A: DEVICE CSR as for mpk_plan_create; p = co->p <= MPK_MAX_P; flags: any mpk_apply flags
  * but MPK_HOST_IO, MPK_Y0_IS_X, MPK_UNBLOCKED and the debug flag (MPK_ERR_ARG).  The tuner

@@ -70,7 +70,9 @@ class mpk_plan_opts(ctypes.Structure):
                 ("schedule", ctypes.c_int32), ("slack_tasks", ctypes.c_int32),
                 ("block_threads", ctypes.c_int32), ("stage", ctypes.c_int32),
                 ("kernel", ctypes.c_int32), ("blocked", ctypes.c_int32),
-                ("jacobi", ctypes.c_int32), ("shard_warps", ctypes.c_int32)]
+                ("jacobi", ctypes.c_int32), ("shard_warps", ctypes.c_int32),
+                ("lanes_per_row", ctypes.c_int32), ("task_units", ctypes.c_int32),
+                ("task_dispatch", ctypes.c_int32)]
 
 
 class mpk_plan_info(ctypes.Structure):

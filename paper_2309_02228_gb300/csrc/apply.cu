@@ -16,7 +16,24 @@ namespace {
 
 struct Coefs {
     double a[MPK_MAX_P + 1], b[MPK_MAX_P + 1], c[MPK_MAX_P + 1], g[MPK_MAX_P + 2];
+    // the same in FP32 (converted once on the host: a conversion from FP64 runs on the FP64
+    // pipe), and per power and precision which terms the epilogue needs: bit 0 a_k = 1,
+    // bit 1 b_k != 0, bit 2 c_k != 0 (tested as integers, not by FP64 compares per row)
+    float af[MPK_MAX_P + 1], bf[MPK_MAX_P + 1], cf[MPK_MAX_P + 1], gf[MPK_MAX_P + 2];
+    unsigned char fl64[MPK_MAX_P + 1], fl32[MPK_MAX_P + 1];
 };
+
+// Fills the FP32 copies and the term flags from the FP64 coefficients (host).
+static void coefs_finish(Coefs &cf) {
+    for (int k = 0; k <= MPK_MAX_P; k++) {
+        cf.af[k] = (float)cf.a[k];
+        cf.bf[k] = (float)cf.b[k];
+        cf.cf[k] = (float)cf.c[k];
+        cf.fl64[k] = (unsigned char)((cf.a[k] == 1.0 ? 1 : 0) | (cf.b[k] != 0.0 ? 2 : 0) | (cf.c[k] != 0.0 ? 4 : 0));
+        cf.fl32[k] = (unsigned char)((cf.af[k] == 1.0f ? 1 : 0) | (cf.bf[k] != 0.0f ? 2 : 0) | (cf.cf[k] != 0.0f ? 4 : 0));
+    }
+    for (int k = 0; k <= MPK_MAX_P + 1; k++) cf.gf[k] = (float)cf.g[k];
+}
 
 // Vector set of one launch.  Power k (absolute) lives at vec(k); element (row r, rhs q) at
 // vec(k)[r * ld_row + q] with ld_row = n_rhs.
@@ -282,25 +299,28 @@ __device__ __forceinline__ void row_finish(const T (&acc)[NR], int32_t row, int 
     const T *y1 = vec_ro<T>(V, k - 1);
     const T *y2 = k >= 2 ? vec_ro<T>(V, k - 2) : nullptr;
     T *yk = vec_rw<T>(V, k);
-    const T a = (T)cf.a[k], b = (T)cf.b[k], c = (T)cf.c[k];
+    constexpr bool F64 = sizeof(T) == 8;
+    const T a = F64 ? (T)cf.a[k] : (T)cf.af[k], b = F64 ? (T)cf.b[k] : (T)cf.bf[k];
+    const T c = F64 ? (T)cf.c[k] : (T)cf.cf[k];
+    const unsigned fl = F64 ? cf.fl64[k] : cf.fl32[k];
     const int64_t o = (int64_t)row * n_rhs + q0;
     T res[NR];
     // a = 1 (monomial and Newton bases): the product is exact, so skipping it changes nothing
     // but saves one FP64 pipe operation per row, where that pipe is the bound
-    if (a == (T)1) {
+    if (fl & 1u) {
 #pragma unroll
         for (int q = 0; q < NR; q++) res[q] = acc[q];
     } else {
 #pragma unroll
         for (int q = 0; q < NR; q++) res[q] = a * acc[q];
     }
-    if (b != (T)0) {
+    if (fl & 2u) {
         T yv[NR];
         VecLoad<T, NR>::ld(y1 + o, yv);
 #pragma unroll
         for (int q = 0; q < NR; q++) res[q] = fma(b, yv[q], res[q]);
     }
-    if (c != (T)0 && y2) {
+    if ((fl & 4u) && y2) {
         T yv[NR];
         VecLoad<T, NR>::ld(y2 + o, yv);
 #pragma unroll
@@ -313,10 +333,10 @@ __device__ __forceinline__ void row_finish(const T (&acc)[NR], int32_t row, int 
     }
     if (V.use_gamma) {
         T *acc_out = reinterpret_cast<T *>(V.final_out);
-        const T gk = (T)cf.g[k];
+        const T gk = F64 ? (T)cf.g[k] : (T)cf.gf[k];
         if (k == 1) {
             const T *x = reinterpret_cast<const T *>(V.x);
-            const T g0 = (T)cf.g[0];
+            const T g0 = F64 ? (T)cf.g[0] : (T)cf.gf[0];
 #pragma unroll
             for (int q = 0; q < NR; q++) acc_out[o + q] = fma(gk, res[q], g0 * x[o + q]);
         } else {
@@ -1136,6 +1156,285 @@ __global__ void __launch_bounds__(WAVE_BLOCK, ((PAIRS || GS2) ? 4 : wave_min_blo
 }
 
 // ------------------------------------------------------------------------------------------
+// Lanes sharing a row (lanes_per_row = LPR > 1).  A warp covers sub-slice h of slice s: the
+// R = 32 / LPR rows slice_row[s] + h*R + (0 .. R-1).  Lane (part, rr) = (lane / R, lane % R)
+// takes the entries j = part, part + LPR, part + 2 LPR, ... of its row, in ascending order,
+// one FMA each into its partial sum; the LPR partial sums are then added by a fixed butterfly
+// over the lane offsets R, 2R, ..., 16 (floating-point addition commutes, so every lane of the
+// row ends with the same value).  Each entry step reads LPR runs of R consecutive words.
+// The blocked lane-task kernel and the unblocked lane power kernel both call this function,
+// so they give identical values.
+// FP32 keeps predicated batches of eight entry steps in flight; FP64 runs full batches of
+// 8, 4, 2 and 1 steps (the step count is the same for the whole warp), so that no FMA is
+// issued past the end of the slice on the FP64 pipe.
+// ------------------------------------------------------------------------------------------
+// Core: rows row0 .. row0 + R - 1 (those below rend), the unit's first entry (j = 0, rr = 0)
+// at colb / valb, L entries per row (the slice length).
+template <typename T, int LPR, int LD = LD_KEEP>
+__device__ __forceinline__ void lane_rows(const int32_t *colb, const T *valb, int32_t row0, int32_t rend,
+                                          int32_t L, int lane, const VecSet &V, int k, const Coefs &cf) {
+    constexpr int R = 32 / LPR;
+    const int part = lane / R, rr = lane - part * R;
+    const int32_t row = row0 + rr;
+    const int32_t *colp = colb + rr;
+    const T *valp = valb + rr;
+    const T *y1 = vec_ro<T>(V, k - 1);
+    const int32_t nu = (L + LPR - 1) / LPR;   // entry steps
+    T acc = (T)0;
+    // NB entry steps u0 .. u0 + NB - 1; entries past the slice length and padding (column
+    // -1) gather row row0 and are dropped by a select
+    auto batch = [&](auto nb_tag, int32_t u0) {
+        constexpr int NB = decltype(nb_tag)::value;
+        int32_t cc[NB];
+        T vv[NB];
+#pragma unroll
+        for (int u = 0; u < NB; u++) {
+            const int32_t j = part + LPR * (u0 + u);
+            const bool in = j < L;
+            cc[u] = in ? ldm<LD>(colp + 32 * j) : -1;
+            vv[u] = in ? ldm<LD>(valp + 32 * j) : (T)0;
+        }
+        T xx[NB];
+#pragma unroll
+        for (int u = 0; u < NB; u++) xx[u] = y1[cc[u] >= 0 ? cc[u] : row0];
+#pragma unroll
+        for (int u = 0; u < NB; u++) {
+            const T f = fma(vv[u], xx[u], acc);
+            acc = cc[u] >= 0 ? f : acc;
+        }
+    };
+    if constexpr (sizeof(T) == 4) {
+        for (int32_t u0 = 0; u0 < nu; u0 += 8) batch(std::integral_constant<int, 8>{}, u0);
+    } else {
+        int32_t u0 = 0;
+        for (; u0 + 8 <= nu; u0 += 8) batch(std::integral_constant<int, 8>{}, u0);
+        if (nu - u0 >= 4) {
+            batch(std::integral_constant<int, 4>{}, u0);
+            u0 += 4;
+        }
+        if (nu - u0 >= 2) {
+            batch(std::integral_constant<int, 2>{}, u0);
+            u0 += 2;
+        }
+        if (nu - u0 >= 1) batch(std::integral_constant<int, 1>{}, u0);
+    }
+#pragma unroll
+    for (int off = R; off < 32; off <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (part == 0 && row < rend) {
+        T a1[1] = {acc};
+        row_finish<T, 1>(a1, row, 1, 0, V, k, cf);
+    }
+}
+
+// Sub-slice h of slice s (LPR > 1).
+template <typename T, int LPR, int LD = LD_KEEP>
+__device__ __forceinline__ void lane_power(const SellView &A, int32_t s, int h, int lane, const VecSet &V,
+                                           int k, const Coefs &cf) {
+    constexpr int R = 32 / LPR;
+    const int32_t r0 = __ldg(A.slice_row + s), r1 = __ldg(A.slice_row + s + 1);
+    const long long o = 32ll * __ldg(A.slice_ptr + s) + h * R;
+    lane_rows<T, LPR, LD>(A.col + o, reinterpret_cast<const T *>(A.val) + o, r0 + h * R, r1,
+                          __ldg(A.slice_len + s), lane, V, k, cf);
+}
+
+// One whole slice, one row per lane (LPR = 1): the unblocked power kernel's row function
+// (row_sum, row_finish) on rows [r0, r1) whose first entries are at colb / valb.
+template <typename T, int LD = LD_KEEP>
+__device__ __forceinline__ void slice_rows(const int32_t *colb, const T *valb, int32_t r0, int32_t r1,
+                                           int32_t L, int lane, const VecSet &V, int k, const Coefs &cf) {
+    const int32_t row = r0 + lane;
+    if (row >= r1) return;
+    const T *y1 = vec_ro<T>(V, k - 1);
+    T acc[1];
+    row_sum<T, 1, false, false, 8, LD>(colb + lane, valb + lane, L, row, y1, 1, 0, acc);
+    row_finish<T, 1>(acc, row, 1, 0, V, k, cf);
+}
+
+// Unblocked powers with lanes sharing rows (one launch per power, one sub-slice per warp).
+template <typename T, int LPR>
+__global__ void __launch_bounds__(256) mpk_lane_power_kernel(SellView A, int64_t n_slices, VecSet V, int k,
+                                                             Coefs cf) {
+    constexpr int R = 32 / LPR;
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    // the matrix is read once per launch (streaming loads for FP64, as mpk_power_kernel)
+    constexpr int LD = sizeof(T) == 8 ? LD_STREAM : LD_KEEP;
+    for (int64_t u = w0; u < n_slices * LPR; u += nw) {
+        const int32_t s = (int32_t)(u / LPR);
+        const int h = (int)(u % LPR);
+        if (__ldg(A.slice_row + s) + h * R >= __ldg(A.slice_row + s + 1)) continue;   // empty
+        lane_power<T, LPR, LD>(A, s, h, lane, V, k, cf);
+    }
+}
+
+// ------------------------------------------------------------------------------------------
+// Lane-task kernel (opts.kernel = 4, or lanes_per_row > 1, single right-hand side).  Tasks
+// (chunk c, power k) of the lane graph, a chunk being a few sub-slices of 32 / LPR rows, in
+// lag-greedy order.  Ticket t belongs to CTA t mod G (G CTAs); inside a CTA the next ticket
+// goes to whichever warp is free first (a shared-memory counter), so no global atomic is
+// taken per task - at tens of thousands of small tasks per power a single dispenser
+// serialises.  A task waits until the counter blocks up to the one holding max(dep_hi(c), c)
+// have finished power k-1 (the CTA shares, per power, the first block not yet seen
+// complete), computes its sub-slices with lane_power (slice_power for LPR = 1, the unblocked
+// kernel's row function), and publishes with one release add to its block counter.
+// Progress: a CTA hands out its tickets in ascending order and every task depends only on
+// lower tickets, so the lowest unfinished ticket has been handed out and can run.  Waits are
+// bounded; on a timeout the error is latched and every warp stops.
+// ------------------------------------------------------------------------------------------
+struct LaneArgs {
+    const int4 *unit_meta;            // {first SELL entry, slice length, first row, row end}
+    const int32_t *chunk_unit;        // first unit of each chunk (n_chunks + 1)
+    const int32_t *cblk_size;         // chunks per counter block
+    const int4 *desc;                 // {chunk | power << 24, counter block, last block waited
+                                      //  for, first unit}
+    int64_t n_tasks;
+    uint32_t *cnt;                    // [(k) * n_cblk + b]
+    uint32_t *kep;                    // launches that ran each local power
+    MpkCtrl *ctrl;
+    int32_t n_cblk;
+    int k0, seg;
+    int one_unit;                     // every chunk is one unit
+
+    uint64_t timeout_ns;
+    uint32_t debug_drop;              // 1: task (chunk 0, power 1) does not publish
+};
+
+template <typename T, int LPR> constexpr int lane_min_blocks() { return 5; }
+
+template <typename T, int LPR, int LD>
+__device__ __forceinline__ void lane_unit(const SellView &A, const int4 &m, int lane, const VecSet &V, int k,
+                                          const Coefs &cf) {
+    const int32_t *colb = A.col + m.x;
+    const T *valb = reinterpret_cast<const T *>(A.val) + m.x;
+    if constexpr (LPR == 1) slice_rows<T, LD>(colb, valb, m.z, m.w, m.y, lane, V, k, cf);
+    else lane_rows<T, LPR, LD>(colb, valb, m.z, m.w, m.y, lane, V, k, cf);
+}
+
+template <typename T, int LPR, int DISP>
+__global__ void __launch_bounds__(WAVE_BLOCK, (lane_min_blocks<T, LPR>())) mpk_lane_kernel(
+    SellView A, VecSet V, Coefs cf, LaneArgs W) {
+    __shared__ uint32_t s_next;
+    __shared__ int32_t s_wm[MPK_MAX_P + 1];
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) s_next = 0;
+    for (int i = threadIdx.x; i <= MPK_MAX_P; i += blockDim.x) s_wm[i] = 0;
+    __syncthreads();
+    // tickets: DISP 0 = dealt round robin to the CTAs and inside a CTA to the first free warp;
+    // 1 = the grid-wide dispenser; 2 = static, warp w of the grid runs w, w + Wg, w + 2 Wg, ...
+    auto take = [&](int64_t prev) -> int64_t {
+        if constexpr (DISP == 2) {
+            return prev < 0 ? (int64_t)blockIdx.x * (WAVE_BLOCK / 32) + (threadIdx.x >> 5)
+                            : prev + (int64_t)gridDim.x * (WAVE_BLOCK / 32);
+        } else {
+            uint32_t j = 0;
+            if (lane == 0) j = DISP == 1 ? atomicAdd(&W.ctrl->ticket, 1u) : atomicAdd(&s_next, 1u);
+            j = __shfl_sync(0xffffffffu, j, 0);
+            return DISP == 1 ? (int64_t)j : (int64_t)blockIdx.x + (int64_t)j * gridDim.x;
+        }
+    };
+    // software pipeline: the next ticket is claimed, and its descriptor and first unit's
+    // metadata loaded, while the current task waits and computes (a warp holds at most two
+    // tickets; the one it has not started is above the one it runs, so the lowest unfinished
+    // ticket is always running)
+    int64_t t = take(-1);
+    int4 d = make_int4(0, 0, 0, 0), mt = make_int4(0, 0, 0, 0);
+    if (t < W.n_tasks) {
+        d = __ldg(&W.desc[t]);
+        mt = __ldg(&W.unit_meta[d.w]);
+    }
+    bool stop = false;
+    while (t < W.n_tasks) {
+        const int64_t tn = take(t);
+        int4 dn = make_int4(0, 0, 0, 0);
+        if (tn < W.n_tasks) dn = __ldg(&W.desc[tn]);
+        const int32_t c = d.x & 0xffffff;
+        const int kl = (int)((uint32_t)d.x >> 24);
+        if (kl > 1) {
+            const int32_t hb = d.z;
+            int32_t wm = *(volatile int32_t *)&s_wm[kl - 1];
+            if (wm <= hb) {
+                const uint32_t mult = *(volatile uint32_t *)(W.kep + kl - 1) + 1u;
+                const uint32_t *cp = W.cnt + (int64_t)(kl - 1) * W.n_cblk;
+                bool timing = false;
+                uint64_t t0 = 0;
+                while (wm <= hb) {
+                    const int32_t b = wm + lane;
+                    bool done = true;
+                    if (b <= hb) {
+                        const uint32_t v = ld_relaxed_u32(cp + b);
+                        done = (int32_t)(v - mult * (uint32_t)__ldg(W.cblk_size + b)) >= 0;
+                    }
+                    const unsigned nd = __ballot_sync(0xffffffffu, !done);
+                    if (nd == 0) {
+                        wm = min(wm + 32, hb + 1);
+                        continue;
+                    }
+                    wm += __ffs(nd) - 1;
+                    uint64_t now = 0;
+                    uint32_t err = 0;
+                    if (lane == 0) {
+                        now = globaltimer_ns();
+                        err = *(volatile uint32_t *)&W.ctrl->error;
+                    }
+                    now = __shfl_sync(0xffffffffu, now, 0);
+                    err = __shfl_sync(0xffffffffu, err, 0);
+                    if (err) {
+                        stop = true;
+                        break;
+                    }
+                    if (!timing) {
+                        timing = true;
+                        t0 = now;
+                    } else if (now - t0 > W.timeout_ns) {
+                        if (lane == 0 && atomicOr(&W.ctrl->error, 1u) == 0u) W.ctrl->err_task = (uint32_t)d.x;
+                        stop = true;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+                if (stop) break;
+                if (lane == 0) atomicMax(&s_wm[kl - 1], wm);
+            }
+            fence_acq_rel_gpu();   // acquire: counters observed before the vectors read below
+        }
+        int4 mn = make_int4(0, 0, 0, 0);
+        if (tn < W.n_tasks) mn = __ldg(&W.unit_meta[dn.w]);
+        const int k = W.k0 + kl;
+        // the last local power is the units' last read in this launch: streaming loads
+        const bool last = kl == W.seg;
+        if (last) lane_unit<T, LPR, LD_STREAM>(A, mt, lane, V, k, cf);
+        else lane_unit<T, LPR, LD_KEEP>(A, mt, lane, V, k, cf);
+        if (!W.one_unit) {
+            const int32_t i1 = __ldg(W.chunk_unit + c + 1);
+            for (int32_t i = d.w + 1; i < i1; i++) {
+                const int4 m2 = __ldg(&W.unit_meta[i]);
+                if (last) lane_unit<T, LPR, LD_STREAM>(A, m2, lane, V, k, cf);
+                else lane_unit<T, LPR, LD_KEEP>(A, m2, lane, V, k, cf);
+            }
+        }
+        // publish: the warp barrier orders every lane's results before lane 0's release add
+        __syncwarp();
+        if (lane == 0 && !(W.debug_drop && c == 0 && kl == 1)) red_release_add_u32(W.cnt + (int64_t)kl * W.n_cblk + d.y, 1u);
+        t = tn;
+        d = dn;
+        mt = mn;
+    }
+    // every CTA gets here; the last one counts this launch for every power it ran
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const uint32_t dn2 = atomicAdd(&W.ctrl->done_ctas, 1u);
+        if (dn2 == gridDim.x - 1) {
+            W.ctrl->ticket = 0;
+            W.ctrl->done_ctas = 0;
+            for (int kk = 1; kk <= W.seg; kk++) W.kep[kk] += 1u;
+            __threadfence();
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
 // Ready-first warp tasks (opts.kernel = 3).  The tasks are the warp-task kernel's (chunk c,
 // local power k), but none is scheduled ahead.  Chunks are dealt to n_shards interleaved
 // shards (chunk c to shard c % n_shards, every shard served by the same number of warps, at
@@ -1469,9 +1768,127 @@ mpk_status launch_wave(mpk_plan_s *P, const SellView &A, int n_rhs, const VecSet
     return MPK_OK;
 }
 
+// Lag-greedy schedule of a lane graph for p local powers and the given slack (cached).
+static mpk_status lane_schedule(LaneGraph *G, int p, int64_t slack, Schedule **out, cudaStream_t s) {
+    const int64_t key = ((int64_t)p << 40) + slack;
+    auto it = G->schedules.find(key);
+    if (it != G->schedules.end()) {
+        *out = it->second.get();
+        return MPK_OK;
+    }
+    std::vector<uint32_t> h;
+    MPK_TRY(mpk_lag_greedy_order(p, G->n_chunks, G->h_dep_hi_blk, slack, h));
+    std::unique_ptr<Schedule> sch(new Schedule());
+    sch->p = p;
+    sch->slack = slack;
+    sch->n_tasks = (int64_t)h.size();
+    std::vector<int4> hd(h.size());
+    for (size_t i = 0; i < h.size(); i++) {
+        const int32_t c = (int32_t)(h[i] & 0xffffffu);
+        hd[i] = make_int4((int)h[i], G->h_chunk_blk[c], G->h_wait_blk[c], G->h_chunk_unit[c]);
+    }
+    MPK_TRY(sch->desc.alloc(std::max<size_t>(hd.size(), 1) * sizeof(int4)));
+    if (!hd.empty())
+        MPK_CUDA(cudaMemcpyAsync(sch->desc.p, hd.data(), hd.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+    MPK_CUDA(cudaStreamSynchronize(s));   // the host vector must outlive the copy
+    *out = sch.get();
+    G->schedules[key] = std::move(sch);
+    return MPK_OK;
+}
+
+template <typename T, int LPR>
+mpk_status launch_lane_blocked(mpk_plan_s *P, const SellView &A, const VecSet &V, const Coefs &cf,
+                               int p, uint32_t flags, cudaStream_t s) {
+    LaneGraph *G = nullptr;
+    MPK_TRY(mpk_get_lane_graph(P, LPR, std::max(1, (int)P->opts.task_units), &G, s));
+    auto kern = P->opts.task_dispatch == 2 ? mpk_lane_kernel<T, LPR, 2>
+                : (P->opts.task_dispatch == 1 ? mpk_lane_kernel<T, LPR, 1> : mpk_lane_kernel<T, LPR, 0>);
+    int occ = 0;
+    MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, WAVE_BLOCK, 0));
+    if (occ < 1) return MPK_ERR_UNIMPLEMENTED;
+    const int per_sm = P->opts.ctas_per_sm > 0 ? std::min(occ, P->opts.ctas_per_sm) : occ;
+    int k0 = 0;
+    while (k0 < p) {
+        const int seg = std::min(P->p_blk, p - k0);
+        const int64_t ntask = (int64_t)seg * G->n_chunks;
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)P->n_sm * per_sm, ceil_div(ntask, WAVE_BLOCK / 32)));
+        // slack: three tickets per resident warp.  A warp holds two tickets (the one it runs
+        // and the next, claimed early so that its descriptor is loaded in the background), so
+        // about two rounds are in flight; with less slack dependants start before their
+        // dependencies finish and wait (measured on the 27-point 160^3 matrix: FP64 p = 4
+        // 2.87 / 1.02 / 0.97 ms at one, two and three tickets per warp)
+        const int64_t slack = P->lane_slack > 0 ? P->lane_slack : 3 * grid * (WAVE_BLOCK / 32);
+        Schedule *sch = nullptr;
+        MPK_TRY(lane_schedule(G, seg, slack, &sch, s));
+        if (sch->n_tasks >= (1ll << 31)) return MPK_ERR_UNIMPLEMENTED;
+        LaneArgs W;
+        memset(&W, 0, sizeof(W));
+        W.unit_meta = G->unit_meta.as<int4>();
+        W.chunk_unit = G->chunk_unit.as<int32_t>();
+        W.one_unit = G->units == 1 ? 1 : 0;
+        W.cblk_size = G->cblk_size.as<int32_t>();
+        W.desc = sch->desc.as<int4>();
+        W.n_tasks = sch->n_tasks;
+        W.cnt = G->cnt.as<uint32_t>();
+        W.kep = G->kep.as<uint32_t>();
+        W.ctrl = P->ctrl.as<MpkCtrl>();
+        W.n_cblk = G->n_cblk;
+        W.k0 = k0;
+        W.seg = seg;
+        W.timeout_ns = (uint64_t)P->opts.wait_timeout_us * 1000ull;
+        W.debug_drop = (flags & MPK_DEBUG_DROP_FLAG) && k0 == 0 ? 1u : 0u;
+        // cooperative (all CTAs co-resident, which the ticket order relies on); launched
+        // through cudaLaunchKernelEx so that stream capture can record it
+        cudaLaunchConfig_t lc;
+        memset(&lc, 0, sizeof(lc));
+        lc.gridDim = dim3((unsigned)grid);
+        lc.blockDim = dim3(WAVE_BLOCK);
+        lc.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        lc.attrs = attr;
+        lc.numAttrs = 1;
+        MPK_CUDA(cudaLaunchKernelEx(&lc, kern, A, V, cf, W));
+        k0 += seg;
+    }
+    return MPK_OK;
+}
+
+// Single right-hand side with lanes sharing rows (or the lane-task kernel): blocked lane
+// tasks, or unblocked launches with the same row function.
+template <typename T>
+mpk_status launch_lane_powers(mpk_plan_s *P, const SellView &A, const VecSet &V, const Coefs &cf,
+                              int p, bool blocked, uint32_t flags, cudaStream_t s) {
+    const int lpr = P->lanes;
+    if (!blocked) {
+        if (lpr == 1) return MPK_ERR_ARG;   // the caller runs the slice power kernel
+        const int64_t warps = (int64_t)P->n_slices * lpr;
+        const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(std::max<int64_t>(warps, 1), 8), 1 << 30);
+        for (int k = 1; k <= p; k++) {
+            if (lpr == 2) mpk_lane_power_kernel<T, 2><<<grid, 256, 0, s>>>(A, P->n_slices, V, k, cf);
+            else if (lpr == 4) mpk_lane_power_kernel<T, 4><<<grid, 256, 0, s>>>(A, P->n_slices, V, k, cf);
+            else mpk_lane_power_kernel<T, 8><<<grid, 256, 0, s>>>(A, P->n_slices, V, k, cf);
+        }
+        MPK_CUDA(cudaGetLastError());
+        return MPK_OK;
+    }
+    switch (lpr) {
+    case 1: return launch_lane_blocked<T, 1>(P, A, V, cf, p, flags, s);
+    case 2: return launch_lane_blocked<T, 2>(P, A, V, cf, p, flags, s);
+    case 4: return launch_lane_blocked<T, 4>(P, A, V, cf, p, flags, s);
+    default: return launch_lane_blocked<T, 8>(P, A, V, cf, p, flags, s);
+    }
+}
+
 template <typename T, int NR>
 mpk_status launch_powers(mpk_plan_s *P, const SellView &A, int n_rhs, const VecSet &V,
                          const Coefs &cf, int p, bool blocked, uint32_t flags, cudaStream_t s) {
+    if constexpr (NR == 1) {
+        // one right-hand side only: wider blocks run one rhs per lane pass (NR = 1, n_rhs > 1)
+        if (P->lane_kernel && n_rhs == 1 && (blocked || P->lanes > 1))
+            return launch_lane_powers<T>(P, A, V, cf, p, blocked, flags, s);
+    }
     if (!blocked) {
         // p back-to-back SpMV launches (Alg. 1)
         const bool pairs = NR == 1 && P->short_rows;
@@ -1595,6 +2012,34 @@ mpk_status mpk_launch_residual(mpk_plan_s *P, const double *x, const double *b, 
 // ready powers the highest goes first, which keeps the window between the leading and the
 // trailing power - the L2 working set - as short as the dependencies allow.
 // ============================================================================================
+mpk_status mpk_lag_greedy_order(int p, int32_t NC, const std::vector<int32_t> &dh, int64_t slack,
+                                std::vector<uint32_t> &h) {
+    std::vector<int32_t> nxt(p + 1, 0);
+    std::vector<int64_t> when((size_t)(p + 1) * std::max(NC, 1), 0);
+    const int64_t total = (int64_t)p * NC;
+    h.reserve(h.size() + (size_t)total);
+    for (int64_t t = 0; t < total; t++) {
+        int pick = 0;
+        for (int k = p; k >= 2 && !pick; k--) {
+            const int32_t c = nxt[k];
+            if (c >= NC) continue;
+            const int32_t hi = dh[c];
+            if (nxt[k - 1] > hi && t - when[(size_t)(k - 1) * NC + hi] >= slack) pick = k;
+        }
+        if (!pick) {
+            if (nxt[1] < NC) pick = 1;
+            else
+                for (int k = 2; k <= p && !pick; k++)
+                    if (nxt[k] < NC && nxt[k - 1] > dh[nxt[k]]) pick = k;
+        }
+        if (!pick) return MPK_ERR_CUDA;   // cannot happen: dependencies are acyclic
+        const int32_t c = nxt[pick]++;
+        when[(size_t)pick * NC + c] = t;
+        h.push_back((uint32_t)c | ((uint32_t)pick << 24));
+    }
+    return MPK_OK;
+}
+
 mpk_status mpk_get_schedule(mpk_plan_s *P, int p, Schedule **out, cudaStream_t s) {
     const int key = p * 1024 + P->sched_type * 512 + (P->wave ? 256 : 0);
     const int64_t slack_now = P->wave ? P->wave_slack : P->sched_slack;
@@ -1617,30 +2062,7 @@ mpk_status mpk_get_schedule(mpk_plan_s *P, int p, Schedule **out, cudaStream_t s
             }
     } else {
         // the warp-task kernel waits for whole counter blocks: schedule against that bound
-        const std::vector<int32_t> &dh = P->wave ? P->h_dep_hi_blk : P->h_dep_hi;
-        std::vector<int32_t> nxt(p + 1, 0);
-        std::vector<int64_t> when((size_t)(p + 1) * std::max(NC, 1), 0);
-        const int64_t slack = slack_now;
-        const int64_t total = (int64_t)p * NC;
-        for (int64_t t = 0; t < total; t++) {
-            int pick = 0;
-            for (int k = p; k >= 2 && !pick; k--) {
-                const int32_t c = nxt[k];
-                if (c >= NC) continue;
-                const int32_t hi = dh[c];
-                if (nxt[k - 1] > hi && t - when[(size_t)(k - 1) * NC + hi] >= slack) pick = k;
-            }
-            if (!pick) {
-                if (nxt[1] < NC) pick = 1;
-                else
-                    for (int k = 2; k <= p && !pick; k++)
-                        if (nxt[k] < NC && nxt[k - 1] > dh[nxt[k]]) pick = k;
-            }
-            if (!pick) return MPK_ERR_CUDA;   // cannot happen: dependencies are acyclic
-            const int32_t c = nxt[pick]++;
-            when[(size_t)pick * NC + c] = t;
-            h.push_back((uint32_t)c | ((uint32_t)pick << 24));
-        }
+        MPK_TRY(mpk_lag_greedy_order(p, NC, P->wave ? P->h_dep_hi_blk : P->h_dep_hi, slack_now, h));
     }
     std::unique_ptr<Schedule> sch(new Schedule());
     sch->p = p;
@@ -1710,6 +2132,7 @@ mpk_status mpk_apply_internal(mpk_plan_s *P, const mpk_coeffs *co, mpk_dtype dty
     const bool use_gamma = final_only && co->gamma;
     if (use_gamma)
         for (int k = 0; k <= p; k++) cf.g[k] = co->gamma[k];
+    coefs_finish(cf);
 
     // host I/O: stage X in and Y out through device buffers
     const void *Xd = X;
@@ -1893,6 +2316,7 @@ mpk_status mpk_gs2_inner(mpk_plan_s *P, mpk_dtype dtype, int gamma, const void *
     A.val = dtype == MPK_F64 ? P->s_jval64.p : P->s_jval32.p;
     Coefs cf;
     memset(&cf, 0, sizeof(cf));
+    coefs_finish(cf);
     const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(std::max<int64_t>(P->n_slices, 1), 8), 1 << 30);
     for (int t = 1; t <= gamma; t++) {
         if (dtype == MPK_F64)
@@ -1924,6 +2348,10 @@ extern "C" mpk_status mpk_plan_sync(mpk_plan_t P, cudaStream_t s) {
         if (P->wave_cnt.p) MPK_CUDA(cudaMemset(P->wave_cnt.p, 0, P->wave_cnt.bytes));
         if (P->wave_kep.p) MPK_CUDA(cudaMemset(P->wave_kep.p, 0, P->wave_kep.bytes));
         if (P->wave_cur.p) MPK_CUDA(cudaMemset(P->wave_cur.p, 0, P->wave_cur.bytes));
+        for (auto &kv : P->lane_graphs) {
+            MPK_CUDA(cudaMemset(kv.second->cnt.p, 0, kv.second->cnt.bytes));
+            MPK_CUDA(cudaMemset(kv.second->kep.p, 0, kv.second->kep.bytes));
+        }
         return MPK_ERR_TIMEOUT;
     }
     return MPK_OK;
@@ -2088,6 +2516,7 @@ extern "C" mpk_status mpk_apply_final_noalloc(mpk_plan_t P, const mpk_coeffs *co
     const bool use_gamma = co->gamma != nullptr;
     if (use_gamma)
         for (int k = 0; k <= p; k++) cf.g[k] = co->gamma[k];
+    coefs_finish(cf);
 
     VecSet V;
     memset(&V, 0, sizeof(V));

@@ -92,6 +92,29 @@ struct Schedule {
     DevBuf desc;    // int4 per ticket: {chunk | (k << 24), first SELL entry, entries, 0}
 };
 
+// Task graph of the lane-task kernel (opts.kernel = 4, or lanes_per_row > 1): units are
+// sub-slices of 32 / lpr rows of the SELL-32 slices (only those holding a row); a chunk is up
+// to `units` consecutive units of one level group; chunks are counted in blocks of up to 32
+// consecutive chunks of one group.  A task (chunk c, power k) waits until every block up to
+// the one holding max(dep_hi(c), c) has finished power k-1.  Built on first use per
+// (lpr, units) and kept by the plan.
+struct LaneGraph {
+    int lpr = 1, units = 1;
+    int32_t n_units = 0, n_chunks = 0, n_cblk = 0;
+    DevBuf unit_code;                  // int32 per unit: slice * lpr + sub-slice, ascending
+    DevBuf unit_meta;                  // int4 per unit: {first SELL entry, slice length,
+                                       // first row, end of the slice's rows}
+    DevBuf chunk_unit;                 // int32 [n_chunks + 1]: first unit of each chunk
+    DevBuf cblk_size;                  // chunks per counter block
+    DevBuf cnt;                        // uint32 [(p_blk + 1) * n_cblk]: counters [(k) * n_cblk + b]
+    DevBuf kep;                        // uint32 per local power: launches that ran it
+    std::vector<int32_t> h_chunk_unit; // first unit of each chunk (n_chunks + 1)
+    std::vector<int32_t> h_chunk_blk;  // counter block of each chunk
+    std::vector<int32_t> h_wait_blk;   // last block a chunk's task waits for
+    std::vector<int32_t> h_dep_hi_blk; // last chunk of that block (the schedule's bound)
+    std::map<int64_t, std::unique_ptr<struct Schedule>> schedules;   // key: p and slack
+};
+
 // The plan: level structure, permuted matrix in SELL-32 form, blocked-task metadata.
 struct mpk_plan_s {
     int device = 0;
@@ -174,6 +197,13 @@ struct mpk_plan_s {
     int blocked_block = 256;
     std::map<int, std::unique_ptr<Schedule>> schedules;
 
+    // lane tasks: lanes per row of the single-rhs kernels (1, 2, 4, 8), whether the blocked
+    // single-rhs path runs the lane-task kernel, and its graphs per (lpr, units)
+    int lanes = 1;
+    int lane_kernel = 0;
+    int64_t lane_slack = 0;            // lag-greedy slack of the lane tasks (0: resident warps)
+    std::map<int, std::unique_ptr<LaneGraph>> lane_graphs;
+
     // workspace for permuted / interleaved vectors; ws_h: the GS2 inner iterates (2 vectors)
     DevBuf ws_x, ws_y, ws_host, ws_h;
     uint32_t latched_error = 0;
@@ -189,6 +219,13 @@ mpk_status exclusive_scan_i32(const int32_t *in, int32_t *out, int64_t n, void *
                               cudaStream_t s);
 
 mpk_status mpk_get_schedule(mpk_plan_s *P, int p, Schedule **out, cudaStream_t s);
+// Lag-greedy task order (tickets: chunk | power << 24) over nc chunks and p powers, each
+// power's chunks ascending; a chunk of power k is emitted once every chunk up to dh[c] has
+// been emitted at power k-1 at least `slack` tickets earlier.
+mpk_status mpk_lag_greedy_order(int p, int32_t nc, const std::vector<int32_t> &dh, int64_t slack,
+                                std::vector<uint32_t> &out);
+// The lane-task graph of a plan for (lpr, units), built on first use (plan.cu).
+mpk_status mpk_get_lane_graph(mpk_plan_s *P, int lpr, int units, LaneGraph **out, cudaStream_t s);
 mpk_status mpk_build_blocks(mpk_plan_s *P, cudaStream_t s);
 
 // Row-sum kernels shared by the MPK and the solver (apply.cu)

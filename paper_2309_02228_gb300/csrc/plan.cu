@@ -817,7 +817,7 @@ extern "C" mpk_status mpk_plan_opts_default(mpk_plan_opts *o) {
     o->slack_tasks = 0;
     o->block_threads = 256;
     o->stage = -1;
-    o->kernel = 0;
+    o->kernel = 4;
     o->blocked = -1;
     o->jacobi = 0;
     return MPK_OK;
@@ -1277,9 +1277,119 @@ static mpk_status plan_create_impl(const mpk_csr *A, int32_t p_max, const mpk_pl
     // warp tasks: four tasks per resident warp (32 per SM) - measured best on the 27-point
     // 160^3 matrix in FP32 and FP64; smaller slack makes warps wait for their dependencies
     P->wave_slack = o.slack_tasks > 0 ? o.slack_tasks : 4ll * 32 * P->n_sm;
+    // lane tasks: lanes per row of the single-rhs kernels (automatic: 1 - sharing rows
+    // measured slower in both precisions on the 27-point 160^3 matrix, unblocked and blocked)
+    if (o.lanes_per_row == 0) P->lanes = 1;
+    else if (o.lanes_per_row == 1 || o.lanes_per_row == 2 || o.lanes_per_row == 4 || o.lanes_per_row == 8)
+        P->lanes = o.lanes_per_row;
+    else return MPK_ERR_ARG;
+    if (o.task_units < 0 || o.kernel < 0 || o.kernel > 4 || o.task_dispatch < 0 || o.task_dispatch > 2)
+        return MPK_ERR_ARG;
+    P->lane_kernel = (o.kernel == 4 || P->lanes > 1) ? 1 : 0;
+    P->lane_slack = o.slack_tasks > 0 ? o.slack_tasks : 0;
     MPK_CUDA(cudaStreamSynchronize(s));
     auto t1 = std::chrono::steady_clock::now();
     P->create_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+    return MPK_OK;
+}
+
+// ---- lane-task graph: units = sub-slices of 32 / lpr rows, chunks of `units` units inside
+// one level group, dependency ranges over the rows (as for the slice chunks), counter blocks
+// of up to 32 chunks of one group
+mpk_status mpk_get_lane_graph(mpk_plan_s *P, int lpr, int units, LaneGraph **out, cudaStream_t s) {
+    if (lpr != 1 && lpr != 2 && lpr != 4 && lpr != 8) return MPK_ERR_ARG;
+    if (units < 1) units = 1;
+    const int key = lpr * 65536 + units;
+    auto it = P->lane_graphs.find(key);
+    if (it != P->lane_graphs.end()) {
+        *out = it->second.get();
+        return MPK_OK;
+    }
+    std::unique_ptr<LaneGraph> G(new LaneGraph());
+    G->lpr = lpr;
+    G->units = units;
+    const int64_t n = P->n;
+    const int R = 32 / lpr;
+    std::vector<int32_t> sr(P->n_slices + 1, 0), slen(P->n_slices + 1, 0);
+    std::vector<long long> sp(P->n_slices + 1, 0);
+    if (P->n_slices > 0) {
+        MPK_CUDA(cudaMemcpyAsync(sr.data(), P->slice_row.p, (P->n_slices + 1) * 4, cudaMemcpyDeviceToHost, s));
+        MPK_CUDA(cudaMemcpyAsync(slen.data(), P->slice_len.p, P->n_slices * 4, cudaMemcpyDeviceToHost, s));
+        MPK_CUDA(cudaMemcpyAsync(sp.data(), P->slice_ptr.p, (P->n_slices + 1) * 8, cudaMemcpyDeviceToHost, s));
+    }
+    MPK_CUDA(cudaStreamSynchronize(s));
+    std::vector<int32_t> code, cu, crow, cgroup;
+    std::vector<int4> meta;
+    int32_t sl = 0;
+    for (int32_t g = 0; g < P->n_groups; g++) {
+        const int32_t gend = P->h_level_ptr[P->h_group_ptr[g + 1]];
+        int in_chunk = 0;
+        for (; sl < P->n_slices && sr[sl] < gend; sl++) {
+            const int32_t rows = sr[sl + 1] - sr[sl];
+            for (int h = 0; h * R < rows; h++) {
+                if (in_chunk == 0 || in_chunk == units) {
+                    cu.push_back((int32_t)code.size());
+                    crow.push_back(sr[sl] + h * R);
+                    cgroup.push_back(g);
+                    in_chunk = 0;
+                }
+                code.push_back(sl * lpr + h);
+                meta.push_back(make_int4((int)(32ll * sp[sl] + h * R), slen[sl], sr[sl] + h * R, sr[sl + 1]));
+                in_chunk++;
+            }
+        }
+    }
+    G->n_units = (int32_t)code.size();
+    G->n_chunks = (int32_t)cu.size();
+    cu.push_back(G->n_units);
+    crow.push_back((int32_t)n);
+    MPK_TRY(upload(G->unit_code, code, s));
+    MPK_TRY(upload(G->unit_meta, meta, s));
+    MPK_TRY(upload(G->chunk_unit, cu, s));
+    G->h_chunk_unit = cu;
+    std::vector<int32_t> dep_hi(G->n_chunks, 0);
+    if (G->n_chunks > 0) {
+        DevBuf d_crow, row_chunk, dlo, dhi;
+        MPK_TRY(upload(d_crow, crow, s));
+        MPK_TRY(row_chunk.alloc_on(n * 4, s));
+        MPK_TRY(dlo.alloc_on((size_t)G->n_chunks * 4, s));
+        MPK_TRY(dhi.alloc_on((size_t)G->n_chunks * 4, s));
+        row_chunk_kernel<<<(unsigned)std::min<int64_t>(G->n_chunks, 65535), 256, 0, s>>>(d_crow.as<int32_t>(), G->n_chunks, row_chunk.as<int32_t>());
+        fill_i32_kernel<<<grid_for(G->n_chunks), 256, 0, s>>>(dlo.as<int32_t>(), G->n_chunks, 0x7fffffff);
+        fill_i32_kernel<<<grid_for(G->n_chunks), 256, 0, s>>>(dhi.as<int32_t>(), G->n_chunks, -1);
+        dep_kernel<<<grid_for(n), 256, 0, s>>>(P->rp.as<int32_t>(), P->ci.as<int32_t>(), row_chunk.as<int32_t>(), n,
+                                               P->opts.assume_symmetric ? 0 : 1, dlo.as<int32_t>(), dhi.as<int32_t>());
+        MPK_CUDA(cudaGetLastError());
+        MPK_CUDA(cudaMemcpyAsync(dep_hi.data(), dhi.p, (size_t)G->n_chunks * 4, cudaMemcpyDeviceToHost, s));
+        MPK_CUDA(cudaStreamSynchronize(s));
+    }
+    std::vector<int32_t> cbs, blast;
+    G->h_chunk_blk.assign(G->n_chunks, 0);
+    for (int32_t c = 0; c < G->n_chunks; c++) {
+        if (c == 0 || cgroup[c] != cgroup[c - 1] || cbs.back() == 32) {
+            cbs.push_back(0);
+            blast.push_back(c);
+        }
+        cbs.back()++;
+        blast.back() = c;
+        G->h_chunk_blk[c] = (int32_t)cbs.size() - 1;
+    }
+    G->n_cblk = (int32_t)cbs.size();
+    G->h_wait_blk.assign(G->n_chunks, 0);
+    G->h_dep_hi_blk.assign(G->n_chunks, 0);
+    for (int32_t c = 0; c < G->n_chunks; c++) {
+        const int32_t hi = std::max(dep_hi[c], c);
+        G->h_wait_blk[c] = G->h_chunk_blk[hi];
+        G->h_dep_hi_blk[c] = blast[G->h_wait_blk[c]];
+    }
+    MPK_TRY(upload(G->cblk_size, cbs, s));
+    MPK_TRY(G->cnt.alloc((size_t)(P->p_blk + 1) * std::max(G->n_cblk, 1) * 4));
+    MPK_CUDA(cudaMemsetAsync(G->cnt.p, 0, G->cnt.bytes, s));
+    MPK_TRY(G->kep.alloc((MPK_MAX_P + 1) * 4));
+    MPK_CUDA(cudaMemsetAsync(G->kep.p, 0, G->kep.bytes, s));
+    MPK_CUDA(cudaStreamSynchronize(s));   // host vectors above outlive their copies
+    *out = G.get();
+    P->lane_graphs[key] = std::move(G);
     return MPK_OK;
 }
 

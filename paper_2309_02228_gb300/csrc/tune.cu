@@ -1,5 +1,5 @@
-// Autotuner for one call shape: plan options (blocked or p x SpMV, blocked kernel, chunk size,
-// level-group budget) timed on the caller's matrix.  The paper picks its blocking depth p_opt
+// Autotuner for one call shape: plan options (blocked or p x SpMV, blocked kernel, slack, lanes
+// per row, task and chunk size, level-group budget) timed on the caller's matrix.  The paper picks its blocking depth p_opt
 // and cache size C by hand per machine (Sec. 3, Sec. 4); on this part the best choice depends
 // on precision and on the number of right-hand sides (FP64 is bound by FP64 FMA issue, FP32 by
 // memory, wide blocks of right-hand sides by vector gathers), so it is measured.
@@ -18,23 +18,33 @@ __global__ void fill_kernel(float *p32, double *p64, int64_t n, double v) {
     }
 }
 
-// the candidate list: deterministic, the caller's base options first
-std::vector<mpk_plan_opts> candidates(const mpk_plan_opts &base, int64_t l2) {
+// the candidate list: deterministic, the caller's base options first.  Axes: blocked or
+// p x SpMV; the blocked kernel (lane tasks, warp tasks with a ticket dispenser); the lane
+// tasks' slack (resident_warps: about one ticket per resident warp) and task size; the warp
+// tasks' chunk size; the level-group budget.  Lanes per row stays the base's: it changes the
+// summation order, and every candidate must give the base's values bit for bit.
+std::vector<mpk_plan_opts> candidates(const mpk_plan_opts &base, int64_t l2, int64_t resident_warps) {
     std::vector<mpk_plan_opts> c;
-    auto add = [&](int blocked, int kernel, int cs, int64_t budget) {
+    auto add = [&](int blocked, int kernel, int cs, int64_t budget, int64_t slack, int lanes, int units) {
         mpk_plan_opts o = base;
         o.blocked = blocked;
         o.kernel = kernel;
         if (cs > 0) o.chunk_slices = cs;
         if (budget > 0) o.l2_budget_bytes = budget;
+        if (slack > 0) o.slack_tasks = (int32_t)slack;
+        if (lanes > 0) o.lanes_per_row = lanes;
+        if (units > 0) o.task_units = units;
         c.push_back(o);
     };
     c.push_back(base);
-    add(0, base.kernel, 0, 0);                // p back-to-back SpMVs
-    for (int cs : {2, 4, 8, 16}) add(1, 0, cs, 0);
-    add(1, 2, 8, 0);                          // static round robin
-    add(1, 0, 8, l2 / 4);                     // smaller level groups
-    add(1, 0, 8, l2);                         // larger level groups
+    add(0, base.kernel, 0, 0, 0, 0, 0);                        // p back-to-back SpMVs
+    add(1, 4, 0, 0, 2 * resident_warps, 0, 0);                 // lane tasks, less slack
+    add(1, 4, 0, 0, 4 * resident_warps, 0, 0);                 // lane tasks, more slack
+    add(1, 4, 0, 0, 0, 0, 2);                                  // two slices per task
+    add(1, 0, 4, 0, 0, 0, 0);                                  // warp tasks, 4-slice chunks
+    add(1, 0, 8, 0, 0, 0, 0);                                  // warp tasks, 8-slice chunks
+    add(1, 4, 0, l2 / 4, 0, 0, 0);                             // smaller level groups
+    add(1, 4, 0, l2, 0, 0, 0);                                 // larger level groups
     return c;
 }
 
@@ -73,7 +83,8 @@ extern "C" mpk_status mpk_autotune(const mpk_csr *A, int32_t p, const mpk_coeffs
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     MPK_CUDA(cudaEventCreate(&e0));
     MPK_CUDA(cudaEventCreate(&e1));
-    const std::vector<mpk_plan_opts> cand = candidates(b, l2);
+    // the lane-task kernel keeps five CTAs of eight warps per SM resident
+    const std::vector<mpk_plan_opts> cand = candidates(b, l2, (int64_t)n_sm * 40);
     double best_ms = 1e300, base_ms = 1e300;
     int best_i = -1, trials = 0;
     mpk_status st = MPK_OK;

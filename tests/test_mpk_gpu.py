@@ -156,16 +156,21 @@ def test_mpk_fp64_vs_oracle(m, basis, name):
     den = abs_powers(A, cf, x)
     rp, ci, vv = to_dev(A)
     # kernel 0 = warp tasks with a ticket dispenser, 1 = CTA tasks, 2 = warp tasks in static
-    # round robin, 3 = ready-first warp tasks; slack 7 makes most warp tasks wait for their
-    # dependencies
-    for budget, cs, stage, sched, kern, slack in ((30_000, 1, -1, 1, 0, 0), (300_000, 2, 0, 1, 1, 0),
-                                                  (1 << 30, 8, -1, 0, 0, 0), (100_000, 4, -1, 0, 2, 0),
-                                                  (60_000, 1, -1, 1, 0, 7), (60_000, 2, -1, 1, 2, 7),
-                                                  (30_000, 1, -1, 1, 1, 0), (30_000, 1, -1, 1, 3, 0),
-                                                  (1 << 30, 8, -1, 1, 3, 0)):
+    # round robin, 3 = ready-first warp tasks, 4 = lane tasks (lanes sharing rows, sub-slice
+    # tasks); slack 7 makes most warp tasks wait for their dependencies.  The last field is
+    # lanes_per_row (the unblocked comparison runs the same row function)
+    for budget, cs, stage, sched, kern, slack, lanes in (
+            (30_000, 1, -1, 1, 0, 0, 1), (300_000, 2, 0, 1, 1, 0, 1),
+            (1 << 30, 8, -1, 0, 0, 0, 1), (100_000, 4, -1, 0, 2, 0, 1),
+            (60_000, 1, -1, 1, 0, 7, 1), (60_000, 2, -1, 1, 2, 7, 1),
+            (30_000, 1, -1, 1, 1, 0, 1), (30_000, 1, -1, 1, 3, 0, 1),
+            (1 << 30, 8, -1, 1, 3, 0, 1),
+            (30_000, 1, -1, 1, 4, 0, 1), (60_000, 3, -1, 1, 4, 7, 1),
+            (30_000, 1, -1, 1, 4, 0, 2), (60_000, 2, -1, 1, 4, 7, 4),
+            (1 << 30, 1, -1, 1, 4, 0, 8), (100_000, 5, -1, 1, 4, 3, 4)):
         plan = m.mpk_plan_create(rp, ci, vv, p, m.mpk_plan_opts_default(
             l2_budget_bytes=budget, chunk_slices=cs, stage=stage, schedule=sched, kernel=kern,
-            slack_tasks=slack, blocked=1))
+            slack_tasks=slack, blocked=1, lanes_per_row=lanes, task_units=cs))
         got_b = _run(m, plan, A, cf, x)
         got_u = _run(m, plan, A, cf, x, flags=m.MPK_UNBLOCKED)
         assert np.array_equal(got_b, got_u)            # blocked == unblocked, bit for bit
@@ -185,12 +190,15 @@ def test_mpk_fp32_vs_oracle(m, name):
     ref = oracle.mpk(A32, p, cf, x)
     den = abs_powers(A32, cf, x)
     rp, ci, vv = to_dev(A, np.float32)
-    plan = m.mpk_plan_create(rp, ci, vv, p, m.mpk_plan_opts_default(l2_budget_bytes=50_000, blocked=1))
-    got = _run(m, plan, A, cf, x, dtype=torch.float32)
-    got_u = _run(m, plan, A, cf, x, dtype=torch.float32, flags=m.MPK_UNBLOCKED)
-    assert np.array_equal(got, got_u)
-    for k in range(1, p + 1):
-        assert max_rel_err(got[k], ref[k], den[k]) <= 64 * k * U32
+    # lanes_per_row 0 is the automatic choice (4 in FP32)
+    for lanes, kern, units in ((0, 0, 1), (1, 0, 1), (1, 4, 2), (2, 4, 1), (4, 4, 3), (8, 4, 1)):
+        plan = m.mpk_plan_create(rp, ci, vv, p, m.mpk_plan_opts_default(
+            l2_budget_bytes=50_000, blocked=1, lanes_per_row=lanes, kernel=kern, task_units=units))
+        got = _run(m, plan, A, cf, x, dtype=torch.float32)
+        got_u = _run(m, plan, A, cf, x, dtype=torch.float32, flags=m.MPK_UNBLOCKED)
+        assert np.array_equal(got, got_u), lanes
+        for k in range(1, p + 1):
+            assert max_rel_err(got[k], ref[k], den[k]) <= 64 * k * U32, (lanes, k)
 
 
 def test_permuted_io_and_y0_is_x(m):
@@ -240,8 +248,8 @@ def test_block_mpk_n_rhs(m, n_rhs, interleaved):
             assert max_rel_err(got[k, :, q], ref[k], den[k]) <= 64 * k * U32
 
 
-@pytest.mark.parametrize("kern", [0, 1, 2, 3])
-def test_final_only_gamma_and_segments(m, kern):
+@pytest.mark.parametrize("kern,lanes", [(0, 1), (1, 1), (2, 1), (3, 1), (4, 1), (4, 4)])
+def test_final_only_gamma_and_segments(m, kern, lanes):
     import torch
     A = MATS["diff7_10"]
     p = 9
@@ -253,7 +261,8 @@ def test_final_only_gamma_and_segments(m, kern):
     rp, ci, vv = to_dev(A)
     # p_blk = 4 -> segments of 4, 4, 1 powers (the remainder launch)
     plan = m.mpk_plan_create(rp, ci, vv, p, m.mpk_plan_opts_default(l2_budget_bytes=60_000, p_blk=4,
-                                                                     kernel=kern, slack_tasks=5, blocked=1))
+                                                                     kernel=kern, slack_tasks=5, blocked=1,
+                                                                     lanes_per_row=lanes))
     full = _run(m, plan, A, cf, x)
     for k in range(1, p + 1):
         assert max_rel_err(full[k], ref[k], den[k]) <= 64 * k * U64
@@ -286,8 +295,8 @@ def test_host_io(m):
     assert np.array_equal(Yh.numpy().reshape(p + 1, -1), dev)
 
 
-@pytest.mark.parametrize("kern", [0, 1, 2, 3])
-def test_timeout_is_reported_and_plan_recovers(m, kern):
+@pytest.mark.parametrize("kern,lanes", [(0, 1), (1, 1), (2, 1), (3, 1), (4, 1), (4, 4)])
+def test_timeout_is_reported_and_plan_recovers(m, kern, lanes):
     """A completion that nothing publishes: the waits on it run out (short bound), the call
     reports MPK_ERR_TIMEOUT, and the plan works again afterwards."""
     A = MATS["s27_12"]
@@ -296,7 +305,7 @@ def test_timeout_is_reported_and_plan_recovers(m, kern):
     x = mi.uniform_vectors(A.n, 0)[0]
     rp, ci, vv = to_dev(A)
     plan = m.mpk_plan_create(rp, ci, vv, p, m.mpk_plan_opts_default(l2_budget_bytes=30_000, wait_timeout_us=20_000,
-                                                                     kernel=kern, blocked=1))
+                                                                     kernel=kern, blocked=1, lanes_per_row=lanes))
     import torch
     X = torch.from_numpy(x).cuda()
     Y = torch.empty((p + 1) * A.n, dtype=torch.float64, device="cuda")
@@ -345,8 +354,8 @@ def test_automatic_blocked_choice(m):
         torch.cuda.empty_cache()
 
 
-@pytest.mark.parametrize("kern", [0, 3])
-def test_graph_capture_replays_the_blocked_kernel(m, kern):
+@pytest.mark.parametrize("kern,lanes", [(0, 1), (3, 1), (4, 4)])
+def test_graph_capture_replays_the_blocked_kernel(m, kern, lanes):
     """A blocked mpk_apply captured in a CUDA graph (after one ordinary call, which builds the
     schedule) replays correctly: the per-power launch counts the dependency waits compare
     against live in device memory, so each replay is a fresh launch.  Each replay's result
@@ -357,7 +366,8 @@ def test_graph_capture_replays_the_blocked_kernel(m, kern):
     cf = BASES["newton"](p)
     rp, ci, vv = to_dev(A)
     plan = m.mpk_plan_create(rp, ci, vv, p, m.mpk_plan_opts_default(l2_budget_bytes=40_000, blocked=1,
-                                                                     slack_tasks=5, kernel=kern))
+                                                                     slack_tasks=5, kernel=kern,
+                                                                     lanes_per_row=lanes))
     X = torch.from_numpy(mi.uniform_vectors(A.n, 2)[0]).cuda()
     Y = torch.empty((p + 1) * A.n, dtype=torch.float64, device="cuda")
     m.mpk_apply(plan, cf, X, Y)
@@ -386,15 +396,17 @@ def test_maximum_power_count_and_rhs_block(m):
     cf = sstep.chebyshev_coeffs(0.0, 2.2 * float(np.abs(A.val).max()), p)
     x = mi.uniform_vectors(A.n, 9)[0]
     rp, ci, vv = to_dev(A)
-    plan = m.mpk_plan_create(rp, ci, vv, p, m.mpk_plan_opts_default(l2_budget_bytes=40_000, blocked=1))
-    assert m.mpk_plan_stats(plan)["p_blk"] == p
-    got = _run(m, plan, A, cf, x)
-    got_u = _run(m, plan, A, cf, x, flags=m.MPK_UNBLOCKED)
-    assert np.array_equal(got, got_u)
     ref = oracle.mpk(A, p, cf, x)
     den = abs_powers(A, cf, x)
-    for k in range(1, p + 1):
-        assert max_rel_err(got[k], ref[k], den[k]) <= 64 * k * U64, k
+    for lanes in (1, 4):
+        plan = m.mpk_plan_create(rp, ci, vv, p, m.mpk_plan_opts_default(l2_budget_bytes=40_000, blocked=1,
+                                                                         lanes_per_row=lanes))
+        assert m.mpk_plan_stats(plan)["p_blk"] == p
+        got = _run(m, plan, A, cf, x)
+        got_u = _run(m, plan, A, cf, x, flags=m.MPK_UNBLOCKED)
+        assert np.array_equal(got, got_u)
+        for k in range(1, p + 1):
+            assert max_rel_err(got[k], ref[k], den[k]) <= 64 * k * U64, (lanes, k)
     # the largest block of right-hand sides
     B = mi.random_sparse(300, 0.02, 4, symmetric=True, diag=True)
     B32 = mi.CSR(B.row_ptr, B.col, B.val.astype(np.float32).astype(np.float64))
