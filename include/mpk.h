@@ -512,6 +512,45 @@ mpk_status sstep_cg_solve(mpk_plan_t A, const double *b, double *x, const mpk_cg
                           mpk_cg_info *info, cudaStream_t stream);
 
 /* ------------------------------------------------------------------------------------------
+ * The orthogonalisation steps of the solvers on their own: the same kernels, callable on the
+ * caller's tall-skinny blocks (all pointers DEVICE, column-major, FP64 results).  Asynchronous
+ * on the stream; each call allocates (and frees, stream-ordered) a small partial-sum buffer.
+ *
+ * Precision of every Gram product in a basis of FP32 values: the products are summed in FP32
+ * over at most 32 terms per lane, those block sums over the lanes by a fixed FP32 tree of at
+ * most eight levels, and the results in FP64 in a fixed order, so for each entry
+ *     |G^ - G| <= (40 u32 + m u64) (|X|^T |Y|),   u32 = 2^-24, u64 = 2^-53,
+ * with m the FP64 additions (about n / 1024); about 2.4e-6 relative to |X|^T |Y| for the sizes
+ * of this library's workloads.  An FP64 basis sums in FP64 throughout.  Results do not
+ * depend on timing (fixed summation order).
+ * ---------------------------------------------------------------------------------------- */
+
+/* Block classical Gram-Schmidt's projection coefficients and CholQR's Gram (Sec. 4,
+ * Alg. 3(c), BOrtho and TSQR): G = X^T Y for X n x K (leading dimension ldx >= n) and Y n x S
+ * (ldy >= n), both of type dtype; G: K x S FP64, column-major (G[a + b K]).
+ * 1 <= K <= 145, 1 <= S <= 16.  n = 0 writes zeros.  MPK_ERR_ARG on bad sizes or NULLs. */
+mpk_status mpk_gram(mpk_dtype dtype, const void *X, int64_t ldx, int32_t K, const void *Y,
+                    int64_t ldy, int32_t S, int64_t n, double *G, cudaStream_t stream);
+
+/* Block update of the orthogonalisation (Sec. 4, Alg. 3(c)): W <- (W - Q C) Rinv in place,
+ * row by row in dtype, with Q n x K1 (ldq >= n; K1 = 0 skips the projection and Q, C may be
+ * NULL), W n x S (ldw >= n), C K1 x S FP64 column-major, Rinv S x S FP64 column-major of which
+ * the upper triangle (rows <= columns) is used - BCGS's projection W - Q C, then CholQR's
+ * W R^-1.  0 <= K1 <= 129, 1 <= S <= 16.  G (may be NULL): receives W^T W of the new W
+ * (S x S FP64), fused into the update for S <= 8 as in the solver, a separate Gram otherwise. */
+mpk_status mpk_block_update(mpk_dtype dtype, const void *Q, int64_t ldq, int32_t K1, void *W,
+                            int64_t ldw, int32_t S, const double *C, const double *Rinv,
+                            int64_t n, double *G, cudaStream_t stream);
+
+/* The Gram matrix of s-step CG's basis storage (see sstep_cg_solve): Y holds s + 1 pairs of
+ * interleaved vectors, pair k at Y + 2 k ldv with its two values for row i at 2i and 2i + 1;
+ * G = Y^T Y over the M = 2s + 2 storage columns in pair order (column 2k + q is slot q of pair
+ * k), written as the full M x M FP64 matrix, column-major.  1 <= s <= 15; Y 16-byte aligned,
+ * ldv >= n rounded up to even (FP32: ldv even).  MPK_ERR_ARG otherwise. */
+mpk_status mpk_gram_pairs(mpk_dtype dtype, const void *Y, int64_t ldv, int32_t s, int64_t n,
+                          double *G, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------------------------
  * Serving: a continuously batched stream of s-step GMRES solves on one GPU.
  * ---------------------------------------------------------------------------------------- */
 typedef struct {

@@ -174,6 +174,9 @@ _SIGS = [
                                     ctypes.POINTER(mpk_plan_opts), ctypes.POINTER(mpk_tune_info), _P]),
     ("mpk_cg_opts_default", ctypes.c_int, [ctypes.POINTER(mpk_cg_opts)]),
     ("sstep_cg_solve", ctypes.c_int, [_P, _P, _P, ctypes.POINTER(mpk_cg_opts), ctypes.POINTER(mpk_cg_info), _P]),
+    ("mpk_gram", ctypes.c_int, [ctypes.c_int, _P, _I64, _I32, _P, _I64, _I32, _I64, _P, _P]),
+    ("mpk_block_update", ctypes.c_int, [ctypes.c_int, _P, _I64, _I32, _P, _I64, _I32, _P, _P, _I64, _P, _P]),
+    ("mpk_gram_pairs", ctypes.c_int, [ctypes.c_int, _P, _I64, _I32, _I64, _P, _P]),
     ("mpk_server_opts_default", ctypes.c_int, [ctypes.POINTER(mpk_server_opts)]),
     ("mpk_server_create", ctypes.c_int, [ctypes.POINTER(mpk_server_opts), ctypes.POINTER(_P)]),
     ("mpk_server_submit", ctypes.c_int, [_P, _I64, _I64, _P, _P, _P, _P, _P, ctypes.POINTER(_I64)]),
@@ -565,3 +568,71 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------------------------
+# Orthogonalisation steps (the solvers' Gram and block-update kernels on caller blocks)
+# ---------------------------------------------------------------------------------------------
+def _colmajor(t, name):
+    """(n, k) view of a column-major block given as a 2-D tensor of shape (k, ld) (row q is
+    column q) - the layout the C ABI expects; returns (ld, k)."""
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError("%s: a contiguous (columns, ld) tensor is expected" % name)
+    return t.stride(0), t.shape[0]
+
+
+def mpk_gram(X, Y, n=None, stream=None):
+    """G = X^T Y (FP64, K x S) for column blocks X (K, ldx) and Y (S, ldy) on the device, both
+    float32 or both float64; the first n rows of each column are used (default: all)."""
+    import torch
+    if X.dtype != Y.dtype:
+        raise ValueError("X and Y must have the same dtype")
+    ldx, K = _colmajor(X, "X")
+    ldy, S = _colmajor(Y, "Y")
+    n = min(X.shape[1], Y.shape[1]) if n is None else int(n)
+    if n > X.shape[1] or n > Y.shape[1]:
+        raise ValueError("n exceeds the columns' length")
+    G = torch.empty((S, K), dtype=torch.float64, device=X.device)   # row b = column b of G
+    _check(lib().mpk_gram(_dtype_code(X.dtype), _ptr(X), ldx, K, _ptr(Y), ldy, S, n, _ptr(G),
+                          _stream_ptr(stream)), "mpk_gram")
+    return G.t()
+
+
+def mpk_block_update(Q, W, C, Rinv, n=None, gram=True, stream=None):
+    """W <- (W - Q C) Rinv in place (Q: (K1, ldq) or None, W: (S, ldw), C: (K1, S) FP64,
+    Rinv: (S, S) FP64, upper triangle used); returns W^T W of the new W (FP64) or None."""
+    import torch
+    ldw, S = _colmajor(W, "W")
+    K1, ldq = 0, 0
+    if Q is not None:
+        if Q.dtype != W.dtype:
+            raise ValueError("Q and W must have the same dtype")
+        ldq, K1 = _colmajor(Q, "Q")
+    n = W.shape[1] if n is None else int(n)
+    if n > W.shape[1] or (Q is not None and n > Q.shape[1]):
+        raise ValueError("n exceeds the columns' length")
+    Cd = None
+    if K1:
+        if tuple(C.shape) != (K1, S):
+            raise ValueError("C must be K1 x S")
+        Cd = C.to(W.device, torch.float64).t().contiguous()          # column-major K1 x S
+    if tuple(Rinv.shape) != (S, S):
+        raise ValueError("Rinv must be S x S")
+    Rd = Rinv.to(W.device, torch.float64).t().contiguous()
+    G = torch.empty((S, S), dtype=torch.float64, device=W.device) if gram else None
+    _check(lib().mpk_block_update(_dtype_code(W.dtype), _ptr(Q), ldq, K1, _ptr(W), ldw, S, _ptr(Cd),
+                                  _ptr(Rd), n, _ptr(G), _stream_ptr(stream)), "mpk_block_update")
+    return G.t() if gram else None
+
+
+def mpk_gram_pairs(Y, s, n, ldv, stream=None):
+    """Gram of s-step CG's basis storage: Y a flat device tensor holding s + 1 pairs of 2 ldv
+    values; returns the (2s + 2) x (2s + 2) FP64 matrix over the storage columns in pair order."""
+    import torch
+    if Y.numel() < (s + 1) * 2 * ldv:
+        raise ValueError("Y holds fewer than s + 1 pairs of 2 ldv values")
+    M = 2 * s + 2
+    G = torch.empty((M, M), dtype=torch.float64, device=Y.device)
+    _check(lib().mpk_gram_pairs(_dtype_code(Y.dtype), _ptr(Y), ldv, s, n, _ptr(G), _stream_ptr(stream)),
+           "mpk_gram_pairs")
+    return G.t()

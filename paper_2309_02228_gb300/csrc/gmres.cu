@@ -99,18 +99,45 @@ static inline unsigned redp_grid(int m) { return (unsigned)((m + REDP_WARPS - 1)
 // A warp owns a tile of CT columns of X and streams 32 rows per step straight from global
 // memory (lane l takes row r0 + l: every column load is one coalesced 128-byte line); each lane
 // keeps the CT x S products of its rows in registers (64 FMAs per CT + S loads).  With fewer
-// tiles than warps, the warps of a tile split the steps.  Sums: FP32 per lane over its rows,
-// an FP32 shuffle tree over the 32 lanes, FP64 over the warps of a tile (fixed order) and
-// over CTAs (one partial per CTA, reduced by reduce_partials_kernel).
+// tiles than warps, the warps of a tile split the steps.
+// Precision (FP32 basis): a lane sums its products in FP32 over one visit of the CTA to a
+// range of GRAM_RANGE rows, i.e. at most GRAM_RANGE / 32 = 32 terms; the 32 lanes' block sums
+// are then added by a fixed five-level FP32 tree (lane_halve) and the result is added to FP64
+// totals in shared memory; the totals of the warps of a tile and of the CTAs are summed in
+// FP64 in a fixed order (reduce_partials_kernel).  So |G^ - G| <= (37 u32 + m u64) |X|^T |Y|
+// entrywise (u32 = 2^-24, m the number of FP64 additions), about 2.2e-6 relative to |X|^T|Y|.
 // ------------------------------------------------------------------------------------------
-constexpr int GRAM_RANGE = 2048;       // rows a CTA takes per visit
+constexpr int GRAM_RANGE = 1024;       // rows a CTA takes per visit
+
+// Sum over the 32 lanes of each of the N values of every lane, by recursive halving: at the
+// level of offset o a lane keeps one half of its values (the upper half when lane & o), adds
+// its partner's copy of that half, and sends the other half.  After the five levels lane l
+// holds N / 32 values, the sums of entries base .. base + N/32 - 1 over all lanes, each a fixed
+// five-level tree.  62 shuffles for N = 64 instead of 320 for one butterfly per value.
+template <typename T, int N>
+__device__ __forceinline__ int lane_halve(T (&v)[N], int lane) {
+    static_assert(N >= 32 && (N & (N - 1)) == 0, "power of two, at least one value per lane");
+    int base = 0;
+#pragma unroll
+    for (int o = 16, c = N; o >= 1; o >>= 1, c >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < c / 2; i++) {
+            const T keep = up ? v[i + c / 2] : v[i];
+            const T send = up ? v[i] : v[i + c / 2];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+        if (up) base += c / 2;
+    }
+    return base;
+}
 
 template <typename T, int SB>
 __global__ void __launch_bounds__(256, 2) gram_kernel(const T *X, int64_t ldx, int K, const T *Y,
                                                       int64_t ldy, int S, int64_t n, double *part) {
     constexpr int ACC = sizeof(T) == 4 ? 64 : 32;   // accumulators per lane
     constexpr int CT = ACC / SB;                     // X columns per tile
-    // per warp group: slot[rpart][a][b] (a < K, b < S); rsplit * K * S <= 8 * ACC fits
+    // FP64 totals per warp group: slot[rpart][a][b] (a < K, b < S); rsplit * K * S <= 8 * ACC fits
     __shared__ double slot[(MMAX + 1 + SMAX) * SMAX];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ntiles = (K + CT - 1) / CT;
@@ -118,15 +145,15 @@ __global__ void __launch_bounds__(256, 2) gram_kernel(const T *X, int64_t ldx, i
     const int rsplit = many ? 1 : 8 / ntiles;        // warps per tile
     const int active = many ? 8 : ntiles * rsplit;
     const int rpart = many ? 0 : warp / ntiles;
+    for (int e = tid; e < (MMAX + 1 + SMAX) * SMAX; e += 256) slot[e] = 0.0;
+    __syncthreads();
     if (warp < active) {
         for (int tile = many ? warp : warp % ntiles; tile < ntiles; tile += many ? 8 : ntiles) {
             const int c0 = tile * CT;
-            T acc[CT][SB];
-#pragma unroll
-            for (int a = 0; a < CT; a++)
-#pragma unroll
-                for (int b = 0; b < SB; b++) acc[a][b] = (T)0;
             for (int64_t base = (int64_t)blockIdx.x * GRAM_RANGE; base < n; base += (int64_t)gridDim.x * GRAM_RANGE) {
+                T acc[ACC];   // acc[a * SB + b]
+#pragma unroll
+                for (int e = 0; e < ACC; e++) acc[e] = (T)0;
                 for (int st = rpart; st < GRAM_RANGE / 32; st += rsplit) {
                     if (base + st * 32 >= n) break;
                     const int64_t r = base + st * 32 + lane;
@@ -139,18 +166,17 @@ __global__ void __launch_bounds__(256, 2) gram_kernel(const T *X, int64_t ldx, i
 #pragma unroll
                     for (int a = 0; a < CT; a++)
 #pragma unroll
-                        for (int b = 0; b < SB; b++) acc[a][b] = fma(xv[a], yv[b], acc[a][b]);
+                        for (int b = 0; b < SB; b++) acc[a * SB + b] = fma(xv[a], yv[b], acc[a * SB + b]);
+                }
+                // this visit's block sums over the lanes, then into the FP64 totals (each entry
+                // has one owner lane, so no two lanes add to the same slot)
+                const int e0 = lane_halve<T, ACC>(acc, lane);
+#pragma unroll
+                for (int j = 0; j < ACC / 32; j++) {
+                    const int a = (e0 + j) / SB, b = (e0 + j) % SB;
+                    if (c0 + a < K && b < S) slot[((int64_t)rpart * K + c0 + a) * S + b] += (double)acc[j];
                 }
             }
-#pragma unroll
-            for (int a = 0; a < CT; a++)
-#pragma unroll
-                for (int b = 0; b < SB; b++) {
-                    T v = acc[a][b];
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                    if (lane == 0 && c0 + a < K && b < S) slot[((int64_t)rpart * K + c0 + a) * S + b] = (double)v;
-                }
         }
     }
     __syncthreads();
@@ -172,72 +198,90 @@ template <typename T, int SB>
 __global__ void __launch_bounds__(256) update_kernel(const T *Q, int64_t ldq, int K1, T *W, int64_t ldw,
                                                      int S, const double *C, const double *Rinv, int64_t n,
                                                      double *gpart) {
+    // fused Gram of the new block only up to s = 8 (register budget); larger blocks take a
+    // separate Gram pass.  Precision of the fused Gram (FP32 basis): a lane sums its rows'
+    // products in FP32 over at most 32 rows, the lanes' block sums are added by a five-level
+    // FP32 butterfly, and the result goes into FP64 totals per warp (shared memory), summed over
+    // the warps and CTAs in FP64 in a fixed order: the bound of gram_kernel, (37 u32 + m u64)
+    // times |W|^T |W| entrywise.
+    constexpr bool FUSE = SB <= 8;
+    constexpr int NG = FUSE ? SB * (SB + 1) / 2 : 1;
     __shared__ T cs[MMAX + 1][SB];
     __shared__ T ri[SB][SB];
     __shared__ double red[SB * SB];
+    __shared__ double wred[8][NG];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int e = threadIdx.x; e < K1 * S; e += blockDim.x) cs[e % K1][e / K1] = (T)C[e];
     for (int e = threadIdx.x; e < S * S; e += blockDim.x) ri[e % S][e / S] = (T)Rinv[e];
     for (int e = threadIdx.x; e < SB * SB; e += blockDim.x) red[e] = 0.0;
+    for (int e = threadIdx.x; e < 8 * NG; e += blockDim.x) wred[e / NG][e % NG] = 0.0;
     __syncthreads();
-    // fused Gram of the new block only up to s = 8 (register budget); larger blocks take a
-    // separate Gram pass
-    constexpr bool FUSE = SB <= 8;
-    constexpr int NG = FUSE ? SB * (SB + 1) / 2 : 1;
     T g2[NG];
 #pragma unroll
     for (int e = 0; e < NG; e++) g2[e] = (T)0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        T w[SB];
+    const bool gram = FUSE && gpart != nullptr;
+    // the lanes' FP32 block sums into this warp's FP64 totals (entry e by lane e % 32)
+    auto flush = [&]() {
 #pragma unroll
-        for (int b = 0; b < SB; b++) w[b] = b < S ? W[(int64_t)b * ldw + i] : (T)0;
-        // eight basis columns' loads in flight before their FMAs (ascending order kept)
-        for (int a0 = 0; a0 < K1; a0 += 8) {
-            T q[8];
+        for (int e = 0; e < NG; e++) {
+            T v = g2[e];
 #pragma unroll
-            for (int u = 0; u < 8; u++) q[u] = a0 + u < K1 ? Q[(int64_t)(a0 + u) * ldq + i] : (T)0;
-#pragma unroll
-            for (int u = 0; u < 8; u++)
-                if (a0 + u < K1) {
-#pragma unroll
-                    for (int b = 0; b < SB; b++)
-                        if (b < S) w[b] = fma(-q[u], cs[a0 + u][b], w[b]);
-                }
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == (e & 31) && warp < 8) wred[warp][e] += (double)v;
+            g2[e] = (T)0;
         }
-        T wn[SB];
+    };
+    int since = 0;
+    // warp-uniform rounds of 32 consecutive rows (the flush needs every lane)
+    for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x + warp * 32; i0 < n; i0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = i0 + lane;
+        if (i < n) {
+            T w[SB];
 #pragma unroll
-        for (int b = 0; b < SB; b++) {
-            T v = (T)0;
+            for (int b = 0; b < SB; b++) w[b] = b < S ? W[(int64_t)b * ldw + i] : (T)0;
+            // eight basis columns' loads in flight before their FMAs (ascending order kept)
+            for (int a0 = 0; a0 < K1; a0 += 8) {
+                T q[8];
 #pragma unroll
-            for (int c = 0; c < SB; c++)
-                if (c <= b && b < S) v = fma(w[c], ri[c][b], v);
-            wn[b] = v;
-        }
+                for (int u = 0; u < 8; u++) q[u] = a0 + u < K1 ? Q[(int64_t)(a0 + u) * ldq + i] : (T)0;
 #pragma unroll
-        for (int b = 0; b < SB; b++)
-            if (b < S) W[(int64_t)b * ldw + i] = wn[b];
-        if (FUSE && gpart) {
-            int e = 0;
+                for (int u = 0; u < 8; u++)
+                    if (a0 + u < K1) {
+#pragma unroll
+                        for (int b = 0; b < SB; b++)
+                            if (b < S) w[b] = fma(-q[u], cs[a0 + u][b], w[b]);
+                    }
+            }
+            T wn[SB];
+#pragma unroll
+            for (int b = 0; b < SB; b++) {
+                T v = (T)0;
+#pragma unroll
+                for (int c = 0; c < SB; c++)
+                    if (c <= b && b < S) v = fma(w[c], ri[c][b], v);
+                wn[b] = v;
+            }
 #pragma unroll
             for (int b = 0; b < SB; b++)
+                if (b < S) W[(int64_t)b * ldw + i] = wn[b];
+            if (gram) {
+                int e = 0;
 #pragma unroll
-                for (int c = 0; c <= b; c++) {
-                    if (b < S && e < NG) g2[e] = fma(wn[b], wn[c], g2[e]);
-                    e++;
-                }
+                for (int b = 0; b < SB; b++)
+#pragma unroll
+                    for (int c = 0; c <= b; c++) {
+                        if (b < S && e < NG) g2[e] = fma(wn[b], wn[c], g2[e]);
+                        e++;
+                    }
+            }
+        }
+        if (gram && ++since == 32) {
+            flush();
+            since = 0;
         }
     }
-    if (!FUSE || !gpart) return;
-    // per-CTA sum over threads: a shuffle tree inside each warp (basis precision, five
-    // levels), then the warps' partials in FP64 in warp order
-    __shared__ double wred[8][NG];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int e = 0; e < NG; e++) {
-        T v = g2[e];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0 && warp < 8) wred[warp][e] = (double)v;
-    }
+    if (!gram) return;
+    flush();
     __syncthreads();
     for (int e = threadIdx.x; e < NG; e += blockDim.x) {
         double t = 0.0;
@@ -1308,11 +1352,13 @@ __global__ void __launch_bounds__(32) cg_coord_kernel(CgState *cs, const double 
 // block of columns is then whole pairs (FP32: two, FP64: one), read from the staged tile by
 // vector loads.  A CTA stages 128-row tiles of Y in shared
 // memory; thread t owns block pair t % NBP and the rows g, g + RG, ... of each tile
-// (g = t / NBP, RG = 256 / NBP row groups).  Products are summed in the basis precision over
-// up to 32 tiles, then added to FP64 totals; the CTA sums its row groups in order (in the
-// shared memory the tiles used) and writes one FP64 partial per entry, which
-// reduce_partials_kernel sums over the CTAs in a fixed order.  BS = 4 for FP32 (loads of 8
-// values per 16 FMAs), 2 for FP64 (fewer wasted products on the slow FP64 pipe).
+// (g = t / NBP, RG = 256 / NBP row groups).  Precision: a thread sums its products in the
+// basis precision over at most 32 rows (F tiles), the RG row groups' block sums of each entry
+// are then added by a fixed pairwise tree in shared memory (at most eight levels), and the
+// result is added to an FP64 total; the CTA writes one FP64 partial per entry, which
+// reduce_partials_kernel sums over the CTAs in a fixed order.  For an FP32 basis
+// |G^ - G| <= (40 u32 + m u64) |Y|^T |Y| entrywise.  BS = 4 for FP32 (loads of 8 values per
+// 16 FMAs), 2 for FP64 (fewer wasted products on the slow FP64 pipe).
 // Tiles arrive by 16-byte asynchronous copies (cp.async) into a ring of GSYM_STAGES shared
 // buffers, GSYM_STAGES - 1 tiles ahead of the one being summed: with one tile in flight per
 // CTA the kernel was bound by memory latency (about 1 TB/s on the FP32 basis).
@@ -1330,13 +1376,14 @@ template <typename T> constexpr int gsym_pstride() { return 2 * GSYM_TR + 16 / (
 // pairs of a stage for np stored pairs: whole column blocks (FP32: an even number of pairs;
 // the padding pair reads zeros)
 template <typename T> constexpr int gsym_pairs(int np) { return sizeof(T) == 4 ? (np + 1) / 2 * 2 : np; }
-// dynamic shared memory of gram_sym_kernel for np pairs: the stage ring, reused afterwards for
-// the row groups' FP64 totals (at most 256 BS^2 values)
+// dynamic shared memory of gram_sym_kernel for np pairs: the stage ring, then the row groups'
+// block sums (256 BS^2 values of the basis type)
+template <typename T> __host__ __device__ size_t gsym_ring_bytes(int np) {
+    return (size_t)GSYM_STAGES * gsym_pairs<T>(np) * gsym_pstride<T>() * sizeof(T);
+}
 template <typename T> size_t gsym_smem_bytes(int np) {
     constexpr int BS = sizeof(T) == 4 ? 4 : 2;
-    const size_t ring = (size_t)GSYM_STAGES * gsym_pairs<T>(np) * gsym_pstride<T>() * sizeof(T);
-    const size_t red = (size_t)256 * BS * BS * sizeof(double);
-    return ring > red ? ring : red;
+    return gsym_ring_bytes<T>(np) + (size_t)256 * BS * BS * sizeof(T);
 }
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
@@ -1398,6 +1445,35 @@ __global__ void __launch_bounds__(256) gram_sym_kernel(const T *Y, int64_t ldv, 
         acc[k] = 0.0;
         tacc[k] = (T)0;
     }
+    // block sums of the row groups: fl[(g * NBP + pb) * BS^2 + k], after the stage ring
+    T *fl = reinterpret_cast<T *>(sh_raw + gsym_ring_bytes<T>(np));
+    const int rpt = (GSYM_TR + RG - 1) / RG;          // rows of a tile per thread, at most
+    const int F = rpt >= 32 ? 1 : 32 / rpt;           // tiles per block sum: <= 32 terms
+    // every thread of the CTA (the barriers): the row groups' block sums of each entry by a
+    // pairwise tree over g, added to the FP64 totals of the g = 0 threads
+    auto flush = [&]() {
+        if (act) {
+#pragma unroll
+            for (int k = 0; k < BS * BS; k++) {
+                fl[(g * NBP + pb) * BS * BS + k] = tacc[k];
+                tacc[k] = (T)0;
+            }
+        }
+        __syncthreads();
+        for (int step = 1; step < RG; step <<= 1) {
+            if (act && (g % (2 * step)) == 0 && g + step < RG) {
+#pragma unroll
+                for (int k = 0; k < BS * BS; k++)
+                    fl[(g * NBP + pb) * BS * BS + k] += fl[((g + step) * NBP + pb) * BS * BS + k];
+            }
+            __syncthreads();
+        }
+        if (act && g == 0) {
+#pragma unroll
+            for (int k = 0; k < BS * BS; k++) acc[k] += (double)fl[pb * BS * BS + k];
+        }
+        __syncthreads();
+    };
     int since = 0;
     const int64_t ntiles = (n + GSYM_TR - 1) / GSYM_TR;
     // copies of the rows of `tile` that exist (pair k: 2 rows' values per row, contiguous)
@@ -1441,30 +1517,20 @@ __global__ void __launch_bounds__(256) gram_sym_kernel(const T *Y, int64_t ldv, 
 #pragma unroll
                     for (int j = 0; j < BS; j++) tacc[i * BS + j] = fma(xa[i], xb[j], tacc[i * BS + j]);
             }
-            if (++since == 32) {
-#pragma unroll
-                for (int k = 0; k < BS * BS; k++) {
-                    acc[k] += (double)tacc[k];
-                    tacc[k] = (T)0;
-                }
-                since = 0;
-            }
         }
         __syncthreads();
+        if (++since == F) {   // the same count in every thread
+            flush();
+            since = 0;
+        }
     }
     cp_async_wait<0>();
     __syncthreads();
+    flush();
     const int m = NBP * BS * BS;
-    double *red = reinterpret_cast<double *>(sh_raw);
-    if (act) {
+    if (act && g == 0) {
 #pragma unroll
-        for (int k = 0; k < BS * BS; k++) red[g * m + pb * BS * BS + k] = acc[k] + (double)tacc[k];
-    }
-    __syncthreads();
-    for (int e = t; e < m; e += blockDim.x) {
-        double v = 0.0;
-        for (int q = 0; q < RG; q++) v += red[q * m + e];
-        part[(int64_t)blockIdx.x * m + e] = v;
+        for (int k = 0; k < BS * BS; k++) part[(int64_t)blockIdx.x * m + pb * BS * BS + k] = acc[k];
     }
 }
 
@@ -1551,8 +1617,10 @@ struct CgSolver {
         // symmetric Gram partials: (CTA, row group) x packed entries <= CTAs x 256 threads x BS^2
         MPK_TRY(part.alloc_on((size_t)(2 * P->n_sm) * 256 * BS * BS * sizeof(double) + 4096, st));
         MPK_TRY(G.alloc_on((size_t)GSYM_MP * GSYM_MP * sizeof(double), st));
+        // the attribute is per function and shared by every caller: always the same maximum,
+        // never this solve's size, so that concurrent launches cannot race on it
         MPK_CUDA(cudaFuncSetAttribute(gram_sym_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)gsym_smem_bytes<T>(o.s + 1)));
+                                      (int)gsym_smem_bytes<T>(CG_SMAX + 1)));
         MPK_TRY(cstate.alloc_on(sizeof(CgState), st));
         MPK_TRY(dth.alloc_on(CG_SMAX * sizeof(double), st));
         MPK_TRY(vec.alloc_on((size_t)3 * ldv * sizeof(double) + 64 * sizeof(double), st));
@@ -1871,4 +1939,139 @@ extern "C" mpk_status sstep_cg_solve(mpk_plan_t A, const double *b, double *x, c
     inf.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (info) *info = inf;
     return st;
+}
+
+// ==========================================================================================
+// The orthogonalisation steps on their own (the kernels the solvers run, callable directly).
+// ==========================================================================================
+namespace {
+mpk_status sm_count(int *nsm) {
+    int dev = 0;
+    MPK_CUDA(cudaGetDevice(&dev));
+    MPK_CUDA(cudaDeviceGetAttribute(nsm, cudaDevAttrMultiProcessorCount, dev));
+    return MPK_OK;
+}
+
+template <typename T>
+mpk_status gram_launch(const T *X, int64_t ldx, int K, const T *Y, int64_t ldy, int S, int64_t n, double *G,
+                       cudaStream_t s) {
+    int nsm = 1;
+    MPK_TRY(sm_count(&nsm));
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(8 * nsm, ceil_div(n, GRAM_RANGE)));
+    DevBuf part;
+    MPK_TRY(part.alloc_on((size_t)g * K * S * sizeof(double), s));
+    if (S <= 4) gram_kernel<T, 4><<<g, 256, 0, s>>>(X, ldx, K, Y, ldy, S, n, part.as<double>());
+    else if (S <= 8) gram_kernel<T, 8><<<g, 256, 0, s>>>(X, ldx, K, Y, ldy, S, n, part.as<double>());
+    else gram_kernel<T, 16><<<g, 256, 0, s>>>(X, ldx, K, Y, ldy, S, n, part.as<double>());
+    reduce_partials_kernel<<<redp_grid(K * S), 32 * REDP_WARPS, 0, s>>>(part.as<double>(), g, K * S, (int64_t)K * S, G, 0);
+    MPK_CUDA(cudaGetLastError());
+    return MPK_OK;
+}
+
+template <typename T>
+mpk_status update_launch(const T *Q, int64_t ldq, int K1, T *W, int64_t ldw, int S, const double *C,
+                         const double *Rinv, int64_t n, double *G, cudaStream_t s) {
+    int nsm = 1;
+    MPK_TRY(sm_count(&nsm));
+    const int ug = (int)std::max<int64_t>(1, std::min<int64_t>(4 * nsm, ceil_div(n, 256)));
+    const bool fused = G && S <= 8;
+    DevBuf gp;
+    if (fused) MPK_TRY(gp.alloc_on((size_t)ug * S * S * sizeof(double), s));
+    double *gpp = fused ? gp.as<double>() : nullptr;
+    if (S <= 4) update_kernel<T, 4><<<ug, 256, 0, s>>>(Q, ldq, K1, W, ldw, S, C, Rinv, n, gpp);
+    else if (S <= 8) update_kernel<T, 8><<<ug, 256, 0, s>>>(Q, ldq, K1, W, ldw, S, C, Rinv, n, gpp);
+    else update_kernel<T, 16><<<ug, 256, 0, s>>>(Q, ldq, K1, W, ldw, S, C, Rinv, n, nullptr);
+    MPK_CUDA(cudaGetLastError());
+    if (fused) {
+        reduce_partials_kernel<<<redp_grid(S * S), 32 * REDP_WARPS, 0, s>>>(gp.as<double>(), ug, S * S, (int64_t)S * S, G, 0);
+        MPK_CUDA(cudaGetLastError());
+    } else if (G) {
+        MPK_TRY(gram_launch<T>(W, ldw, S, W, ldw, S, n, G, s));
+    }
+    return MPK_OK;
+}
+
+// the packed block-pair layout of gram_sym_kernel -> the full M x M matrix (column-major)
+__global__ void gsym_unpack_kernel(const double *packed, int M, int bs, double *G) {
+    const int nb = (M + bs - 1) / bs;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < M * M; e += gridDim.x * blockDim.x) {
+        const int i = e % M, j = e / M;
+        int a = i, b = j;
+        if (a / bs > b / bs) {   // the lower block is the transpose of a stored upper one
+            a = j;
+            b = i;
+        }
+        const int ab = a / bs, bb = b / bs;
+        const int pb = ab * nb - ab * (ab - 1) / 2 + (bb - ab);
+        G[e] = packed[(int64_t)pb * bs * bs + (a % bs) * bs + (b % bs)];
+    }
+}
+
+template <typename T>
+mpk_status gram_pairs_launch(const T *Y, int64_t ldv, int s, int64_t n, double *G, cudaStream_t st) {
+    int nsm = 1;
+    MPK_TRY(sm_count(&nsm));
+    constexpr int BS = gsym_bs<T>();
+    const int g = (int)std::min<int64_t>(2 * nsm, std::max<int64_t>(1, ceil_div(n, GSYM_TR)));
+    const int M = 2 * s + 2;
+    const int m = gsym_nbp(M, BS) * BS * BS;
+    DevBuf part, packed;
+    MPK_TRY(part.alloc_on((size_t)g * m * sizeof(double), st));
+    MPK_TRY(packed.alloc_on((size_t)m * sizeof(double), st));
+    const size_t smem = gsym_smem_bytes<T>(s + 1);
+    MPK_CUDA(cudaFuncSetAttribute(gram_sym_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)gsym_smem_bytes<T>(CG_SMAX + 1)));
+    gram_sym_kernel<T><<<g, 256, smem, st>>>(Y, ldv, s, n, part.as<double>());
+    reduce_partials_kernel<<<redp_grid(m), 32 * REDP_WARPS, 0, st>>>(part.as<double>(), g, m, (int64_t)m, packed.as<double>(), 0);
+    gsym_unpack_kernel<<<(M * M + 255) / 256, 256, 0, st>>>(packed.as<double>(), M, BS, G);
+    MPK_CUDA(cudaGetLastError());
+    return MPK_OK;
+}
+}  // namespace
+
+extern "C" mpk_status mpk_gram(mpk_dtype dtype, const void *X, int64_t ldx, int32_t K, const void *Y,
+                               int64_t ldy, int32_t S, int64_t n, double *G, cudaStream_t s) {
+    if (dtype != MPK_F32 && dtype != MPK_F64) return MPK_ERR_ARG;
+    if (K < 1 || K > MMAX + 1 + SMAX || S < 1 || S > SMAX || n < 0 || !G) return MPK_ERR_ARG;
+    if (n > 0 && (!X || !Y || ldx < n || ldy < n)) return MPK_ERR_ARG;
+    if (n == 0) {
+        MPK_CUDA(cudaMemsetAsync(G, 0, (size_t)K * S * sizeof(double), s));
+        return MPK_OK;
+    }
+    if (dtype == MPK_F32)
+        return gram_launch<float>((const float *)X, ldx, K, (const float *)Y, ldy, S, n, G, s);
+    return gram_launch<double>((const double *)X, ldx, K, (const double *)Y, ldy, S, n, G, s);
+}
+
+extern "C" mpk_status mpk_block_update(mpk_dtype dtype, const void *Q, int64_t ldq, int32_t K1, void *W,
+                                       int64_t ldw, int32_t S, const double *C, const double *Rinv,
+                                       int64_t n, double *G, cudaStream_t s) {
+    if (dtype != MPK_F32 && dtype != MPK_F64) return MPK_ERR_ARG;
+    if (K1 < 0 || K1 > MMAX + 1 || S < 1 || S > SMAX || n < 0 || !Rinv) return MPK_ERR_ARG;
+    if (K1 > 0 && (!C || !Q || ldq < n)) return MPK_ERR_ARG;
+    if (n > 0 && (!W || ldw < n)) return MPK_ERR_ARG;
+    if (n == 0) {
+        if (G) MPK_CUDA(cudaMemsetAsync(G, 0, (size_t)S * S * sizeof(double), s));
+        return MPK_OK;
+    }
+    if (dtype == MPK_F32)
+        return update_launch<float>((const float *)Q, ldq, K1, (float *)W, ldw, S, C, Rinv, n, G, s);
+    return update_launch<double>((const double *)Q, ldq, K1, (double *)W, ldw, S, C, Rinv, n, G, s);
+}
+
+extern "C" mpk_status mpk_gram_pairs(mpk_dtype dtype, const void *Y, int64_t ldv, int32_t s, int64_t n,
+                                     double *G, cudaStream_t st) {
+    if (dtype != MPK_F32 && dtype != MPK_F64) return MPK_ERR_ARG;
+    if (s < 1 || s > CG_SMAX || n < 0 || !G) return MPK_ERR_ARG;
+    const int M = 2 * s + 2;
+    if (n == 0) {
+        MPK_CUDA(cudaMemsetAsync(G, 0, (size_t)M * M * sizeof(double), st));
+        return MPK_OK;
+    }
+    // 16-byte copies: an aligned base, pairs 16-byte aligned, and room for the copy that
+    // carries the last (odd) row of a pair
+    if (!Y || (uintptr_t)Y % 16 != 0 || ldv < n + (n & 1) || (dtype == MPK_F32 && ldv % 2 != 0))
+        return MPK_ERR_ARG;
+    if (dtype == MPK_F32) return gram_pairs_launch<float>((const float *)Y, ldv, s, n, G, st);
+    return gram_pairs_launch<double>((const double *)Y, ldv, s, n, G, st);
 }

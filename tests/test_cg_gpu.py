@@ -100,7 +100,12 @@ def test_cg_setup_shifts_are_the_oracles_ritz_values(m):
     setup = ocg.cg(A, b, tol=0.0, max_iters=4 * s)
     want = ocg.ritz_shifts(setup["alphas"], setup["betas"], s)
     got = info["shifts"]
-    assert np.allclose(got, want, rtol=1e-6, atol=1e-6 * np.abs(want).max()), (got, want)
+    # The setup phase runs CG in s-step form (s = 1: coefficients from the Gram matrix of
+    # [p, Ap, r] and coordinate vectors), whose coefficients lose accuracy as the residual
+    # falls.  In FP64 NumPy that form's Ritz values differ from textbook CG's by 5.2e-6 of the
+    # largest on this matrix, and by up to 2e-5 when the Gram entries are perturbed by 1e-15
+    # relative (a change of summation order), so the bound is 5e-5 of the largest shift.
+    assert np.allclose(got, want, rtol=0.0, atol=5e-5 * np.abs(want).max()), (got, want)
 
 
 @pytest.mark.parametrize("basis", ["f32", "f64"])
