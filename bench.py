@@ -51,16 +51,54 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-# FP64 FMA peak derived from unit counts and clock: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x
-# 2.07 GHz (the part's FP64 rate is 1.25 TFLOP/s nominal).
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# DRAM traffic of the dominant kernel: a committed ncu summary records, per kernel and call,
+# dram__bytes_read.sum + dram__bytes_write.sum per launch and the SHA-256 of the kernel's
+# source file when it was captured.  The bench reports the figure only while the source is
+# unchanged, and null (with the reason) once the kernel has changed since the capture.
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "lane_kernel_f64_p4_27pt160_dram.md")
+KERNEL_SOURCE = os.path.join(ROOT, "paper_2309_02228_gb300", "csrc", "apply.cu")
 
-# DRAM bytes (read + write) of one blocked FP64 p = 4 launch of the headline call (original
-# order in and out, 4-slice chunks), from an ncu capture (dram__bytes_read.sum +
-# dram__bytes_write.sum) of the same kernel and call on the 27-point 128^3 matrix
-# (2.821 + 0.109 GB), scaled by stored SELL entries (109,664,800 / 56,041,696).  Valid for the
-# kernel as captured; set to None when the kernel changes until it is captured again.
-TRAFFIC_F64_P4_BYTES = 5.734e9
+
+def source_sha(path):
+    import hashlib
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def recorded_traffic(path=TRAFFIC_PROFILE):
+    """(bytes per launch, note) from the committed capture, or (None, why)."""
+    try:
+        rec = {}
+        with open(path) as f:
+            for line in f:
+                if line.startswith("traffic_bytes_per_launch:"):
+                    rec["bytes"] = float(line.split(":", 1)[1])
+                elif line.startswith("source_sha256_16:"):
+                    rec["sha"] = line.split(":", 1)[1].strip()
+        if "bytes" not in rec or "sha" not in rec:
+            return None, "no capture recorded in %s" % os.path.relpath(path, ROOT)
+        now = source_sha(KERNEL_SOURCE)
+        if now != rec["sha"]:
+            return None, "stale: kernel source changed since the capture (%s, now %s)" % (rec["sha"], now)
+        return rec["bytes"], "ncu capture of this call, %s" % os.path.relpath(path, ROOT)
+    except OSError as e:
+        return None, "no capture: %s" % e
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
 
 
 class ClockSampler:
@@ -144,25 +182,33 @@ def whole_job_gflops(flop_per_rank, world, ms_step):
     return world * flop_per_rank / (ms_step * 1e-3) / 1e9
 
 
-def cpu_baseline(A, x, theta, budget_s=10.0):
-    """The oracle as it stands (plain FP64 CSR loops, static OpenMP rows) on the host cores:
-    full 27-point matrix, p = 4 Newton, repeated until about budget_s seconds."""
+def cpu_baseline(A, x, theta, budget_s=8.0, budget_1core_s=6.0):
+    """The oracle as it stands (plain FP64 CSR loops) on the host cores: full 27-point matrix,
+    p = 4 Newton, repeated until about budget_s seconds with a static OpenMP row loop on all
+    cores, and until about budget_1core_s seconds on one core."""
     import oracle
     from oracle import sstep
     oracle.build()
     cf = sstep.newton_coeffs(theta[:P_MAIN])
-    reps, t_total = 0, 0.0
-    while t_total < budget_s or reps == 0:
-        t0 = time.perf_counter()
-        oracle.mpk(A, P_MAIN, cf, x, threads=True)
-        t_total += time.perf_counter() - t0
-        reps += 1
-        if reps >= 1000:
-            break
-    gf = 2.0 * A.nnz * P_MAIN * reps / t_total / 1e9
+
+    def run(threads, budget):
+        reps, t_total = 0, 0.0
+        while t_total < budget or reps == 0:
+            t0 = time.perf_counter()
+            oracle.mpk(A, P_MAIN, cf, x, threads=threads)
+            t_total += time.perf_counter() - t0
+            reps += 1
+            if reps >= 1000:
+                break
+        return 2.0 * A.nnz * P_MAIN * reps / t_total / 1e9, reps, t_total
+
+    gf, reps, t_total = run(True, budget_s)
+    gf1, reps1, t1 = run(False, budget_1core_s)
     return {"value": gf, "unit": "GFLOP/s", "cores": oracle.omp_threads(), "kind": "oracle",
             "sample": "full 160^3 27-point FP64 matrix, p=4 Newton, %d calls in %.1f s" % (reps, t_total),
-            "seconds": t_total}
+            "seconds": t_total, "cpu_model": cpu_model(),
+            "one_core": {"value": gf1, "unit": "GFLOP/s", "cores": 1,
+                         "sample": "the same call, %d calls in %.1f s" % (reps1, t1)}}
 
 
 def headline_config(n, nnz):
@@ -687,28 +733,36 @@ def main():
     e2e = {"value": world * flop / t_e2e / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": 8 * n,
            "d2h_bytes_per_step": 8 * n * (P_MAIN + 1)}
 
-    # ---- roofline of the dominant kernel (blocked, p = 4): FP64 FMA issue bounds it on this
-    # part (2 FP64 FMA/clk/SM), not HBM: compare both bounds and report the binding one.
+    # ---- roofline of the dominant kernel (blocked, p = 4).  Its two bounds: FP64 FMA issue
+    # (the FP64 FMA rate measured on this device by mpk_fma_peak) and HBM (the measured copy
+    # bandwidth on the algorithmic minimum bytes); the binding one is reported, the other
+    # beside it.
     kb = kern["p%d" % P_MAIN]["blocked_ms"]
     bytes_min = kern["p%d" % P_MAIN]["blocked_min_bytes"]
+    fp64_peak = m.mpk_fma_peak(m.MPK_F64)
+    fp32_peak = m.mpk_fma_peak(m.MPK_F32)
+    lane = int(tuned.kernel) == 4 or int(tuned.lanes_per_row) > 1
+    kname = "mpk_lane_kernel<double,%d,%d>" % (max(1, int(tuned.lanes_per_row)), int(tuned.task_dispatch)) \
+        if lane else "mpk_wave_kernel<double,1>"
+    traffic, traffic_note = recorded_traffic() if lane else (None, "no capture of this kernel")
     t_hbm = bytes_min / (hbm_peak * 1e9)
-    t_alu = flop / (FP64_PEAK_TFLOPS * 1e12)
+    t_alu = flop / (fp64_peak * 1e12)
+    hbm_view = {"achieved_gbs": bytes_min / (kb * 1e-3) / 1e9, "peak_gbs": hbm_peak,
+                "frac": bytes_min / (kb * 1e-3) / 1e9 / hbm_peak, "peak_kind": peak_kind}
     if t_alu >= t_hbm:
         ach = flop / (kb * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": ach / FP64_PEAK_TFLOPS,
-                "traffic": TRAFFIC_F64_P4_BYTES if P_MAIN == 4 else None,
-                "traffic_note": "ncu DRAM bytes on the 128^3 case scaled by stored entries; "
-                                "algorithmic minimum %.3g bytes" % bytes_min,
-                "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
-                "kernel": "mpk_wave_kernel<double,1>",
-                "hbm_view": {"achieved_gbs": bytes_min / (kb * 1e-3) / 1e9, "peak_gbs": hbm_peak,
-                             "frac": bytes_min / (kb * 1e-3) / 1e9 / hbm_peak, "peak_kind": peak_kind}}
+        roof = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": ach / fp64_peak, "traffic": traffic,
+                "traffic_note": traffic_note + "; algorithmic minimum %.4g bytes" % bytes_min,
+                "peak_source": "measured: mpk_fma_peak(FP64) on this device (of measured)",
+                "kernel": kname, "hbm_view": hbm_view}
     else:
         ach = bytes_min / (kb * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-                "frac": ach / hbm_peak, "traffic": None, "peak_kind": peak_kind,
-                "kernel": "mpk_wave_kernel<double,1>"}
+                "frac": ach / hbm_peak, "traffic": traffic, "traffic_note": traffic_note,
+                "peak_kind": peak_kind, "kernel": kname,
+                "alu_view": {"achieved_tflops": flop / (kb * 1e-3) / 1e12, "peak_tflops": fp64_peak}}
+    roof["fma_peaks_tflops"] = {"f64": fp64_peak, "f32": fp32_peak}
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -726,6 +780,9 @@ def main():
                                                       "l2_budget_bytes", "sell_nnz", "root")},
                                  autotuned={"candidate": tinfo["best_index"], "kernel": int(tuned.kernel),
                                             "chunk_slices": int(tuned.chunk_slices),
+                                            "lanes_per_row": int(tuned.lanes_per_row),
+                                            "task_units": int(tuned.task_units),
+                                            "slack_tasks": int(tuned.slack_tasks),
                                             "best_ms": tinfo["best_ms"], "base_ms": tinfo["base_ms"]})),
         "pxspmv_gflops": sweep["p%d" % P_MAIN]["pxspmv_gflops"],
         "speedup_vs_pxspmv": sweep["p%d" % P_MAIN]["speedup"],

@@ -292,7 +292,8 @@ mpk_status mpk_plan_sync(mpk_plan_t plan, cudaStream_t stream);
  * Computes the same result as mpk_apply(plan, co, dtype, X, n, Y, n, 1,
  * MPK_FINAL_ONLY | MPK_UNBLOCKED | flags, stream), with the same kernels:
  * Y = y_p, or sum_k gamma_k y_k when co->gamma is set (the recurrence of mpk_apply above),
- * for ONE right-hand side, by p back-to-back SpMV launches (Alg. 1).
+ * for ONE right-hand side, by p back-to-back SpMV launches (the plan's unblocked row
+ * function: one row per lane, or lanes_per_row lanes sharing a row).
  *   co     coefficients (host), 1 <= co->p <= 63
  *   dtype  MPK_F64 or MPK_F32 (the plan must keep that precision)
  *   X      device vector of n elements (original row order, or level order with
@@ -310,10 +311,17 @@ mpk_status mpk_plan_sync(mpk_plan_t plan, cudaStream_t stream);
  * calls ordered: one stream, or events between streams.
  * Set-up: the first call on each device, with that device current, looks up the array's
  * address (cudaGetSymbolAddress) and keeps it; make that first call before any stream capture
- * begins on the device.  Asynchronous on stream. */
+ * begins on the device.  The kept address does not survive a reset of the device's primary
+ * context (cudaDeviceReset): call mpk_noalloc_forget() after such a reset, before the next
+ * call.  Asynchronous on stream. */
 #define MPK_NOALLOC_SCRATCH_BYTES (32u << 20)
 mpk_status mpk_apply_final_noalloc(mpk_plan_t plan, const mpk_coeffs *co, mpk_dtype dtype,
                                    const void *X, void *Y, uint32_t flags, cudaStream_t stream);
+/* Drops the scratch addresses kept by mpk_apply_final_noalloc for every device, so that the
+ * next call on each device looks its array up again (needed after cudaDeviceReset, whose
+ * context reset moves the array).  Not to be called while such calls may run on other
+ * threads.  Always MPK_OK.  No counterpart in the paper. */
+mpk_status mpk_noalloc_forget(void);
 
 /* Host helpers for coefficient triples (host arrays of length p). */
 /* Chebyshev basis on [alpha, beta]: y_k = T_k((A - c0 I)/d) x, c0 = (alpha+beta)/2,
@@ -510,6 +518,14 @@ mpk_status mpk_cg_opts_default(mpk_cg_opts *o);
  * MPK_ERR_BREAKDOWN, or an argument / CUDA error. */
 mpk_status sstep_cg_solve(mpk_plan_t A, const double *b, double *x, const mpk_cg_opts *o,
                           mpk_cg_info *info, cudaStream_t stream);
+
+/* Measured FMA rate of this device: `tflops` (host) receives 2 x FMAs / s in TFLOP/s of a
+ * kernel whose threads run eight independent FMA chains of type dtype (best of three timed
+ * launches of about 20 ms each, CUDA events on `stream`, after one warm-up launch).  The
+ * paper has no counterpart: it is the arithmetic roofline against which the measurement
+ * reports a kernel bound by FMA issue (the FP64 MPK on this part) rather than by memory.
+ * Synchronous; allocates a small output buffer. */
+mpk_status mpk_fma_peak(mpk_dtype dtype, double *tflops, cudaStream_t stream);
 
 /* ------------------------------------------------------------------------------------------
  * The orthogonalisation steps of the solvers on their own: the same kernels, callable on the

@@ -164,6 +164,7 @@ _SIGS = [
     ("mpk_apply", ctypes.c_int, [_P, ctypes.POINTER(mpk_coeffs), ctypes.c_int, _P, _I64, _P, _I64, _I32, _U32, _P]),
     ("mpk_plan_sync", ctypes.c_int, [_P, _P]),
     ("mpk_apply_final_noalloc", ctypes.c_int, [_P, ctypes.POINTER(mpk_coeffs), ctypes.c_int, _P, _P, _U32, _P]),
+    ("mpk_noalloc_forget", ctypes.c_int, []),
     ("mpk_coeffs_chebyshev", ctypes.c_int, [_D, _D, _I32, _P, _P, _P]),
     ("mpk_coeffs_newton", ctypes.c_int, [_P, _I32, _P, _P, _P]),
     ("mpk_leja_order", ctypes.c_int, [_P, _I32, _I32, _P]),
@@ -174,6 +175,7 @@ _SIGS = [
                                     ctypes.POINTER(mpk_plan_opts), ctypes.POINTER(mpk_tune_info), _P]),
     ("mpk_cg_opts_default", ctypes.c_int, [ctypes.POINTER(mpk_cg_opts)]),
     ("sstep_cg_solve", ctypes.c_int, [_P, _P, _P, ctypes.POINTER(mpk_cg_opts), ctypes.POINTER(mpk_cg_info), _P]),
+    ("mpk_fma_peak", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_D), _P]),
     ("mpk_gram", ctypes.c_int, [ctypes.c_int, _P, _I64, _I32, _P, _I64, _I32, _I64, _P, _P]),
     ("mpk_block_update", ctypes.c_int, [ctypes.c_int, _P, _I64, _I32, _P, _I64, _I32, _P, _P, _I64, _P, _P]),
     ("mpk_gram_pairs", ctypes.c_int, [ctypes.c_int, _P, _I64, _I32, _I64, _P, _P]),
@@ -344,6 +346,10 @@ class Coeffs:
         self.c = np.ascontiguousarray(c, dtype=np.float64)
         self.gamma = None if gamma is None else np.ascontiguousarray(gamma, dtype=np.float64)
         self.p = int(self.a.shape[0])
+        if self.b.shape[0] != self.p or self.c.shape[0] != self.p:
+            raise ValueError("a, b and c must have p entries each")
+        if self.gamma is not None and self.gamma.shape[0] != self.p + 1:
+            raise ValueError("gamma must have p + 1 entries")
         self.struct = mpk_coeffs(self.p, self.a.ctypes.data, self.b.ctypes.data,
                                  self.c.ctypes.data,
                                  self.gamma.ctypes.data if self.gamma is not None else 0)
@@ -363,6 +369,19 @@ def mpk_apply(plan, coeffs, X, Y, n_rhs=1, flags=0, ldx=None, ldy=None, dtype=No
     n = plan.n
     ldx = n if ldx is None else ldx
     ldy = n if ldy is None else ldy
+    # the extent the call touches (a short tensor would be read or written past its end)
+    inter = (flags & MPK_RHS_INTERLEAVED) != 0
+    if n > 0:
+        if X is not None:
+            if X.dtype != Y.dtype:
+                raise ValueError("X and Y must have the same dtype")
+            need_x = n * n_rhs if inter else (n_rhs - 1) * ldx + n
+            if X.numel() < need_x:
+                raise ValueError("X holds %d elements, the call reads %d" % (X.numel(), need_x))
+        nb = 1 if flags & MPK_FINAL_ONLY else coeffs.p + 1
+        need_y = (nb - 1) * ldy * n_rhs + (n * n_rhs if inter else (n_rhs - 1) * ldy + n)
+        if Y.numel() < need_y:
+            raise ValueError("Y holds %d elements, the call writes %d" % (Y.numel(), need_y))
     st = lib().mpk_apply(plan.handle, ctypes.byref(coeffs.struct), d, _ptr(X), int(ldx), _ptr(Y),
                          int(ldy), int(n_rhs), int(flags), _stream_ptr(stream))
     _check(st, "mpk_apply")
@@ -375,6 +394,10 @@ def mpk_apply_final_noalloc(plan, coeffs, X, Y, flags=0, dtype=None, stream=None
     if not isinstance(coeffs, Coeffs):
         coeffs = Coeffs.from_triples(coeffs)
     d = _dtype_code(Y.dtype if dtype is None else dtype)
+    if X.dtype != Y.dtype:
+        raise ValueError("X and Y must have the same dtype")
+    if X.numel() < plan.n or Y.numel() < plan.n:
+        raise ValueError("X and Y must hold n = %d elements" % plan.n)
     st = lib().mpk_apply_final_noalloc(plan.handle, ctypes.byref(coeffs.struct), d, _ptr(X),
                                        _ptr(Y), int(flags), _stream_ptr(stream))
     _check(st, "mpk_apply_final_noalloc")
@@ -636,3 +659,15 @@ def mpk_gram_pairs(Y, s, n, ldv, stream=None):
     _check(lib().mpk_gram_pairs(_dtype_code(Y.dtype), _ptr(Y), ldv, s, n, _ptr(G), _stream_ptr(stream)),
            "mpk_gram_pairs")
     return G.t()
+
+
+def mpk_fma_peak(dtype, stream=None):
+    """Measured FMA rate of the current device in TFLOP/s (MPK_F32 or MPK_F64)."""
+    v = ctypes.c_double(0.0)
+    _check(lib().mpk_fma_peak(int(dtype), ctypes.byref(v), _stream_ptr(stream)), "mpk_fma_peak")
+    return v.value
+
+
+def mpk_noalloc_forget():
+    """Drop the scratch addresses mpk_apply_final_noalloc kept (after a device reset)."""
+    _check(lib().mpk_noalloc_forget(), "mpk_noalloc_forget")

@@ -1435,6 +1435,243 @@ __global__ void __launch_bounds__(WAVE_BLOCK, (lane_min_blocks<T, LPR>())) mpk_l
 }
 
 // ------------------------------------------------------------------------------------------
+// Staged warp tasks (opts.kernel = 5; single right-hand side, one row per lane, one slice per
+// task).  The lane-task kernel's tasks, schedule and hand-out, but each task's slice (its
+// column indices and values, 32 L entries, contiguous in the SELL-32 arrays) is copied into
+// the warp's shared memory by the tensor memory accelerator (cp.async.bulk, completion on an
+// mbarrier) while the warp runs the previous task.  A task's chain of dependent memory
+// accesses is then the vector gathers and the publication only: with a few warps per SM a
+// launch keeps few rows in flight, so consecutive powers run close together and the slices
+// are still in L2 when the next power reads them, and the short chain keeps those few warps
+// busy.  Two buffers per warp: the next task's copy goes into the buffer the previous task
+// used.  Every wait is bounded; a warp that stops waits (bounded) for its copy in flight.
+// ------------------------------------------------------------------------------------------
+constexpr int STAGE_NBUF = 2;
+constexpr int STAGE_WARPS = WAVE_BLOCK / 32;
+
+// One slice's power k from its staged columns and values (entry j of lane l at scol[32 j + l]):
+// the same sums as row_sum - entries ascending, one FMA each, FP64 even / odd partial sums -
+// so the values equal the unblocked power kernel's.  All gathers of a batch are issued before
+// its first FMA; an FP32 batch holds a whole row of up to 32 entries.
+template <typename T>
+__device__ __forceinline__ void staged_rows(const int32_t *scol, const T *sval, int32_t r0, int32_t r1,
+                                            int32_t L, int lane, const VecSet &V, int k, const Coefs &cf) {
+    constexpr bool TWO = sizeof(T) == 8;
+    constexpr int BG = sizeof(T) == 4 ? 32 : 16;
+    const int32_t row = r0 + lane;
+    const T *y1 = vec_ro<T>(V, k - 1);
+    T acc = (T)0, acc2 = (T)0;
+    for (int32_t j0 = 0; j0 < L; j0 += BG) {
+        T xx[BG];
+#pragma unroll
+        for (int u = 0; u < BG; u++) {
+            if (j0 + u < L) {
+                const int32_t c = scol[32 * (j0 + u) + lane];
+                xx[u] = y1[c >= 0 ? c : r0];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < BG; u++) {
+            const int32_t j = j0 + u;
+            if (j < L) {
+                const int32_t c = scol[32 * j + lane];
+                const T v = sval[32 * j + lane];
+                if (TWO && (j & 1)) {
+                    const T f = fma(v, xx[u], acc2);
+                    acc2 = c >= 0 ? f : acc2;
+                } else {
+                    const T f = fma(v, xx[u], acc);
+                    acc = c >= 0 ? f : acc;
+                }
+            }
+        }
+    }
+    if (TWO) acc += acc2;
+    if (row < r1) {
+        T a1[1] = {acc};
+        row_finish<T, 1>(a1, row, 1, 0, V, k, cf);
+    }
+}
+
+// bytes of one staging buffer (columns, then values) for slices of up to lmax entries per row
+template <typename T> __host__ __device__ constexpr size_t stage_buf_bytes(int32_t lmax) {
+    return (size_t)32 * lmax * (4 + sizeof(T));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(WAVE_BLOCK, 1) mpk_stage_kernel(SellView A, VecSet V, Coefs cf, LaneArgs W,
+                                                                  int32_t lmax) {
+    extern __shared__ __align__(128) unsigned char stage_sm[];
+    __shared__ __align__(8) uint64_t s_bar[STAGE_WARPS][STAGE_NBUF];
+    __shared__ uint32_t s_next;
+    __shared__ int32_t s_wm[MPK_MAX_P + 1];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const size_t bb = stage_buf_bytes<T>(lmax);
+    unsigned char *mybuf = stage_sm + (size_t)wib * STAGE_NBUF * bb;
+    if (threadIdx.x == 0) s_next = 0;
+    for (int i = threadIdx.x; i <= MPK_MAX_P; i += blockDim.x) s_wm[i] = 0;
+    if (lane == 0) {
+        for (int b = 0; b < STAGE_NBUF; b++) mbar_init(&s_bar[wib][b], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const T *gval = reinterpret_cast<const T *>(A.val);
+    auto take = [&]() -> int64_t {
+        uint32_t j = 0;
+        if (lane == 0) j = atomicAdd(&s_next, 1u);
+        j = __shfl_sync(0xffffffffu, j, 0);
+        return (int64_t)blockIdx.x + (int64_t)j * gridDim.x;
+    };
+    // lane 0: the slice of metadata m into buffer b (nothing for an empty slice)
+    auto issue = [&](int b, const int4 &m) {
+        if (lane == 0 && m.y > 0) {
+            int32_t *scol = reinterpret_cast<int32_t *>(mybuf + (size_t)b * bb);
+            T *sval = reinterpret_cast<T *>(mybuf + (size_t)b * bb + (size_t)128 * lmax);
+            // the buffer was last read by this warp's generic loads (two tasks ago, finished)
+            fence_proxy_async_smem();
+            mbar_expect_tx(&s_bar[wib][b], (uint32_t)(32 * m.y * (4 + (int)sizeof(T))));
+            bulk_g2s(scol, A.col + m.x, (uint32_t)(128 * m.y), &s_bar[wib][b]);
+            bulk_g2s(sval, gval + m.x, (uint32_t)(32 * m.y * sizeof(T)), &s_bar[wib][b]);
+        }
+    };
+    // bounded wait for buffer b's copy; false on a timeout
+    auto wait_buf = [&](int b, uint32_t ph) -> bool {
+        if (mbar_try_wait(&s_bar[wib][b], ph)) return true;
+        const uint64_t t0 = globaltimer_ns();
+        while (!mbar_try_wait(&s_bar[wib][b], ph))
+            if (globaltimer_ns() - t0 > W.timeout_ns) return false;
+        return true;
+    };
+    int b = 0;
+    uint32_t ph0 = 0, ph1 = 0;             // the phase each buffer's next completion ends
+    bool if0 = false, if1 = false;         // a copy into the buffer has not been waited for
+    int64_t t = take();
+    int4 d = make_int4(0, 0, 0, 0), mt = make_int4(0, 0, 0, 0);
+    if (t < W.n_tasks) {
+        d = __ldg(&W.desc[t]);
+        mt = __ldg(&W.unit_meta[d.w]);
+        issue(0, mt);
+        if0 = mt.y > 0;
+    }
+    int4 mn = make_int4(0, 0, 0, 0);
+    bool stop = false;
+    while (t < W.n_tasks) {
+        const int64_t tn = take();
+        const int32_t c = d.x & 0xffffff;
+        const int kl = (int)((uint32_t)d.x >> 24);
+        if (kl > 1) {
+            const int32_t hb = d.z;
+            int32_t wm = *(volatile int32_t *)&s_wm[kl - 1];
+            if (wm <= hb) {
+                const uint32_t mult = *(volatile uint32_t *)(W.kep + kl - 1) + 1u;
+                const uint32_t *cp = W.cnt + (int64_t)(kl - 1) * W.n_cblk;
+                bool timing = false;
+                uint64_t t0 = 0;
+                while (wm <= hb) {
+                    const int32_t bk = wm + lane;
+                    bool done = true;
+                    if (bk <= hb) {
+                        const uint32_t v = ld_relaxed_u32(cp + bk);
+                        done = (int32_t)(v - mult * (uint32_t)__ldg(W.cblk_size + bk)) >= 0;
+                    }
+                    const unsigned nd = __ballot_sync(0xffffffffu, !done);
+                    if (nd == 0) {
+                        wm = min(wm + 32, hb + 1);
+                        continue;
+                    }
+                    wm += __ffs(nd) - 1;
+                    uint64_t now = 0;
+                    uint32_t err = 0;
+                    if (lane == 0) {
+                        now = globaltimer_ns();
+                        err = *(volatile uint32_t *)&W.ctrl->error;
+                    }
+                    now = __shfl_sync(0xffffffffu, now, 0);
+                    err = __shfl_sync(0xffffffffu, err, 0);
+                    if (err) {
+                        stop = true;
+                        break;
+                    }
+                    if (!timing) {
+                        timing = true;
+                        t0 = now;
+                    } else if (now - t0 > W.timeout_ns) {
+                        if (lane == 0 && atomicOr(&W.ctrl->error, 1u) == 0u) W.ctrl->err_task = (uint32_t)d.x;
+                        stop = true;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+                if (stop) break;
+                if (lane == 0) atomicMax(&s_wm[kl - 1], wm);
+            }
+            fence_acq_rel_gpu();   // acquire: counters observed before the vectors read below
+        }
+        // the next task's descriptor and metadata, loaded while this task waits and computes
+        // (after the fence, which would otherwise wait for them)
+        int4 dn = make_int4(0, 0, 0, 0);
+        mn = make_int4(0, 0, 0, 0);
+        if (tn < W.n_tasks) {
+            dn = __ldg(&W.desc[tn]);
+            mn = __ldg(&W.unit_meta[dn.w]);
+        }
+        // this task's slice
+        if (mt.y > 0) {
+            if (!wait_buf(b, b ? ph1 : ph0)) {
+                if (lane == 0 && atomicOr(&W.ctrl->error, 1u) == 0u) W.ctrl->err_task = (uint32_t)d.x;
+                stop = true;
+                break;
+            }
+            if (b) {
+                ph1 ^= 1u;
+                if1 = false;
+            } else {
+                ph0 ^= 1u;
+                if0 = false;
+            }
+        }
+        __syncwarp();
+        const int32_t *scol = reinterpret_cast<const int32_t *>(mybuf + (size_t)b * bb);
+        const T *sval = reinterpret_cast<const T *>(mybuf + (size_t)b * bb + (size_t)128 * lmax);
+        staged_rows<T>(scol, sval, mt.z, mt.w, mt.y, lane, V, W.k0 + kl, cf);
+        // the next task's slice into the other buffer (read by the previous task, finished)
+        __syncwarp();
+        if (tn < W.n_tasks && mn.y > 0) {
+            issue(b ^ 1, mn);
+            if (b) if0 = true;
+            else if1 = true;
+        }
+        // publish: the warp barrier above orders every lane's results before lane 0's release
+        if (lane == 0 && !(W.debug_drop && c == 0 && kl == 1)) red_release_add_u32(W.cnt + (int64_t)kl * W.n_cblk + d.y, 1u);
+        t = tn;
+        d = dn;
+        mt = mn;
+        b ^= 1;
+    }
+    // a warp that stopped may have copies in flight into its buffers: wait for them (bounded)
+    // before the CTA exits, so that no copy lands in shared memory the CTA no longer owns
+    if (stop) {
+        const uint64_t t0 = globaltimer_ns();
+        if (if0)
+            while (!mbar_try_wait(&s_bar[wib][0], ph0))
+                if (globaltimer_ns() - t0 > W.timeout_ns) break;
+        if (if1)
+            while (!mbar_try_wait(&s_bar[wib][1], ph1))
+                if (globaltimer_ns() - t0 > W.timeout_ns) break;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const uint32_t dn2 = atomicAdd(&W.ctrl->done_ctas, 1u);
+        if (dn2 == gridDim.x - 1) {
+            W.ctrl->done_ctas = 0;
+            for (int kk = 1; kk <= W.seg; kk++) W.kep[kk] += 1u;
+            __threadfence();
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
 // Ready-first warp tasks (opts.kernel = 3).  The tasks are the warp-task kernel's (chunk c,
 // local power k), but none is scheduled ahead.  Chunks are dealt to n_shards interleaved
 // shards (chunk c to shard c % n_shards, every shard served by the same number of warps, at
@@ -1855,6 +2092,70 @@ mpk_status launch_lane_blocked(mpk_plan_s *P, const SellView &A, const VecSet &V
     return MPK_OK;
 }
 
+// Staged warp tasks (kernel 5): one slice per task, matrix slices copied into shared memory.
+// MPK_ERR_UNIMPLEMENTED when two buffers per warp of the longest slice do not fit.
+template <typename T>
+mpk_status launch_stage_blocked(mpk_plan_s *P, const SellView &A, const VecSet &V, const Coefs &cf,
+                                int p, uint32_t flags, cudaStream_t s) {
+    LaneGraph *G = nullptr;
+    MPK_TRY(mpk_get_lane_graph(P, 1, 1, &G, s));
+    auto kern = mpk_stage_kernel<T>;
+    cudaFuncAttributes fa;
+    MPK_CUDA(cudaFuncGetAttributes(&fa, kern));
+    const int maxdyn = P->smem_optin - (int)fa.sharedSizeBytes;
+    const size_t dyn = (size_t)STAGE_WARPS * STAGE_NBUF * stage_buf_bytes<T>(std::max(1, G->max_len));
+    if ((int64_t)dyn > maxdyn) return MPK_ERR_UNIMPLEMENTED;
+    // per function, shared by every caller: always the same maximum, never this launch's size
+    MPK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, maxdyn));
+    int occ = 0;
+    MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, WAVE_BLOCK, dyn));
+    if (occ < 1) return MPK_ERR_UNIMPLEMENTED;
+    const int per_sm = P->opts.ctas_per_sm > 0 ? std::min(occ, P->opts.ctas_per_sm) : occ;
+    int k0 = 0;
+    while (k0 < p) {
+        const int seg = std::min(P->p_blk, p - k0);
+        const int64_t ntask = (int64_t)seg * G->n_chunks;
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)P->n_sm * per_sm, ceil_div(ntask, STAGE_WARPS)));
+        // slack: three tickets per resident warp (each warp holds two: the one it runs and
+        // the next, whose slice is on its way)
+        const int64_t slack = P->lane_slack > 0 ? P->lane_slack : 3 * grid * STAGE_WARPS;
+        Schedule *sch = nullptr;
+        MPK_TRY(lane_schedule(G, seg, slack, &sch, s));
+        if (sch->n_tasks >= (1ll << 31)) return MPK_ERR_UNIMPLEMENTED;
+        LaneArgs W;
+        memset(&W, 0, sizeof(W));
+        W.unit_meta = G->unit_meta.as<int4>();
+        W.chunk_unit = G->chunk_unit.as<int32_t>();
+        W.one_unit = 1;
+        W.cblk_size = G->cblk_size.as<int32_t>();
+        W.desc = sch->desc.as<int4>();
+        W.n_tasks = sch->n_tasks;
+        W.cnt = G->cnt.as<uint32_t>();
+        W.kep = G->kep.as<uint32_t>();
+        W.ctrl = P->ctrl.as<MpkCtrl>();
+        W.n_cblk = G->n_cblk;
+        W.k0 = k0;
+        W.seg = seg;
+        W.timeout_ns = (uint64_t)P->opts.wait_timeout_us * 1000ull;
+        W.debug_drop = (flags & MPK_DEBUG_DROP_FLAG) && k0 == 0 ? 1u : 0u;
+        cudaLaunchConfig_t lc;
+        memset(&lc, 0, sizeof(lc));
+        lc.gridDim = dim3((unsigned)grid);
+        lc.blockDim = dim3(WAVE_BLOCK);
+        lc.dynamicSmemBytes = dyn;
+        lc.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        lc.attrs = attr;
+        lc.numAttrs = 1;
+        const int32_t lmax = std::max(1, G->max_len);
+        MPK_CUDA(cudaLaunchKernelEx(&lc, kern, A, V, cf, W, lmax));
+        k0 += seg;
+    }
+    return MPK_OK;
+}
+
 // Single right-hand side with lanes sharing rows (or the lane-task kernel): blocked lane
 // tasks, or unblocked launches with the same row function.
 template <typename T>
@@ -1872,6 +2173,10 @@ mpk_status launch_lane_powers(mpk_plan_s *P, const SellView &A, const VecSet &V,
         }
         MPK_CUDA(cudaGetLastError());
         return MPK_OK;
+    }
+    if (lpr == 1 && P->opts.kernel == 5) {
+        const mpk_status st = launch_stage_blocked<T>(P, A, V, cf, p, flags, s);
+        if (st != MPK_ERR_UNIMPLEMENTED) return st;   // else: slices too long to stage
     }
     switch (lpr) {
     case 1: return launch_lane_blocked<T, 1>(P, A, V, cf, p, flags, s);
@@ -2476,6 +2781,12 @@ mpk_status noalloc_scratch(void **out) {
 
 inline size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
 }  // namespace
+
+extern "C" mpk_status mpk_noalloc_forget(void) {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    for (int d = 0; d < kNoAllocMaxDevices; d++) g_noalloc_ptr[d].store(nullptr, std::memory_order_release);
+    return MPK_OK;
+}
 
 extern "C" mpk_status mpk_apply_final_noalloc(mpk_plan_t P, const mpk_coeffs *co,
                                               mpk_dtype dtype, const void *X, void *Y,

@@ -101,6 +101,7 @@ struct Schedule {
 struct LaneGraph {
     int lpr = 1, units = 1;
     int32_t n_units = 0, n_chunks = 0, n_cblk = 0;
+    int32_t max_len = 0;               // longest slice (entries per row)
     DevBuf unit_code;                  // int32 per unit: slice * lpr + sub-slice, ascending
     DevBuf unit_meta;                  // int4 per unit: {first SELL entry, slice length,
                                        // first row, end of the slice's rows}

@@ -1283,9 +1283,9 @@ static mpk_status plan_create_impl(const mpk_csr *A, int32_t p_max, const mpk_pl
     else if (o.lanes_per_row == 1 || o.lanes_per_row == 2 || o.lanes_per_row == 4 || o.lanes_per_row == 8)
         P->lanes = o.lanes_per_row;
     else return MPK_ERR_ARG;
-    if (o.task_units < 0 || o.kernel < 0 || o.kernel > 4 || o.task_dispatch < 0 || o.task_dispatch > 2)
+    if (o.task_units < 0 || o.kernel < 0 || o.kernel > 5 || o.task_dispatch < 0 || o.task_dispatch > 2)
         return MPK_ERR_ARG;
-    P->lane_kernel = (o.kernel == 4 || P->lanes > 1) ? 1 : 0;
+    P->lane_kernel = (o.kernel == 4 || o.kernel == 5 || P->lanes > 1) ? 1 : 0;
     P->lane_slack = o.slack_tasks > 0 ? o.slack_tasks : 0;
     MPK_CUDA(cudaStreamSynchronize(s));
     auto t1 = std::chrono::steady_clock::now();
@@ -1335,6 +1335,7 @@ mpk_status mpk_get_lane_graph(mpk_plan_s *P, int lpr, int units, LaneGraph **out
                 }
                 code.push_back(sl * lpr + h);
                 meta.push_back(make_int4((int)(32ll * sp[sl] + h * R), slen[sl], sr[sl] + h * R, sr[sl + 1]));
+                G->max_len = std::max(G->max_len, slen[sl]);
                 in_chunk++;
             }
         }

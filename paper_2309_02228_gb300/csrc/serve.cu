@@ -46,6 +46,8 @@ struct CachedPlan {
     int64_t n, nnz;
     mpk_plan_t plan;
     int64_t bytes;
+    // the pattern itself (host): a matching hash is confirmed entry by entry before reuse
+    std::shared_ptr<const std::vector<int32_t>> rp, ci;
 };
 
 uint64_t hash_pattern(const std::vector<int32_t> &rp, const std::vector<int32_t> &ci) {
@@ -105,7 +107,8 @@ struct mpk_server_s {
         {
             std::lock_guard<std::mutex> lk(mu);
             for (auto it = idle_plans.begin(); it != idle_plans.end(); ++it) {
-                if (it->pattern == r.pattern && it->n == r.n && it->nnz == r.nnz) {
+                if (it->pattern == r.pattern && it->n == r.n && it->nnz == r.nnz && *it->rp == r.rp &&
+                    *it->ci == r.ci) {
                     *out = it->plan;
                     *plan_bytes = it->bytes;
                     idle_bytes -= it->bytes;
@@ -171,7 +174,9 @@ struct mpk_server_s {
         used_bytes -= r.est_bytes;
         if (plan) {
             if (st == MPK_OK && used_bytes + idle_bytes + plan_bytes <= o.hbm_budget_bytes) {
-                idle_plans.push_back(CachedPlan{r.pattern, r.n, r.nnz, plan, plan_bytes});
+                idle_plans.push_back(CachedPlan{r.pattern, r.n, r.nnz, plan, plan_bytes,
+                                                std::make_shared<const std::vector<int32_t>>(r.rp),
+                                                std::make_shared<const std::vector<int32_t>>(r.ci)});
                 idle_bytes += plan_bytes;
             } else {
                 mpk_plan_destroy(plan);

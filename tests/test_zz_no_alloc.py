@@ -1,10 +1,14 @@
-"""The allocation-free final-power call (mpk_apply_final_noalloc) against mpk_apply.
+"""The allocation-free final-power call (mpk_apply_final_noalloc) against the oracle and
+against mpk_apply.
 
 mpk_apply_final_noalloc keeps its intermediate vectors in the library's fixed per-device
 scratch array.  Each case calls it twice in a row, on different inputs, and compares each
-result with mpk_apply(..., MPK_FINAL_ONLY | MPK_UNBLOCKED) on the same plan.  The tolerance is
-the MPK's own, per entry relative to (|A_theta|^p |x|)_i: 64*p*2^-53 in FP64, 64*p*2^-24 in
-FP32.  The two calls run the same kernels, so the results are also expected to be identical.
+result with the CPU oracle's recurrence (oracle.mpk, on the matrix and vector as the GPU holds
+them: FP32-rounded for FP32 cases, level-ordered for level-order I/O) and with
+mpk_apply(..., MPK_FINAL_ONLY | MPK_UNBLOCKED) on the same plan.  The tolerance is the MPK's
+own, per entry relative to (|A_theta|^p |x|)_i: 64*p*2^-53 in FP64, 64*p*2^-24 in FP32 (one
+more power's worth for the gamma sums).  The two GPU calls run the same kernels, so their
+results are also expected to be identical.
 Also checked: device free memory does not change across calls after the first, and a plan
 above the scratch limit is refused before any work.  This file is collected last, so it also
 runs after every other GPU test in the same process."""
@@ -12,6 +16,7 @@ import numpy as np
 import pytest
 
 import mpk_inputs as mi
+import oracle
 from tests.gpu_util import U32, U64, abs_powers, max_rel_err, to_dev
 
 pytestmark = pytest.mark.gpu
@@ -99,9 +104,14 @@ def test_noalloc_matches_mpk_apply_twice(m, case):
             # level-order I/O: measure against the plan's own (level-ordered) matrix
             grp, gci, gval = m.mpk_plan_csr(plan, tdt)
             B = mi.CSR(grp.cpu().numpy(), gci.cpu().numpy(), gval.cpu().numpy().astype(np.float64))
-            den = _den(B, coeffs, x, gamma)
         else:
-            den = _den(A, coeffs, x, gamma)
+            B = mi.CSR(A.row_ptr, A.col, A.val.astype(np.float32).astype(np.float64)) if dt == "f32" else A
+        den = _den(B, coeffs, x, gamma)
+        xo = x.cpu().numpy().astype(np.float64)
+        ys_or = oracle.mpk(B, p, coeffs, xo)
+        want_or = ys_or[p] if gamma is None else sum(g * ys_or[k] for k, g in enumerate(gamma))
+        tol_or = 64 * (p + (1 if gamma is not None else 0)) * (U64 if dt == "f64" else U32)
+        assert max_rel_err(got, want_or, den) <= tol_or
         assert max_rel_err(got, want, den) <= tol
         assert np.array_equal(got, want)
 
