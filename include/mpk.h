@@ -323,6 +323,15 @@ mpk_status mpk_apply_final_noalloc(mpk_plan_t plan, const mpk_coeffs *co, mpk_dt
  * threads.  Always MPK_OK.  No counterpart in the paper. */
 mpk_status mpk_noalloc_forget(void);
 
+/* Ritz values (Sec. 4: the Newton shifts are "eigenvalue information" from a few steps of
+ * standard GMRES): the eigenvalues of the k x k leading block of an upper Hessenberg matrix,
+ * by the implicitly double-shifted QR iteration.  H: HOST, column-major with leading
+ * dimension ldh >= k (entries below the subdiagonal are ignored); wr, wi: HOST arrays of k
+ * receiving real and imaginary parts (complex pairs consecutive, positive imaginary part
+ * first).  MPK_ERR_NOT_CONVERGED after 60 k steps without convergence; MPK_ERR_ARG for NULLs,
+ * k < 1 or non-finite entries.  Synchronous, host only (no device work). */
+mpk_status mpk_hessenberg_eigvals(const double *H, int64_t ldh, int32_t k, double *wr, double *wi);
+
 /* Host helpers for coefficient triples (host arrays of length p). */
 /* Chebyshev basis on [alpha, beta]: y_k = T_k((A - c0 I)/d) x, c0 = (alpha+beta)/2,
  * d = (beta-alpha)/2 (three-term recursion; Sec. 5.3 Chebyshev smoother). */
@@ -423,6 +432,15 @@ typedef struct {
                                excludes jacobi and poly_degree.  Default 0 */
     int32_t gs2_gamma;      /* inner iterations of GS2, 0..15 (default 1, as in the paper's
                                GS2 experiments) */
+    double *trace_hist;     /* HOST, trace_cap doubles, or NULL: receives, for the first
+                               restart cycle in the s-step (Newton) basis, the residual
+                               estimate |g_{c+1}| / ||r|| after each column c's Givens
+                               rotation (Alg. 3(c)'s convergence check), r the cycle's
+                               right-hand side; info.trace_len counts the entries */
+    int32_t trace_cap;      /* capacity of trace_hist */
+    double *trace_H;        /* HOST, (restart + 1) x restart doubles, column-major, or NULL:
+                               that cycle's Arnoldi Hessenberg (before the rotations), zero past
+                               its last column */
 } mpk_gmres_opts;
 
 typedef struct {
@@ -435,6 +453,7 @@ typedef struct {
     double ms_total, ms_mpk, ms_ortho, ms_other;   /* CUDA-event timings per phase */
     int32_t poly_degree;    /* degree of the polynomial preconditioner used (0: none) */
     double poly_interval[2];/* smallest and largest root of the polynomial */
+    int32_t trace_len;      /* entries written to opts.trace_hist */
 } mpk_gmres_info;
 
 mpk_status mpk_gmres_opts_default(mpk_gmres_opts *o);
@@ -446,8 +465,9 @@ mpk_status mpk_gmres_opts_default(mpk_gmres_opts *o);
  * Each outer step computes r = b - A x in FP64, runs one restart cycle of s-step GMRES on
  * A d = r in the basis precision (to inner_tol relative to ||r||, or to tol overall with an
  * FP64 basis) and adds d to x; it stops when ||b - A x|| <= tol ||b||.  Without shifts, the
- * first cycle is plain GMRES(m) (classical Gram-Schmidt, two sweeps) whose Ritz values give
- * the Newton shifts.  A Cholesky breakdown ends the cycle at the last good block and halves
+ * first cycle is plain GMRES(m) (classical Gram-Schmidt, two sweeps) whose Ritz values (the
+ * real parts of the eigenvalues of its k x k Arnoldi Hessenberg, mpk_hessenberg_eigvals),
+ * Leja-ordered, give the Newton shifts.  A Cholesky breakdown ends the cycle at the last good block and halves
  * s for later cycles; at s = 1 it returns MPK_ERR_BREAKDOWN.
  * Synchronous on stream (the host reads a few status words per block).  Returns MPK_OK,
  * MPK_ERR_NOT_CONVERGED (limits reached; x holds the best iterate), MPK_ERR_BREAKDOWN, or an

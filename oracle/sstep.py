@@ -202,7 +202,9 @@ def sstep_gmres(A, b, x0=None, s=4, m=48, tol=1e-8, max_restarts=1000, shifts=No
     Without ``shifts`` the first cycle runs plain GMRES(m) and its Ritz values give the
     shifts (Sec. 4).  ``precond`` (v -> P^-1 v) makes it right-preconditioned: the basis is
     that of A P^-1, y_k = (A P^-1 - theta_k I) y_{k-1}, and x += P^-1 (Q y).
-    Returns dict(x, iters, hist, shifts, converged, block_hist)."""
+    Returns dict(x, iters, hist, shifts, converged, block_hist, H_cycle, k_cycle): H_cycle is
+    the unrotated Arnoldi Hessenberg ((m+1) x m) of the first s-step cycle and k_cycle its
+    columns (None, 0 when no s-step cycle ran)."""
     M = precond if precond is not None else (lambda v: v)
     n = b.shape[0]
     x = np.zeros(n) if x0 is None else x0.astype(np.float64).copy()
@@ -211,6 +213,7 @@ def sstep_gmres(A, b, x0=None, s=4, m=48, tol=1e-8, max_restarts=1000, shifts=No
     block_hist = []
     iters = 0
     cycle0 = 0
+    H_cycle, k_cycle = None, 0
     if basis == "newton" and shifts is None:
         r0 = gmres(A, b, x, m=m, tol=tol, max_restarts=1, precond=precond)
         x = r0["x"]
@@ -221,7 +224,7 @@ def sstep_gmres(A, b, x0=None, s=4, m=48, tol=1e-8, max_restarts=1000, shifts=No
         cycle0 = 1
         if r0["converged"]:
             return dict(x=x, iters=iters, hist=hist, shifts=shifts, converged=True,
-                        block_hist=block_hist)
+                        block_hist=block_hist, H_cycle=H_cycle, k_cycle=k_cycle)
     if basis == "monomial":
         theta = np.zeros(s)
     else:
@@ -231,7 +234,7 @@ def sstep_gmres(A, b, x0=None, s=4, m=48, tol=1e-8, max_restarts=1000, shifts=No
         beta = np.linalg.norm(r)
         if beta <= tol * nb:
             return dict(x=x, iters=iters, hist=hist, shifts=theta, converged=True,
-                        block_hist=block_hist)
+                        block_hist=block_hist, H_cycle=H_cycle, k_cycle=k_cycle)
         Q = np.zeros((n, m + 1))
         Harn = np.zeros((m + 1, m))   # Arnoldi H (kept unrotated for the reconstruction)
         H = np.zeros((m + 1, m))      # H with the Givens rotations applied
@@ -297,11 +300,14 @@ def sstep_gmres(A, b, x0=None, s=4, m=48, tol=1e-8, max_restarts=1000, shifts=No
                     break
             block_hist.append(abs(g[k]) / nb)
             j += S
+        if H_cycle is None:
+            H_cycle, k_cycle = Harn.copy(), k
         y = np.linalg.solve(np.triu(H[:k, :k]), g[:k])
         x = x + M(Q[:, :k] @ y)
     r = b - spmv(A, x)
     return dict(x=x, iters=iters, hist=hist, shifts=theta,
-                converged=bool(np.linalg.norm(r) <= tol * nb), block_hist=block_hist)
+                converged=bool(np.linalg.norm(r) <= tol * nb), block_hist=block_hist,
+                H_cycle=H_cycle, k_cycle=k_cycle)
 
 
 def refine_solve(A, b, tol=1e-8, s=8, m=48, inner_tol=1e-5, max_outer=50, inner_cycles=1,

@@ -99,7 +99,9 @@ class mpk_gmres_opts(ctypes.Structure):
                 ("basis", ctypes.c_int), ("bcgs_passes", ctypes.c_int32),
                 ("shifts", ctypes.c_void_p), ("mpk_flags", ctypes.c_uint32),
                 ("poly_degree", ctypes.c_int32), ("poly_f64", ctypes.c_int32),
-                ("jacobi", ctypes.c_int32), ("gs2", ctypes.c_int32), ("gs2_gamma", ctypes.c_int32)]
+                ("jacobi", ctypes.c_int32), ("gs2", ctypes.c_int32), ("gs2_gamma", ctypes.c_int32),
+                ("trace_hist", ctypes.c_void_p), ("trace_cap", ctypes.c_int32),
+                ("trace_H", ctypes.c_void_p)]
 
 
 class mpk_gmres_info(ctypes.Structure):
@@ -108,7 +110,7 @@ class mpk_gmres_info(ctypes.Structure):
                 ("shifts", ctypes.c_double * 64), ("ms_total", ctypes.c_double),
                 ("ms_mpk", ctypes.c_double), ("ms_ortho", ctypes.c_double),
                 ("ms_other", ctypes.c_double), ("poly_degree", ctypes.c_int32),
-                ("poly_interval", ctypes.c_double * 2)]
+                ("poly_interval", ctypes.c_double * 2), ("trace_len", ctypes.c_int32)]
 
 
 class mpk_tune_info(ctypes.Structure):
@@ -168,6 +170,7 @@ _SIGS = [
     ("mpk_coeffs_chebyshev", ctypes.c_int, [_D, _D, _I32, _P, _P, _P]),
     ("mpk_coeffs_newton", ctypes.c_int, [_P, _I32, _P, _P, _P]),
     ("mpk_leja_order", ctypes.c_int, [_P, _I32, _I32, _P]),
+    ("mpk_hessenberg_eigvals", ctypes.c_int, [_P, _I64, _I32, _P, _P]),
     ("mpk_gmres_opts_default", ctypes.c_int, [ctypes.POINTER(mpk_gmres_opts)]),
     ("sstep_gmres_solve", ctypes.c_int, [_P, _P, _P, ctypes.POINTER(mpk_gmres_opts), ctypes.POINTER(mpk_gmres_info), _P]),
     ("mpk_autotune", ctypes.c_int, [ctypes.POINTER(mpk_csr), _I32, ctypes.POINTER(mpk_coeffs), ctypes.c_int,
@@ -448,14 +451,24 @@ def mpk_gmres_opts_default(**overrides) -> mpk_gmres_opts:
     return o
 
 
-def sstep_gmres_solve(plan, b, x, opts=None, shifts=None, stream=None, check=True):
+def sstep_gmres_solve(plan, b, x, opts=None, shifts=None, stream=None, check=True, trace=False):
     """Solve A x = b (b, x: CUDA float64 tensors in the original order).  Returns the info
-    struct as a dict; raises on an error status unless check=False."""
+    struct as a dict; raises on an error status unless check=False.  trace=True also returns
+    the first s-step cycle's residual estimates ("trace_hist") and Arnoldi Hessenberg
+    ("trace_H", (m+1) x m)."""
     o = opts if opts is not None else mpk_gmres_opts_default()
     keep = None
     if shifts is not None:
         keep = np.ascontiguousarray(shifts, dtype=np.float64)
         o.shifts = keep.ctypes.data
+    th = tH = None
+    if trace:
+        m = int(o.restart)
+        th = np.zeros(m)
+        tH = np.zeros((m, m + 1))          # row c = column c of the (m+1) x m Hessenberg
+        o.trace_hist = th.ctypes.data
+        o.trace_cap = m
+        o.trace_H = tH.ctypes.data
     info = mpk_gmres_info()
     st = lib().sstep_gmres_solve(plan.handle, _ptr(b), _ptr(x), ctypes.byref(o),
                                  ctypes.byref(info), _stream_ptr(stream))
@@ -463,6 +476,12 @@ def sstep_gmres_solve(plan, b, x, opts=None, shifts=None, stream=None, check=Tru
     d["poly_interval"] = (info.poly_interval[0], info.poly_interval[1])
     d["shifts"] = np.array(info.shifts[: o.s])
     d["status_code"] = int(st)
+    if trace:
+        d["trace_hist"] = th[: info.trace_len].copy()
+        d["trace_H"] = tH.T.copy()
+        o.trace_hist = None
+        o.trace_H = None
+        o.trace_cap = 0
     if check:
         _check(st, "sstep_gmres_solve")
     del keep
@@ -671,3 +690,17 @@ def mpk_fma_peak(dtype, stream=None):
 def mpk_noalloc_forget():
     """Drop the scratch addresses mpk_apply_final_noalloc kept (after a device reset)."""
     _check(lib().mpk_noalloc_forget(), "mpk_noalloc_forget")
+
+
+def mpk_hessenberg_eigvals(H, k=None):
+    """Eigenvalues (complex numpy array) of the leading k x k block of the upper Hessenberg
+    host matrix H (a 2-D numpy array), computed by the library's host QR iteration."""
+    Hc = np.asfortranarray(np.asarray(H, dtype=np.float64))
+    k = Hc.shape[1] if k is None else int(k)
+    if Hc.shape[0] < k or Hc.shape[1] < k:
+        raise ValueError("H is smaller than k x k")
+    wr = np.zeros(k)
+    wi = np.zeros(k)
+    _check(lib().mpk_hessenberg_eigvals(Hc.ctypes.data, Hc.shape[0], k, wr.ctypes.data, wi.ctypes.data),
+           "mpk_hessenberg_eigvals")
+    return wr + 1j * wi

@@ -2721,6 +2721,126 @@ extern "C" mpk_status mpk_leja_order(const double *values, int32_t n, int32_t co
     return MPK_OK;
 }
 
+// Eigenvalues of a real upper Hessenberg matrix by the implicitly double-shifted QR
+// iteration (Francis): on the active unreduced block [lo, hi], one step applies the
+// polynomial (H - mu1 I)(H - mu2 I) of the trailing 2 x 2 block's eigenvalues mu1, mu2 through
+// its first column, a 3-vector, and restores the Hessenberg form by chasing the bulge with
+// 3 x 3 Householder reflections (2 x 2 at the bottom).  A subdiagonal entry below
+// eps (|h_{i-1,i-1}| + |h_ii|) is set to zero, splitting the block; 1 x 1 and 2 x 2 blocks give
+// their eigenvalues directly.  Every tenth step of a block without a split uses a shift
+// built from the last two subdiagonal entries instead, which breaks up cycles.
+extern "C" mpk_status mpk_hessenberg_eigvals(const double *H, int64_t ldh, int32_t k, double *wr, double *wi) {
+    if (!H || !wr || !wi || k < 1 || ldh < k) return MPK_ERR_ARG;
+    const int n = k;
+    std::vector<double> a((size_t)n * n, 0.0);   // row-major working copy
+    auto A = [&](int i, int j) -> double & { return a[(size_t)i * n + j]; };
+    double anorm = 0.0;
+    for (int j = 0; j < n; j++)
+        for (int i = 0; i <= std::min(j + 1, n - 1); i++) {
+            A(i, j) = H[(size_t)i + (size_t)j * ldh];
+            anorm += std::fabs(A(i, j));
+        }
+    if (!std::isfinite(anorm)) return MPK_ERR_ARG;
+    const double eps = 2.220446049250313e-16;
+    int hi = n - 1, iter = 0, total = 0;
+    while (hi >= 0) {
+        int lo = hi;
+        for (; lo > 0; lo--) {
+            double sc = std::fabs(A(lo - 1, lo - 1)) + std::fabs(A(lo, lo));
+            if (sc == 0.0) sc = anorm;
+            if (std::fabs(A(lo, lo - 1)) <= eps * sc) {
+                A(lo, lo - 1) = 0.0;
+                break;
+            }
+        }
+        if (lo == hi) {                       // a 1 x 1 block
+            wr[hi] = A(hi, hi);
+            wi[hi] = 0.0;
+            hi--;
+            iter = 0;
+            continue;
+        }
+        if (lo == hi - 1) {                   // a 2 x 2 block: its characteristic polynomial
+            const double p = A(hi - 1, hi - 1), q = A(hi - 1, hi), r = A(hi, hi - 1), t = A(hi, hi);
+            const double mean = 0.5 * (p + t), half = 0.5 * (p - t);
+            const double disc = half * half + q * r;
+            if (disc >= 0.0) {
+                const double sq = std::sqrt(disc);
+                const double big = mean + (half >= 0.0 ? sq : -sq);     // no cancellation
+                const double det = p * t - q * r;
+                const double small = big != 0.0 ? det / big : mean - (half >= 0.0 ? sq : -sq);
+                wr[hi - 1] = big;
+                wr[hi] = small;
+                wi[hi - 1] = wi[hi] = 0.0;
+            } else {
+                const double im = std::sqrt(-disc);
+                wr[hi - 1] = wr[hi] = mean;
+                wi[hi - 1] = im;
+                wi[hi] = -im;
+            }
+            hi -= 2;
+            iter = 0;
+            continue;
+        }
+        if (++total > 60 * n) return MPK_ERR_NOT_CONVERGED;
+        ++iter;
+        // the shift polynomial t^2 - sm t + pr of the trailing 2 x 2 block (or the cycle breaker)
+        double sm, pr;
+        if (iter % 10 == 0) {
+            const double sig = std::fabs(A(hi, hi - 1)) + std::fabs(A(hi - 1, hi - 2));
+            const double x = A(hi, hi) + 0.7 * sig;
+            sm = 2.0 * x;
+            pr = x * x + 0.4 * sig * sig;
+        } else {
+            sm = A(hi - 1, hi - 1) + A(hi, hi);
+            pr = A(hi - 1, hi - 1) * A(hi, hi) - A(hi - 1, hi) * A(hi, hi - 1);
+        }
+        // first column of (H^2 - sm H + pr I) restricted to the block: rows lo .. lo + 2
+        double x1 = A(lo, lo) * A(lo, lo) + A(lo, lo + 1) * A(lo + 1, lo) - sm * A(lo, lo) + pr;
+        double x2 = A(lo + 1, lo) * (A(lo, lo) + A(lo + 1, lo + 1) - sm);
+        double x3 = A(lo + 1, lo) * A(lo + 2, lo + 1);
+        for (int c = lo; c <= hi - 1; c++) {
+            const int len = c + 2 <= hi ? 3 : 2;   // the last reflection acts on two rows
+            if (c > lo) {
+                x1 = A(c, c - 1);
+                x2 = A(c + 1, c - 1);
+                x3 = len == 3 ? A(c + 2, c - 1) : 0.0;
+            }
+            const double nrm = std::sqrt(x1 * x1 + x2 * x2 + x3 * x3);
+            if (nrm == 0.0) continue;
+            const double alpha = x1 > 0.0 ? -nrm : nrm;
+            const double v1 = x1 - alpha, v2 = x2, v3 = x3;
+            const double vv = v1 * v1 + v2 * v2 + v3 * v3;
+            if (vv == 0.0) continue;
+            const double beta = 2.0 / vv;
+            // from the left: rows c .. c + len - 1, the block's columns from c - 1 on
+            for (int j = std::max(lo, c - 1); j <= hi; j++) {
+                double sdot = v1 * A(c, j) + v2 * A(c + 1, j);
+                if (len == 3) sdot += v3 * A(c + 2, j);
+                sdot *= beta;
+                A(c, j) -= sdot * v1;
+                A(c + 1, j) -= sdot * v2;
+                if (len == 3) A(c + 2, j) -= sdot * v3;
+            }
+            if (c > lo) {                     // the bulge column is now (alpha, 0, 0)
+                A(c, c - 1) = alpha;
+                A(c + 1, c - 1) = 0.0;
+                if (len == 3) A(c + 2, c - 1) = 0.0;
+            }
+            // from the right: columns c .. c + len - 1, the block's rows up to c + 3
+            for (int i = lo; i <= std::min(c + 3, hi); i++) {
+                double sdot = A(i, c) * v1 + A(i, c + 1) * v2;
+                if (len == 3) sdot += A(i, c + 2) * v3;
+                sdot *= beta;
+                A(i, c) -= sdot * v1;
+                A(i, c + 1) -= sdot * v2;
+                if (len == 3) A(i, c + 2) -= sdot * v3;
+            }
+        }
+    }
+    return MPK_OK;
+}
+
 extern "C" const char *mpk_status_str(mpk_status s) {
     switch (s) {
     case MPK_OK: return "MPK_OK";

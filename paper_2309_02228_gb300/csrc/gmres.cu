@@ -349,7 +349,7 @@ struct CycleState {            // device memory, one per solve
     double C2[(MMAX + 1) * SMAX];
     double R1[SMAX * SMAX], R2[SMAX * SMAX], Rinv[SMAX * SMAX];
     double y[MMAX + 1];
-    double ritz[MMAX];
+    double hist[MMAX];                // |g_{c+1}| after column c's rotation (residual estimate)
     double nrm[4];
     // scratch of the single-thread kernels (kept here: device memory, not per-thread stack)
     double A[SMAX * SMAX];
@@ -528,6 +528,7 @@ __global__ void __launch_bounds__(256) hess_kernel(CycleState *cst, int j, int S
             cst->g[c] = cs * cst->g[c];
             cst->kdone = c + 1;
             cst->est = fabs(cst->g[c + 1]);
+            cst->hist[c] = cst->est;
             if (fabs(cst->g[c + 1]) <= tol_abs) {
                 cst->conv_k = c + 1;
                 s_stop = 1;
@@ -563,105 +564,6 @@ __global__ void __launch_bounds__(128) lsq_kernel(CycleState *cst, int k) {
         __syncthreads();
     }
     for (int i = tid; i < k; i += nt) cst->y[i] = yy[i];
-}
-
-// Ritz values: eigenvalues of the symmetric part of the leading k x k Arnoldi H by Jacobi
-// rotations (for a symmetric A the Arnoldi H is symmetric tridiagonal up to rounding, so these
-// are its Ritz values; for an unsymmetric A they are real values from its field of values).
-// Parallel ordering: each round rotates kp/2 disjoint pairs at once (round-robin schedule of
-// the kp = k rounded up to even indices; a padding index stays decoupled), kp - 1 rounds per
-// sweep; sweeps stop once the off-diagonal part is below 1e-15 of the Frobenius norm.
-// Shared memory: kp x (kp + 1) doubles.
-static constexpr int RITZ_THREADS = 256;
-__global__ void __launch_bounds__(RITZ_THREADS) ritz_kernel(CycleState *cst, int k) {
-    extern __shared__ double sA[];
-    __shared__ double s_c[MMAX / 2 + 1], s_s[MMAX / 2 + 1], s_red[RITZ_THREADS / 32];
-    __shared__ int s_p[MMAX / 2 + 1], s_q[MMAX / 2 + 1];
-    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
-    const int ldh = MMAX + 1;
-    const int kp = (k + 1) & ~1, ld = kp + 1, half = kp / 2;
-    for (int e = tid; e < kp * kp; e += nt) {
-        const int r = e % kp, c = e / kp;
-        sA[r + c * ld] = (r < k && c < k) ? 0.5 * (cst->H[r + c * ldh] + cst->H[c + r * ldh]) : 0.0;
-    }
-    __syncthreads();
-    auto block_sum = [&](double v) -> double {
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) s_red[wid] = v;
-        __syncthreads();
-        double t = 0.0;
-        for (int w = 0; w < nt / 32; w++) t += s_red[w];
-        __syncthreads();
-        return t;
-    };
-    double fro = 0.0;
-    for (int e = tid; e < kp * kp; e += nt) {
-        const double v = sA[(e % kp) + (e / kp) * ld];
-        fro += v * v;
-    }
-    fro = block_sum(fro);
-    for (int sweep = 0; sweep < 30; sweep++) {
-        double off = 0.0;
-        for (int e = tid; e < kp * kp; e += nt) {
-            const int r = e % kp, c = e / kp;
-            if (r != c) {
-                const double v = sA[r + c * ld];
-                off += v * v;
-            }
-        }
-        off = block_sum(off);
-        if (!(off > 1e-30 * fro)) break;
-        for (int round = 0; round < kp - 1; round++) {
-            if (tid < half) {
-                int p, q;
-                if (tid == 0) {
-                    p = round;
-                    q = kp - 1;
-                } else {
-                    p = (round + tid) % (kp - 1);
-                    q = (round - tid + kp - 1) % (kp - 1);
-                }
-                if (p > q) {
-                    const int t = p;
-                    p = q;
-                    q = t;
-                }
-                const double apq = sA[p + q * ld];
-                double c = 1.0, s = 0.0;
-                if (fabs(apq) >= 1e-300) {
-                    const double app = sA[p + p * ld], aqq = sA[q + q * ld];
-                    const double tau = (aqq - app) / (2.0 * apq);
-                    const double t = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                    c = 1.0 / sqrt(1.0 + t * t);
-                    s = t * c;
-                }
-                s_p[tid] = p;
-                s_q[tid] = q;
-                s_c[tid] = c;
-                s_s[tid] = s;
-            }
-            __syncthreads();
-            for (int e = tid; e < half * kp; e += nt) {   // columns p, q
-                const int i = e / kp, r = e % kp;
-                const int p = s_p[i], q = s_q[i];
-                const double c = s_c[i], s = s_s[i];
-                const double arp = sA[r + p * ld], arq = sA[r + q * ld];
-                sA[r + p * ld] = c * arp - s * arq;
-                sA[r + q * ld] = s * arp + c * arq;
-            }
-            __syncthreads();
-            for (int e = tid; e < half * kp; e += nt) {   // rows p, q
-                const int i = e / kp, r = e % kp;
-                const int p = s_p[i], q = s_q[i];
-                const double c = s_c[i], s = s_s[i];
-                const double apr = sA[p + r * ld], aqr = sA[q + r * ld];
-                sA[p + r * ld] = c * apr - s * aqr;
-                sA[q + r * ld] = s * apr + c * aqr;
-            }
-            __syncthreads();
-        }
-    }
-    for (int i = tid; i < k; i += nt) cst->ritz[i] = sA[i + i * ld];
 }
 
 __global__ void cycle_init_kernel(CycleState *cst, const double *beta) {
@@ -738,6 +640,28 @@ struct Solver {
     std::vector<double> theta;
     int s_cur;
     mpk_gmres_info info{};
+    bool trace_pending = false;   // the first Newton-basis cycle still has to be recorded
+    double trace_scale = 1.0;     // norm of that cycle's right-hand side
+
+    // the residual estimates |g_{c+1}| / ||r|| of the cycle's k columns and its Arnoldi H
+    // ((m+1) x m, column-major, zeros past column k) into the caller's host buffers
+    mpk_status record_trace(int k) {
+        const int m = o.restart;
+        std::vector<double> hist(k), Hh((size_t)(MMAX + 1) * m, 0.0);
+        MPK_CUDA(cudaMemcpyAsync(hist.data(), cst->hist, k * sizeof(double), cudaMemcpyDeviceToHost, st));
+        MPK_CUDA(cudaMemcpyAsync(Hh.data(), cst->H, (size_t)(MMAX + 1) * k * sizeof(double), cudaMemcpyDeviceToHost, st));
+        MPK_CUDA(cudaStreamSynchronize(st));
+        const int cnt = std::min(k, std::max(0, o.trace_cap));
+        if (o.trace_hist)
+            for (int c = 0; c < cnt; c++) o.trace_hist[c] = trace_scale > 0 ? hist[c] / trace_scale : hist[c];
+        if (o.trace_H)
+            for (int c = 0; c < m; c++)
+                for (int r = 0; r <= m; r++)
+                    o.trace_H[(size_t)r + (size_t)c * (m + 1)] = c < k ? Hh[(size_t)r + (size_t)c * (MMAX + 1)] : 0.0;
+        info.trace_len = cnt;
+        trace_pending = false;
+        return MPK_OK;
+    }
 
     Solver(mpk_plan_s *p, cudaStream_t s_) : P(p), st(s_), t_mpk(s_), t_ortho(s_), t_other(s_) {}
 
@@ -968,18 +892,16 @@ struct Solver {
             t_other.stop();
         }
         if (!newton && !poly_on && k > 0) {
-            const int kp = (k + 1) & ~1;
-            // the attribute is shared by all threads: always the same maximum (m <= MMAX)
-            MPK_CUDA(cudaFuncSetAttribute(ritz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)(MMAX * (MMAX + 1) * sizeof(double))));
-            ritz_kernel<<<1, RITZ_THREADS, (size_t)kp * (kp + 1) * sizeof(double), st>>>(cst, k);
-            MPK_CUDA(cudaGetLastError());
-            std::vector<double> rz(k);
-            MPK_CUDA(cudaMemcpyAsync(rz.data(), cst->ritz, k * sizeof(double), cudaMemcpyDeviceToHost, st));
+            // Ritz values: eigenvalues of the leading k x k block of the cycle's Arnoldi H
+            // (QR iteration on the host: k <= 128), real parts, Leja-ordered
+            std::vector<double> Hh((size_t)(MMAX + 1) * k), wr(k), wi(k);
+            MPK_CUDA(cudaMemcpyAsync(Hh.data(), cst->H, Hh.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
             MPK_CUDA(cudaStreamSynchronize(st));
+            MPK_TRY(mpk_hessenberg_eigvals(Hh.data(), MMAX + 1, k, wr.data(), wi.data()));
             theta.assign(o.s, 0.0);
-            mpk_leja_order(rz.data(), k, o.s, theta.data());
+            mpk_leja_order(wr.data(), k, o.s, theta.data());
         }
+        if (newton && trace_pending && k > 0) MPK_TRY(record_trace(k));
         *k_used = k;
         return MPK_OK;
     }
@@ -1127,6 +1049,7 @@ struct Solver {
             need_shifts = false;
         }
         bool have_shifts = !need_shifts;
+        trace_pending = o.trace_hist != nullptr || o.trace_H != nullptr;
         mpk_status result = MPK_ERR_NOT_CONVERGED;
         double relres = 1.0, best_rel = 1e300;
         int since_best = 0;
@@ -1167,6 +1090,7 @@ struct Solver {
             } else if (poly_on) {
                 MPK_TRY(cycle(tol_abs, false, 1, &k, &bd));   // single columns on A q(A)
             } else {
+                trace_scale = hr;
                 MPK_TRY(cycle(tol_abs, true, s_cur, &k, &bd));
                 if (bd) {
                     if (s_cur == 1) { result = MPK_ERR_BREAKDOWN; break; }
