@@ -154,19 +154,30 @@ __global__ void __launch_bounds__(256, 2) gram_kernel(const T *X, int64_t ldx, i
                 T acc[ACC];   // acc[a * SB + b]
 #pragma unroll
                 for (int e = 0; e < ACC; e++) acc[e] = (T)0;
-                for (int st = rpart; st < GRAM_RANGE / 32; st += rsplit) {
-                    if (base + st * 32 >= n) break;
+                // the values of one step (32 rows of the tile's columns); the next step's are
+                // loaded before this step's FMAs, so two steps' loads are in flight per lane
+                auto load = [&](int st, T (&xv)[CT], T (&yv)[SB]) {
                     const int64_t r = base + st * 32 + lane;
-                    const bool in = r < n;
-                    T xv[CT], yv[SB];
+                    const bool in = st < GRAM_RANGE / 32 && r < n;
 #pragma unroll
                     for (int a = 0; a < CT; a++) xv[a] = (in && c0 + a < K) ? X[(int64_t)(c0 + a) * ldx + r] : (T)0;
 #pragma unroll
                     for (int b = 0; b < SB; b++) yv[b] = (in && b < S) ? Y[(int64_t)b * ldy + r] : (T)0;
+                };
+                T xv[CT], yv[SB];
+                load(rpart, xv, yv);
+                for (int st = rpart; st < GRAM_RANGE / 32; st += rsplit) {
+                    if (base + st * 32 >= n) break;
+                    T xn[CT], yn[SB];
+                    load(st + rsplit, xn, yn);
 #pragma unroll
                     for (int a = 0; a < CT; a++)
 #pragma unroll
                         for (int b = 0; b < SB; b++) acc[a * SB + b] = fma(xv[a], yv[b], acc[a * SB + b]);
+#pragma unroll
+                    for (int a = 0; a < CT; a++) xv[a] = xn[a];
+#pragma unroll
+                    for (int b = 0; b < SB; b++) yv[b] = yn[b];
                 }
                 // this visit's block sums over the lanes, then into the FP64 totals (each entry
                 // has one owner lane, so no two lanes add to the same slot)
@@ -239,11 +250,15 @@ __global__ void __launch_bounds__(256) update_kernel(const T *Q, int64_t ldq, in
             T w[SB];
 #pragma unroll
             for (int b = 0; b < SB; b++) w[b] = b < S ? W[(int64_t)b * ldw + i] : (T)0;
-            // eight basis columns' loads in flight before their FMAs (ascending order kept)
-            for (int a0 = 0; a0 < K1; a0 += 8) {
-                T q[8];
+            // groups of eight basis columns; the next group's loads are issued before this
+            // group's FMAs (ascending order of the FMAs kept)
+            T q[8];
 #pragma unroll
-                for (int u = 0; u < 8; u++) q[u] = a0 + u < K1 ? Q[(int64_t)(a0 + u) * ldq + i] : (T)0;
+            for (int u = 0; u < 8; u++) q[u] = u < K1 ? Q[(int64_t)u * ldq + i] : (T)0;
+            for (int a0 = 0; a0 < K1; a0 += 8) {
+                T qn[8];
+#pragma unroll
+                for (int u = 0; u < 8; u++) qn[u] = a0 + 8 + u < K1 ? Q[(int64_t)(a0 + 8 + u) * ldq + i] : (T)0;
 #pragma unroll
                 for (int u = 0; u < 8; u++)
                     if (a0 + u < K1) {
@@ -251,6 +266,8 @@ __global__ void __launch_bounds__(256) update_kernel(const T *Q, int64_t ldq, in
                         for (int b = 0; b < SB; b++)
                             if (b < S) w[b] = fma(-q[u], cs[a0 + u][b], w[b]);
                     }
+#pragma unroll
+                for (int u = 0; u < 8; u++) q[u] = qn[u];
             }
             T wn[SB];
 #pragma unroll
