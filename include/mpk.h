@@ -548,6 +548,40 @@ mpk_status sstep_cg_solve(mpk_plan_t A, const double *b, double *x, const mpk_cg
 mpk_status mpk_fma_peak(mpk_dtype dtype, double *tflops, cudaStream_t stream);
 
 /* ------------------------------------------------------------------------------------------
+ * Batched MPK over many systems (Sec. 3's level-blocked MPK, run for many matrices at once).
+ * The systems' task graphs are concatenated into one block-diagonal graph and run by one
+ * persistent launch: many small, uneven systems - each alone too small to fill the GPU, its
+ * wavefront short and narrow - share the device, and the pipeline does not drain between
+ * systems.  Every system's values equal its own mpk_apply's bit for bit (the same row
+ * function as the unblocked power kernel).
+ * ---------------------------------------------------------------------------------------- */
+typedef struct mpk_batch_s *mpk_batch_t;
+
+/* plans: HOST array of count plans (each keeping values of `dtype`, all on the current
+ * device; a plan must outlive the batch and must not be used by another call while the
+ * batch runs).  p: the powers every mpk_batch_apply runs (1..63).  Builds the union's task
+ * graph and schedule (synchronous on stream).  MPK_ERR_ARG on bad arguments. */
+mpk_status mpk_batch_create(const mpk_plan_t *plans, int32_t count, int32_t p, mpk_dtype dtype,
+                            cudaStream_t stream, mpk_batch_t *out);
+
+/* For every system i: y_k = a_k A_i y_{k-1} + b_k y_{k-1} + c_k y_{k-2}, k = 1..p, all powers
+ * out, in the plan's level order.  co: HOST array of count coefficient sets (each with p
+ * triples; gamma ignored).  X, Y: HOST arrays of count DEVICE pointers; Y[i] holds (p + 1)
+ * blocks of n_i values (power k at Y[i] + k n_i), X[i] n_i values copied into block 0 (or,
+ * with MPK_Y0_IS_X, block 0 of Y[i] already holds x and X may be NULL).  flags: MPK_PERMUTED_IO
+ * (required), MPK_Y0_IS_X, MPK_UNBLOCKED (each system by its own p back-to-back SpMV
+ * launches instead, the baseline).  Asynchronous on stream.  When the per-system records
+ * (matrices, vector pointers, coefficients) differ from the previous call they are uploaded,
+ * which first synchronises the stream; a call with the same records neither copies nor
+ * synchronises, so it can be captured in a CUDA graph after one ordinary call, and every
+ * replay is a fresh launch.  Waits are bounded; mpk_batch_sync reports MPK_ERR_TIMEOUT. */
+mpk_status mpk_batch_apply(mpk_batch_t batch, const mpk_coeffs *co, const void *const *X,
+                           void *const *Y, uint32_t flags, cudaStream_t stream);
+/* Synchronises stream; returns and clears a latched device error of the batch's launches. */
+mpk_status mpk_batch_sync(mpk_batch_t batch, cudaStream_t stream);
+mpk_status mpk_batch_destroy(mpk_batch_t batch);
+
+/* ------------------------------------------------------------------------------------------
  * The orthogonalisation steps of the solvers on their own: the same kernels, callable on the
  * caller's tall-skinny blocks (all pointers DEVICE, column-major, FP64 results).  Asynchronous
  * on the stream; each call allocates (and frees, stream-ordered) a small partial-sum buffer.

@@ -179,6 +179,10 @@ _SIGS = [
     ("mpk_cg_opts_default", ctypes.c_int, [ctypes.POINTER(mpk_cg_opts)]),
     ("sstep_cg_solve", ctypes.c_int, [_P, _P, _P, ctypes.POINTER(mpk_cg_opts), ctypes.POINTER(mpk_cg_info), _P]),
     ("mpk_fma_peak", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_D), _P]),
+    ("mpk_batch_create", ctypes.c_int, [_P, _I32, _I32, ctypes.c_int, _P, ctypes.POINTER(_P)]),
+    ("mpk_batch_apply", ctypes.c_int, [_P, _P, _P, _P, _U32, _P]),
+    ("mpk_batch_sync", ctypes.c_int, [_P, _P]),
+    ("mpk_batch_destroy", ctypes.c_int, [_P]),
     ("mpk_gram", ctypes.c_int, [ctypes.c_int, _P, _I64, _I32, _P, _I64, _I32, _I64, _P, _P]),
     ("mpk_block_update", ctypes.c_int, [ctypes.c_int, _P, _I64, _I32, _P, _I64, _I32, _P, _P, _I64, _P, _P]),
     ("mpk_gram_pairs", ctypes.c_int, [ctypes.c_int, _P, _I64, _I32, _I64, _P, _P]),
@@ -704,3 +708,45 @@ def mpk_hessenberg_eigvals(H, k=None):
     _check(lib().mpk_hessenberg_eigvals(Hc.ctypes.data, Hc.shape[0], k, wr.ctypes.data, wi.ctypes.data),
            "mpk_hessenberg_eigvals")
     return wr + 1j * wi
+
+
+class Batch:
+    """Batched MPK over several plans (mpk_batch_*): one persistent launch for all systems."""
+
+    def __init__(self, plans, p, dtype, stream=None):
+        import torch
+        self.plans = list(plans)            # kept alive with the batch
+        arr = (ctypes.c_void_p * len(self.plans))(*[pl.handle.value for pl in self.plans])
+        h = ctypes.c_void_p()
+        self.p = int(p)
+        self.dtype = _dtype_code(dtype) if not isinstance(dtype, int) else dtype
+        _check(lib().mpk_batch_create(arr, len(self.plans), self.p, self.dtype, _stream_ptr(stream),
+                                      ctypes.byref(h)), "mpk_batch_create")
+        self.handle = h
+
+    def apply(self, coeffs, X, Y, flags=MPK_PERMUTED_IO, stream=None):
+        """coeffs: one Coeffs (or triples) per system; X, Y: lists of CUDA tensors (X may be
+        None with MPK_Y0_IS_X)."""
+        cs = [c if isinstance(c, Coeffs) else Coeffs.from_triples(c) for c in coeffs]
+        if len(cs) != len(self.plans) or len(Y) != len(self.plans):
+            raise ValueError("one coefficient set and one output per system")
+        for pl, y in zip(self.plans, Y):
+            if y.numel() < (self.p + 1) * pl.n:
+                raise ValueError("Y[i] must hold p + 1 blocks of n_i values")
+        co = (mpk_coeffs * len(cs))(*[c.struct for c in cs])
+        xs = (ctypes.c_void_p * len(cs))(*[(x.data_ptr() if x is not None else 0) for x in (X or [None] * len(cs))])
+        ys = (ctypes.c_void_p * len(cs))(*[y.data_ptr() for y in Y])
+        self._keep = (cs, co, xs, ys)
+        _check(lib().mpk_batch_apply(self.handle, co, xs, ys, int(flags), _stream_ptr(stream)),
+               "mpk_batch_apply")
+
+    def sync(self, stream=None):
+        return int(lib().mpk_batch_sync(self.handle, _stream_ptr(stream)))
+
+    def __del__(self):
+        try:
+            if self.handle:
+                lib().mpk_batch_destroy(self.handle)
+                self.handle = None
+        except Exception:
+            pass

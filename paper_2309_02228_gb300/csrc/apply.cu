@@ -1672,6 +1672,147 @@ __global__ void __launch_bounds__(WAVE_BLOCK, 1) mpk_stage_kernel(SellView A, Ve
 }
 
 // ------------------------------------------------------------------------------------------
+// Batched MPK over many systems (mpk_batch_apply).  The systems' lane-task graphs (one slice
+// per task) are concatenated into one block-diagonal graph: chunk, unit and counter-block
+// indices of system i are offset by those of the systems before it, and one lag-greedy
+// schedule orders the union, each power's chunks in ascending order.  A task waits, as in the
+// lane-task kernel, for every counter block up to its last dependency at the previous power
+// (blocks of earlier systems included, which the union's order satisfies first), then runs
+// its slice with its own system's matrix, vectors and coefficients: the row function of the
+// unblocked power kernel, so every system's values equal its own mpk_apply's.  Small systems,
+// whose own wavefronts are short and narrow, then share one persistent launch that keeps the
+// whole GPU busy; the pipeline does not drain between systems.
+// ------------------------------------------------------------------------------------------
+struct BatchSys {
+    SellView A;
+    VecSet V;
+};
+
+struct BatchArgs {
+    const int4 *unit_meta;     // union units: {first SELL entry, slice length, first row, row end}
+    const int32_t *unit_sys;   // system of each unit
+    const int32_t *cblk_size;
+    const int4 *desc;          // {chunk | power << 24, counter block, last block waited for, unit}
+    int64_t n_tasks;
+    uint32_t *cnt;             // [(k) * n_cblk + b]
+    uint32_t *kep;
+    MpkCtrl *ctrl;
+    const BatchSys *sys;       // per system (device)
+    const Coefs *coefs;        // per system (device)
+    int32_t n_cblk;
+    int seg;
+    uint64_t timeout_ns;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(WAVE_BLOCK, 5) mpk_batch_kernel(BatchArgs W) {
+    __shared__ uint32_t s_next;
+    __shared__ int32_t s_wm[MPK_MAX_P + 1];
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) s_next = 0;
+    for (int i = threadIdx.x; i <= MPK_MAX_P; i += blockDim.x) s_wm[i] = 0;
+    __syncthreads();
+    auto take = [&]() -> int64_t {
+        uint32_t j = 0;
+        if (lane == 0) j = atomicAdd(&s_next, 1u);
+        j = __shfl_sync(0xffffffffu, j, 0);
+        return (int64_t)blockIdx.x + (int64_t)j * gridDim.x;
+    };
+    int64_t t = take();
+    int4 d = make_int4(0, 0, 0, 0), mt = make_int4(0, 0, 0, 0);
+    int32_t sy = 0;
+    if (t < W.n_tasks) {
+        d = __ldg(&W.desc[t]);
+        mt = __ldg(&W.unit_meta[d.w]);
+        sy = __ldg(&W.unit_sys[d.w]);
+    }
+    bool stop = false;
+    while (t < W.n_tasks) {
+        const int64_t tn = take();
+        int4 dn = make_int4(0, 0, 0, 0);
+        if (tn < W.n_tasks) dn = __ldg(&W.desc[tn]);
+        const int kl = (int)((uint32_t)d.x >> 24);
+        if (kl > 1) {
+            const int32_t hb = d.z;
+            int32_t wm = *(volatile int32_t *)&s_wm[kl - 1];
+            if (wm <= hb) {
+                const uint32_t mult = *(volatile uint32_t *)(W.kep + kl - 1) + 1u;
+                const uint32_t *cp = W.cnt + (int64_t)(kl - 1) * W.n_cblk;
+                bool timing = false;
+                uint64_t t0 = 0;
+                while (wm <= hb) {
+                    const int32_t b = wm + lane;
+                    bool done = true;
+                    if (b <= hb) {
+                        const uint32_t v = ld_relaxed_u32(cp + b);
+                        done = (int32_t)(v - mult * (uint32_t)__ldg(W.cblk_size + b)) >= 0;
+                    }
+                    const unsigned nd = __ballot_sync(0xffffffffu, !done);
+                    if (nd == 0) {
+                        wm = min(wm + 32, hb + 1);
+                        continue;
+                    }
+                    wm += __ffs(nd) - 1;
+                    uint64_t now = 0;
+                    uint32_t err = 0;
+                    if (lane == 0) {
+                        now = globaltimer_ns();
+                        err = *(volatile uint32_t *)&W.ctrl->error;
+                    }
+                    now = __shfl_sync(0xffffffffu, now, 0);
+                    err = __shfl_sync(0xffffffffu, err, 0);
+                    if (err) {
+                        stop = true;
+                        break;
+                    }
+                    if (!timing) {
+                        timing = true;
+                        t0 = now;
+                    } else if (now - t0 > W.timeout_ns) {
+                        if (lane == 0 && atomicOr(&W.ctrl->error, 1u) == 0u) W.ctrl->err_task = (uint32_t)d.x;
+                        stop = true;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+                if (stop) break;
+                if (lane == 0) atomicMax(&s_wm[kl - 1], wm);
+            }
+            fence_acq_rel_gpu();   // acquire: counters observed before the vectors read below
+        }
+        int4 mn = make_int4(0, 0, 0, 0);
+        int32_t syn = 0;
+        if (tn < W.n_tasks) {
+            mn = __ldg(&W.unit_meta[dn.w]);
+            syn = __ldg(&W.unit_sys[dn.w]);
+        }
+        const BatchSys &bs = W.sys[sy];
+        const Coefs &cf = W.coefs[sy];
+        const int32_t *colb = bs.A.col + mt.x;
+        const T *valb = reinterpret_cast<const T *>(bs.A.val) + mt.x;
+        if (kl == W.seg) slice_rows<T, LD_STREAM>(colb, valb, mt.z, mt.w, mt.y, lane, bs.V, kl, cf);
+        else slice_rows<T, LD_KEEP>(colb, valb, mt.z, mt.w, mt.y, lane, bs.V, kl, cf);
+        // publish: the warp barrier orders every lane's results before lane 0's release add
+        __syncwarp();
+        if (lane == 0) red_release_add_u32(W.cnt + (int64_t)kl * W.n_cblk + d.y, 1u);
+        t = tn;
+        d = dn;
+        mt = mn;
+        sy = syn;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const uint32_t dn2 = atomicAdd(&W.ctrl->done_ctas, 1u);
+        if (dn2 == gridDim.x - 1) {
+            W.ctrl->done_ctas = 0;
+            for (int kk = 1; kk <= W.seg; kk++) W.kep[kk] += 1u;
+            __threadfence();
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
 // Ready-first warp tasks (opts.kernel = 3).  The tasks are the warp-task kernel's (chunk c,
 // local power k), but none is scheduled ahead.  Chunks are dealt to n_shards interleaved
 // shards (chunk c to shard c % n_shards, every shard served by the same number of warps, at
@@ -2988,5 +3129,225 @@ extern "C" mpk_status mpk_apply_final_noalloc(mpk_plan_t P, const mpk_coeffs *co
             scatter_out_kernel<float><<<grid2, 256, 0, s>>>((const float *)V.final_out, n, P->iperm.as<int32_t>(), n, 1, (float *)Y, n, false);
         MPK_CUDA(cudaGetLastError());
     }
+    return MPK_OK;
+}
+
+// ==========================================================================================
+// Batched MPK over many systems: one block-diagonal task graph, one persistent launch.
+// ==========================================================================================
+struct mpk_batch_s {
+    int device = 0;
+    int n_sm = 0;
+    int32_t count = 0, p = 0;
+    mpk_dtype dtype = MPK_F64;
+    std::vector<mpk_plan_t> plans;
+    std::vector<int64_t> n;               // rows of each system
+    int32_t n_units = 0, n_chunks = 0, n_cblk = 0;
+    DevBuf unit_meta, unit_sys, cblk_size, cnt, kep, desc, ctrl, sysbuf, coefbuf;
+    int64_t n_tasks = 0;
+    int grid = 0;
+    void *stage = nullptr;                // pinned host staging of the per-system records
+    size_t stage_bytes = 0;
+    std::vector<char> uploaded;           // the records last copied to the device
+    ~mpk_batch_s() {
+        if (stage) cudaFreeHost(stage);
+    }
+};
+
+extern "C" mpk_status mpk_batch_create(const mpk_plan_t *plans, int32_t count, int32_t p, mpk_dtype dtype,
+                                       cudaStream_t s, mpk_batch_t *out) {
+    if (!out) return MPK_ERR_ARG;
+    *out = nullptr;
+    if (!plans || count < 1 || p < 1 || p > MPK_MAX_P || (dtype != MPK_F32 && dtype != MPK_F64))
+        return MPK_ERR_ARG;
+    std::unique_ptr<mpk_batch_s> B(new (std::nothrow) mpk_batch_s());
+    if (!B) return MPK_ERR_OOM;
+    MPK_CUDA(cudaGetDevice(&B->device));
+    MPK_CUDA(cudaDeviceGetAttribute(&B->n_sm, cudaDevAttrMultiProcessorCount, B->device));
+    B->count = count;
+    B->p = p;
+    B->dtype = dtype;
+    std::vector<int4> meta;
+    std::vector<int32_t> usys, cbs, chunk_blk, wait_blk, dep_hi_blk;
+    for (int32_t i = 0; i < count; i++) {
+        mpk_plan_s *P = plans[i];
+        if (!P || P->device != B->device) return MPK_ERR_ARG;
+        if ((dtype == MPK_F64 && !P->has64) || (dtype == MPK_F32 && !P->has32)) return MPK_ERR_ARG;
+        B->plans.push_back(P);
+        B->n.push_back(P->n);
+        if (P->n == 0) continue;
+        LaneGraph *G = nullptr;
+        MPK_TRY(mpk_get_lane_graph(P, 1, 1, &G, s));
+        const int32_t uo = (int32_t)meta.size(), co = (int32_t)chunk_blk.size(), bo = (int32_t)cbs.size();
+        for (const int4 &m : G->h_meta) {
+            meta.push_back(m);
+            usys.push_back(i);
+        }
+        for (int32_t c = 0; c < G->n_chunks; c++) {
+            if (G->h_chunk_unit[c + 1] - G->h_chunk_unit[c] != 1) return MPK_ERR_CUDA;   // one unit per chunk
+            chunk_blk.push_back(bo + G->h_chunk_blk[c]);
+            wait_blk.push_back(bo + G->h_wait_blk[c]);
+            dep_hi_blk.push_back(co + G->h_dep_hi_blk[c]);
+        }
+        cbs.insert(cbs.end(), G->h_cblk_size.begin(), G->h_cblk_size.end());
+        (void)uo;
+    }
+    B->n_units = (int32_t)meta.size();
+    B->n_chunks = (int32_t)chunk_blk.size();
+    B->n_cblk = (int32_t)cbs.size();
+    // the union's schedule: slack of three tickets per resident warp, as for one plan
+    int occ = 0;
+    MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &occ, dtype == MPK_F64 ? mpk_batch_kernel<double> : mpk_batch_kernel<float>, WAVE_BLOCK, 0));
+    if (occ < 1) return MPK_ERR_UNIMPLEMENTED;
+    const int64_t ntask = (int64_t)p * B->n_chunks;
+    B->grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)B->n_sm * occ, ceil_div(ntask, WAVE_BLOCK / 32)));
+    std::vector<uint32_t> order;
+    MPK_TRY(mpk_lag_greedy_order(p, B->n_chunks, dep_hi_blk, 3ll * B->grid * (WAVE_BLOCK / 32), order));
+    B->n_tasks = (int64_t)order.size();
+    if (B->n_tasks >= (1ll << 31) || B->n_chunks >= (1 << 24)) return MPK_ERR_UNIMPLEMENTED;
+    std::vector<int4> hd(order.size());
+    for (size_t t = 0; t < order.size(); t++) {
+        const int32_t c = (int32_t)(order[t] & 0xffffffu);
+        hd[t] = make_int4((int)order[t], chunk_blk[c], wait_blk[c], c);   // one unit per chunk
+    }
+    auto up = [&](DevBuf &b, const void *h, size_t bytes) -> mpk_status {
+        MPK_TRY(b.alloc(std::max<size_t>(bytes, 16)));
+        if (bytes) MPK_CUDA(cudaMemcpyAsync(b.p, h, bytes, cudaMemcpyHostToDevice, s));
+        return MPK_OK;
+    };
+    MPK_TRY(up(B->unit_meta, meta.data(), meta.size() * sizeof(int4)));
+    MPK_TRY(up(B->unit_sys, usys.data(), usys.size() * 4));
+    MPK_TRY(up(B->cblk_size, cbs.data(), cbs.size() * 4));
+    MPK_TRY(up(B->desc, hd.data(), hd.size() * sizeof(int4)));
+    MPK_TRY(B->cnt.alloc((size_t)(p + 1) * std::max(B->n_cblk, 1) * 4));
+    MPK_CUDA(cudaMemsetAsync(B->cnt.p, 0, B->cnt.bytes, s));
+    MPK_TRY(B->kep.alloc((MPK_MAX_P + 1) * 4));
+    MPK_CUDA(cudaMemsetAsync(B->kep.p, 0, B->kep.bytes, s));
+    MPK_TRY(B->ctrl.alloc(sizeof(MpkCtrl)));
+    MPK_CUDA(cudaMemsetAsync(B->ctrl.p, 0, sizeof(MpkCtrl), s));
+    MPK_TRY(B->sysbuf.alloc((size_t)count * sizeof(BatchSys)));
+    MPK_TRY(B->coefbuf.alloc((size_t)count * sizeof(Coefs)));
+    B->stage_bytes = (size_t)count * (sizeof(BatchSys) + sizeof(Coefs));
+    MPK_CUDA(cudaMallocHost(&B->stage, B->stage_bytes));
+    MPK_CUDA(cudaStreamSynchronize(s));   // the host vectors above outlive their copies
+    *out = B.release();
+    return MPK_OK;
+}
+
+extern "C" mpk_status mpk_batch_apply(mpk_batch_t B, const mpk_coeffs *co, const void *const *X, void *const *Y,
+                                      uint32_t flags, cudaStream_t s) {
+    if (!B || !co || !Y) return MPK_ERR_ARG;
+    if (!(flags & MPK_PERMUTED_IO) || (flags & ~(uint32_t)(MPK_PERMUTED_IO | MPK_Y0_IS_X | MPK_UNBLOCKED)))
+        return MPK_ERR_ARG;
+    const bool y0x = (flags & MPK_Y0_IS_X) != 0;
+    if (!y0x && !X) return MPK_ERR_ARG;
+    const size_t es = B->dtype == MPK_F64 ? 8 : 4;
+    BatchSys *hs = reinterpret_cast<BatchSys *>(B->stage);
+    Coefs *hc = reinterpret_cast<Coefs *>(reinterpret_cast<char *>(B->stage) + (size_t)B->count * sizeof(BatchSys));
+    for (int32_t i = 0; i < B->count; i++) {
+        const mpk_coeffs &c = co[i];
+        if (c.p != B->p || !c.a || !c.b || !c.c || !Y[i] || (!y0x && !X[i])) return MPK_ERR_ARG;
+    }
+    if (flags & MPK_UNBLOCKED) {
+        // the baseline: each system by its own p back-to-back SpMV launches
+        for (int32_t i = 0; i < B->count; i++) {
+            if (B->n[i] == 0) continue;
+            MPK_TRY(mpk_apply_internal(B->plans[i], &co[i], B->dtype, y0x ? nullptr : X[i], B->n[i], Y[i], B->n[i], 1,
+                                       flags, s));
+        }
+        return MPK_OK;
+    }
+    // the per-system records (matrix, vectors, coefficients) of this call
+    std::vector<char> rec(B->stage_bytes, 0);
+    hs = reinterpret_cast<BatchSys *>(rec.data());
+    hc = reinterpret_cast<Coefs *>(rec.data() + (size_t)B->count * sizeof(BatchSys));
+    for (int32_t i = 0; i < B->count; i++) {
+        mpk_plan_s *P = B->plans[i];
+        const int64_t n = B->n[i];
+        if (n > 0 && !y0x) MPK_CUDA(cudaMemcpyAsync(Y[i], X[i], (size_t)n * es, cudaMemcpyDeviceToDevice, s));
+        BatchSys bs;
+        memset(&bs, 0, sizeof(bs));
+        bs.A.slice_ptr = P->slice_ptr.as<long long>();
+        bs.A.slice_row = P->slice_row.as<int32_t>();
+        bs.A.slice_len = P->slice_len.as<int32_t>();
+        bs.A.col = P->s_col.as<int32_t>();
+        bs.A.val = B->dtype == MPK_F64 ? P->s_val64.p : P->s_val32.p;
+        bs.V.x = Y[i];
+        bs.V.ybase = Y[i];
+        bs.V.bstride = n;
+        bs.V.p_total = B->p;
+        hs[i] = bs;
+        Coefs cf;
+        memset(&cf, 0, sizeof(cf));
+        for (int k = 1; k <= B->p; k++) {
+            cf.a[k] = co[i].a[k - 1];
+            cf.b[k] = co[i].b[k - 1];
+            cf.c[k] = co[i].c[k - 1];
+        }
+        coefs_finish(cf);
+        hc[i] = cf;
+    }
+    // upload only when they changed since the last call: then the staging buffer must first
+    // be free of that call's copy (a stream synchronisation); an unchanged call neither copies
+    // nor synchronises, so it can be captured in a CUDA graph after one ordinary call
+    if (rec != B->uploaded) {
+        MPK_CUDA(cudaStreamSynchronize(s));
+        memcpy(B->stage, rec.data(), rec.size());
+        const char *st = reinterpret_cast<const char *>(B->stage);
+        MPK_CUDA(cudaMemcpyAsync(B->sysbuf.p, st, (size_t)B->count * sizeof(BatchSys), cudaMemcpyHostToDevice, s));
+        MPK_CUDA(cudaMemcpyAsync(B->coefbuf.p, st + (size_t)B->count * sizeof(BatchSys),
+                                 (size_t)B->count * sizeof(Coefs), cudaMemcpyHostToDevice, s));
+        B->uploaded.swap(rec);
+    }
+    if (B->n_tasks == 0) return MPK_OK;
+    BatchArgs W;
+    memset(&W, 0, sizeof(W));
+    W.unit_meta = B->unit_meta.as<int4>();
+    W.unit_sys = B->unit_sys.as<int32_t>();
+    W.cblk_size = B->cblk_size.as<int32_t>();
+    W.desc = B->desc.as<int4>();
+    W.n_tasks = B->n_tasks;
+    W.cnt = B->cnt.as<uint32_t>();
+    W.kep = B->kep.as<uint32_t>();
+    W.ctrl = B->ctrl.as<MpkCtrl>();
+    W.sys = B->sysbuf.as<BatchSys>();
+    W.coefs = B->coefbuf.as<Coefs>();
+    W.n_cblk = B->n_cblk;
+    W.seg = B->p;
+    W.timeout_ns = 2000000000ull;
+    cudaLaunchConfig_t lc;
+    memset(&lc, 0, sizeof(lc));
+    lc.gridDim = dim3((unsigned)B->grid);
+    lc.blockDim = dim3(WAVE_BLOCK);
+    lc.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    lc.attrs = attr;
+    lc.numAttrs = 1;
+    if (B->dtype == MPK_F64) MPK_CUDA(cudaLaunchKernelEx(&lc, mpk_batch_kernel<double>, W));
+    else MPK_CUDA(cudaLaunchKernelEx(&lc, mpk_batch_kernel<float>, W));
+    return MPK_OK;
+}
+
+extern "C" mpk_status mpk_batch_sync(mpk_batch_t B, cudaStream_t s) {
+    if (!B) return MPK_ERR_ARG;
+    MPK_CUDA(cudaStreamSynchronize(s));
+    MpkCtrl h;
+    MPK_CUDA(cudaMemcpy(&h, B->ctrl.p, sizeof(h), cudaMemcpyDeviceToHost));
+    if (h.error) {
+        MPK_CUDA(cudaMemset(B->ctrl.p, 0, sizeof(MpkCtrl)));
+        MPK_CUDA(cudaMemset(B->cnt.p, 0, B->cnt.bytes));
+        MPK_CUDA(cudaMemset(B->kep.p, 0, B->kep.bytes));
+        return MPK_ERR_TIMEOUT;
+    }
+    return MPK_OK;
+}
+
+extern "C" mpk_status mpk_batch_destroy(mpk_batch_t B) {
+    if (!B) return MPK_ERR_ARG;
+    cudaDeviceSynchronize();
+    delete B;
     return MPK_OK;
 }

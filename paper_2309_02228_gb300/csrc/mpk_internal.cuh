@@ -109,6 +109,8 @@ struct LaneGraph {
     DevBuf cblk_size;                  // chunks per counter block
     DevBuf cnt;                        // uint32 [(p_blk + 1) * n_cblk]: counters [(k) * n_cblk + b]
     DevBuf kep;                        // uint32 per local power: launches that ran it
+    std::vector<int4> h_meta;          // unit_meta on the host
+    std::vector<int32_t> h_cblk_size;  // cblk_size on the host
     std::vector<int32_t> h_chunk_unit; // first unit of each chunk (n_chunks + 1)
     std::vector<int32_t> h_chunk_blk;  // counter block of each chunk
     std::vector<int32_t> h_wait_blk;   // last block a chunk's task waits for

@@ -1346,6 +1346,7 @@ mpk_status mpk_get_lane_graph(mpk_plan_s *P, int lpr, int units, LaneGraph **out
     crow.push_back((int32_t)n);
     MPK_TRY(upload(G->unit_code, code, s));
     MPK_TRY(upload(G->unit_meta, meta, s));
+    G->h_meta = meta;
     MPK_TRY(upload(G->chunk_unit, cu, s));
     G->h_chunk_unit = cu;
     std::vector<int32_t> dep_hi(G->n_chunks, 0);
@@ -1384,6 +1385,7 @@ mpk_status mpk_get_lane_graph(mpk_plan_s *P, int lpr, int units, LaneGraph **out
         G->h_dep_hi_blk[c] = blast[G->h_wait_blk[c]];
     }
     MPK_TRY(upload(G->cblk_size, cbs, s));
+    G->h_cblk_size = cbs;
     MPK_TRY(G->cnt.alloc((size_t)(P->p_blk + 1) * std::max(G->n_cblk, 1) * 4));
     MPK_CUDA(cudaMemsetAsync(G->cnt.p, 0, G->cnt.bytes, s));
     MPK_TRY(G->kep.alloc((MPK_MAX_P + 1) * 4));
