@@ -61,6 +61,8 @@ def _load():
         lib.oracle_levels.restype = I32
         lib.oracle_level_perm.argtypes = [I32, i32p, I32, i32p, i32p, i32p]
         lib.oracle_level_perm.restype = None
+        lib.oracle_level_perm_bfs.argtypes = [I32, i32p, i32p, i32p, I32, i32p, i32p, i32p]
+        lib.oracle_level_perm_bfs.restype = I32
         lib.oracle_permute_csr.argtypes = [I32, i32p, i32p, VP, I32, i32p, i32p, i32p, i32p, VP]
         lib.oracle_permute_csr.restype = None
         lib.oracle_level_groups.argtypes = [I32, i32p, i32p, I32, I32, I64, i32p]
@@ -139,6 +141,21 @@ def level_perm(level, n_levels):
     return perm, iperm, lp
 
 
+def level_perm_bfs(A, level, n_levels):
+    """Rows by level, and inside a level in breadth-first order: by the position of the row's
+    earliest-placed neighbour (in G(A + A^T)) one level down, then by index (see
+    mpk_oracle.c).  Returns (perm, iperm, level_ptr)."""
+    lib = _load()
+    n = int(level.shape[0])
+    perm = np.empty(n, dtype=np.int32)
+    iperm = np.empty(n, dtype=np.int32)
+    lp = np.empty(n_levels + 1, dtype=np.int32)
+    if lib.oracle_level_perm_bfs(n, _i32(A.row_ptr), _i32(A.col), _i32(level), int(n_levels),
+                                 perm, iperm, lp) != 0:
+        raise MemoryError("oracle_level_perm_bfs")
+    return perm, iperm, lp
+
+
 def permute_csr(A, perm, iperm, val_dtype=np.float64):
     """B = P A P^T with columns ascending per row; values moved bit-exactly.
     Returns (row_ptr, col, val)."""
@@ -165,8 +182,12 @@ def level_groups(level_ptr, rp_perm, val_bytes: int, p: int, budget: int):
     return gp[: ng + 1].copy()
 
 
-def level_structure(A, root_rule: int = 0, n_sweeps: int = 2):
-    """levels + level_perm in one call: (level, root, n_levels, perm, iperm, level_ptr)."""
+def level_structure(A, root_rule: int = 0, n_sweeps: int = 2, level_order: int = 0):
+    """levels + the level permutation in one call: (level, root, n_levels, perm, iperm,
+    level_ptr).  level_order 0: index order inside a level; 1: breadth-first order."""
     lev, root, nl = levels(A, root_rule, n_sweeps)
-    perm, iperm, lp = level_perm(lev, nl)
+    if level_order == 1:
+        perm, iperm, lp = level_perm_bfs(A, lev, nl)
+    else:
+        perm, iperm, lp = level_perm(lev, nl)
     return lev, root, nl, perm, iperm, lp

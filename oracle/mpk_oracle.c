@@ -19,6 +19,8 @@
  *                         outputs depends on (for full-size checks).
  *   oracle_levels         BFS levels of the graph of A (Sec. 3: RACE's level structure).
  *   oracle_level_perm     rows sorted by (level, original index), and the level pointer.
+ *   oracle_level_perm_bfs rows by level, and inside a level in breadth-first order (the
+ *                         earliest-placed neighbour one level down, then the index).
  *   oracle_permute_csr    B = P A P^T in the level order, columns ascending per row.
  *   oracle_level_groups   consecutive levels grouped under a cache budget (Sec. 3 / Sec. 4:
  *                         the cache size parameter C).
@@ -273,6 +275,56 @@ void oracle_level_perm(int32_t n, const int32_t *level, int32_t n_levels, int32_
     for (int32_t i = 0; i < n; i++) perm[pos[level[i]]++] = i;
     for (int32_t r = 0; r < n; r++) iperm[perm[r]] = r;
     free(pos);
+}
+
+/* Breadth-first order inside levels (the plan's level_order = 1).  The paper fixes the levels
+   but not the order of the rows inside one; this reading places level l's rows, levels in
+   ascending order, by the key (position of the row's earliest-placed neighbour in level l - 1,
+   row index), the neighbours taken in G(A + A^T).  A row with no neighbour in level l - 1 (a
+   component's root, alone in its level) takes key -1.  The result is the queue order of a
+   breadth-first search from each root in which every row, taken from the queue in order,
+   appends its not yet placed neighbours of the next level in ascending index: Cuthill-McKee
+   without its degree sort.  perm, iperm, level_ptr as in oracle_level_perm.  Returns 0, or -1
+   on allocation failure. */
+typedef struct { int32_t key, row; } key_row;
+
+static int cmp_key_row(const void *a, const void *b)
+{
+    const key_row *x = (const key_row *)a, *y = (const key_row *)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    return (x->row > y->row) - (x->row < y->row);
+}
+
+int32_t oracle_level_perm_bfs(int32_t n, const int32_t *rp, const int32_t *ci, const int32_t *level,
+                              int32_t n_levels, int32_t *perm, int32_t *iperm, int32_t *level_ptr)
+{
+    /* rows grouped by level, ascending index inside a level (the index order) */
+    oracle_level_perm(n, level, n_levels, perm, iperm, level_ptr);
+    if (n == 0) return 0;
+    sym_graph g;
+    if (build_sym(n, rp, ci, &g)) return -1;
+    key_row *buf = (key_row *)malloc((size_t)n * sizeof(key_row));
+    if (!buf) { free(g.ptr); free(g.adj); return -1; }
+    for (int32_t l = 0; l < n_levels; l++) {
+        int32_t lo = level_ptr[l], hi = level_ptr[l + 1];
+        for (int32_t q = lo; q < hi; q++) {
+            int32_t i = perm[q], key = -1;
+            for (int64_t t = g.ptr[i]; t < g.ptr[i + 1]; t++) {
+                int32_t j = g.adj[t];
+                /* level l - 1 is already in its final order: iperm[j] is j's new position */
+                if (level[j] == l - 1 && (key < 0 || iperm[j] < key)) key = iperm[j];
+            }
+            buf[q - lo].key = key;
+            buf[q - lo].row = i;
+        }
+        qsort(buf, (size_t)(hi - lo), sizeof(key_row), cmp_key_row);
+        for (int32_t q = lo; q < hi; q++) {
+            perm[q] = buf[q - lo].row;
+            iperm[perm[q]] = q;
+        }
+    }
+    free(buf); free(g.ptr); free(g.adj);
+    return 0;
 }
 
 /* B = P A P^T: row r of B is row perm[r] of A with each column j replaced by iperm[j];

@@ -203,3 +203,120 @@ def test_level_groups_rule():
                 assert cost(gp[g], gp[g + 1] + 1) > budget
         if budget == 10 ** 12:
             assert gp.tolist() == [0, nl]
+
+
+# ---- breadth-first order inside levels (the plan's level_order = 1)
+
+def _queue_bfs_order(A, lev):
+    """The same order by its other definition: a queue breadth-first search from each
+    component's root (the row alone on the first level of its component), every row taken
+    from the queue appending its not yet placed next-level neighbours (in G(A + A^T)) in
+    ascending index.  Plain Python, for small graphs."""
+    n = A.n
+    nb = [set() for _ in range(n)]
+    for i in range(n):
+        for j in A.col[A.row_ptr[i]:A.row_ptr[i + 1]]:
+            if j != i:
+                nb[i].add(int(j))
+                nb[int(j)].add(i)
+    roots = sorted((int(lev[i]), i) for i in range(n)
+                   if not any(lev[j] == lev[i] - 1 for j in nb[i]))
+    order, placed = [], np.zeros(n, bool)
+    for _, r in roots:
+        q = [r]
+        placed[r] = True
+        order.append(r)
+        h = 0
+        while h < len(q):
+            i = q[h]
+            h += 1
+            for j in sorted(nb[i]):
+                if lev[j] == lev[i] + 1 and not placed[j]:
+                    placed[j] = True
+                    order.append(j)
+                    q.append(j)
+    return np.array(order, dtype=np.int32)
+
+
+def test_bfs_order_golden_hand_worked():
+    with open(os.path.join(GOLD, "level_order_bfs_small.json")) as f:
+        g = json.load(f)
+    A = mi.CSR(np.array(g["row_ptr"], dtype=np.int32), np.array(g["col"], dtype=np.int32),
+               np.ones(len(g["col"])))
+    lev, root, nl = oracle.levels(A, root_rule=g["root_rule"])
+    assert lev.tolist() == g["level"] and nl == g["n_levels"]
+    perm, iperm, lp = oracle.level_perm(lev, nl)
+    assert perm.tolist() == g["perm_index"] and lp.tolist() == g["level_ptr"]
+    perm, iperm, lp = oracle.level_perm_bfs(A, lev, nl)
+    assert perm.tolist() == g["perm_bfs"] and lp.tolist() == g["level_ptr"]
+    assert np.array_equal(iperm[perm], np.arange(A.n))
+
+
+@pytest.mark.parametrize("seed,comp,sym", [(0, 1, True), (1, 3, False), (2, 1, False), (3, 5, True)])
+def test_bfs_order_matches_queue_definition(seed, comp, sym):
+    A = mi.random_sparse(400, 0.01, seed, symmetric=sym, components=comp)
+    lev, root, nl = oracle.levels(A)
+    perm, iperm, lp = oracle.level_perm_bfs(A, lev, nl)
+    assert np.array_equal(perm, _queue_bfs_order(A, lev))
+    assert np.array_equal(iperm[perm], np.arange(A.n))
+    assert np.array_equal(lp, oracle.level_perm(lev, nl)[2])     # the same levels and sizes
+
+
+def test_bfs_order_on_permuted_grid_matches_queue_and_keys():
+    """A randomly relabelled 7-point grid (the solver workload's structure): the queue
+    definition, levels still contiguous, and inside each level the keys (earliest lower
+    neighbour's position) non-decreasing with ties in ascending index."""
+    A = mi.diffusion7_lognormal(7)
+    lev, root, nl = oracle.levels(A)
+    perm, iperm, lp = oracle.level_perm_bfs(A, lev, nl)
+    assert np.array_equal(perm, _queue_bfs_order(A, lev))
+    assert np.all(np.diff(lev[perm]) >= 0)
+    S = sp.csr_matrix((np.ones(A.nnz), A.col, A.row_ptr), shape=(A.n, A.n))
+    S = (S + S.T).tocsr()
+    for q in range(1, A.n):
+        if lev[perm[q]] != lev[perm[q - 1]] or lev[perm[q]] == 0:
+            continue
+        def key(r):
+            nbr = S.indices[S.indptr[r]:S.indptr[r + 1]]
+            return min(iperm[j] for j in nbr if lev[j] == lev[r] - 1)
+        a, b = perm[q - 1], perm[q]
+        assert (key(a), a) < (key(b), b)
+
+
+@pytest.mark.parametrize("N", [1, 2, 5, 12])
+def test_bfs_order_on_natural_2d_grid_is_index_order(N):
+    """On a 5-point grid numbered row by row, from the corner root, the earliest lower
+    neighbour of (i, j) is (i-1, j) (or (0, j-1) on the first row, which shares its key with
+    (1, j-1) and wins the tie by index), so the breadth-first order inside each anti-diagonal
+    is the index order."""
+    A = mi.poisson2d_5pt(N)
+    lev, root, nl = oracle.levels(A, root_rule=1)
+    pb = oracle.level_perm_bfs(A, lev, nl)
+    pi = oracle.level_perm(lev, nl)
+    for a, b in zip(pb, pi):
+        assert np.array_equal(a, b)
+
+
+def test_bfs_order_planted_mistakes_fail_the_queue_check():
+    """Plausible mistakes in the breadth-first key (the latest lower neighbour instead of the
+    earliest; ties by descending index) give another order on a permuted grid."""
+    A = mi.diffusion7_lognormal(6)
+    lev, root, nl = oracle.levels(A)
+    want = _queue_bfs_order(A, lev)
+    S = sp.csr_matrix((np.ones(A.nnz), A.col, A.row_ptr), shape=(A.n, A.n))
+    S = (S + S.T).tocsr()
+    perm0, _, lp = oracle.level_perm(lev, nl)
+    for variant in ("latest", "desc"):
+        pos = np.empty(A.n, np.int64)
+        out = []
+        for l in range(nl):
+            rows = perm0[lp[l]:lp[l + 1]]
+            keys = []
+            for r in rows:
+                ks = [pos[j] for j in S.indices[S.indptr[r]:S.indptr[r + 1]] if lev[j] == l - 1]
+                k = -1 if not ks else (max(ks) if variant == "latest" else min(ks))
+                keys.append((k, -r if variant == "desc" else r))
+            for q, (_, r) in enumerate(sorted(zip(keys, rows))):
+                pos[r] = lp[l] + q
+                out.append(r)
+        assert not np.array_equal(np.array(out), want), variant
