@@ -80,7 +80,8 @@ def recorded_traffic(path=TRAFFIC_PROFILE):
         now = source_sha(KERNEL_SOURCE)
         if now != rec["sha"]:
             return None, "stale: kernel source changed since the capture (%s, now %s)" % (rec["sha"], now)
-        return rec["bytes"], "ncu capture of this call, %s" % os.path.relpath(path, ROOT)
+        return rec["bytes"], ("ncu capture of one launch of the default plan on this matrix and call "
+                              "(one slice per task), %s" % os.path.relpath(path, ROOT))
     except OSError as e:
         return None, "no capture: %s" % e
 
@@ -359,10 +360,15 @@ def gs2_mpk_leg(m, torch, dev, A, rp, ci, vv, p=P_MAIN, gammas=(1, 2), reps=20):
     return out
 
 
-def serving_leg(m, n_req=32, n_min=32, n_max=64, seed=7):
+def serving_leg(m, n_req=24, n_min=32, n_max=192, seed=7):
     """The solve stream (Poisson arrivals at 200/s, 7- or 27-point anisotropic diffusion,
-    anisotropy log-uniform in [1, 100], grid edge uniform in [n_min, n_max]) through the
-    server, FP32 basis + FP64 refinement to 1e-8, then the same stream with an FP64 basis."""
+    anisotropy log-uniform in [1, 100], grid edge uniform in [n_min, n_max], the c5
+    distribution) through the server under a 120 GB budget, FP32 basis + FP64 refinement to
+    1e-8, then the same stream with an FP64 basis.  A bounded sample of n_req requests: at
+    200/s the stream offers far more work than one GPU completes (an average request of this
+    size distribution is a solve of about half a second), so the server runs saturated, the
+    reported solves/s is its saturation throughput and the latency percentiles are dominated
+    by queueing."""
     stream = mi.solve_stream(n_req, seed=seed, n_min=n_min, n_max=n_max)
     mats = []
     for r in stream:
@@ -400,10 +406,64 @@ def serving_leg(m, n_req=32, n_min=32, n_max=64, seed=7):
         srv.close()
         lat = [1e3 * (done[r][0] - sub[r]) for r in ids]
         statuses = [done[r][1]["status"] for r in ids]
+        span = max(stream[-1]["t_arrival"], 1e-9)
         out[basis] = {"solves_per_s": n_req / (t_end - t_start), "p50_ms": float(np.percentile(lat, 50)),
                       "p99_ms": float(np.percentile(lat, 99)),
+                      "offered_per_s": n_req / span,
+                      "offered_over_served": (n_req / span) / (n_req / (t_end - t_start)),
                       "all_converged": all(st == m.MPK_OK for st in statuses),
                       "max_rel_residual": max(done[r][1]["rel_residual"] for r in ids)}
+    return out
+
+
+def batch_leg(m, torch, dev, p=8, reps=10, cases=((256, 8, 32), (64, 16, 48)), seed=7):
+    """Batched MPK (mpk_batch_apply): many uneven systems (7- or 27-point anisotropic
+    diffusion, anisotropy log-uniform in [1, 100], grid edge uniform in [lo, hi]) in one
+    persistent launch, against one mpk_apply per system (automatic blocked / unblocked
+    choice) and p back-to-back SpMVs per system; Newton p = 8 with Leja shifts, level-order
+    I/O, each variant graph-captured once and replayed.  GFLOP/s = sum_i 2 nnz_i p / t."""
+    rng = np.random.default_rng(seed)
+    out = {}
+    for count, lo, hi in cases:
+        for dt in ("f32", "f64"):
+            tdt = torch.float32 if dt == "f32" else torch.float64
+            plans, cfs, Ys, nnz = [], [], [], 0
+            for i in range(count):
+                N = int(rng.integers(lo, hi + 1))
+                A = mi.anisotropic(N, 7 if i % 2 else 27, float(np.exp(rng.uniform(0.0, np.log(100.0)))))
+                nnz += A.nnz
+                plans.append(m.mpk_plan_create(torch.from_numpy(A.row_ptr).to(dev), torch.from_numpy(A.col).to(dev),
+                                               torch.from_numpy(A.val).to(dev, tdt), p))
+                cfs.append(m.mpk_coeffs_newton(mi.leja_points_interval(0.0, 6.6 * float(np.abs(A.val).max()), p)))
+                Y = torch.zeros(((p + 1) * A.n,), dtype=tdt, device=dev)
+                Y[: A.n] = 1.0
+                Ys.append(Y)
+            B = m.Batch(plans, p, tdt)
+            fl = m.MPK_PERMUTED_IO | m.MPK_Y0_IS_X
+
+            def batch():
+                B.apply(cfs, None, Ys, flags=fl)
+
+            def each(extra=0):
+                for pl, c, y in zip(plans, cfs, Ys):
+                    m.mpk_apply(pl, c, None, y, flags=fl | extra)
+            res = {"systems": count, "grid_edges": [lo, hi], "nnz": nnz}
+            for name, fn in (("batch", batch), ("each_auto", each),
+                             ("each_pxspmv", lambda: each(m.MPK_UNBLOCKED))):
+                fn()
+                fn()
+                torch.cuda.synchronize()
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, capture_error_mode="relaxed"):
+                    fn()
+                g.replay()
+                ms = time_stream(g.replay, reps, torch)
+                res[name] = {"ms": ms, "gflops": 2.0 * nnz * p / ms / 1e6}
+            assert B.sync() == m.MPK_OK
+            res["speedup_vs_each"] = res["each_auto"]["ms"] / res["batch"]["ms"]
+            out["%d_systems_%d_%d_%s" % (count, lo, hi, dt)] = res
+            del B, plans, Ys
+            torch.cuda.empty_cache()
     return out
 
 
@@ -412,6 +472,25 @@ def run_profile(args, m, torch, local):
     plan, --profile-reps repetitions of one blocked and one unblocked call with y_0 already in
     level order.  The blocked kernel's launches are the (2r)-th kernel launches of this family."""
     dev = torch.device("cuda", local)
+    if args.profile_nrhs > 0:
+        # block MPK: per repetition one blocked and one unblocked call, level-order interleaved
+        A = mi.stencil27(args.profile_n, seed=5)
+        p, nr = 6, args.profile_nrhs
+        rp = torch.from_numpy(A.row_ptr).to(dev)
+        ci = torch.from_numpy(A.col).to(dev)
+        vv = torch.from_numpy(A.val.astype(np.float32)).to(dev)
+        plan = m.mpk_plan_create(rp, ci, vv, p, m.mpk_plan_opts_default(assume_symmetric=1, p_blk=p, blocked=1))
+        co = m.mpk_coeffs_chebyshev(0.1, 52.0, p)
+        X = torch.from_numpy(mi.uniform_vectors(A.n, 6, nr).T.copy()).to(dev, torch.float32)
+        Y = torch.empty((p + 1) * A.n * nr, dtype=torch.float32, device=dev)
+        fl = m.MPK_PERMUTED_IO | m.MPK_RHS_INTERLEAVED
+        for _ in range(args.profile_reps):
+            m.mpk_apply(plan, co, X, Y, n_rhs=nr, flags=fl)
+            m.mpk_apply(plan, co, X, Y, n_rhs=nr, flags=fl | m.MPK_UNBLOCKED)
+        torch.cuda.synchronize()
+        status = m.mpk_plan_sync(plan)
+        print(json.dumps({"profile": "block", "status": status, "n": A.n, "nnz": A.nnz, "p": p, "n_rhs": nr}))
+        return 0 if status == m.MPK_OK else 1
     A = mi.stencil27(args.profile_n, seed=2)
     x = mi.uniform_vectors(A.n, 0)[0]
     p = args.profile_p
@@ -560,6 +639,9 @@ def main():
     ap.add_argument("--profile-cg", action="store_true",
                     help="profiling run of s-step CG: --profile-reps solves (FP32 basis) on the "
                          "log-normal diffusion matrix at --profile-n")
+    ap.add_argument("--profile-nrhs", type=int, default=0,
+                    help="profiling run of the block MPK (c4: 27-point --profile-n grid, seed 5, FP32, "
+                         "Chebyshev p = 6 on [0.1, 52]) with this many interleaved right-hand sides")
     ap.add_argument("--profile-cs", type=int, default=0, help="chunk_slices (0: plan default)")
     ap.add_argument("--profile-slack", type=int, default=0, help="slack_tasks (0: plan default)")
     args = ap.parse_args()
@@ -720,6 +802,9 @@ def main():
     block = None
     if not args.no_block:
         block = block_mpk_leg(m, torch, dev, hbm_peak)
+    batch = None
+    if not args.no_block:
+        batch = batch_leg(m, torch, dev)
 
     # ---- end to end through the C ABI with pinned host buffers (copies inside the timing)
     Xh = torch.from_numpy(x.copy()).pin_memory()
@@ -788,7 +873,7 @@ def main():
         "speedup_vs_pxspmv": sweep["p%d" % P_MAIN]["speedup"],
         "sweep": sweep, "kernel_only": kern, "fp32": fp32, "plan_ms": plan_ms,
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "solver": solver, "serving": serving,
-        "block_mpk": block, "gs2_mpk": gs2_mpk,
+        "block_mpk": block, "batch_mpk": batch, "gs2_mpk": gs2_mpk,
         "gpu_launches": launches_per_step * args.steps, "clocks": clk,
     }
     if rank == 0:

@@ -69,3 +69,50 @@ def test_argument_errors_without_gpu(built):
     assert m.lib().mpk_plan_create(ctypes.byref(A), 0, None, None, ctypes.byref(h)) == m.MPK_ERR_ARG
     assert m.lib().mpk_plan_create(ctypes.byref(A), 64, None, None, ctypes.byref(h)) == m.MPK_ERR_ARG
     assert m.lib().mpk_coeffs_chebyshev(1.0, 0.5, 3, None, None, None) == m.MPK_ERR_ARG
+
+
+def _match(got, ref):
+    """Largest distance between two eigenvalue multisets (greedy nearest matching)."""
+    used = np.zeros(len(got), bool)
+    worst = 0.0
+    for z in ref:
+        d = np.abs(got - z)
+        d[used] = np.inf
+        i = int(np.argmin(d))
+        used[i] = True
+        worst = max(worst, float(d[i]))
+    return worst
+
+
+def test_hessenberg_eigenvalues_match_numpy(built):
+    """The Ritz values' eigen solver (mpk_hessenberg_eigvals, host QR iteration) against
+    numpy.linalg.eigvals (LAPACK): random upper Hessenberg matrices (complex pairs), split
+    subdiagonals, symmetric tridiagonals, a Jordan-like defective block, and k up to 128."""
+    m = built
+    rng = np.random.default_rng(11)
+    for n in (1, 2, 3, 4, 7, 16, 48, 128):
+        cases = [np.triu(rng.standard_normal((n, n)), -1)]
+        if n > 3:
+            H = np.triu(rng.standard_normal((n, n)), -1)
+            H[n // 2, n // 2 - 1] = 0.0
+            H[1, 0] = 0.0
+            cases.append(H)
+        d = rng.uniform(-5, 5, n)
+        e = rng.standard_normal(max(n - 1, 0))
+        cases.append(np.diag(d) + np.diag(e, 1) + np.diag(e, -1))
+        for H in cases:
+            got = m.mpk_hessenberg_eigvals(H)
+            ref = np.linalg.eigvals(H)
+            assert _match(got, ref) <= 1e-10 * max(1.0, np.linalg.norm(H)), n
+            # complex pairs come as (a + bi, a - bi)
+            for i in np.nonzero(got.imag > 0)[0]:
+                assert got[i + 1] == np.conj(got[i])
+    # a 2 x 2 rotation block inside a triangular matrix: eigenvalues 3 +- 2i, 1, 5
+    H = np.array([[3.0, 2.0, 1.0, 0.5], [-2.0, 3.0, 0.2, 0.1], [0.0, 0.0, 1.0, 4.0], [0.0, 0.0, 0.0, 5.0]])
+    got = np.sort_complex(m.mpk_hessenberg_eigvals(H))
+    assert np.allclose(got, np.sort_complex(np.array([1.0, 5.0, 3 + 2j, 3 - 2j])), atol=1e-13)
+    # defective: a Jordan block of size 4 (eigenvalue 2, sensitive as eps^(1/4))
+    J = 2.0 * np.eye(4) + np.diag(np.ones(3), 1)
+    assert _match(m.mpk_hessenberg_eigvals(J), np.full(4, 2.0)) <= 1e-3
+    with pytest.raises(m.MpkError):
+        m.mpk_hessenberg_eigvals(np.full((3, 3), np.nan))

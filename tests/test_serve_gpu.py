@@ -2,9 +2,10 @@
 
 Each request's solution is bitwise identical whether it runs alone or mixed with others
 (every reduction in the solve has a fixed order), also with GS2-preconditioned solves, every
-solution reaches the 1e-8 true
-residual, a request larger than the budget is refused, and a budget that fits one request at
-a time serialises admission."""
+solution reaches the 1e-8 true residual, solves run concurrently (their [start, done]
+intervals overlap), a request submitted while others run is admitted before they all finish,
+a request larger than the budget is refused, and a budget that fits one request at a time
+serialises admission."""
 import time
 
 import numpy as np
@@ -76,6 +77,41 @@ def test_alone_vs_mixed_bitwise(m, precond):
         rr = np.linalg.norm(b - sstep.spmv(A, res["x"])) / np.linalg.norm(b)
         assert rr <= 1e-8, rr
         assert res["t_submit_ms"] <= res["t_start_ms"] <= res["t_done_ms"]
+
+
+def test_concurrent_solves_and_admission_mid_run(m):
+    """Three solves submitted together run concurrently (their [start, done] intervals
+    overlap); a fourth submitted while they run is admitted (started) before all three have
+    finished; every result is the same as the request's solve alone."""
+    reqs = []
+    # the first three are large enough (a few hundred thousand rows, anisotropy up to 40) to
+    # run for well over the 10 ms before the fourth is submitted; the fourth is small
+    for N, st, a in ((64, 27, 5.0), (60, 27, 12.0), (72, 7, 40.0), (20, 27, 3.0)):
+        A = mi.anisotropic(N, st, a)
+        reqs.append((A, mi.uniform_vectors(A.n, N)[0]))
+    srv = m.Server(m.mpk_server_opts_default(max_active=4))
+    ids = [srv.submit(A.row_ptr, A.col, A.val, b)[0] for A, b in reqs[:3]]
+    time.sleep(0.01)
+    late, _ = srv.submit(reqs[3][0].row_ptr, reqs[3][0].col, reqs[3][0].val, reqs[3][1])
+    got = _drain(srv, 4)
+    srv.close()
+    first = [got[i] for i in ids]
+    for r in first + [got[late]]:
+        assert r["status"] == m.MPK_OK, r
+    spans = [(r["t_start_ms"], r["t_done_ms"]) for r in first]
+    overlap = any(min(d0, d1) > max(s0, s1) for i, (s0, d0) in enumerate(spans)
+                  for (s1, d1) in spans[i + 1:])
+    assert overlap, spans
+    lr = got[late]
+    assert min(s for s, _ in spans) < lr["t_submit_ms"] < max(d for _, d in spans), (lr, spans)
+    assert lr["t_start_ms"] < max(d for _, d in spans), (lr, spans)   # admitted before all done
+    # the same solutions alone
+    srv = m.Server(m.mpk_server_opts_default(max_active=1))
+    for (A, b), rid in zip(reqs, ids + [late]):
+        aid, _ = srv.submit(A.row_ptr, A.col, A.val, b)
+        alone = _drain(srv, 1)[aid]
+        assert np.array_equal(alone["x"], got[rid]["x"])
+    srv.close()
 
 
 def test_budget_refusal_and_serialised_admission(m):
