@@ -509,6 +509,8 @@ def run_profile(args, m, torch, local):
         opts.slack_tasks = args.profile_slack
     if args.profile_kernel >= 0:
         opts.kernel = args.profile_kernel
+    if args.profile_lag > 0:
+        opts.owner_lag = args.profile_lag
     plan = m.mpk_plan_create(rp, ci, vv, pmax, opts)
     perm = m.mpk_plan_perm(plan)["perm"].long()
     Y = torch.empty((p + 1) * A.n, dtype=dt, device=dev)
@@ -644,6 +646,7 @@ def main():
                          "Chebyshev p = 6 on [0.1, 52]) with this many interleaved right-hand sides")
     ap.add_argument("--profile-cs", type=int, default=0, help="chunk_slices (0: plan default)")
     ap.add_argument("--profile-slack", type=int, default=0, help="slack_tasks (0: plan default)")
+    ap.add_argument("--profile-lag", type=int, default=0, help="owner_lag of the owner kernel (0: plan default)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

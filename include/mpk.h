@@ -112,7 +112,13 @@ typedef struct {
                                  (a shared-memory counter: no global atomic per task), waiting
                                  on per-block completion counters; lanes_per_row > 1 selects
                                  this kernel for single right-hand sides whatever the value of
-                                 kernel */
+                                 kernel; 6 = owner shares (single right-hand side, one lane
+                                 per row, not MPK_GS2; other calls run kernel 0): every level
+                                 group is split into one share per CTA, CTA c owning share c
+                                 of every group for every power; warp groups of a CTA each run
+                                 one power through the groups in the level-group wavefront
+                                 (Sec. 3), each task waiting on per-CTA progress counters of
+                                 the CTAs whose shares its rows read */
     int32_t blocked;          /* mpk_apply without MPK_UNBLOCKED: 1 = always the blocked
                                  kernel, 0 = never, -1 = automatic (default): p >= 2 and a
                                  matrix larger than the L2 cache, and then whichever kernel
@@ -149,6 +155,14 @@ typedef struct {
                                  a CTA to whichever warp is free (default); 1 = one ticket
                                  dispenser for the whole grid (a global atomic per task);
                                  2 = static: warp w of W runs tickets w, w + W, w + 2W, ... */
+    int32_t owner_lag;        /* kernel = 6: groups between consecutive local powers in the
+                                 wavefront (task (g, k) runs in step g + owner_lag (k - 1));
+                                 1 (default) is the paper's wavefront, larger values give a
+                                 power more time to publish at the cost of a wider window;
+                                 0 = 1 */
+    int32_t owner_prefetch;   /* kernel = 6: while local power 1 runs group g, the CTA asks the
+                                 copy engine to prefetch its share of group g + owner_prefetch
+                                 into L2 (cp.async.bulk.prefetch); 0 = off, default 1 */
 } mpk_plan_opts;
 
 typedef struct mpk_plan_s *mpk_plan_t;

@@ -72,7 +72,8 @@ class mpk_plan_opts(ctypes.Structure):
                 ("kernel", ctypes.c_int32), ("blocked", ctypes.c_int32),
                 ("jacobi", ctypes.c_int32), ("shard_warps", ctypes.c_int32),
                 ("lanes_per_row", ctypes.c_int32), ("task_units", ctypes.c_int32),
-                ("task_dispatch", ctypes.c_int32)]
+                ("task_dispatch", ctypes.c_int32), ("owner_lag", ctypes.c_int32),
+                ("owner_prefetch", ctypes.c_int32)]
 
 
 class mpk_plan_info(ctypes.Structure):

@@ -1435,6 +1435,226 @@ __global__ void __launch_bounds__(WAVE_BLOCK, (lane_min_blocks<T, LPR>())) mpk_l
 }
 
 // ------------------------------------------------------------------------------------------
+// Owner kernel (opts.kernel = 6; single right-hand side, one row per lane).  The level-group
+// wavefront of Sec. 3 - group g at local power k in step g + lag (k - 1) - with every group
+// split into G shares of about equal work and share (g, c) owned by CTA c at every power, so
+// a launch holds about seg + 1 groups between the first and the last read of a group's
+// matrix whatever the number of warps in flight (the dynamic hand-outs above keep their
+// window as wide as their slack).  Inside a CTA, power groups of warps each run the local
+// powers k with (k - 1) mod NG equal to their index, in step order.  A task (g, k) of CTA c:
+//   - one warp waits until every CTA in the share's dependency range has finished power k - 1
+//     through the last group the share's rows read (per-CTA progress counters, relaxed loads
+//     then an acquire fence); local power 1 instead waits until the CTA's own last power has
+//     finished group g - lag (seg - 1) - 1, which bounds the window, and asks the copy engine
+//     to prefetch the CTA's share of group g + pf into L2;
+//   - a named barrier of the power group, then its warps run the share's slices with the
+//     unblocked kernel's row function (results equal p x SpMV's bit for bit);
+//   - a second named barrier, then one thread publishes with a release add to the CTA's
+//     progress counter of power k (the barrier orders the group's stores before it).
+// Progress: every wait is for a task earlier in (step, power) order, and each power group runs
+// its tasks in that order, so the earliest unfinished task of the launch is running and its
+// dependencies are complete (all CTAs are co-resident: cooperative launch).  Waits are bounded;
+// on a timeout the error is latched and every power group stops at its next task.
+// ------------------------------------------------------------------------------------------
+static constexpr int OWN_BLOCK = 1024;
+static constexpr int OWN_MAX_GROUPS = 8;
+
+struct OwnArgs {
+    const int32_t *share;     // [n_groups * G + 1]: first slice of share (g, c) at g * G + c
+    const int4 *dep;          // per share {clo, chi, last group read, 0}
+    uint32_t *prog;           // [k * G + c]: groups CTA c finished at local power k
+    uint32_t *kep;            // launches that ran each local power
+    MpkCtrl *ctrl;
+    int32_t n_groups, G;
+    int k0, seg, ng, lag, pf;
+    uint64_t timeout_ns;
+    uint32_t debug_drop;      // 1: task (group 0, power 1) of CTA 0 does not publish
+};
+
+__device__ __forceinline__ void own_bar_sync(int id, int n) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void prefetch_l2_bulk(const void *p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// One warp: wait until counter cnt[c] - base >= need for every c in [lo, hi] (a lane per
+// counter, 32 at a time).  false on a timeout (latched in ctrl) or an error latched elsewhere.
+__device__ __forceinline__ bool own_wait(const uint32_t *cnt, int32_t lo, int32_t hi, uint32_t base,
+                                         int32_t need, int lane, const OwnArgs &W, uint32_t task) {
+    bool timing = false;
+    uint64_t t0 = 0;
+    for (int32_t c0 = lo; c0 <= hi;) {
+        const int32_t c = c0 + lane;
+        bool done = true;
+        if (c <= hi) done = (int32_t)(ld_relaxed_u32(cnt + c) - base) >= need;
+        if (__all_sync(0xffffffffu, done)) {
+            c0 += 32;
+            continue;
+        }
+        uint64_t now = 0;
+        uint32_t err = 0;
+        if (lane == 0) {
+            now = globaltimer_ns();
+            err = *(volatile uint32_t *)&W.ctrl->error;
+        }
+        now = __shfl_sync(0xffffffffu, now, 0);
+        err = __shfl_sync(0xffffffffu, err, 0);
+        if (err) return false;
+        if (!timing) {
+            timing = true;
+            t0 = now;
+        } else if (now - t0 > W.timeout_ns) {
+            if (lane == 0 && atomicOr(&W.ctrl->error, 1u) == 0u) W.ctrl->err_task = task;
+            return false;
+        }
+        __nanosleep(32);
+    }
+    return true;
+}
+
+__device__ __forceinline__ void cp_async4(uint32_t saddr, const void *g) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(saddr), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// FP32 slice rows with a whole 32-entry chunk of every row in flight at once: the values go
+// to the warp's shared memory by asynchronous copies (no registers held while they fly), the
+// columns to registers, then every gather is issued before the first FMA - two dependent
+// memory round trips per chunk instead of one per batch of eight.  The FMAs run in the row's
+// stored order with padding dropped by a select, as in row_sum, so the sums are the same.
+// sv: this warp's 32 x 32 floats of shared memory.
+template <int LD>
+__device__ __forceinline__ void slice_rows_f32_wide(const int32_t *colb, const float *valb, int32_t r0, int32_t r1,
+                                                    int32_t L, int lane, const VecSet &V, int k, const Coefs &cf,
+                                                    float *sv) {
+    const int32_t row = r0 + lane;
+    if (row >= r1) return;
+    const float *y1 = vec_ro<float>(V, k - 1);
+    const int32_t *colp = colb + lane;
+    const float *valp = valb + lane;
+    const uint32_t sb = (uint32_t)__cvta_generic_to_shared(sv + lane);
+    float acc = 0.f;
+    for (int32_t j0 = 0; j0 < L; j0 += 32) {
+        const int32_t mm = min(32, L - j0);
+#pragma unroll
+        for (int u = 0; u < 32; u++)
+            if (u < mm) cp_async4(sb + 128u * u, valp + 32 * (j0 + u));
+        cp_async_commit();
+        int32_t cc[32];
+#pragma unroll
+        for (int u = 0; u < 32; u++) cc[u] = u < mm ? ldm<LD>(colp + 32 * (j0 + u)) : -1;
+        float xx[32];
+#pragma unroll
+        for (int u = 0; u < 32; u++) xx[u] = cc[u] >= 0 ? y1[cc[u]] : 0.f;
+        cp_async_wait_all();
+#pragma unroll
+        for (int u = 0; u < 32; u++) {
+            const float f = fmaf(sv[32 * u + lane], xx[u], acc);
+            acc = cc[u] >= 0 ? f : acc;
+        }
+    }
+    float a1[1] = {acc};
+    row_finish<float, 1>(a1, row, 1, 0, V, k, cf);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(OWN_BLOCK, 1) mpk_owner_kernel(SellView A, VecSet V, Coefs cf, OwnArgs W) {
+    __shared__ uint32_t s_base[MPK_MAX_P + 1];
+    __shared__ int s_stop[OWN_MAX_GROUPS];
+    extern __shared__ float own_smem[];   // FP32: 32 x 32 values per warp
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wg = (int)(blockDim.x >> 5) / W.ng;   // warps per power group
+    const int j = warp / wg, wi = warp - j * wg;
+    const int c = blockIdx.x, G = W.G;
+    for (int k = threadIdx.x; k <= W.seg; k += blockDim.x)
+        s_base[k] = *(volatile uint32_t *)(W.kep + k) * (uint32_t)W.n_groups;
+    if (threadIdx.x < OWN_MAX_GROUPS) s_stop[threadIdx.x] = 0;
+    __syncthreads();
+    if (j < W.ng) {
+        const int nthr = wg * 32;
+        const int bar = 1 + j;
+        const int tmax = W.n_groups - 1 + W.lag * (W.seg - 1);
+        bool stop = false;
+        for (int t = 0; t <= tmax && !stop; t++) {
+            for (int kl = j + 1; kl <= W.seg; kl += W.ng) {
+                const int g = t - W.lag * (kl - 1);
+                if (g < 0 || g >= W.n_groups) continue;
+                const int32_t sh = g * G + c;
+                const int32_t s0 = __ldg(W.share + sh), s1 = __ldg(W.share + sh + 1);
+                if (wi == 0) {
+                    bool ok = true;
+                    const uint32_t task = (uint32_t)g | ((uint32_t)kl << 24);
+                    if (kl > 1) {
+                        if (s1 > s0) {
+                            const int4 d = __ldg(W.dep + sh);
+                            ok = own_wait(W.prog + (int64_t)(kl - 1) * G, d.x, d.y, s_base[kl - 1], d.z + 1, lane, W, task);
+                            fence_acq_rel_gpu();   // acquire: counters observed before the vectors read below
+                        }
+                    } else {
+                        if (W.seg > 1) {
+                            // window bound: the CTA's own last power has finished group g - lag (seg - 1) - 1
+                            const int32_t need = g - W.lag * (W.seg - 1);
+                            if (need > 0)
+                                ok = own_wait(W.prog + (int64_t)W.seg * G, c, c, s_base[W.seg], need, lane, W, task);
+                        }
+                        if (ok && W.pf > 0 && lane == 0 && g + W.pf < W.n_groups) {
+                            const int32_t sp = __ldg(W.share + sh + W.pf * G), sq = __ldg(W.share + sh + W.pf * G + 1);
+                            if (sq > sp) {
+                                const long long e0 = 32ll * __ldg(A.slice_ptr + sp), e1 = 32ll * __ldg(A.slice_ptr + sq);
+                                const char *pc = reinterpret_cast<const char *>(A.col + e0);
+                                const char *pv = reinterpret_cast<const char *>(reinterpret_cast<const T *>(A.val) + e0);
+                                const long long bc = (e1 - e0) * 4, bv = (e1 - e0) * (long long)sizeof(T);
+                                for (long long o = 0; o < bc; o += 65536) prefetch_l2_bulk(pc + o, (uint32_t)min(65536ll, bc - o));
+                                for (long long o = 0; o < bv; o += 65536) prefetch_l2_bulk(pv + o, (uint32_t)min(65536ll, bv - o));
+                            }
+                        }
+                    }
+                    if (!ok && lane == 0) *(volatile int *)&s_stop[j] = 1;
+                }
+                own_bar_sync(bar, nthr);
+                if (*(volatile int *)&s_stop[j]) {
+                    stop = true;
+                    break;
+                }
+                const int k = W.k0 + kl;
+                const bool last = kl == W.seg;
+                for (int32_t sl = s0 + wi; sl < s1; sl += wg) {
+                    const long long o = 32ll * __ldg(A.slice_ptr + sl);
+                    const int32_t r0 = __ldg(A.slice_row + sl), r1 = __ldg(A.slice_row + sl + 1);
+                    const int32_t L = __ldg(A.slice_len + sl);
+                    const T *valb = reinterpret_cast<const T *>(A.val) + o;
+                    // the last local power is the slices' last read in this launch: streaming loads
+                    if constexpr (sizeof(T) == 4) {
+                        float *sv = own_smem + warp * 1024;
+                        if (last) slice_rows_f32_wide<LD_STREAM>(A.col + o, valb, r0, r1, L, lane, V, k, cf, sv);
+                        else slice_rows_f32_wide<LD_KEEP>(A.col + o, valb, r0, r1, L, lane, V, k, cf, sv);
+                    } else {
+                        if (last) slice_rows<T, LD_STREAM>(A.col + o, valb, r0, r1, L, lane, V, k, cf);
+                        else slice_rows<T, LD_KEEP>(A.col + o, valb, r0, r1, L, lane, V, k, cf);
+                    }
+                }
+                own_bar_sync(bar, nthr);
+                if (wi == wg - 1 && lane == 0 && !(W.debug_drop && c == 0 && g == 0 && kl == 1))
+                    red_release_add_u32(W.prog + (int64_t)kl * G + c, 1u);
+            }
+        }
+    }
+    // every CTA gets here; the last one counts this launch for every local power
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const uint32_t dn = atomicAdd(&W.ctrl->done_ctas, 1u);
+        if (dn == gridDim.x - 1) {
+            W.ctrl->done_ctas = 0;
+            for (int kk = 1; kk <= W.seg; kk++) W.kep[kk] += 1u;
+            __threadfence();
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------
 // Staged warp tasks (opts.kernel = 5; single right-hand side, one row per lane, one slice per
 // task).  The lane-task kernel's tasks, schedule and hand-out, but each task's slice (its
 // column indices and values, 32 L entries, contiguous in the SELL-32 arrays) is copied into
@@ -2233,6 +2453,56 @@ mpk_status launch_lane_blocked(mpk_plan_s *P, const SellView &A, const VecSet &V
     return MPK_OK;
 }
 
+// Owner kernel (kernel 6): one CTA of 1024 threads per SM, cooperative, in segments of at
+// most p_blk powers.
+template <typename T>
+mpk_status launch_owner_blocked(mpk_plan_s *P, const SellView &A, const VecSet &V, const Coefs &cf,
+                                int p, uint32_t flags, cudaStream_t s) {
+    const size_t dsm = sizeof(T) == 4 ? (size_t)OWN_BLOCK * 32 * sizeof(float) : 0;
+    if (dsm > 0)
+        MPK_CUDA(cudaFuncSetAttribute(mpk_owner_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
+    int occ = 0;
+    MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mpk_owner_kernel<T>, OWN_BLOCK, dsm));
+    if (occ < 1) return MPK_ERR_UNIMPLEMENTED;
+    const int G = P->n_sm;
+    OwnerGraph *O = nullptr;
+    MPK_TRY(mpk_get_owner_graph(P, G, &O, s));
+    int k0 = 0;
+    while (k0 < p) {
+        const int seg = std::min(P->p_blk, p - k0);
+        OwnArgs W;
+        memset(&W, 0, sizeof(W));
+        W.share = O->share.as<int32_t>();
+        W.dep = O->dep.as<int4>();
+        W.prog = O->prog.as<uint32_t>();
+        W.kep = O->kep.as<uint32_t>();
+        W.ctrl = P->ctrl.as<MpkCtrl>();
+        W.n_groups = P->n_groups;
+        W.G = G;
+        W.k0 = k0;
+        W.seg = seg;
+        W.ng = std::min(seg, OWN_MAX_GROUPS);
+        W.lag = std::max(1, (int)P->opts.owner_lag);
+        W.pf = std::max(0, (int)P->opts.owner_prefetch);
+        W.timeout_ns = (uint64_t)P->opts.wait_timeout_us * 1000ull;
+        W.debug_drop = (flags & MPK_DEBUG_DROP_FLAG) && k0 == 0 ? 1u : 0u;
+        cudaLaunchConfig_t lc;
+        memset(&lc, 0, sizeof(lc));
+        lc.gridDim = dim3((unsigned)G);
+        lc.blockDim = dim3(OWN_BLOCK);
+        lc.dynamicSmemBytes = dsm;
+        lc.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        lc.attrs = attr;
+        lc.numAttrs = 1;
+        MPK_CUDA(cudaLaunchKernelEx(&lc, mpk_owner_kernel<T>, A, V, cf, W));
+        k0 += seg;
+    }
+    return MPK_OK;
+}
+
 // Staged warp tasks (kernel 5): one slice per task, matrix slices copied into shared memory.
 // MPK_ERR_UNIMPLEMENTED when two buffers per warp of the longest slice do not fit.
 template <typename T>
@@ -2314,6 +2584,10 @@ mpk_status launch_lane_powers(mpk_plan_s *P, const SellView &A, const VecSet &V,
         }
         MPK_CUDA(cudaGetLastError());
         return MPK_OK;
+    }
+    if (lpr == 1 && P->opts.kernel == 6) {
+        const mpk_status st = launch_owner_blocked<T>(P, A, V, cf, p, flags, s);
+        if (st != MPK_ERR_UNIMPLEMENTED) return st;
     }
     if (lpr == 1 && P->opts.kernel == 5) {
         const mpk_status st = launch_stage_blocked<T>(P, A, V, cf, p, flags, s);
@@ -2796,6 +3070,10 @@ extern "C" mpk_status mpk_plan_sync(mpk_plan_t P, cudaStream_t s) {
         if (P->wave_cur.p) MPK_CUDA(cudaMemset(P->wave_cur.p, 0, P->wave_cur.bytes));
         for (auto &kv : P->lane_graphs) {
             MPK_CUDA(cudaMemset(kv.second->cnt.p, 0, kv.second->cnt.bytes));
+            MPK_CUDA(cudaMemset(kv.second->kep.p, 0, kv.second->kep.bytes));
+        }
+        for (auto &kv : P->owner_graphs) {
+            MPK_CUDA(cudaMemset(kv.second->prog.p, 0, kv.second->prog.bytes));
             MPK_CUDA(cudaMemset(kv.second->kep.p, 0, kv.second->kep.bytes));
         }
         return MPK_ERR_TIMEOUT;

@@ -118,6 +118,22 @@ struct LaneGraph {
     std::map<int64_t, std::unique_ptr<struct Schedule>> schedules;   // key: p and slack
 };
 
+// Share graph of the owner kernel (opts.kernel = 6): every level group's slices split into G
+// contiguous shares balanced by stored entries, share (g, c) = slices [share[g G + c],
+// share[g G + c + 1]) owned by CTA c for every power.  dep holds, per share, the range of
+// CTAs [clo, chi] owning any share its rows read (and, unless the pattern is declared
+// symmetric, any share whose rows read it: the closure over A^T that the 3-buffer ring of
+// MPK_FINAL_ONLY needs) and the last group among them.  prog counts, per (local power, CTA),
+// the groups finished, accumulating over launches against kep.  Built on first use per G.
+struct OwnerGraph {
+    int32_t G = 0;
+    int32_t max_share_slices = 0;
+    DevBuf share;      // int32 [n_groups * G + 1]
+    DevBuf dep;        // int4 per share {clo, chi, gdep, 0}
+    DevBuf prog;       // uint32 [(p_blk + 1) * G]
+    DevBuf kep;        // uint32 per local power: launches that ran it
+};
+
 // The plan: level structure, permuted matrix in SELL-32 form, blocked-task metadata.
 struct mpk_plan_s {
     int device = 0;
@@ -206,6 +222,8 @@ struct mpk_plan_s {
     int lane_kernel = 0;
     int64_t lane_slack = 0;            // lag-greedy slack of the lane tasks (0: resident warps)
     std::map<int, std::unique_ptr<LaneGraph>> lane_graphs;
+    // owner kernel: share graphs per grid size
+    std::map<int, std::unique_ptr<OwnerGraph>> owner_graphs;
 
     // workspace for permuted / interleaved vectors; ws_h: the GS2 inner iterates (2 vectors)
     DevBuf ws_x, ws_y, ws_host, ws_h;
@@ -230,6 +248,8 @@ mpk_status mpk_lag_greedy_order(int p, int32_t nc, const std::vector<int32_t> &d
 // The lane-task graph of a plan for (lpr, units), built on first use (plan.cu).
 mpk_status mpk_get_lane_graph(mpk_plan_s *P, int lpr, int units, LaneGraph **out, cudaStream_t s);
 mpk_status mpk_build_blocks(mpk_plan_s *P, cudaStream_t s);
+// The owner kernel's share graph of a plan for G CTAs, built on first use (plan.cu).
+mpk_status mpk_get_owner_graph(mpk_plan_s *P, int G, OwnerGraph **out, cudaStream_t s);
 
 // Row-sum kernels shared by the MPK and the solver (apply.cu)
 mpk_status mpk_launch_residual(mpk_plan_s *P, const double *x, const double *b, double *r,

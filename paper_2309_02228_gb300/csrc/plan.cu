@@ -820,6 +820,8 @@ extern "C" mpk_status mpk_plan_opts_default(mpk_plan_opts *o) {
     o->kernel = 4;
     o->blocked = -1;
     o->jacobi = 0;
+    o->owner_lag = 1;
+    o->owner_prefetch = 1;
     return MPK_OK;
 }
 
@@ -1283,9 +1285,10 @@ static mpk_status plan_create_impl(const mpk_csr *A, int32_t p_max, const mpk_pl
     else if (o.lanes_per_row == 1 || o.lanes_per_row == 2 || o.lanes_per_row == 4 || o.lanes_per_row == 8)
         P->lanes = o.lanes_per_row;
     else return MPK_ERR_ARG;
-    if (o.task_units < 0 || o.kernel < 0 || o.kernel > 5 || o.task_dispatch < 0 || o.task_dispatch > 2)
+    if (o.task_units < 0 || o.kernel < 0 || o.kernel > 6 || o.task_dispatch < 0 || o.task_dispatch > 2 ||
+        o.owner_lag < 0 || o.owner_lag > 4 || o.owner_prefetch < 0 || o.owner_prefetch > 4)
         return MPK_ERR_ARG;
-    P->lane_kernel = (o.kernel == 4 || o.kernel == 5 || P->lanes > 1) ? 1 : 0;
+    P->lane_kernel = (o.kernel == 4 || o.kernel == 5 || o.kernel == 6 || P->lanes > 1) ? 1 : 0;
     P->lane_slack = o.slack_tasks > 0 ? o.slack_tasks : 0;
     MPK_CUDA(cudaStreamSynchronize(s));
     auto t1 = std::chrono::steady_clock::now();
@@ -1393,6 +1396,121 @@ mpk_status mpk_get_lane_graph(mpk_plan_s *P, int lpr, int units, LaneGraph **out
     MPK_CUDA(cudaStreamSynchronize(s));   // host vectors above outlive their copies
     *out = G.get();
     P->lane_graphs[key] = std::move(G);
+    return MPK_OK;
+}
+
+// Owner-kernel dependencies (one thread per row): the CTA range and last group of the shares
+// holding the row's columns, merged into the row's share; with `sym_close` also the row's
+// share merged into each of those shares (closure over A^T).  dlo / dhi / dg start at the
+// share's own CTA and group.
+__global__ void owner_dep_kernel(const int32_t *rp, const int32_t *ci, const int32_t *row_share, int64_t n,
+                                 int G, int sym_close, int32_t *dlo, int32_t *dhi, int32_t *dg) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t sh = row_share[r];
+        const int32_t c = sh % G, g = sh / G;
+        int32_t lo = c, hi = c, gd = g;
+        for (int32_t t = rp[r]; t < rp[r + 1]; t++) {
+            const int32_t s2 = row_share[ci[t]];
+            const int32_t c2 = s2 % G, g2 = s2 / G;
+            lo = min(lo, c2);
+            hi = max(hi, c2);
+            gd = max(gd, g2);
+            if (sym_close) {
+                atomicMin(&dlo[s2], c);
+                atomicMax(&dhi[s2], c);
+                atomicMax(&dg[s2], g);
+            }
+        }
+        atomicMin(&dlo[sh], lo);
+        atomicMax(&dhi[sh], hi);
+        atomicMax(&dg[sh], gd);
+    }
+}
+
+__global__ void owner_dep_init_kernel(int64_t n_shares, int G, int32_t *dlo, int32_t *dhi, int32_t *dg) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_shares;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        dlo[i] = (int32_t)(i % G);
+        dhi[i] = (int32_t)(i % G);
+        dg[i] = (int32_t)(i / G);
+    }
+}
+
+__global__ void owner_dep_pack_kernel(int64_t n_shares, const int32_t *dlo, const int32_t *dhi,
+                                      const int32_t *dg, int4 *dep) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_shares;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dep[i] = make_int4(dlo[i], dhi[i], dg[i], 0);
+}
+
+mpk_status mpk_get_owner_graph(mpk_plan_s *P, int G, OwnerGraph **out, cudaStream_t s) {
+    if (G < 1) return MPK_ERR_ARG;
+    auto it = P->owner_graphs.find(G);
+    if (it != P->owner_graphs.end()) {
+        *out = it->second.get();
+        return MPK_OK;
+    }
+    std::unique_ptr<OwnerGraph> O(new OwnerGraph());
+    O->G = G;
+    const int64_t n = P->n;
+    const int64_t n_shares = (int64_t)P->n_groups * G;
+    if (n_shares >= (1ll << 31)) return MPK_ERR_UNIMPLEMENTED;
+    std::vector<int32_t> sr(P->n_slices + 1, 0), slen(P->n_slices + 1, 0);
+    if (P->n_slices > 0) {
+        MPK_CUDA(cudaMemcpyAsync(sr.data(), P->slice_row.p, (P->n_slices + 1) * 4, cudaMemcpyDeviceToHost, s));
+        MPK_CUDA(cudaMemcpyAsync(slen.data(), P->slice_len.p, P->n_slices * 4, cudaMemcpyDeviceToHost, s));
+    }
+    MPK_CUDA(cudaStreamSynchronize(s));
+    // split each group's slices into G shares of about equal work: a slice weighs its stored
+    // entries per row plus two (the per-slice cost of the row epilogue)
+    std::vector<int32_t> share((size_t)n_shares + 1, 0), share_row((size_t)n_shares + 1, 0);
+    int32_t sl = 0;
+    for (int32_t g = 0; g < P->n_groups; g++) {
+        const int32_t gend = P->h_level_ptr[P->h_group_ptr[g + 1]];
+        const int32_t g0 = sl;
+        while (sl < P->n_slices && sr[sl] < gend) sl++;
+        const int32_t g1 = sl;
+        int64_t wsum = 0;
+        for (int32_t t = g0; t < g1; t++) wsum += slen[t] + 2;
+        int32_t cur = g0;
+        int64_t acc = 0;
+        for (int c = 0; c < G; c++) {
+            const int64_t target = wsum * c / G;
+            while (cur < g1 && acc < target) acc += slen[cur++] + 2;
+            share[(size_t)g * G + c] = cur;
+        }
+        for (int c = 0; c < G; c++) {
+            const int32_t a = share[(size_t)g * G + c];
+            const int32_t b = c + 1 < G ? share[(size_t)g * G + c + 1] : g1;
+            O->max_share_slices = std::max(O->max_share_slices, b - a);
+        }
+    }
+    share[(size_t)n_shares] = P->n_slices;
+    for (int64_t i = 0; i <= n_shares; i++) share_row[i] = share[i] < P->n_slices ? sr[share[i]] : (int32_t)n;
+    MPK_TRY(upload(O->share, share, s));
+    MPK_TRY(O->dep.alloc((size_t)std::max<int64_t>(n_shares, 1) * sizeof(int4)));
+    if (n_shares > 0 && n > 0) {
+        DevBuf d_srow, row_share, dlo, dhi, dg;
+        MPK_TRY(upload(d_srow, share_row, s));
+        MPK_TRY(row_share.alloc_on(n * 4, s));
+        MPK_TRY(dlo.alloc_on((size_t)n_shares * 4, s));
+        MPK_TRY(dhi.alloc_on((size_t)n_shares * 4, s));
+        MPK_TRY(dg.alloc_on((size_t)n_shares * 4, s));
+        row_chunk_kernel<<<(unsigned)std::min<int64_t>(n_shares, 65535), 256, 0, s>>>(d_srow.as<int32_t>(), n_shares, row_share.as<int32_t>());
+        owner_dep_init_kernel<<<grid_for(n_shares), 256, 0, s>>>(n_shares, G, dlo.as<int32_t>(), dhi.as<int32_t>(), dg.as<int32_t>());
+        owner_dep_kernel<<<grid_for(n), 256, 0, s>>>(P->rp.as<int32_t>(), P->ci.as<int32_t>(), row_share.as<int32_t>(), n, G,
+                                                     P->opts.assume_symmetric ? 0 : 1, dlo.as<int32_t>(), dhi.as<int32_t>(), dg.as<int32_t>());
+        owner_dep_pack_kernel<<<grid_for(n_shares), 256, 0, s>>>(n_shares, dlo.as<int32_t>(), dhi.as<int32_t>(), dg.as<int32_t>(), O->dep.as<int4>());
+        MPK_CUDA(cudaGetLastError());
+    }
+    MPK_TRY(O->prog.alloc((size_t)(P->p_blk + 1) * G * 4));
+    MPK_CUDA(cudaMemsetAsync(O->prog.p, 0, O->prog.bytes, s));
+    MPK_TRY(O->kep.alloc((MPK_MAX_P + 1) * 4));
+    MPK_CUDA(cudaMemsetAsync(O->kep.p, 0, O->kep.bytes, s));
+    MPK_CUDA(cudaStreamSynchronize(s));   // host vectors above outlive their copies
+    *out = O.get();
+    P->owner_graphs[G] = std::move(O);
     return MPK_OK;
 }
 

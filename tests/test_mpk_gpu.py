@@ -157,7 +157,8 @@ def test_mpk_fp64_vs_oracle(m, basis, name):
     rp, ci, vv = to_dev(A)
     # kernel 0 = warp tasks with a ticket dispenser, 1 = CTA tasks, 2 = warp tasks in static
     # round robin, 3 = ready-first warp tasks, 4 = lane tasks (lanes sharing rows, sub-slice
-    # tasks), 5 = staged warp tasks (slices copied into shared memory); slack 7 makes most warp
+    # tasks), 5 = staged warp tasks (slices copied into shared memory), 6 = owner shares (one
+    # share of every level group per CTA, warp groups per power); slack 7 makes most warp
     # tasks wait for their dependencies.  The last field is lanes_per_row (the unblocked
     # comparison runs the same row function)
     for budget, cs, stage, sched, kern, slack, lanes in (
@@ -169,7 +170,8 @@ def test_mpk_fp64_vs_oracle(m, basis, name):
             (30_000, 1, -1, 1, 4, 0, 1), (60_000, 3, -1, 1, 4, 7, 1),
             (30_000, 1, -1, 1, 4, 0, 2), (60_000, 2, -1, 1, 4, 7, 4),
             (1 << 30, 1, -1, 1, 4, 0, 8), (100_000, 5, -1, 1, 4, 3, 4),
-            (30_000, 1, -1, 1, 5, 0, 1), (60_000, 1, -1, 1, 5, 7, 1), (1 << 30, 1, -1, 1, 5, 0, 1)):
+            (30_000, 1, -1, 1, 5, 0, 1), (60_000, 1, -1, 1, 5, 7, 1), (1 << 30, 1, -1, 1, 5, 0, 1),
+            (30_000, 1, -1, 1, 6, 0, 1), (1 << 30, 1, -1, 1, 6, 0, 1)):
         plan = m.mpk_plan_create(rp, ci, vv, p, m.mpk_plan_opts_default(
             l2_budget_bytes=budget, chunk_slices=cs, stage=stage, schedule=sched, kernel=kern,
             slack_tasks=slack, blocked=1, lanes_per_row=lanes, task_units=cs))
@@ -193,7 +195,7 @@ def test_mpk_fp32_vs_oracle(m, name):
     den = abs_powers(A32, cf, x)
     rp, ci, vv = to_dev(A, np.float32)
     # lanes_per_row 0 is the automatic choice (4 in FP32)
-    for lanes, kern, units in ((0, 0, 1), (1, 0, 1), (1, 4, 2), (2, 4, 1), (4, 4, 3), (8, 4, 1), (1, 5, 1)):
+    for lanes, kern, units in ((0, 0, 1), (1, 0, 1), (1, 4, 2), (2, 4, 1), (4, 4, 3), (8, 4, 1), (1, 5, 1), (1, 6, 1)):
         plan = m.mpk_plan_create(rp, ci, vv, p, m.mpk_plan_opts_default(
             l2_budget_bytes=50_000, blocked=1, lanes_per_row=lanes, kernel=kern, task_units=units))
         got = _run(m, plan, A, cf, x, dtype=torch.float32)
@@ -250,7 +252,7 @@ def test_block_mpk_n_rhs(m, n_rhs, interleaved):
             assert max_rel_err(got[k, :, q], ref[k], den[k]) <= 64 * k * U32
 
 
-@pytest.mark.parametrize("kern,lanes", [(0, 1), (1, 1), (2, 1), (3, 1), (4, 1), (4, 4), (5, 1)])
+@pytest.mark.parametrize("kern,lanes", [(0, 1), (1, 1), (2, 1), (3, 1), (4, 1), (4, 4), (5, 1), (6, 1)])
 def test_final_only_gamma_and_segments(m, kern, lanes):
     import torch
     A = MATS["diff7_10"]
@@ -297,7 +299,7 @@ def test_host_io(m):
     assert np.array_equal(Yh.numpy().reshape(p + 1, -1), dev)
 
 
-@pytest.mark.parametrize("kern,lanes", [(0, 1), (1, 1), (2, 1), (3, 1), (4, 1), (4, 4), (5, 1)])
+@pytest.mark.parametrize("kern,lanes", [(0, 1), (1, 1), (2, 1), (3, 1), (4, 1), (4, 4), (5, 1), (6, 1)])
 def test_timeout_is_reported_and_plan_recovers(m, kern, lanes):
     """A completion that nothing publishes: the waits on it run out (short bound), the call
     reports MPK_ERR_TIMEOUT, and the plan works again afterwards."""
@@ -356,7 +358,7 @@ def test_automatic_blocked_choice(m):
         torch.cuda.empty_cache()
 
 
-@pytest.mark.parametrize("kern,lanes", [(0, 1), (3, 1), (4, 4), (5, 1)])
+@pytest.mark.parametrize("kern,lanes", [(0, 1), (3, 1), (4, 4), (5, 1), (6, 1)])
 def test_graph_capture_replays_the_blocked_kernel(m, kern, lanes):
     """A blocked mpk_apply captured in a CUDA graph (after one ordinary call, which builds the
     schedule) replays correctly: the per-power launch counts the dependency waits compare
