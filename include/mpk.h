@@ -163,6 +163,17 @@ typedef struct {
     int32_t owner_prefetch;   /* kernel = 6: while local power 1 runs group g, the CTA asks the
                                  copy engine to prefetch its share of group g + owner_prefetch
                                  into L2 (cp.async.bulk.prefetch); 0 = off, default 1 */
+    int32_t level_order;      /* order of the rows inside a level (Sec. 3 fixes the levels, not
+                                 this order): 0 = ascending original index; 1 (default) =
+                                 breadth-first: level l's rows by the position of their
+                                 earliest-placed neighbour in level l - 1 (in G(A + A^T)), then
+                                 by index - the queue order of a breadth-first search that
+                                 appends each row's next-level neighbours in ascending index,
+                                 which keeps rows that share neighbours together when the
+                                 caller's numbering carries no locality (measured on the
+                                 randomly permuted 7-point 256^3 matrix: FP32 SpMV 1.55x faster
+                                 than with index order).  Built on the device one level after
+                                 another. */
 } mpk_plan_opts;
 
 typedef struct mpk_plan_s *mpk_plan_t;

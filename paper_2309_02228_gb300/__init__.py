@@ -73,7 +73,7 @@ class mpk_plan_opts(ctypes.Structure):
                 ("jacobi", ctypes.c_int32), ("shard_warps", ctypes.c_int32),
                 ("lanes_per_row", ctypes.c_int32), ("task_units", ctypes.c_int32),
                 ("task_dispatch", ctypes.c_int32), ("owner_lag", ctypes.c_int32),
-                ("owner_prefetch", ctypes.c_int32)]
+                ("owner_prefetch", ctypes.c_int32), ("level_order", ctypes.c_int32)]
 
 
 class mpk_plan_info(ctypes.Structure):

@@ -504,6 +504,80 @@ __global__ void iperm_kernel(const int32_t *perm, int64_t n, int32_t *iperm) {
          r += (int64_t)gridDim.x * blockDim.x)
         iperm[perm[r]] = (int32_t)r;
 }
+
+// ============================================================================================
+// Breadth-first order inside levels (opts.level_order = 1).  Level l's rows are ordered by the
+// key (position of the row's earliest-placed neighbour in level l - 1, row index), neighbours
+// taken in G(A + A^T); a row without a neighbour one level down (a component's root) takes the
+// smallest key.  Levels are placed in ascending order, each after the one below it is final.
+// The rows of a level enter in ascending index (the stable sort by level), so a stable sort by
+// the neighbour position alone gives the (position, index) order.
+// ============================================================================================
+// key of the level's rows: 0 for no neighbour one level down, else 1 + that neighbour's
+// position relative to the start of level l - 1
+__global__ void bfs_order_key_kernel(const int32_t *rp, const int32_t *ci, const int32_t *rpT,
+                                     const int32_t *ciT, const int32_t *level, const int32_t *perm,
+                                     const int32_t *iperm, int32_t lo, int32_t m, int32_t l,
+                                     int32_t prev_lo, int32_t *keys, int32_t *rows) {
+    for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < m; t += gridDim.x * blockDim.x) {
+        const int32_t i = perm[lo + t];
+        int32_t key = 0x7fffffff;
+        for (int32_t e = rp[i]; e < rp[i + 1]; e++) {
+            const int32_t j = ci[e];
+            if (level[j] == l - 1) key = min(key, iperm[j]);
+        }
+        if (rpT)
+            for (int32_t e = rpT[i]; e < rpT[i + 1]; e++) {
+                const int32_t j = ciT[e];
+                if (level[j] == l - 1) key = min(key, iperm[j]);
+            }
+        keys[t] = key == 0x7fffffff ? 0 : key - prev_lo + 1;
+        rows[t] = i;
+    }
+}
+
+static constexpr int BOS_MAX = 4096;   // rows a level may hold for the one-block sort
+
+// One block: sort (key, row) of m <= BOS_MAX rows (bitonic network on the packed 64-bit
+// pairs in shared memory) and place them at positions lo .. lo + m - 1.
+__global__ void __launch_bounds__(512) bfs_order_small_kernel(const int32_t *keys, const int32_t *rows, int32_t m,
+                                                              int32_t lo, int32_t *perm, int32_t *iperm) {
+    __shared__ unsigned long long v[BOS_MAX];
+    int32_t np = 1;
+    while (np < m) np <<= 1;
+    for (int32_t t = threadIdx.x; t < np; t += blockDim.x)
+        v[t] = t < m ? (((unsigned long long)(uint32_t)keys[t] << 32) | (uint32_t)rows[t]) : ~0ull;
+    __syncthreads();
+    for (int32_t k = 2; k <= np; k <<= 1) {
+        for (int32_t jj = k >> 1; jj > 0; jj >>= 1) {
+            for (int32_t t = threadIdx.x; t < np; t += blockDim.x) {
+                const int32_t u = t ^ jj;
+                if (u > t) {
+                    const bool up = (t & k) == 0;
+                    const unsigned long long a = v[t], b = v[u];
+                    if ((a > b) == up) {
+                        v[t] = b;
+                        v[u] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int32_t t = threadIdx.x; t < m; t += blockDim.x) {
+        const int32_t r = (int32_t)(v[t] & 0xffffffffull);
+        perm[lo + t] = r;
+        iperm[r] = lo + t;
+    }
+}
+
+__global__ void bfs_order_place_kernel(const int32_t *rows, int32_t m, int32_t lo, int32_t *perm, int32_t *iperm) {
+    for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < m; t += gridDim.x * blockDim.x) {
+        const int32_t r = rows[t];
+        perm[lo + t] = r;
+        iperm[r] = lo + t;
+    }
+}
 __global__ void level_hist_kernel(const int32_t *level, int64_t n, int32_t *cnt) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
@@ -822,6 +896,7 @@ extern "C" mpk_status mpk_plan_opts_default(mpk_plan_opts *o) {
     o->jacobi = 0;
     o->owner_lag = 1;
     o->owner_prefetch = 1;
+    o->level_order = 1;
     return MPK_OK;
 }
 
@@ -838,7 +913,8 @@ static mpk_status plan_create_impl(const mpk_csr *A, int32_t p_max, const mpk_pl
     if (opts) P->opts = *opts;
     else mpk_plan_opts_default(&P->opts);
     mpk_plan_opts &o = P->opts;
-    if (o.n_sweeps < 0 || o.chunk_slices <= 0 || o.root_rule < 0 || o.root_rule > 1)
+    if (o.n_sweeps < 0 || o.chunk_slices <= 0 || o.root_rule < 0 || o.root_rule > 1 ||
+        o.level_order < 0 || o.level_order > 1)
         return MPK_ERR_ARG;
     const int64_t n = A->n, nnz = A->nnz;
     P->n = n;
@@ -1023,6 +1099,51 @@ static mpk_status plan_create_impl(const mpk_csr *A, int32_t p_max, const mpk_pl
         MPK_TRY(exclusive_scan<int32_t, int32_t>(cnt.as<int32_t>(), P->level_ptr.as<int32_t>(), n_levels, tmp.p, s));
     } else {
         MPK_CUDA(cudaMemsetAsync(P->level_ptr.p, 0, 4, s));
+    }
+    // ---- breadth-first order inside levels (level_order = 1), one level after another
+    if (o.level_order == 1 && n > 0 && n_levels > 1) {
+        std::vector<int32_t> lp(n_levels + 1);
+        MPK_CUDA(cudaMemcpyAsync(lp.data(), P->level_ptr.p, (n_levels + 1) * 4, cudaMemcpyDeviceToHost, s));
+        MPK_CUDA(cudaStreamSynchronize(s));
+        int32_t maxm = 0;
+        for (int32_t l = 0; l < n_levels; l++) maxm = std::max(maxm, lp[l + 1] - lp[l]);
+        const int64_t tiles = ceil_div(maxm, RS_TILE);
+        DevBuf kA, kB, vA, vB, hist, offs, stmp;
+        MPK_TRY(kA.alloc_on((size_t)maxm * 4, s));
+        MPK_TRY(kB.alloc_on((size_t)maxm * 4, s));
+        MPK_TRY(vA.alloc_on((size_t)maxm * 4, s));
+        MPK_TRY(vB.alloc_on((size_t)maxm * 4, s));
+        MPK_TRY(hist.alloc_on((256 * tiles + 1) * sizeof(int32_t), s));
+        MPK_TRY(offs.alloc_on((256 * tiles + 1) * sizeof(int32_t), s));
+        MPK_TRY(stmp.alloc_on(scan_tmp_bytes(256 * tiles + 1), s));
+        const int32_t *rT = sym ? nullptr : rpT.as<int32_t>();
+        const int32_t *cT = sym ? nullptr : ciT.as<int32_t>();
+        for (int32_t l = 1; l < n_levels; l++) {
+            const int32_t lo = lp[l], m = lp[l + 1] - lp[l];
+            if (m <= 1) continue;
+            bfs_order_key_kernel<<<grid_for(m), 256, 0, s>>>(A->row_ptr, A->col, rT, cT, P->level.as<int32_t>(),
+                                                             P->perm.as<int32_t>(), P->iperm.as<int32_t>(), lo, m, l,
+                                                             lp[l - 1], kA.as<int32_t>(), vA.as<int32_t>());
+            if (m <= BOS_MAX) {
+                bfs_order_small_kernel<<<1, 512, 0, s>>>(kA.as<int32_t>(), vA.as<int32_t>(), m, lo,
+                                                         P->perm.as<int32_t>(), P->iperm.as<int32_t>());
+            } else {
+                // stable radix sort by key (the rows are in ascending index within the level)
+                const int64_t nt = ceil_div(m, RS_TILE);
+                const int32_t maxkey = lp[l] - lp[l - 1];
+                int32_t *ki = kA.as<int32_t>(), *ko = kB.as<int32_t>();
+                int32_t *vi = vA.as<int32_t>(), *vo = vB.as<int32_t>();
+                for (int shift = 0; shift == 0 || (shift < 31 && ((int64_t)1 << shift) <= maxkey); shift += 8) {
+                    rs_hist_kernel<<<(unsigned)nt, RS_BLOCK, 0, s>>>(ki, m, shift, hist.as<int32_t>(), nt);
+                    MPK_TRY(exclusive_scan<int32_t, int32_t>(hist.as<int32_t>(), offs.as<int32_t>(), 256 * nt, stmp.p, s));
+                    rs_scatter_kernel<<<(unsigned)nt, RS_BLOCK, 0, s>>>(ki, vi, m, shift, offs.as<int32_t>(), nt, ko, vo);
+                    std::swap(ki, ko);
+                    std::swap(vi, vo);
+                }
+                bfs_order_place_kernel<<<grid_for(m), 256, 0, s>>>(vi, m, lo, P->perm.as<int32_t>(), P->iperm.as<int32_t>());
+            }
+            MPK_CUDA(cudaGetLastError());
+        }
     }
     rpT.release();
     ciT.release();
@@ -1286,7 +1407,8 @@ static mpk_status plan_create_impl(const mpk_csr *A, int32_t p_max, const mpk_pl
         P->lanes = o.lanes_per_row;
     else return MPK_ERR_ARG;
     if (o.task_units < 0 || o.kernel < 0 || o.kernel > 6 || o.task_dispatch < 0 || o.task_dispatch > 2 ||
-        o.owner_lag < 0 || o.owner_lag > 4 || o.owner_prefetch < 0 || o.owner_prefetch > 4)
+        o.owner_lag < 0 || o.owner_lag > 4 || o.owner_prefetch < 0 || o.owner_prefetch > 4 ||
+        o.level_order < 0 || o.level_order > 1)
         return MPK_ERR_ARG;
     P->lane_kernel = (o.kernel == 4 || o.kernel == 5 || o.kernel == 6 || P->lanes > 1) ? 1 : 0;
     P->lane_slack = o.slack_tasks > 0 ? o.slack_tasks : 0;

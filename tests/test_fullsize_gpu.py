@@ -100,13 +100,16 @@ def test_headline_27pt_160_sampled(m, s27_160, prec):
     theta = mi.leja_points_interval(0.0, 52.0, 8)
     Aref = mi.CSR(A.row_ptr, A.col, vals)
     if prec == "f64":
-        # levels: closed form from the root's grid point, stable (level, index) order
+        # levels: closed form from the root's grid point; the rows inside a level in the
+        # oracle's breadth-first order (the plan's default)
         P = m.mpk_plan_perm(plan)
         lev = P["level"].cpu().numpy()
         assert np.array_equal(lev, _chebyshev_dist_levels(160, st["root"]))
         assert st["n_levels"] == int(lev.max()) + 1
         perm = P["perm"].cpu().numpy()
-        assert np.array_equal(perm, np.lexsort((np.arange(n), lev)).astype(np.int32))
+        operm, _, olp = oracle.level_perm_bfs(A, lev, st["n_levels"])
+        assert np.array_equal(perm, operm)
+        assert np.array_equal(P["level_ptr"].cpu().numpy(), olp)
     lp = None
     for p in (2, 4, 8):
         cf = sstep.newton_coeffs(theta[:p])
@@ -149,9 +152,14 @@ def test_diffusion256_levels_mpk_and_solves(m, diff256):
     ci_, cj, ck = np.unravel_index(cell, (N, N, N))
     r0 = np.unravel_index(cell[st["root"]], (N, N, N))
     want = np.abs(ci_ - r0[0]) + np.abs(cj - r0[1]) + np.abs(ck - r0[2])
-    lev = m.mpk_plan_perm(plan)["level"].cpu().numpy()
+    P = m.mpk_plan_perm(plan)
+    lev = P["level"].cpu().numpy()
     assert np.array_equal(lev, want)
     assert st["n_levels"] == int(want.max()) + 1
+    # the breadth-first order inside the levels (766 of them, one device sort each)
+    operm, _, _ = oracle.level_perm_bfs(A, lev, st["n_levels"])
+    assert np.array_equal(P["perm"].cpu().numpy(), operm)
+    del P
     # FP32 MPK (the solver's basis precision) at sampled rows
     p = 8
     th = mi.leja_points_interval(0.0, 4.0 * float(np.abs(A.val).max()), p)

@@ -45,7 +45,8 @@ def _check_plan(m, A, opts, p_blk, val_bytes=8):
     plan = m.mpk_plan_create(rp, ci, vv, p_blk, opts)
     st = m.mpk_plan_stats(plan)
     lev, root, nl, perm, iperm, lp = oracle.level_structure(A, root_rule=opts.root_rule,
-                                                            n_sweeps=opts.n_sweeps)
+                                                            n_sweeps=opts.n_sweeps,
+                                                            level_order=opts.level_order)
     P = m.mpk_plan_perm(plan)
     torch.cuda.synchronize()
     assert st["root"] == root and st["n_levels"] == nl
@@ -65,11 +66,36 @@ def _check_plan(m, A, opts, p_blk, val_bytes=8):
 
 @pytest.mark.parametrize("name", sorted(MATS))
 @pytest.mark.parametrize("root_rule", [0, 1])
-def test_plan_bit_exact(m, name, root_rule):
+@pytest.mark.parametrize("level_order", [0, 1])
+def test_plan_bit_exact(m, name, root_rule, level_order):
     A = MATS[name]
     for budget in (20_000, 400_000, 1 << 30):
-        opts = m.mpk_plan_opts_default(l2_budget_bytes=budget, root_rule=root_rule)
+        opts = m.mpk_plan_opts_default(l2_budget_bytes=budget, root_rule=root_rule, level_order=level_order)
         _check_plan(m, A, opts, 4)
+
+
+def test_breadth_first_order_large_levels(m):
+    """Both sorting paths of the breadth-first order: the randomly permuted log-normal
+    diffusion matrix at 48^3 (levels up to about 1700 rows: one-block sorts) and a randomly
+    permuted 27-point 48^3 stencil (corner shells up to 6900 rows: radix passes), against the
+    oracle's breadth-first order bit for bit; then an MPK on that plan, blocked against
+    unblocked and within the oracle's tolerance."""
+    import torch
+    s27 = mi.stencil27(48, seed=3)
+    for A in (mi.diffusion7_lognormal(48),
+              mi.symmetric_permute(s27, np.random.default_rng(11).permutation(s27.n))):
+        opts = m.mpk_plan_opts_default(level_order=1, assume_symmetric=1, blocked=1)
+        plan = _check_plan(m, A, opts, 4)
+        cf = BASES["newton"](4)
+        x = mi.uniform_vectors(A.n, 2)[0]
+        got = _run(m, plan, A, cf, x)
+        assert np.array_equal(got, _run(m, plan, A, cf, x, flags=m.MPK_UNBLOCKED))
+        ref = oracle.mpk(A, 4, cf, x)
+        den = abs_powers(A, cf, x)
+        for k in range(1, 5):
+            assert max_rel_err(got[k], ref[k], den[k]) <= 64 * k * U64
+        del plan
+        torch.cuda.empty_cache()
 
 
 def test_plan_edge_cases(m):
