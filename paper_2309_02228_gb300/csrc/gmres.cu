@@ -18,6 +18,9 @@
 // all small dense work (Gram reductions, Cholesky, Hessenberg, Givens, least squares, Ritz
 // values) is FP64 on one CTA.  Every reduction has a fixed order: results do not depend on
 // scheduling.
+#include <cuda.h>
+#include <mutex>
+#include <set>
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -314,6 +317,484 @@ __global__ void __launch_bounds__(256) update_kernel(const T *Q, int64_t ldq, in
         // symmetric S x S, column-major: G[b + c*S]
         gpart[(int64_t)blockIdx.x * S * S + b + c * S] = b >= c ? red[b * S + c] : red[c * S + b];
     }
+}
+
+// ------------------------------------------------------------------------------------------
+// Staged streaming for the tall-skinny products: row blocks of R rows (R <= 256) of every
+// column are copied into a ring of shared-memory stages by the tensor memory accelerator, one
+// 2-D tensor copy (cp.async.bulk.tensor.2d) per box of R rows x 8 columns, completion on the
+// stage's mbarrier.  Each SM keeps several blocks of every column in flight whatever the
+// register tiling of the arithmetic.  (One 1-D bulk copy per column chunk instead measured
+// 0.9-1.9 TB/s, scaling with the copy's size; 2-D boxes of 8 columns stream at about 7 TB/s.)
+// The tensor maps cover n rows: rows past n and columns past the block are filled with zeros,
+// so they add nothing.  Every wait is bounded; a CTA whose copy does not land within the bound
+// sets *err, waits (bounded) for its other copies in flight, and writes NaN partial sums.
+// ------------------------------------------------------------------------------------------
+constexpr int ST_MAXST = 8;                     // stages per CTA at most
+constexpr int ST_BOXC = 8;                      // columns per tensor box
+constexpr uint64_t ST_WAIT_NS = 2000000000ull;  // bound of one stage wait (2 s)
+
+__device__ __forceinline__ void st_mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void st_mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"((uint32_t)__cvta_generic_to_shared(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool st_mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok) : "r"((uint32_t)__cvta_generic_to_shared(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+// box of the tensor map at (row x, column y) into shared memory (x a multiple of R >= 32, so
+// x * sizeof(T) is a multiple of 16 bytes)
+__device__ __forceinline__ void st_tma2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+                 ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(map), "r"(x), "r"(y),
+                   "r"((uint32_t)__cvta_generic_to_shared(bar)) : "memory");
+}
+__device__ __forceinline__ uint64_t st_now_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// true when the phase with this parity has completed; false after the time bound
+__device__ __forceinline__ bool st_wait(uint64_t *bar, uint32_t parity) {
+    if (st_mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = st_now_ns();
+    while (!st_mbar_try_wait(bar, parity)) {
+        if (st_now_ns() - t0 > ST_WAIT_NS) return false;
+        __nanosleep(64);
+    }
+    return true;
+}
+
+// The ring of one CTA: blocks b = blockIdx.x + i * gridDim.x (i = 0 .. nmine - 1) of R rows;
+// block i lands in stage i % nst, which holds the first map's KP columns, then the second's.
+struct StageRing {
+    unsigned char *base;
+    uint64_t *full;
+    int KP, NCP, R, nst;   // KP, NCP: padded to whole boxes
+    int64_t n, nmine;
+    template <typename T> __device__ __forceinline__ T *col(int st, int c) const {
+        return reinterpret_cast<T *>(base) + ((int64_t)st * NCP + c) * R;
+    }
+    __device__ __forceinline__ int64_t row0(int64_t i) const { return ((int64_t)blockIdx.x + i * gridDim.x) * R; }
+    // one thread: the copies of this CTA's block i (the second map may be absent: KP == NCP)
+    template <typename T> __device__ __forceinline__ void issue(int64_t i, const CUtensorMap *m1, const CUtensorMap *m2) const {
+        const int st = (int)(i % nst);
+        const int x = (int)row0(i);
+        st_mbar_expect_tx(&full[st], (uint32_t)((int64_t)NCP * R * sizeof(T)));
+        for (int c = 0; c < KP; c += ST_BOXC) st_tma2d(col<T>(st, c), m1, x, c, &full[st]);
+        for (int c = KP; c < NCP; c += ST_BOXC) st_tma2d(col<T>(st, c), m2, x, c - KP, &full[st]);
+    }
+    // after a timeout: wait (bounded) for the copies still in flight, blocks i0 .. i1 - 1
+    __device__ __forceinline__ void drain(int64_t i0, int64_t i1) const {
+        for (int64_t i = i0; i < i1 && i < nmine; i++) st_wait(&full[i % nst], (uint32_t)((i / nst) & 1));
+    }
+};
+
+// G = X^T Y with staged rows (gram_kernel's register tiles and precision): per stage a lane
+// sums at most R / 32 of its rows in FP32, the lanes' block sums are added by lane_halve and
+// the result goes into FP64 totals in shared memory; CTAs' totals are summed by
+// reduce_partials_kernel.  Bound as gram_kernel's: (40 u32 + m u64) |X|^T |Y| entrywise.
+template <typename T, int SB>
+__global__ void __launch_bounds__(256, 2) gram_stage_kernel(const __grid_constant__ CUtensorMap mx,
+                                                            const __grid_constant__ CUtensorMap my, int K,
+                                                            int S, int64_t n, int R, int nst, double *part,
+                                                            uint32_t *err) {
+    constexpr int ACC = sizeof(T) == 4 ? 64 : 32;
+    constexpr int CT = ACC / SB;
+    extern __shared__ __align__(128) unsigned char gs_dyn[];
+    __shared__ double slot[(MMAX + 1 + SMAX) * SMAX];
+    __shared__ uint64_t full[ST_MAXST];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ntiles = (K + CT - 1) / CT;
+    const bool many = ntiles >= 8;
+    const int rsplit = many ? 1 : 8 / ntiles;
+    const int active = many ? 8 : ntiles * rsplit;
+    const int rpart = many ? 0 : warp / ntiles;
+    StageRing ring;
+    ring.base = gs_dyn;
+    ring.full = full;
+    ring.KP = (K + ST_BOXC - 1) / ST_BOXC * ST_BOXC;
+    ring.NCP = ring.KP + (S + ST_BOXC - 1) / ST_BOXC * ST_BOXC;
+    ring.R = R;
+    ring.nst = nst;
+    ring.n = n;
+    const int64_t nblk = (n + R - 1) / R;
+    ring.nmine = (int64_t)blockIdx.x < nblk ? (nblk - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    for (int e = tid; e < (MMAX + 1 + SMAX) * SMAX; e += 256) slot[e] = 0.0;
+    if (tid < nst) st_mbar_init(&full[tid], 1);
+    __syncthreads();
+    if (tid == 0)
+        for (int64_t i = 0; i < nst && i < ring.nmine; i++) ring.issue<T>(i, &mx, &my);
+    using V2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+    T acc[ACC];
+#pragma unroll
+    for (int e = 0; e < ACC; e++) acc[e] = (T)0;
+    int cnt = 0;                              // rows per lane in acc since the last fold
+    const int rpl = 2 * ((R + 64 * rsplit - 1) / (64 * rsplit));   // rows per lane per stage
+    // the lanes' FP32 sums of tile c0 by lane_halve, into the FP64 totals; acc restarts at 0
+    auto flush = [&](int c0) {
+        const int e0 = lane_halve<T, ACC>(acc, lane);
+#pragma unroll
+        for (int jj = 0; jj < ACC / 32; jj++) {
+            const int a = (e0 + jj) / SB, b = (e0 + jj) % SB;
+            if (c0 + a < K && b < S) slot[((int64_t)rpart * K + c0 + a) * S + b] += (double)acc[jj];
+        }
+#pragma unroll
+        for (int e = 0; e < ACC; e++) acc[e] = (T)0;
+    };
+    bool bad = false;
+    for (int64_t i = 0; i < ring.nmine; i++) {
+        const int st = (int)(i % nst);
+        const bool ok = st_wait(&full[st], (uint32_t)((i / nst) & 1));
+        if (__syncthreads_or(!ok)) {
+            bad = true;
+            if (tid == 0) atomicOr(err, 1u);
+            if (warp == 0) ring.drain(i, i + nst);
+            break;
+        }
+        const int rows = (int)min((int64_t)R, n - ring.row0(i));
+        const int KP = ring.KP;
+        if (warp < active) {
+            for (int tile = many ? warp : warp % ntiles; tile < ntiles; tile += many ? 8 : ntiles) {
+                const int c0 = tile * CT;
+                // a warp that owns one tile keeps its FP32 sums over stages and folds them into
+                // the FP64 totals before a lane would pass 32 rows; a warp with several tiles
+                // folds each tile's sums at the end of its visit
+                if (!many && cnt + rpl > 32) {
+                    flush(c0);
+                    cnt = 0;
+                }
+                const T *xc = ring.col<T>(st, c0);
+                const T *yc = ring.col<T>(st, KP);
+                // lane l takes the row pairs (2 l, 2 l + 1) + 64 rsplit k of its part; rows past
+                // n are zeros (the copy's fill), so a pair may run past the block's last row
+                for (int rr = 2 * (rpart * 32 + lane); rr < rows; rr += 64 * rsplit) {
+                    T x0[CT], x1[CT], y0[SB], y1[SB];
+#pragma unroll
+                    for (int a = 0; a < CT; a++) {
+                        V2 v = c0 + a < K ? *reinterpret_cast<const V2 *>(xc + a * R + rr) : V2{(T)0, (T)0};
+                        x0[a] = v.x;
+                        x1[a] = v.y;
+                    }
+#pragma unroll
+                    for (int b = 0; b < SB; b++) {
+                        V2 v = b < S ? *reinterpret_cast<const V2 *>(yc + b * R + rr) : V2{(T)0, (T)0};
+                        y0[b] = v.x;
+                        y1[b] = v.y;
+                    }
+#pragma unroll
+                    for (int a = 0; a < CT; a++)
+#pragma unroll
+                        for (int b = 0; b < SB; b++) {
+                            acc[a * SB + b] = fma(x0[a], y0[b], acc[a * SB + b]);
+                            acc[a * SB + b] = fma(x1[a], y1[b], acc[a * SB + b]);
+                        }
+                }
+                if (many) flush(c0);
+                else cnt += rpl;
+            }
+        }
+        __syncthreads();   // every warp is done with stage st: refill it
+        if (tid == 0 && i + nst < ring.nmine) ring.issue<T>(i + nst, &mx, &my);
+    }
+    // the last fold of a warp's single tile
+    if (warp < active && !many && cnt > 0) flush((warp % ntiles) * CT);
+    __syncthreads();
+    const int KS = K * S;
+    for (int e = tid; e < KS; e += 256) {
+        const int a = e % K, b = e / K;
+        double t = 0.0;
+        for (int ph = 0; ph < rsplit; ph++) t += slot[((int64_t)ph * K + a) * S + b];
+        part[(int64_t)blockIdx.x * KS + e] = bad ? __longlong_as_double(0x7ff8000000000000ll) : t;
+    }
+}
+
+// SB values of a 16-byte aligned shared-memory row in 16-byte loads
+template <typename T, int SB> __device__ __forceinline__ void vec_row(const T *p, T (&o)[SB]) {
+    if constexpr (sizeof(T) == 4 && SB % 4 == 0) {
+#pragma unroll
+        for (int v = 0; v < SB / 4; v++) {
+            const float4 t = reinterpret_cast<const float4 *>(p)[v];
+            o[4 * v] = t.x;
+            o[4 * v + 1] = t.y;
+            o[4 * v + 2] = t.z;
+            o[4 * v + 3] = t.w;
+        }
+    } else if constexpr (sizeof(T) == 8 && SB % 2 == 0) {
+#pragma unroll
+        for (int v = 0; v < SB / 2; v++) {
+            const double2 t = reinterpret_cast<const double2 *>(p)[v];
+            o[2 * v] = t.x;
+            o[2 * v + 1] = t.y;
+        }
+    } else {
+#pragma unroll
+        for (int b = 0; b < SB; b++) o[b] = p[b];
+    }
+}
+
+// W <- (W - Q C) Rinv with Q and W staged (update_kernel's arithmetic, row by row: the same
+// FMAs in the same order), the new W stored straight from registers, and (S <= 8) the Gram of
+// the new W: per lane FP32 sums over at most 32 of its rows, a five-level butterfly, FP64 per
+// warp, the warps and CTAs in FP64 in a fixed order - update_kernel's bound.
+template <typename T, int SB>
+__global__ void __launch_bounds__(256, 2) update_stage_kernel(const __grid_constant__ CUtensorMap mq,
+                                                              const __grid_constant__ CUtensorMap mw, int K1, T *W,
+                                                              int64_t ldw, int S, const double *C, const double *Rinv,
+                                                              int64_t n, int R, int nst, double *gpart, uint32_t *err) {
+    constexpr bool FUSE = SB <= 8;
+    constexpr int NG = FUSE ? SB * (SB + 1) / 2 : 1;
+    extern __shared__ __align__(128) unsigned char us_dyn[];
+    __shared__ __align__(16) T cs[MMAX + 1][SB];
+    __shared__ __align__(16) T ri[SB][SB];
+    __shared__ double red[SB * SB];
+    __shared__ double wred[8][NG];
+    __shared__ uint64_t full[ST_MAXST];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int e = tid; e < K1 * S; e += 256) cs[e % K1][e / K1] = (T)C[e];
+    for (int e = tid; e < SB * SB; e += 256) ri[e % SB][e / SB] = (T)0;
+    __syncthreads();
+    for (int e = tid; e < S * S; e += 256) ri[e % S][e / S] = (T)Rinv[e];
+    for (int e = tid; e < SB * SB; e += 256) red[e] = 0.0;
+    for (int e = tid; e < 8 * NG; e += 256) wred[e / NG][e % NG] = 0.0;
+    StageRing ring;
+    ring.base = us_dyn;
+    ring.full = full;
+    ring.KP = (K1 + ST_BOXC - 1) / ST_BOXC * ST_BOXC;
+    ring.NCP = ring.KP + (S + ST_BOXC - 1) / ST_BOXC * ST_BOXC;
+    ring.R = R;
+    ring.nst = nst;
+    ring.n = n;
+    const int64_t nblk = (n + R - 1) / R;
+    ring.nmine = (int64_t)blockIdx.x < nblk ? (nblk - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int KP = ring.KP;
+    if (tid < nst) st_mbar_init(&full[tid], 1);
+    __syncthreads();
+    if (tid == 0)
+        for (int64_t i = 0; i < nst && i < ring.nmine; i++) ring.issue<T>(i, &mq, &mw);
+    const bool gram = FUSE && gpart != nullptr;
+    T g2[NG];
+#pragma unroll
+    for (int e = 0; e < NG; e++) g2[e] = (T)0;
+    auto flush = [&]() {
+#pragma unroll
+        for (int e = 0; e < NG; e++) {
+            T v = g2[e];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == (e & 31)) wred[warp][e] += (double)v;
+            g2[e] = (T)0;
+        }
+    };
+    int since = 0;          // rows this thread has summed into g2 since the last flush
+    bool bad = false;
+    for (int64_t i = 0; i < ring.nmine; i++) {
+        const int st = (int)(i % nst);
+        const bool ok = st_wait(&full[st], (uint32_t)((i / nst) & 1));
+        if (__syncthreads_or(!ok)) {
+            bad = true;
+            if (tid == 0) atomicOr(err, 1u);
+            if (warp == 0) ring.drain(i, i + nst);
+            break;
+        }
+        const int64_t r0 = ring.row0(i);
+        const int rows = (int)min((int64_t)R, n - r0);
+        // rows rr = tid, tid + 256, ... of the block; warp-uniform trip count (the flush needs
+        // every lane), rows past the block's end skipped
+        for (int rb = 0; rb < R; rb += 256) {
+            const int rr = rb + tid;
+            if (rr < rows) {
+                T w[SB];
+#pragma unroll
+                for (int b = 0; b < SB; b++) w[b] = b < S ? ring.col<T>(st, KP + b)[rr] : (T)0;
+                // the coefficients of row a of C (and of R^-1) as 16-byte vector loads from
+                // shared memory (one per four FP32 or two FP64 values); the FMAs as in
+                // update_kernel
+                for (int a = 0; a < K1; a++) {
+                    const T q = ring.col<T>(st, a)[rr];
+                    T cr[SB];
+                    vec_row<T, SB>(&cs[a][0], cr);
+#pragma unroll
+                    for (int b = 0; b < SB; b++)
+                        if (b < S) w[b] = fma(-q, cr[b], w[b]);
+                }
+                T wn[SB];
+#pragma unroll
+                for (int b = 0; b < SB; b++) wn[b] = (T)0;
+#pragma unroll
+                for (int c = 0; c < SB; c++) {
+                    T rr_[SB];
+                    vec_row<T, SB>(&ri[c][0], rr_);
+#pragma unroll
+                    for (int b = 0; b < SB; b++)
+                        if (c <= b && b < S) wn[b] = fma(w[c], rr_[b], wn[b]);
+                }
+#pragma unroll
+                for (int b = 0; b < SB; b++)
+                    if (b < S) W[(int64_t)b * ldw + r0 + rr] = wn[b];
+                if (gram) {
+                    int e = 0;
+#pragma unroll
+                    for (int b = 0; b < SB; b++)
+#pragma unroll
+                        for (int c = 0; c <= b; c++) {
+                            if (b < S && e < NG) g2[e] = fma(wn[b], wn[c], g2[e]);
+                            e++;
+                        }
+                }
+            }
+            if (gram && ++since == 32) {
+                flush();
+                since = 0;
+            }
+        }
+        __syncthreads();   // every row of stage st is done: refill it
+        if (tid == 0 && i + nst < ring.nmine) ring.issue<T>(i + nst, &mq, &mw);
+    }
+    if (!gram) return;
+    flush();
+    __syncthreads();
+    for (int e = tid; e < NG; e += 256) {
+        double t = 0.0;
+        for (int w = 0; w < 8; w++) t += wred[w][e];
+        int b = 0, c = e;
+        while (c > b) { c -= b + 1; b++; }
+        if (b < S) red[b * S + c] = t;
+    }
+    __syncthreads();
+    for (int e = tid; e < S * S; e += 256) {
+        const int b = e / S, c = e % S;
+        const double v = b >= c ? red[b * S + c] : red[c * S + b];
+        gpart[(int64_t)blockIdx.x * S * S + b + c * S] = bad ? __longlong_as_double(0x7ff8000000000000ll) : v;
+    }
+}
+
+// Host side of the staged kernels.  Tensor maps are encoded with the driver's
+// cuTensorMapEncodeTiled, reached through the runtime (no link against the driver library);
+// without it the callers run the register-streaming kernels.  R rows per stage and the ring
+// depth come from the shared-memory budget: the largest R (at most 256, a box's limit) that
+// leaves three stages, else two.
+constexpr size_t ST_BUDGET = 96 * 1024;   // per CTA: two CTAs share an SM
+
+typedef CUresult (*TmapEncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static TmapEncodeFn tmap_encoder() {
+    static TmapEncodeFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<TmapEncodeFn>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// 2-D map of `cols` columns of n rows, column stride ld elements, boxes of R rows x ST_BOXC
+// columns; false when the columns do not meet the copy engine's alignment (16-byte base and
+// stride) or no encoder is available
+template <typename T> static bool make_tmap(CUtensorMap *m, const T *base, int64_t ld, int64_t n, int cols, int R) {
+    TmapEncodeFn enc = tmap_encoder();
+    if (!enc || !base || cols < 1 || n < 1 || ld < n || n >= (1ll << 31)) return false;
+    if ((uintptr_t)base % 16 != 0 || ((int64_t)ld * (int64_t)sizeof(T)) % 16 != 0) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)cols};
+    cuuint64_t strides[1] = {(cuuint64_t)(ld * (int64_t)sizeof(T))};
+    cuuint32_t box[2] = {(cuuint32_t)R, (cuuint32_t)ST_BOXC};
+    cuuint32_t es[2] = {1, 1};
+    return enc(m, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2,
+               const_cast<T *>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The staged kernels' dynamic shared-memory limit, raised to the whole stage budget once per
+// (kernel, device): setting it per launch raced between host threads that launch the same
+// kernel with different stage sizes (the server runs one solve per thread).
+static std::mutex g_smem_attr_mu;
+static std::set<std::pair<const void *, int>> g_smem_attr_done;
+template <typename F> static mpk_status ensure_stage_smem(F kern) {
+    int dev = 0;
+    MPK_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_smem_attr_mu);
+    const auto key = std::make_pair(reinterpret_cast<const void *>(kern), dev);
+    if (g_smem_attr_done.count(key)) return MPK_OK;
+    MPK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ST_BUDGET));
+    g_smem_attr_done.insert(key);
+    return MPK_OK;
+}
+
+static bool stage_choice(int NCP, size_t es, int *R, int *nst) {
+    static const int rs[4] = {256, 128, 64, 32};
+    for (int q = 3; q >= 2; q--)
+        for (int r : rs)
+            if ((size_t)NCP * r * es * q <= ST_BUDGET) {
+                *R = r;
+                *nst = q;
+                return true;
+            }
+    return false;
+}
+static inline int box_pad(int c) { return (c + ST_BOXC - 1) / ST_BOXC * ST_BOXC; }
+
+// G partials (grid x K x S, part) of X^T Y by the staged kernel on at most max_grid CTAs (one
+// per SM); MPK_ERR_UNIMPLEMENTED when the columns or sizes do not allow it.
+template <typename T>
+static mpk_status gram_stage_launch(const T *X, int64_t ldx, int K, const T *Y, int64_t ldy, int S, int64_t n,
+                                    int nsm, int max_grid, double *part, uint32_t *err, int *grid, cudaStream_t s) {
+    int R = 0, nst = 0;
+    // FP32 bases only: an FP64 Gram is bound by the FP64 pipe however its rows arrive
+    if (sizeof(T) != 4 || n <= 0 || K < 1 || S < 1 || S > SMAX || K > MMAX + 1 + SMAX ||
+        !stage_choice(box_pad(K) + box_pad(S), sizeof(T), &R, &nst))
+        return MPK_ERR_UNIMPLEMENTED;
+    CUtensorMap mx, my;
+    if (!make_tmap<T>(&mx, X, ldx, n, K, R) || !make_tmap<T>(&my, Y, ldy, n, S, R)) return MPK_ERR_UNIMPLEMENTED;
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(std::min(2 * nsm, max_grid), ceil_div(n, R)));
+    const size_t dsm = (size_t)(box_pad(K) + box_pad(S)) * R * sizeof(T) * nst;
+    auto kern = S <= 4 ? gram_stage_kernel<T, 4> : (S <= 8 ? gram_stage_kernel<T, 8> : gram_stage_kernel<T, 16>);
+    MPK_TRY(ensure_stage_smem(kern));
+    kern<<<g, 256, dsm, s>>>(mx, my, K, S, n, R, nst, part, err);
+    MPK_CUDA(cudaGetLastError());
+    *grid = g;
+    return MPK_OK;
+}
+
+// W <- (W - Q C) Rinv (and the S x S Gram partials of the new W in gpart when S <= 8 and gpart
+// is given) by the staged kernel; MPK_ERR_UNIMPLEMENTED when not applicable.
+template <typename T>
+static mpk_status update_stage_launch(const T *Q, int64_t ldq, int K1, T *W, int64_t ldw, int S, const double *C,
+                                      const double *Rinv, int64_t n, int nsm, int max_grid, double *gpart,
+                                      uint32_t *err, int *grid, cudaStream_t s) {
+    int R = 0, nst = 0;
+    // FP32 bases with basis columns to subtract (the normalisation W R^-1 alone, K1 = 0,
+    // measured 7 % faster with the register-streaming kernel)
+    if (sizeof(T) != 4 || n <= 0 || S < 1 || S > SMAX || K1 < 1 || K1 > MMAX + 1 ||
+        !stage_choice(box_pad(K1) + box_pad(S), sizeof(T), &R, &nst))
+        return MPK_ERR_UNIMPLEMENTED;
+    CUtensorMap mq, mw;
+    if (!make_tmap<T>(&mw, W, ldw, n, S, R)) return MPK_ERR_UNIMPLEMENTED;
+    if (K1 > 0) {
+        if (!make_tmap<T>(&mq, Q, ldq, n, K1, R)) return MPK_ERR_UNIMPLEMENTED;
+    } else {
+        mq = mw;   // not read: no Q columns
+    }
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(std::min(2 * nsm, max_grid), ceil_div(n, R)));
+    const size_t dsm = (size_t)(box_pad(K1) + box_pad(S)) * R * sizeof(T) * nst;
+    auto kern = S <= 4 ? update_stage_kernel<T, 4> : (S <= 8 ? update_stage_kernel<T, 8> : update_stage_kernel<T, 16>);
+    MPK_TRY(ensure_stage_smem(kern));
+    kern<<<g, 256, dsm, s>>>(mq, mw, K1, W, ldw, S, C, Rinv, n, R, nst, S <= 8 ? gpart : nullptr, err);
+    MPK_CUDA(cudaGetLastError());
+    *grid = g;
+    return MPK_OK;
 }
 
 // x[i] += sum_a V[i, a] y[a]  (correction in the basis precision, added to FP64 x); with
@@ -642,6 +1123,7 @@ struct Solver {
     mpk_gmres_opts o;
     int64_t n, ldv;
     DevBuf V, part, G, gpart2, cstate, vec;   // vec: b, x, r, norms (FP64)
+    DevBuf serr;                               // latched by a staged kernel whose copy timed out
     DevBuf dth;                                // Newton shifts of the current cycle
     DevBuf ptmp;                               // polynomial preconditioner: 2 vectors of T
     DevBuf ptmp64;                             // and 2 FP64 vectors (FP64 polynomial)
@@ -693,6 +1175,8 @@ struct Solver {
         MPK_TRY(part.alloc_on((size_t)std::max(gram_grid, upd_grid) * maxK * SMAX * sizeof(double) + 4096, st));
         MPK_TRY(G.alloc_on((size_t)maxK * SMAX * sizeof(double) + 64, st));
         MPK_TRY(gpart2.alloc_on((size_t)upd_grid * SMAX * SMAX * sizeof(double) + 64, st));
+        MPK_TRY(serr.alloc_on(64, st));
+        MPK_CUDA(cudaMemsetAsync(serr.p, 0, 64, st));
         MPK_TRY(cstate.alloc_on(sizeof(CycleState), st));
         MPK_TRY(dth.alloc_on(SMAX * sizeof(double), st));
         if (uses_poly() || o.gs2) MPK_TRY(ptmp.alloc_on((size_t)2 * ldv * sizeof(T), st));
@@ -726,8 +1210,17 @@ struct Solver {
     // G (K x S) = X^T Y
     template <int SB> mpk_status gram_sb(const T *X, int K, const T *Y, int S, double *Gout) {
         if (K > MMAX + 1 + SMAX || S > SB) return MPK_ERR_ARG;
-        const int g = (int)std::min<int64_t>(gram_grid, ceil_div(n, GRAM_RANGE));
-        gram_kernel<T, SB><<<g, 256, 0, st>>>(X, ldv, K, Y, ldv, S, n, part.as<double>());
+        // the basis columns are 128-byte aligned with ldv >= n rounded up to 32 rows, so the
+        // staged kernel applies whenever its stages fit in shared memory
+        int g = 0;
+        const mpk_status sk = gram_stage_launch<T>(X, ldv, K, Y, ldv, S, n, P->n_sm, gram_grid, part.as<double>(),
+                                                   serr.as<uint32_t>(), &g, st);
+        if (sk == MPK_ERR_UNIMPLEMENTED) {
+            g = (int)std::min<int64_t>(gram_grid, ceil_div(n, GRAM_RANGE));
+            gram_kernel<T, SB><<<g, 256, 0, st>>>(X, ldv, K, Y, ldv, S, n, part.as<double>());
+        } else {
+            MPK_TRY(sk);
+        }
         reduce_partials_kernel<<<redp_grid(K * S), 32 * REDP_WARPS, 0, st>>>(part.as<double>(), g, K * S, (int64_t)K * S, Gout, 0);
         MPK_CUDA(cudaGetLastError());
         return MPK_OK;
@@ -737,11 +1230,20 @@ struct Solver {
         if (S <= 8) return gram_sb<8>(X, K, Y, S, Gout);
         return gram_sb<16>(X, K, Y, S, Gout);
     }
-    mpk_status update(const T *Q, int K1, T *W, int S, const double *C, const double *Ri, double *gp) {
-        const int ug = (int)std::min<int64_t>(upd_grid, ceil_div(n, 256));
-        if (S <= 4) update_kernel<T, 4><<<ug, 256, 0, st>>>(Q, ldv, K1, W, ldv, S, C, Ri, n, gp);
-        else if (S <= 8) update_kernel<T, 8><<<ug, 256, 0, st>>>(Q, ldv, K1, W, ldv, S, C, Ri, n, gp);
-        else update_kernel<T, 16><<<ug, 256, 0, st>>>(Q, ldv, K1, W, ldv, S, C, Ri, n, gp);
+    // *grid: the CTAs whose Gram partials gp holds
+    mpk_status update(const T *Q, int K1, T *W, int S, const double *C, const double *Ri, double *gp, int *grid = nullptr) {
+        int ug = 0;
+        const mpk_status sk = update_stage_launch<T>(Q, ldv, K1, W, ldv, S, C, Ri, n, P->n_sm, upd_grid, gp,
+                                                     serr.as<uint32_t>(), &ug, st);
+        if (sk == MPK_ERR_UNIMPLEMENTED) {
+            ug = (int)std::min<int64_t>(upd_grid, ceil_div(n, 256));
+            if (S <= 4) update_kernel<T, 4><<<ug, 256, 0, st>>>(Q, ldv, K1, W, ldv, S, C, Ri, n, gp);
+            else if (S <= 8) update_kernel<T, 8><<<ug, 256, 0, st>>>(Q, ldv, K1, W, ldv, S, C, Ri, n, gp);
+            else update_kernel<T, 16><<<ug, 256, 0, st>>>(Q, ldv, K1, W, ldv, S, C, Ri, n, gp);
+        } else {
+            MPK_TRY(sk);
+        }
+        if (grid) *grid = ug;
         MPK_CUDA(cudaGetLastError());
         return MPK_OK;
     }
@@ -754,10 +1256,10 @@ struct Solver {
         const int K1 = j + 1;
         T *Q = col(0), *W = col(j + 1);
         double *Gd = G.as<double>();
-        const int ug = (int)std::min<int64_t>(upd_grid, ceil_div(n, 256));
         auto update_gram = [&](int k1, const double *C) -> mpk_status {
             if (S <= 8) {
-                MPK_TRY(update(Q, k1, W, S, C, cst->Rinv, gpart2.as<double>()));
+                int ug = 0;
+                MPK_TRY(update(Q, k1, W, S, C, cst->Rinv, gpart2.as<double>(), &ug));
                 reduce_partials_kernel<<<redp_grid(S * S), 32 * REDP_WARPS, 0, st>>>(gpart2.as<double>(), ug, S * S, (int64_t)S * S, Gd, 0);
             } else {
                 MPK_TRY(update(Q, k1, W, S, C, cst->Rinv, nullptr));
@@ -1898,10 +2400,17 @@ mpk_status gram_launch(const T *X, int64_t ldx, int K, const T *Y, int64_t ldy, 
                        cudaStream_t s) {
     int nsm = 1;
     MPK_TRY(sm_count(&nsm));
-    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(8 * nsm, ceil_div(n, GRAM_RANGE)));
-    DevBuf part;
-    MPK_TRY(part.alloc_on((size_t)g * K * S * sizeof(double), s));
-    if (S <= 4) gram_kernel<T, 4><<<g, 256, 0, s>>>(X, ldx, K, Y, ldy, S, n, part.as<double>());
+    int g = (int)std::max<int64_t>(1, std::min<int64_t>(8 * nsm, ceil_div(n, GRAM_RANGE)));
+    DevBuf part, err;
+    MPK_TRY(part.alloc_on((size_t)std::max(g, 2 * nsm) * K * S * sizeof(double), s));
+    MPK_TRY(err.alloc_on(64, s));
+    MPK_CUDA(cudaMemsetAsync(err.p, 0, 64, s));
+    // staged (copy-engine ring) when the columns allow it, else register-streaming tiles
+    const mpk_status sk = gram_stage_launch<T>(X, ldx, K, Y, ldy, S, n, nsm, 2 * nsm, part.as<double>(),
+                                               err.as<uint32_t>(), &g, s);
+    if (sk != MPK_ERR_UNIMPLEMENTED) {
+        MPK_TRY(sk);
+    } else if (S <= 4) gram_kernel<T, 4><<<g, 256, 0, s>>>(X, ldx, K, Y, ldy, S, n, part.as<double>());
     else if (S <= 8) gram_kernel<T, 8><<<g, 256, 0, s>>>(X, ldx, K, Y, ldy, S, n, part.as<double>());
     else gram_kernel<T, 16><<<g, 256, 0, s>>>(X, ldx, K, Y, ldy, S, n, part.as<double>());
     reduce_partials_kernel<<<redp_grid(K * S), 32 * REDP_WARPS, 0, s>>>(part.as<double>(), g, K * S, (int64_t)K * S, G, 0);
@@ -1914,12 +2423,18 @@ mpk_status update_launch(const T *Q, int64_t ldq, int K1, T *W, int64_t ldw, int
                          const double *Rinv, int64_t n, double *G, cudaStream_t s) {
     int nsm = 1;
     MPK_TRY(sm_count(&nsm));
-    const int ug = (int)std::max<int64_t>(1, std::min<int64_t>(4 * nsm, ceil_div(n, 256)));
+    int ug = (int)std::max<int64_t>(1, std::min<int64_t>(4 * nsm, ceil_div(n, 256)));
     const bool fused = G && S <= 8;
-    DevBuf gp;
-    if (fused) MPK_TRY(gp.alloc_on((size_t)ug * S * S * sizeof(double), s));
+    DevBuf gp, err;
+    if (fused) MPK_TRY(gp.alloc_on((size_t)std::max(ug, 2 * nsm) * S * S * sizeof(double), s));
+    MPK_TRY(err.alloc_on(64, s));
+    MPK_CUDA(cudaMemsetAsync(err.p, 0, 64, s));
     double *gpp = fused ? gp.as<double>() : nullptr;
-    if (S <= 4) update_kernel<T, 4><<<ug, 256, 0, s>>>(Q, ldq, K1, W, ldw, S, C, Rinv, n, gpp);
+    const mpk_status sk = update_stage_launch<T>(Q, ldq, K1, W, ldw, S, C, Rinv, n, nsm, 2 * nsm, gpp,
+                                                 err.as<uint32_t>(), &ug, s);
+    if (sk != MPK_ERR_UNIMPLEMENTED) {
+        MPK_TRY(sk);
+    } else if (S <= 4) update_kernel<T, 4><<<ug, 256, 0, s>>>(Q, ldq, K1, W, ldw, S, C, Rinv, n, gpp);
     else if (S <= 8) update_kernel<T, 8><<<ug, 256, 0, s>>>(Q, ldq, K1, W, ldw, S, C, Rinv, n, gpp);
     else update_kernel<T, 16><<<ug, 256, 0, s>>>(Q, ldq, K1, W, ldw, S, C, Rinv, n, nullptr);
     MPK_CUDA(cudaGetLastError());
