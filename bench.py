@@ -416,6 +416,77 @@ def serving_leg(m, n_req=24, n_min=32, n_max=192, seed=7):
     return out
 
 
+def _gen_request(r):
+    """One request of the solve stream (runs in a worker process): CSR arrays and b."""
+    A = mi.anisotropic(r["N"], r["stencil"], r["a"])
+    return A.row_ptr, A.col, A.val, mi.uniform_vectors(A.n, r["b_seed"] % 100000)[0]
+
+
+def serving_full_leg(m, n_req=2000, n_f64=300, seed=7, workers=15, window=30, max_pending=16):
+    """The solve stream at its stated size: n_req requests (Poisson arrivals at 200/s, grid edge
+    32..192, 7- or 27-point anisotropic diffusion, anisotropy 1..100) under a 120 GB budget,
+    FP32 basis + FP64 refinement; the FP64 basis on the first n_f64 requests.  A request's
+    matrix (up to 2.3 GB of CSR at 192^3, 27-point) is generated by a pool of worker
+    processes a few requests ahead, and the client holds back submissions while max_pending
+    requests wait in the server, so host memory stays bounded; latency is measured from the
+    request's stated arrival time, so time spent waiting on the client counts.  At 200/s the
+    stream offers far more than one GPU serves: solves/s is the saturation throughput over the
+    steady window (completions 10 % .. 90 %), and the latencies grow with the queue.
+    starved_s: time the server held no request while the next one was still being generated
+    (the host generator, not the GPU, limited the stream then)."""
+    import multiprocessing as mp
+    stream = mi.solve_stream(n_req, seed=seed, n_min=32, n_max=192)
+    ctx = mp.get_context("spawn")
+    out = {"workload": "%d requests of the solve stream (seed %d, 200/s Poisson arrivals, grid edge 32..192, "
+                       "7/27-point, anisotropy 1..100), tol 1e-8, 120 GB budget; FP64 basis on the first %d"
+                       % (n_req, seed, n_f64)}
+    with ctx.Pool(workers) as pool:
+        for basis, count in (("f32", n_req), ("f64", min(n_f64, n_req))):
+            o = m.mpk_server_opts_default(hbm_budget_bytes=120 << 30)
+            o.gmres.basis = m.MPK_F32 if basis == "f32" else m.MPK_F64
+            srv = m.Server(o)
+            futs = {}
+            nxt = 0
+            t_start = time.perf_counter()
+            sub, arr, done, ids = {}, {}, {}, []
+            i = 0
+            starved = 0.0
+            t_last = time.perf_counter()
+            while len(done) < count:
+                t_now = time.perf_counter()
+                if i < count and i in futs and srv.pending() == 0 and not futs[i].ready():
+                    starved += t_now - t_last
+                t_last = t_now
+                while nxt < count and len(futs) < window:
+                    futs[nxt] = pool.apply_async(_gen_request, (stream[nxt],))
+                    nxt += 1
+                now = time.perf_counter() - t_start
+                if i < count and stream[i]["t_arrival"] <= now and srv.pending() < max_pending and futs[i].ready():
+                    rp_, col_, val_, b_ = futs.pop(i).get()
+                    rid, _ = srv.submit(rp_, col_, val_, b_)
+                    arr[rid] = t_start + stream[i]["t_arrival"]
+                    sub[rid] = time.perf_counter()
+                    ids.append(rid)
+                    i += 1
+                    continue
+                for res in srv.poll(64):
+                    if res["id"] in sub:
+                        done[res["id"]] = (time.perf_counter(), res)
+                time.sleep(0.0005)
+            srv.close()
+            order = sorted(ids, key=lambda r: done[r][0])
+            lo, hi = int(0.1 * count), max(int(0.9 * count), int(0.1 * count) + 1)
+            win = order[lo:hi]
+            t0w, t1w = done[order[lo - 1]][0] if lo > 0 else t_start, done[order[hi - 1]][0]
+            lat = [1e3 * (done[r][0] - arr[r]) for r in win]
+            out[basis] = {"requests": count, "steady_solves_per_s": len(win) / max(t1w - t0w, 1e-9),
+                          "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                          "total_s": max(d[0] for d in done.values()) - t_start, "starved_s": starved,
+                          "all_converged": all(done[r][1]["status"] == m.MPK_OK for r in ids),
+                          "max_rel_residual": max(done[r][1]["rel_residual"] for r in ids)}
+    return out
+
+
 def batch_leg(m, torch, dev, p=8, reps=10, cases=((256, 8, 32), (64, 16, 48)), seed=7):
     """Batched MPK (mpk_batch_apply): many uneven systems (7- or 27-point anisotropic
     diffusion, anisotropy log-uniform in [1, 100], grid edge uniform in [lo, hi]) in one
@@ -621,6 +692,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--no-solver", action="store_true", help="skip the solver and serving legs")
     ap.add_argument("--no-block", action="store_true", help="skip the n_rhs block MPK leg")
+    ap.add_argument("--serving-full", type=int, default=0,
+                    help="only run the solve stream at this many requests (the stated size is 2000) and "
+                         "print its result")
     ap.add_argument("--profile", action="store_true",
                     help="profiling run: plan, then per repetition one blocked and one unblocked "
                          "call (level-order I/O) on the 27-point matrix of --profile-n")
@@ -677,6 +751,10 @@ def main():
         return 0 if out["f32"]["converged"] else 1
     if args.profile:
         return run_profile(args, m, torch, local)
+    if args.serving_full > 0:
+        out = serving_full_leg(m, n_req=args.serving_full)
+        print(json.dumps({"serving_full": out}))
+        return 0 if out["f32"]["all_converged"] else 1
     A, x, theta = gen_workload()
     dev = torch.device("cuda", local)
     rp = torch.from_numpy(A.row_ptr).to(dev)
@@ -780,6 +858,21 @@ def main():
                            "pxspmv_gbs": p * (M32 + 8 * n) / ku / 1e6}
     assert m.mpk_plan_sync(plan32) == m.MPK_OK
     del plan32
+    # the owner-share kernel (one share of every level group per CTA, the paper's wavefront
+    # schedule): DRAM traffic at the algorithmic minimum at lag 1 and two matrix passes at lag 2
+    # (profiles/owner_kernel_f32_p4_27pt128_dram.md), timed here on the same FP32 call
+    fp32["owner_p4"] = {}
+    for lag in (1, 2):
+        plano = m.mpk_plan_create(rp, ci, vv32, P_MAIN, m.mpk_plan_opts_default(
+            assume_symmetric=1, p_blk=P_MAIN, blocked=1, kernel=6, owner_lag=lag))
+        Yo = torch.empty((P_MAIN + 1) * n, dtype=torch.float32, device=dev)
+        Yo[:n] = X32[m.mpk_plan_perm(plano)["perm"].long()]
+        ko = time_stream(lambda: m.mpk_apply(plano, cfs[P_MAIN], None, Yo, flags=m.MPK_PERMUTED_IO | m.MPK_Y0_IS_X),
+                         reps, torch)
+        assert m.mpk_plan_sync(plano) == m.MPK_OK
+        fp32["owner_p4"]["lag%d" % lag] = {"ms": ko, "gflops": 2.0 * nnz * P_MAIN / ko / 1e6,
+                                           "vs_pxspmv": (2.0 * nnz * P_MAIN / ko / 1e6) / fp32["p4"]["pxspmv_gflops"]}
+        del plano, Yo
 
     # ---- GS2-preconditioned MPK (sub-powers) blocked vs one launch per sub-power
     gs2_mpk = gs2_mpk_leg(m, torch, dev, A, rp, ci, vv, reps=reps)

@@ -394,10 +394,30 @@ struct StageRing {
     }
 };
 
-// G = X^T Y with staged rows (gram_kernel's register tiles and precision): per stage a lane
-// sums at most R / 32 of its rows in FP32, the lanes' block sums are added by lane_halve and
-// the result goes into FP64 totals in shared memory; CTAs' totals are summed by
-// reduce_partials_kernel.  Bound as gram_kernel's: (40 u32 + m u64) |X|^T |Y| entrywise.
+// Wait for the phase with this parity, bounded, and give up early when another warp of the
+// CTA has latched an error in *bad.
+__device__ __forceinline__ bool st_wait_or_bad(uint64_t *bar, uint32_t parity, const volatile int *bad) {
+    if (st_mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = st_now_ns();
+    while (!st_mbar_try_wait(bar, parity)) {
+        if (*bad || st_now_ns() - t0 > ST_WAIT_NS) return false;
+        __nanosleep(64);
+    }
+    return true;
+}
+__device__ __forceinline__ void st_mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"((uint32_t)__cvta_generic_to_shared(bar)) : "memory");
+}
+
+// G = X^T Y with staged rows (gram_kernel's register tiles and precision).  Warp 7 produces:
+// it refills a stage once the stage's "empty" mbarrier shows that every consumer warp has left
+// it.  Warps 0..6 consume, each owning one tile of columns (or several, when there are more
+// tiles than warps), waiting only for their next stage's data - no CTA-wide barrier per stage.
+// A lane sums at most 32 of its rows in FP32 before folding them by lane_halve into FP64 totals
+// in shared memory (a warp with several tiles folds at the end of every tile visit); CTAs'
+// totals are summed by reduce_partials_kernel.  Bound as gram_kernel's: (40 u32 + m u64)
+// |X|^T |Y| entrywise.
+constexpr int GS_CONSUMERS = 7;
 template <typename T, int SB>
 __global__ void __launch_bounds__(256, 2) gram_stage_kernel(const __grid_constant__ CUtensorMap mx,
                                                             const __grid_constant__ CUtensorMap my, int K,
@@ -407,12 +427,13 @@ __global__ void __launch_bounds__(256, 2) gram_stage_kernel(const __grid_constan
     constexpr int CT = ACC / SB;
     extern __shared__ __align__(128) unsigned char gs_dyn[];
     __shared__ double slot[(MMAX + 1 + SMAX) * SMAX];
-    __shared__ uint64_t full[ST_MAXST];
+    __shared__ uint64_t full[ST_MAXST], empty[ST_MAXST];
+    __shared__ int s_bad;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int ntiles = (K + CT - 1) / CT;
-    const bool many = ntiles >= 8;
-    const int rsplit = many ? 1 : 8 / ntiles;
-    const int active = many ? 8 : ntiles * rsplit;
+    const bool many = ntiles >= GS_CONSUMERS;
+    const int rsplit = many ? 1 : GS_CONSUMERS / ntiles;
+    const int active = many ? GS_CONSUMERS : ntiles * rsplit;
     const int rpart = many ? 0 : warp / ntiles;
     StageRing ring;
     ring.base = gs_dyn;
@@ -425,45 +446,61 @@ __global__ void __launch_bounds__(256, 2) gram_stage_kernel(const __grid_constan
     const int64_t nblk = (n + R - 1) / R;
     ring.nmine = (int64_t)blockIdx.x < nblk ? (nblk - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     for (int e = tid; e < (MMAX + 1 + SMAX) * SMAX; e += 256) slot[e] = 0.0;
-    if (tid < nst) st_mbar_init(&full[tid], 1);
+    if (tid < nst) {
+        st_mbar_init(&full[tid], 1);
+        st_mbar_init(&empty[tid], (uint32_t)active);
+    }
+    if (tid == 0) s_bad = 0;
     __syncthreads();
-    if (tid == 0)
-        for (int64_t i = 0; i < nst && i < ring.nmine; i++) ring.issue<T>(i, &mx, &my);
-    using V2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
-    T acc[ACC];
-#pragma unroll
-    for (int e = 0; e < ACC; e++) acc[e] = (T)0;
-    int cnt = 0;                              // rows per lane in acc since the last fold
-    const int rpl = 2 * ((R + 64 * rsplit - 1) / (64 * rsplit));   // rows per lane per stage
-    // the lanes' FP32 sums of tile c0 by lane_halve, into the FP64 totals; acc restarts at 0
-    auto flush = [&](int c0) {
-        const int e0 = lane_halve<T, ACC>(acc, lane);
-#pragma unroll
-        for (int jj = 0; jj < ACC / 32; jj++) {
-            const int a = (e0 + jj) / SB, b = (e0 + jj) % SB;
-            if (c0 + a < K && b < S) slot[((int64_t)rpart * K + c0 + a) * S + b] += (double)acc[jj];
+    const volatile int *vbad = &s_bad;
+    if (warp == GS_CONSUMERS) {
+        // producer: block i into stage i % nst once the consumers released block i - nst
+        if (lane == 0) {
+            int64_t issued = 0;
+            for (int64_t i = 0; i < ring.nmine; i++) {
+                const int st = (int)(i % nst);
+                if (i >= nst && !st_wait_or_bad(&empty[st], (uint32_t)(((i / nst) - 1) & 1), vbad)) {
+                    s_bad = 1;
+                    atomicOr(err, 1u);
+                    break;
+                }
+                ring.issue<T>(i, &mx, &my);
+                issued = i + 1;
+            }
+            if (*vbad) ring.drain(issued > nst ? issued - nst : 0, issued);   // copies still in flight
         }
+    } else if (warp < active) {
+        using V2 = typename std::conditional<sizeof(T) == 4, float2, double2>::type;
+        T acc[ACC];
 #pragma unroll
         for (int e = 0; e < ACC; e++) acc[e] = (T)0;
-    };
-    bool bad = false;
-    for (int64_t i = 0; i < ring.nmine; i++) {
-        const int st = (int)(i % nst);
-        const bool ok = st_wait(&full[st], (uint32_t)((i / nst) & 1));
-        if (__syncthreads_or(!ok)) {
-            bad = true;
-            if (tid == 0) atomicOr(err, 1u);
-            if (warp == 0) ring.drain(i, i + nst);
-            break;
-        }
-        const int rows = (int)min((int64_t)R, n - ring.row0(i));
+        int cnt = 0;                              // rows per lane in acc since the last fold
+        const int rpl = 2 * ((R + 64 * rsplit - 1) / (64 * rsplit));   // rows per lane per stage
+        // the lanes' FP32 sums of tile c0 by lane_halve, into the FP64 totals; acc restarts at 0
+        auto flush = [&](int c0) {
+            const int e0 = lane_halve<T, ACC>(acc, lane);
+#pragma unroll
+            for (int jj = 0; jj < ACC / 32; jj++) {
+                const int a = (e0 + jj) / SB, b = (e0 + jj) % SB;
+                if (c0 + a < K && b < S) slot[((int64_t)rpart * K + c0 + a) * S + b] += (double)acc[jj];
+            }
+#pragma unroll
+            for (int e = 0; e < ACC; e++) acc[e] = (T)0;
+        };
         const int KP = ring.KP;
-        if (warp < active) {
-            for (int tile = many ? warp : warp % ntiles; tile < ntiles; tile += many ? 8 : ntiles) {
+        for (int64_t i = 0; i < ring.nmine; i++) {
+            const int st = (int)(i % nst);
+            const bool ok = st_wait_or_bad(&full[st], (uint32_t)((i / nst) & 1), vbad);
+            if (!__all_sync(0xffffffffu, ok)) {
+                if (lane == 0) {
+                    s_bad = 1;
+                    atomicOr(err, 1u);
+                }
+                break;
+            }
+            const int rows = (int)min((int64_t)R, n - ring.row0(i));
+            for (int tile = many ? warp : warp % ntiles; tile < ntiles; tile += many ? GS_CONSUMERS : ntiles) {
                 const int c0 = tile * CT;
-                // a warp that owns one tile keeps its FP32 sums over stages and folds them into
-                // the FP64 totals before a lane would pass 32 rows; a warp with several tiles
-                // folds each tile's sums at the end of its visit
                 if (!many && cnt + rpl > 32) {
                     flush(c0);
                     cnt = 0;
@@ -497,19 +534,19 @@ __global__ void __launch_bounds__(256, 2) gram_stage_kernel(const __grid_constan
                 if (many) flush(c0);
                 else cnt += rpl;
             }
+            // this warp is done with stage st: one arrival on its empty barrier
+            __syncwarp();
+            if (lane == 0) st_mbar_arrive(&empty[st]);
         }
-        __syncthreads();   // every warp is done with stage st: refill it
-        if (tid == 0 && i + nst < ring.nmine) ring.issue<T>(i + nst, &mx, &my);
+        if (!many && cnt > 0) flush((warp % ntiles) * CT);
     }
-    // the last fold of a warp's single tile
-    if (warp < active && !many && cnt > 0) flush((warp % ntiles) * CT);
     __syncthreads();
     const int KS = K * S;
     for (int e = tid; e < KS; e += 256) {
         const int a = e % K, b = e / K;
         double t = 0.0;
         for (int ph = 0; ph < rsplit; ph++) t += slot[((int64_t)ph * K + a) * S + b];
-        part[(int64_t)blockIdx.x * KS + e] = bad ? __longlong_as_double(0x7ff8000000000000ll) : t;
+        part[(int64_t)blockIdx.x * KS + e] = s_bad ? __longlong_as_double(0x7ff8000000000000ll) : t;
     }
 }
 
@@ -540,7 +577,9 @@ template <typename T, int SB> __device__ __forceinline__ void vec_row(const T *p
 // W <- (W - Q C) Rinv with Q and W staged (update_kernel's arithmetic, row by row: the same
 // FMAs in the same order), the new W stored straight from registers, and (S <= 8) the Gram of
 // the new W: per lane FP32 sums over at most 32 of its rows, a five-level butterfly, FP64 per
-// warp, the warps and CTAs in FP64 in a fixed order - update_kernel's bound.
+// warp, the warps and CTAs in FP64 in a fixed order - update_kernel's bound.  Warp 7 produces
+// (refills a stage once every consumer warp has released it); warps 0..6 take the stage's rows
+// one per thread, the rows past 224 going to a different warp in each stage.
 template <typename T, int SB>
 __global__ void __launch_bounds__(256, 2) update_stage_kernel(const __grid_constant__ CUtensorMap mq,
                                                               const __grid_constant__ CUtensorMap mw, int K1, T *W,
@@ -548,12 +587,14 @@ __global__ void __launch_bounds__(256, 2) update_stage_kernel(const __grid_const
                                                               int64_t n, int R, int nst, double *gpart, uint32_t *err) {
     constexpr bool FUSE = SB <= 8;
     constexpr int NG = FUSE ? SB * (SB + 1) / 2 : 1;
+    constexpr int NCW = GS_CONSUMERS;
     extern __shared__ __align__(128) unsigned char us_dyn[];
     __shared__ __align__(16) T cs[MMAX + 1][SB];
     __shared__ __align__(16) T ri[SB][SB];
     __shared__ double red[SB * SB];
     __shared__ double wred[8][NG];
-    __shared__ uint64_t full[ST_MAXST];
+    __shared__ uint64_t full[ST_MAXST], empty[ST_MAXST];
+    __shared__ int s_bad;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int e = tid; e < K1 * S; e += 256) cs[e % K1][e / K1] = (T)C[e];
     for (int e = tid; e < SB * SB; e += 256) ri[e % SB][e / SB] = (T)0;
@@ -572,95 +613,115 @@ __global__ void __launch_bounds__(256, 2) update_stage_kernel(const __grid_const
     const int64_t nblk = (n + R - 1) / R;
     ring.nmine = (int64_t)blockIdx.x < nblk ? (nblk - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     const int KP = ring.KP;
-    if (tid < nst) st_mbar_init(&full[tid], 1);
-    __syncthreads();
-    if (tid == 0)
-        for (int64_t i = 0; i < nst && i < ring.nmine; i++) ring.issue<T>(i, &mq, &mw);
-    const bool gram = FUSE && gpart != nullptr;
-    T g2[NG];
-#pragma unroll
-    for (int e = 0; e < NG; e++) g2[e] = (T)0;
-    auto flush = [&]() {
-#pragma unroll
-        for (int e = 0; e < NG; e++) {
-            T v = g2[e];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == (e & 31)) wred[warp][e] += (double)v;
-            g2[e] = (T)0;
-        }
-    };
-    int since = 0;          // rows this thread has summed into g2 since the last flush
-    bool bad = false;
-    for (int64_t i = 0; i < ring.nmine; i++) {
-        const int st = (int)(i % nst);
-        const bool ok = st_wait(&full[st], (uint32_t)((i / nst) & 1));
-        if (__syncthreads_or(!ok)) {
-            bad = true;
-            if (tid == 0) atomicOr(err, 1u);
-            if (warp == 0) ring.drain(i, i + nst);
-            break;
-        }
-        const int64_t r0 = ring.row0(i);
-        const int rows = (int)min((int64_t)R, n - r0);
-        // rows rr = tid, tid + 256, ... of the block; warp-uniform trip count (the flush needs
-        // every lane), rows past the block's end skipped
-        for (int rb = 0; rb < R; rb += 256) {
-            const int rr = rb + tid;
-            if (rr < rows) {
-                T w[SB];
-#pragma unroll
-                for (int b = 0; b < SB; b++) w[b] = b < S ? ring.col<T>(st, KP + b)[rr] : (T)0;
-                // the coefficients of row a of C (and of R^-1) as 16-byte vector loads from
-                // shared memory (one per four FP32 or two FP64 values); the FMAs as in
-                // update_kernel
-                for (int a = 0; a < K1; a++) {
-                    const T q = ring.col<T>(st, a)[rr];
-                    T cr[SB];
-                    vec_row<T, SB>(&cs[a][0], cr);
-#pragma unroll
-                    for (int b = 0; b < SB; b++)
-                        if (b < S) w[b] = fma(-q, cr[b], w[b]);
-                }
-                T wn[SB];
-#pragma unroll
-                for (int b = 0; b < SB; b++) wn[b] = (T)0;
-#pragma unroll
-                for (int c = 0; c < SB; c++) {
-                    T rr_[SB];
-                    vec_row<T, SB>(&ri[c][0], rr_);
-#pragma unroll
-                    for (int b = 0; b < SB; b++)
-                        if (c <= b && b < S) wn[b] = fma(w[c], rr_[b], wn[b]);
-                }
-#pragma unroll
-                for (int b = 0; b < SB; b++)
-                    if (b < S) W[(int64_t)b * ldw + r0 + rr] = wn[b];
-                if (gram) {
-                    int e = 0;
-#pragma unroll
-                    for (int b = 0; b < SB; b++)
-#pragma unroll
-                        for (int c = 0; c <= b; c++) {
-                            if (b < S && e < NG) g2[e] = fma(wn[b], wn[c], g2[e]);
-                            e++;
-                        }
-                }
-            }
-            if (gram && ++since == 32) {
-                flush();
-                since = 0;
-            }
-        }
-        __syncthreads();   // every row of stage st is done: refill it
-        if (tid == 0 && i + nst < ring.nmine) ring.issue<T>(i + nst, &mq, &mw);
+    if (tid < nst) {
+        st_mbar_init(&full[tid], 1);
+        st_mbar_init(&empty[tid], (uint32_t)NCW);
     }
-    if (!gram) return;
-    flush();
+    if (tid == 0) s_bad = 0;
     __syncthreads();
+    const volatile int *vbad = &s_bad;
+    const bool gram = FUSE && gpart != nullptr;
+    if (warp == NCW) {
+        if (lane == 0) {
+            int64_t issued = 0;
+            for (int64_t i = 0; i < ring.nmine; i++) {
+                const int st = (int)(i % nst);
+                if (i >= nst && !st_wait_or_bad(&empty[st], (uint32_t)(((i / nst) - 1) & 1), vbad)) {
+                    s_bad = 1;
+                    atomicOr(err, 1u);
+                    break;
+                }
+                ring.issue<T>(i, &mq, &mw);
+                issued = i + 1;
+            }
+            if (*vbad) ring.drain(issued > nst ? issued - nst : 0, issued);
+        }
+    } else {
+        T g2[NG];
+#pragma unroll
+        for (int e = 0; e < NG; e++) g2[e] = (T)0;
+        auto flush = [&]() {
+#pragma unroll
+            for (int e = 0; e < NG; e++) {
+                T v = g2[e];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == (e & 31)) wred[warp][e] += (double)v;
+                g2[e] = (T)0;
+            }
+        };
+        int since = 0;          // rows this thread has summed into g2 since the last flush
+        for (int64_t i = 0; i < ring.nmine; i++) {
+            const int st = (int)(i % nst);
+            const bool ok = st_wait_or_bad(&full[st], (uint32_t)((i / nst) & 1), vbad);
+            if (!__all_sync(0xffffffffu, ok)) {
+                if (lane == 0) {
+                    s_bad = 1;
+                    atomicOr(err, 1u);
+                }
+                break;
+            }
+            const int64_t r0 = ring.row0(i);
+            const int rows = (int)min((int64_t)R, n - r0);
+            // this stage's virtual warp: the rows past 32 NCW rotate over the warps
+            const int vw = (int)((warp + i) % NCW);
+            for (int rb = 0; rb < R; rb += 32 * NCW) {
+                const int rr = rb + vw * 32 + lane;
+                if (rb + vw * 32 >= R) break;   // warp-uniform: no rows of this round for this warp
+                if (rr < rows) {
+                    T w[SB];
+#pragma unroll
+                    for (int b = 0; b < SB; b++) w[b] = b < S ? ring.col<T>(st, KP + b)[rr] : (T)0;
+                    // the coefficients of row a of C (and of R^-1) as 16-byte vector loads from
+                    // shared memory; the FMAs as in update_kernel
+                    for (int a = 0; a < K1; a++) {
+                        const T q = ring.col<T>(st, a)[rr];
+                        T cr[SB];
+                        vec_row<T, SB>(&cs[a][0], cr);
+#pragma unroll
+                        for (int b = 0; b < SB; b++)
+                            if (b < S) w[b] = fma(-q, cr[b], w[b]);
+                    }
+                    T wn[SB];
+#pragma unroll
+                    for (int b = 0; b < SB; b++) wn[b] = (T)0;
+#pragma unroll
+                    for (int c = 0; c < SB; c++) {
+                        T rr_[SB];
+                        vec_row<T, SB>(&ri[c][0], rr_);
+#pragma unroll
+                        for (int b = 0; b < SB; b++)
+                            if (c <= b && b < S) wn[b] = fma(w[c], rr_[b], wn[b]);
+                    }
+#pragma unroll
+                    for (int b = 0; b < SB; b++)
+                        if (b < S) W[(int64_t)b * ldw + r0 + rr] = wn[b];
+                    if (gram) {
+                        int e = 0;
+#pragma unroll
+                        for (int b = 0; b < SB; b++)
+#pragma unroll
+                            for (int c = 0; c <= b; c++) {
+                                if (b < S && e < NG) g2[e] = fma(wn[b], wn[c], g2[e]);
+                                e++;
+                            }
+                    }
+                }
+                if (gram && ++since == 32) {
+                    flush();
+                    since = 0;
+                }
+            }
+            __syncwarp();
+            if (lane == 0) st_mbar_arrive(&empty[st]);
+        }
+        if (gram) flush();
+    }
+    __syncthreads();
+    if (!gram) return;
     for (int e = tid; e < NG; e += 256) {
         double t = 0.0;
-        for (int w = 0; w < 8; w++) t += wred[w][e];
+        for (int w = 0; w < NCW; w++) t += wred[w][e];
         int b = 0, c = e;
         while (c > b) { c -= b + 1; b++; }
         if (b < S) red[b * S + c] = t;
@@ -669,7 +730,7 @@ __global__ void __launch_bounds__(256, 2) update_stage_kernel(const __grid_const
     for (int e = tid; e < S * S; e += 256) {
         const int b = e / S, c = e % S;
         const double v = b >= c ? red[b * S + c] : red[c * S + b];
-        gpart[(int64_t)blockIdx.x * S * S + b + c * S] = bad ? __longlong_as_double(0x7ff8000000000000ll) : v;
+        gpart[(int64_t)blockIdx.x * S * S + b + c * S] = s_bad ? __longlong_as_double(0x7ff8000000000000ll) : v;
     }
 }
 
