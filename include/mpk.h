@@ -479,6 +479,9 @@ typedef struct {
     int32_t poly_degree;    /* degree of the polynomial preconditioner used (0: none) */
     double poly_interval[2];/* smallest and largest root of the polynomial */
     int32_t trace_len;      /* entries written to opts.trace_hist */
+    int32_t breakdowns;     /* CholQR breakdowns met (each one's cycle keeps the columns
+                               before the failing block; the following cycles run at s / 2) */
+    int32_t s_final;        /* block size of the last cycle */
 } mpk_gmres_info;
 
 mpk_status mpk_gmres_opts_default(mpk_gmres_opts *o);

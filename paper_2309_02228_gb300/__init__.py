@@ -111,7 +111,8 @@ class mpk_gmres_info(ctypes.Structure):
                 ("shifts", ctypes.c_double * 64), ("ms_total", ctypes.c_double),
                 ("ms_mpk", ctypes.c_double), ("ms_ortho", ctypes.c_double),
                 ("ms_other", ctypes.c_double), ("poly_degree", ctypes.c_int32),
-                ("poly_interval", ctypes.c_double * 2), ("trace_len", ctypes.c_int32)]
+                ("poly_interval", ctypes.c_double * 2), ("trace_len", ctypes.c_int32),
+                ("breakdowns", ctypes.c_int32), ("s_final", ctypes.c_int32)]
 
 
 class mpk_tune_info(ctypes.Structure):
