@@ -104,6 +104,42 @@ def test_block_update_and_fused_gram(m, S):
     _check_gram(G2.cpu().numpy(), W2, W2, gram_bound(n))
 
 
+@pytest.mark.parametrize("K,S", [(41, 8), (9, 8), (3, 4), (70, 16)])
+@pytest.mark.parametrize("n", [100_003, 257, 2_097_157])
+def test_staged_path_ragged_rows(m, K, S, n):
+    """FP32 columns padded to a 16-byte multiple (the solver's basis layout) take the staged
+    kernels, whose last row block is rounded up and filled with zeros by the copy engine: the
+    Gram of a ragged n against the FP64 product, and the block update (with its fused Gram)
+    against the FP64 evaluation; rows past n of the output columns stay untouched."""
+    import torch
+    ld = (n + 31) // 32 * 32
+    rng = np.random.default_rng(K * 7 + S)
+    Xf = np.zeros((K, ld), np.float32)
+    Yf = np.zeros((S, ld), np.float32)
+    Xf[:, :n] = _blocks(n, K, 11, "mixed")
+    Yf[:, :n] = _blocks(n, S, 12, "mixed")
+    Xf[:, n:] = 7.0            # padding rows hold garbage the kernels must not read as data
+    Yf[:, n:] = -3.0
+    G = m.mpk_gram(torch.from_numpy(Xf).cuda(), torch.from_numpy(Yf).cuda(), n=n).cpu().numpy()
+    _check_gram(G, Xf[:, :n], Yf[:, :n], gram_bound(n))
+    C = rng.standard_normal((K, S)) * 0.1
+    R = np.triu(rng.standard_normal((S, S)) * 0.1) + np.eye(S)
+    Rinv = np.linalg.inv(R)
+    Wd = torch.from_numpy(Yf.copy()).cuda()
+    G2 = m.mpk_block_update(torch.from_numpy(Xf).cuda(), Wd, torch.from_numpy(C), torch.from_numpy(Rinv), n=n,
+                            gram=S <= 8)
+    Wn = Wd.cpu().numpy()
+    assert np.array_equal(Wn[:, n:], Yf[:, n:])
+    C32 = C.astype(np.float32).astype(np.float64)
+    R32 = np.triu(Rinv.astype(np.float32).astype(np.float64))
+    W64, Q64 = Yf[:, :n].astype(np.float64).T, Xf[:, :n].astype(np.float64).T
+    ref = (W64 - Q64 @ C32) @ R32
+    den = (np.abs(W64) + np.abs(Q64) @ np.abs(C32)) @ np.abs(R32)
+    assert float((np.abs(Wn[:, :n].T - ref) / den).max()) <= (K + S + 2) * U32
+    if S <= 8:
+        _check_gram(G2.cpu().numpy(), Wn[:, :n], Wn[:, :n], gram_bound(n))
+
+
 @pytest.mark.parametrize("dtype", [np.float32, np.float64])
 @pytest.mark.parametrize("s,n", [(8, 1_000_000), (3, 257), (15, 300_001), (1, 99_999)])
 def test_gram_pairs(m, dtype, s, n):
