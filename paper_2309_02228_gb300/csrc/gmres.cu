@@ -369,6 +369,16 @@ __device__ __forceinline__ bool st_wait(uint64_t *bar, uint32_t parity) {
     return true;
 }
 
+// The staged Gram's X columns in a stage: K rounded up to whole register tiles (CT columns)
+// and whole boxes, so every tile column lies inside the stage; columns past K arrive as zeros
+// (boxes past the tensor map's last column are filled by the copy engine), so the tiles read
+// them without a guard.
+template <typename T, int SB> __host__ __device__ constexpr int gram_ct() { return (sizeof(T) == 4 ? 64 : 32) / SB; }
+template <typename T, int SB> __host__ __device__ inline int gram_kp(int K) {
+    const int m = gram_ct<T, SB>() > ST_BOXC ? gram_ct<T, SB>() : ST_BOXC;
+    return (K + m - 1) / m * m;
+}
+
 // The ring of one CTA: blocks b = blockIdx.x + i * gridDim.x (i = 0 .. nmine - 1) of R rows;
 // block i lands in stage i % nst, which holds the first map's KP columns, then the second's.
 struct StageRing {
@@ -438,7 +448,7 @@ __global__ void __launch_bounds__(256, 2) gram_stage_kernel(const __grid_constan
     StageRing ring;
     ring.base = gs_dyn;
     ring.full = full;
-    ring.KP = (K + ST_BOXC - 1) / ST_BOXC * ST_BOXC;
+    ring.KP = gram_kp<T, SB>(K);
     ring.NCP = ring.KP + (S + ST_BOXC - 1) / ST_BOXC * ST_BOXC;
     ring.R = R;
     ring.nst = nst;
@@ -511,15 +521,17 @@ __global__ void __launch_bounds__(256, 2) gram_stage_kernel(const __grid_constan
                 // n are zeros (the copy's fill), so a pair may run past the block's last row
                 for (int rr = 2 * (rpart * 32 + lane); rr < rows; rr += 64 * rsplit) {
                     T x0[CT], x1[CT], y0[SB], y1[SB];
+                    // no guards: columns past K and past S are zeros in the stage (see gram_kp;
+                    // the S boxes are padded to 8 >= SB or to SB = 16)
 #pragma unroll
                     for (int a = 0; a < CT; a++) {
-                        V2 v = c0 + a < K ? *reinterpret_cast<const V2 *>(xc + a * R + rr) : V2{(T)0, (T)0};
+                        const V2 v = *reinterpret_cast<const V2 *>(xc + a * R + rr);
                         x0[a] = v.x;
                         x1[a] = v.y;
                     }
 #pragma unroll
                     for (int b = 0; b < SB; b++) {
-                        V2 v = b < S ? *reinterpret_cast<const V2 *>(yc + b * R + rr) : V2{(T)0, (T)0};
+                        const V2 v = *reinterpret_cast<const V2 *>(yc + b * R + rr);
                         y0[b] = v.x;
                         y1[b] = v.y;
                     }
@@ -596,9 +608,12 @@ __global__ void __launch_bounds__(256, 2) update_stage_kernel(const __grid_const
     __shared__ uint64_t full[ST_MAXST], empty[ST_MAXST];
     __shared__ int s_bad;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int e = tid; e < K1 * S; e += 256) cs[e % K1][e / K1] = (T)C[e];
+    // coefficients past S (and the tables' unused rows) are zeros, so the FMAs run over all SB
+    // columns without a guard: a column past S stays 0 (its staged values are zeros too)
+    for (int e = tid; e < (MMAX + 1) * SB; e += 256) cs[e / SB][e % SB] = (T)0;
     for (int e = tid; e < SB * SB; e += 256) ri[e % SB][e / SB] = (T)0;
     __syncthreads();
+    for (int e = tid; e < K1 * S; e += 256) cs[e % K1][e / K1] = (T)C[e];
     for (int e = tid; e < S * S; e += 256) ri[e % S][e / S] = (T)Rinv[e];
     for (int e = tid; e < SB * SB; e += 256) red[e] = 0.0;
     for (int e = tid; e < 8 * NG; e += 256) wred[e / NG][e % NG] = 0.0;
@@ -670,8 +685,10 @@ __global__ void __launch_bounds__(256, 2) update_stage_kernel(const __grid_const
                 if (rb + vw * 32 >= R) break;   // warp-uniform: no rows of this round for this warp
                 if (rr < rows) {
                     T w[SB];
+                    // all SB columns without a guard: the staged W columns past S (within the
+                    // padded boxes) are zeros and so are their coefficients
 #pragma unroll
-                    for (int b = 0; b < SB; b++) w[b] = b < S ? ring.col<T>(st, KP + b)[rr] : (T)0;
+                    for (int b = 0; b < SB; b++) w[b] = ring.col<T>(st, KP + b)[rr];
                     // the coefficients of row a of C (and of R^-1) as 16-byte vector loads from
                     // shared memory; the FMAs as in update_kernel
                     for (int a = 0; a < K1; a++) {
@@ -679,8 +696,7 @@ __global__ void __launch_bounds__(256, 2) update_stage_kernel(const __grid_const
                         T cr[SB];
                         vec_row<T, SB>(&cs[a][0], cr);
 #pragma unroll
-                        for (int b = 0; b < SB; b++)
-                            if (b < S) w[b] = fma(-q, cr[b], w[b]);
+                        for (int b = 0; b < SB; b++) w[b] = fma(-q, cr[b], w[b]);
                     }
                     T wn[SB];
 #pragma unroll
@@ -690,8 +706,7 @@ __global__ void __launch_bounds__(256, 2) update_stage_kernel(const __grid_const
                         T rr_[SB];
                         vec_row<T, SB>(&ri[c][0], rr_);
 #pragma unroll
-                        for (int b = 0; b < SB; b++)
-                            if (c <= b && b < S) wn[b] = fma(w[c], rr_[b], wn[b]);
+                        for (int b = c; b < SB; b++) wn[b] = fma(w[c], rr_[b], wn[b]);
                     }
 #pragma unroll
                     for (int b = 0; b < SB; b++)
@@ -814,13 +829,14 @@ static mpk_status gram_stage_launch(const T *X, int64_t ldx, int K, const T *Y, 
                                     int nsm, int max_grid, double *part, uint32_t *err, int *grid, cudaStream_t s) {
     int R = 0, nst = 0;
     // FP32 bases only: an FP64 Gram is bound by the FP64 pipe however its rows arrive
-    if (sizeof(T) != 4 || n <= 0 || K < 1 || S < 1 || S > SMAX || K > MMAX + 1 + SMAX ||
-        !stage_choice(box_pad(K) + box_pad(S), sizeof(T), &R, &nst))
-        return MPK_ERR_UNIMPLEMENTED;
+    if (sizeof(T) != 4 || n <= 0 || K < 1 || S < 1 || S > SMAX || K > MMAX + 1 + SMAX) return MPK_ERR_UNIMPLEMENTED;
+    // the stage's padded X columns, as the kernel instantiated for this S computes them
+    const int kp = S <= 4 ? gram_kp<T, 4>(K) : (S <= 8 ? gram_kp<T, 8>(K) : gram_kp<T, 16>(K));
+    if (!stage_choice(kp + box_pad(S), sizeof(T), &R, &nst)) return MPK_ERR_UNIMPLEMENTED;
     CUtensorMap mx, my;
     if (!make_tmap<T>(&mx, X, ldx, n, K, R) || !make_tmap<T>(&my, Y, ldy, n, S, R)) return MPK_ERR_UNIMPLEMENTED;
     const int g = (int)std::max<int64_t>(1, std::min<int64_t>(std::min(2 * nsm, max_grid), ceil_div(n, R)));
-    const size_t dsm = (size_t)(box_pad(K) + box_pad(S)) * R * sizeof(T) * nst;
+    const size_t dsm = (size_t)(kp + box_pad(S)) * R * sizeof(T) * nst;
     auto kern = S <= 4 ? gram_stage_kernel<T, 4> : (S <= 8 ? gram_stage_kernel<T, 8> : gram_stage_kernel<T, 16>);
     MPK_TRY(ensure_stage_smem(kern));
     kern<<<g, 256, dsm, s>>>(mx, my, K, S, n, R, nst, part, err);
@@ -836,9 +852,8 @@ static mpk_status update_stage_launch(const T *Q, int64_t ldq, int K1, T *W, int
                                       const double *Rinv, int64_t n, int nsm, int max_grid, double *gpart,
                                       uint32_t *err, int *grid, cudaStream_t s) {
     int R = 0, nst = 0;
-    // FP32 bases with basis columns to subtract (the normalisation W R^-1 alone, K1 = 0,
-    // measured 7 % faster with the register-streaming kernel)
-    if (sizeof(T) != 4 || n <= 0 || S < 1 || S > SMAX || K1 < 1 || K1 > MMAX + 1 ||
+    // FP32 bases
+    if (sizeof(T) != 4 || n <= 0 || S < 1 || S > SMAX || K1 < 0 || K1 > MMAX + 1 ||
         !stage_choice(box_pad(K1) + box_pad(S), sizeof(T), &R, &nst))
         return MPK_ERR_UNIMPLEMENTED;
     CUtensorMap mq, mw;
