@@ -19,8 +19,8 @@
 // values) is FP64 on one CTA.  Every reduction has a fixed order: results do not depend on
 // scheduling.
 #include <cuda.h>
+#include <map>
 #include <mutex>
-#include <set>
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -752,9 +752,11 @@ __global__ void __launch_bounds__(256, 2) update_stage_kernel(const __grid_const
 // Host side of the staged kernels.  Tensor maps are encoded with the driver's
 // cuTensorMapEncodeTiled, reached through the runtime (no link against the driver library);
 // without it the callers run the register-streaming kernels.  R rows per stage and the ring
-// depth come from the shared-memory budget: the largest R (at most 256, a box's limit) that
-// leaves three stages, else two.
-constexpr size_t ST_BUDGET = 96 * 1024;   // per CTA: two CTAs share an SM
+// depth come from the kernel's shared-memory budget (stage_budget): the largest R (at most
+// 256, a box's limit) that leaves three stages, else two, then as many stages of that size as
+// the budget holds, so that narrow stages (the CholQR normalisation, short blocks) get a
+// deeper ring.
+constexpr size_t ST_BUDGET = 96 * 1024;   // dynamic shared memory per CTA at most
 
 typedef CUresult (*TmapEncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
@@ -793,31 +795,47 @@ template <typename T> static bool make_tmap(CUtensorMap *m, const T *base, int64
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// The staged kernels' dynamic shared-memory limit, raised to the whole stage budget once per
-// (kernel, device): setting it per launch raced between host threads that launch the same
+// The dynamic shared memory a CTA of `kern` may take while two CTAs stay resident on an SM:
+// half the SM's shared memory, less the per-CTA reservation and the kernel's static arrays, at
+// most ST_BUDGET.  Computed once per (kernel, device), when the kernel's dynamic limit is also
+// raised to ST_BUDGET: setting it per launch raced between host threads that launch the same
 // kernel with different stage sizes (the server runs one solve per thread).
 static std::mutex g_smem_attr_mu;
-static std::set<std::pair<const void *, int>> g_smem_attr_done;
-template <typename F> static mpk_status ensure_stage_smem(F kern) {
+static std::map<std::pair<const void *, int>, size_t> g_stage_budget;
+template <typename F> static mpk_status stage_budget(F kern, size_t *budget) {
     int dev = 0;
     MPK_CUDA(cudaGetDevice(&dev));
     std::lock_guard<std::mutex> lk(g_smem_attr_mu);
     const auto key = std::make_pair(reinterpret_cast<const void *>(kern), dev);
-    if (g_smem_attr_done.count(key)) return MPK_OK;
+    const auto it = g_stage_budget.find(key);
+    if (it != g_stage_budget.end()) {
+        *budget = it->second;
+        return MPK_OK;
+    }
+    int sm_bytes = 0, reserved = 0;
+    MPK_CUDA(cudaDeviceGetAttribute(&sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+    MPK_CUDA(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+    cudaFuncAttributes fa;
+    MPK_CUDA(cudaFuncGetAttributes(&fa, reinterpret_cast<const void *>(kern)));
+    const int64_t half = (int64_t)sm_bytes / 2 - reserved - (int64_t)fa.sharedSizeBytes;
     MPK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ST_BUDGET));
-    g_smem_attr_done.insert(key);
+    const size_t b = (size_t)std::max<int64_t>(0, std::min<int64_t>(half, (int64_t)ST_BUDGET));
+    g_stage_budget.emplace(key, b);
+    *budget = b;
     return MPK_OK;
 }
 
-static bool stage_choice(int NCP, size_t es, int *R, int *nst) {
+static bool stage_choice(int NCP, size_t es, size_t budget, int *R, int *nst) {
     static const int rs[4] = {256, 128, 64, 32};
     for (int q = 3; q >= 2; q--)
-        for (int r : rs)
-            if ((size_t)NCP * r * es * q <= ST_BUDGET) {
+        for (int r : rs) {
+            const size_t sb = (size_t)NCP * r * es;
+            if (sb * q <= budget) {
                 *R = r;
-                *nst = q;
+                *nst = (int)std::min<size_t>(ST_MAXST, budget / sb);
                 return true;
             }
+        }
     return false;
 }
 static inline int box_pad(int c) { return (c + ST_BOXC - 1) / ST_BOXC * ST_BOXC; }
@@ -832,13 +850,14 @@ static mpk_status gram_stage_launch(const T *X, int64_t ldx, int K, const T *Y, 
     if (sizeof(T) != 4 || n <= 0 || K < 1 || S < 1 || S > SMAX || K > MMAX + 1 + SMAX) return MPK_ERR_UNIMPLEMENTED;
     // the stage's padded X columns, as the kernel instantiated for this S computes them
     const int kp = S <= 4 ? gram_kp<T, 4>(K) : (S <= 8 ? gram_kp<T, 8>(K) : gram_kp<T, 16>(K));
-    if (!stage_choice(kp + box_pad(S), sizeof(T), &R, &nst)) return MPK_ERR_UNIMPLEMENTED;
+    auto kern = S <= 4 ? gram_stage_kernel<T, 4> : (S <= 8 ? gram_stage_kernel<T, 8> : gram_stage_kernel<T, 16>);
+    size_t budget = 0;
+    MPK_TRY(stage_budget(kern, &budget));
+    if (!stage_choice(kp + box_pad(S), sizeof(T), budget, &R, &nst)) return MPK_ERR_UNIMPLEMENTED;
     CUtensorMap mx, my;
     if (!make_tmap<T>(&mx, X, ldx, n, K, R) || !make_tmap<T>(&my, Y, ldy, n, S, R)) return MPK_ERR_UNIMPLEMENTED;
     const int g = (int)std::max<int64_t>(1, std::min<int64_t>(std::min(2 * nsm, max_grid), ceil_div(n, R)));
     const size_t dsm = (size_t)(kp + box_pad(S)) * R * sizeof(T) * nst;
-    auto kern = S <= 4 ? gram_stage_kernel<T, 4> : (S <= 8 ? gram_stage_kernel<T, 8> : gram_stage_kernel<T, 16>);
-    MPK_TRY(ensure_stage_smem(kern));
     kern<<<g, 256, dsm, s>>>(mx, my, K, S, n, R, nst, part, err);
     MPK_CUDA(cudaGetLastError());
     *grid = g;
@@ -853,9 +872,11 @@ static mpk_status update_stage_launch(const T *Q, int64_t ldq, int K1, T *W, int
                                       uint32_t *err, int *grid, cudaStream_t s) {
     int R = 0, nst = 0;
     // FP32 bases
-    if (sizeof(T) != 4 || n <= 0 || S < 1 || S > SMAX || K1 < 0 || K1 > MMAX + 1 ||
-        !stage_choice(box_pad(K1) + box_pad(S), sizeof(T), &R, &nst))
-        return MPK_ERR_UNIMPLEMENTED;
+    if (sizeof(T) != 4 || n <= 0 || S < 1 || S > SMAX || K1 < 0 || K1 > MMAX + 1) return MPK_ERR_UNIMPLEMENTED;
+    auto kern = S <= 4 ? update_stage_kernel<T, 4> : (S <= 8 ? update_stage_kernel<T, 8> : update_stage_kernel<T, 16>);
+    size_t budget = 0;
+    MPK_TRY(stage_budget(kern, &budget));
+    if (!stage_choice(box_pad(K1) + box_pad(S), sizeof(T), budget, &R, &nst)) return MPK_ERR_UNIMPLEMENTED;
     CUtensorMap mq, mw;
     if (!make_tmap<T>(&mw, W, ldw, n, S, R)) return MPK_ERR_UNIMPLEMENTED;
     if (K1 > 0) {
@@ -865,8 +886,6 @@ static mpk_status update_stage_launch(const T *Q, int64_t ldq, int K1, T *W, int
     }
     const int g = (int)std::max<int64_t>(1, std::min<int64_t>(std::min(2 * nsm, max_grid), ceil_div(n, R)));
     const size_t dsm = (size_t)(box_pad(K1) + box_pad(S)) * R * sizeof(T) * nst;
-    auto kern = S <= 4 ? update_stage_kernel<T, 4> : (S <= 8 ? update_stage_kernel<T, 8> : update_stage_kernel<T, 16>);
-    MPK_TRY(ensure_stage_smem(kern));
     kern<<<g, 256, dsm, s>>>(mq, mw, K1, W, ldw, S, C, Rinv, n, R, nst, S <= 8 ? gpart : nullptr, err);
     MPK_CUDA(cudaGetLastError());
     *grid = g;
