@@ -1894,40 +1894,50 @@ __global__ void __launch_bounds__(32) cg_coord_kernel(CgState *cs, const double 
 // summed too and not used), stored packed by BS x BS blocks: block pair pb = (ab, bb),
 // ab <= bb, enumerated row by row, entry (i, j) of the block at pb * BS^2 + i * BS + j.  A
 // block of columns is then whole pairs (FP32: two, FP64: one), read from the staged tile by
-// vector loads.  A CTA stages 128-row tiles of Y in shared
-// memory; thread t owns block pair t % NBP and the rows g, g + RG, ... of each tile
-// (g = t / NBP, RG = 256 / NBP row groups).  Precision: a thread sums its products in the
-// basis precision over at most 32 rows (F tiles), the RG row groups' block sums of each entry
-// are then added by a fixed pairwise tree in shared memory (at most eight levels), and the
-// result is added to an FP64 total; the CTA writes one FP64 partial per entry, which
+// vector loads.  A CTA stages tiles of TR rows of Y in shared memory; thread t owns block
+// pair t % NBP and the rows g, g + RG, ... of each tile (g = t / NBP, RG = 256 / NBP row
+// groups).  Precision: a thread sums its products in the basis precision over at most 32 rows
+// (F tiles), the RG row groups' block sums of each entry are then added by a fixed pairwise
+// tree in shared memory (at most eight levels), and the result is added to the CTA's FP64
+// total of the entry (in shared memory); the CTA writes one FP64 partial per entry, which
 // reduce_partials_kernel sums over the CTAs in a fixed order.  For an FP32 basis
-// |G^ - G| <= (40 u32 + m u64) |Y|^T |Y| entrywise.  BS = 4 for FP32 (loads of 8 values per
-// 16 FMAs), 2 for FP64 (fewer wasted products on the slow FP64 pipe).
+// |G^ - G| <= (40 u32 + m u64) |Y|^T |Y| entrywise.  FP32: BS = 6 (three pairs; loads of 12
+// values per 36 FMAs; s = 8 gives 6 block pairs and 216 products per row for the 171 of the
+// triangle, against 15 and 240 with BS = 4) and TR = 168, so that the 42 row groups of s = 8
+// sum four rows each.  FP64: BS = 2 (fewer wasted products on the slow FP64 pipe), TR = 128.
 // Tiles arrive by 16-byte asynchronous copies (cp.async) into a ring of GSYM_STAGES shared
 // buffers, GSYM_STAGES - 1 tiles ahead of the one being summed: with one tile in flight per
 // CTA the kernel was bound by memory latency (about 1 TB/s on the FP32 basis).
-constexpr int GSYM_TR = 128;
 constexpr int GSYM_STAGES = 4;
 constexpr int GSYM_MP = 32;                   // M padded (<= 32 columns)
-template <typename T> constexpr int gsym_bs() { return sizeof(T) == 4 ? 4 : 2; }
+template <typename T> __host__ __device__ constexpr int gsym_bs() { return sizeof(T) == 4 ? 6 : 2; }
+template <typename T> __host__ __device__ constexpr int gsym_tr() { return sizeof(T) == 4 ? 168 : 128; }
 static inline int gsym_nbp(int M, int bs) {
     const int nb = (M + bs - 1) / bs;
     return nb * (nb + 1) / 2;
 }
-// shared elements of one pair's tile: 2 GSYM_TR values and 16 bytes of padding, so that the
-// pairs of a stage start in different banks and every copy stays 16-byte aligned
-template <typename T> constexpr int gsym_pstride() { return 2 * GSYM_TR + 16 / (int)sizeof(T); }
-// pairs of a stage for np stored pairs: whole column blocks (FP32: an even number of pairs;
-// the padding pair reads zeros)
-template <typename T> constexpr int gsym_pairs(int np) { return sizeof(T) == 4 ? (np + 1) / 2 * 2 : np; }
+// shared elements of one pair's tile: 2 TR values and padding that keeps every copy 16-byte
+// aligned and starts the pairs of a stage in different banks (FP32: 356 = 4 mod 32 words, so
+// the three column blocks of a stage start 12 banks apart)
+template <typename T> __host__ __device__ constexpr int gsym_pstride() {
+    return sizeof(T) == 4 ? 2 * gsym_tr<T>() + 20 : 2 * gsym_tr<T>() + 2;
+}
+// pairs of a stage for np stored pairs: whole column blocks of BS / 2 pairs (the padding
+// pairs read zeros)
+template <typename T> __host__ __device__ constexpr int gsym_pairs(int np) {
+    return (np + gsym_bs<T>() / 2 - 1) / (gsym_bs<T>() / 2) * (gsym_bs<T>() / 2);
+}
 // dynamic shared memory of gram_sym_kernel for np pairs: the stage ring, then the row groups'
-// block sums (256 BS^2 values of the basis type)
+// block sums (256 BS^2 values of the basis type), then the CTA's FP64 totals (NBP BS^2)
 template <typename T> __host__ __device__ size_t gsym_ring_bytes(int np) {
     return (size_t)GSYM_STAGES * gsym_pairs<T>(np) * gsym_pstride<T>() * sizeof(T);
 }
+template <typename T> __host__ __device__ size_t gsym_flush_bytes() {
+    return (size_t)256 * gsym_bs<T>() * gsym_bs<T>() * sizeof(T);
+}
 template <typename T> size_t gsym_smem_bytes(int np) {
-    constexpr int BS = sizeof(T) == 4 ? 4 : 2;
-    return gsym_ring_bytes<T>(np) + (size_t)256 * BS * BS * sizeof(T);
+    constexpr int BS = gsym_bs<T>();
+    return gsym_ring_bytes<T>(np) + gsym_flush_bytes<T>() + (size_t)gsym_nbp(2 * np, BS) * BS * BS * sizeof(double);
 }
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
@@ -1950,12 +1960,13 @@ __host__ __device__ __forceinline__ int64_t cg_col_ofs(int a, int s, int64_t ldv
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) gram_sym_kernel(const T *Y, int64_t ldv, int s, int64_t n,
-                                                       double *part) {
+__global__ void __launch_bounds__(256, 2) gram_sym_kernel(const T *Y, int64_t ldv, int s, int64_t n,
+                                                          double *part) {
     constexpr int BS = gsym_bs<T>();
+    constexpr int TR = gsym_tr<T>();
     constexpr int PS = gsym_pstride<T>();
     constexpr int CE = 16 / (int)sizeof(T);          // elements per 16-byte copy
-    constexpr int CH = 2 * GSYM_TR / CE;             // copies per pair and tile
+    constexpr int CH = 2 * TR / CE;                  // copies per pair and tile
     using T2 = typename std::conditional<sizeof(T) == 8, double2, float2>::type;
     extern __shared__ __align__(16) unsigned char sh_raw[];
     T *sY = reinterpret_cast<T *>(sh_raw);
@@ -1982,16 +1993,15 @@ __global__ void __launch_bounds__(256) gram_sym_kernel(const T *Y, int64_t ldv, 
         const int stg = i / ((npad - np) * PS), e = i % ((npad - np) * PS);
         sY[stg * stage + np * PS + e] = (T)0;
     }
-    double acc[BS * BS];
     T tacc[BS * BS];
 #pragma unroll
-    for (int k = 0; k < BS * BS; k++) {
-        acc[k] = 0.0;
-        tacc[k] = (T)0;
-    }
-    // block sums of the row groups: fl[(g * NBP + pb) * BS^2 + k], after the stage ring
+    for (int k = 0; k < BS * BS; k++) tacc[k] = (T)0;
+    // block sums of the row groups: fl[(g * NBP + pb) * BS^2 + k], after the stage ring; then
+    // the CTA's FP64 totals acc[pb * BS^2 + k] (read only after the first flush's barriers)
     T *fl = reinterpret_cast<T *>(sh_raw + gsym_ring_bytes<T>(np));
-    const int rpt = (GSYM_TR + RG - 1) / RG;          // rows of a tile per thread, at most
+    double *acc = reinterpret_cast<double *>(sh_raw + gsym_ring_bytes<T>(np) + gsym_flush_bytes<T>());
+    for (int i = t; i < NBP * BS * BS; i += blockDim.x) acc[i] = 0.0;
+    const int rpt = (TR + RG - 1) / RG;               // rows of a tile per thread, at most
     const int F = rpt >= 32 ? 1 : 32 / rpt;           // tiles per block sum: <= 32 terms
     // every thread of the CTA (the barriers): the row groups' block sums of each entry by a
     // pairwise tree over g, added to the FP64 totals of the g = 0 threads
@@ -2014,18 +2024,18 @@ __global__ void __launch_bounds__(256) gram_sym_kernel(const T *Y, int64_t ldv, 
         }
         if (act && g == 0) {
 #pragma unroll
-            for (int k = 0; k < BS * BS; k++) acc[k] += (double)fl[pb * BS * BS + k];
+            for (int k = 0; k < BS * BS; k++) acc[pb * BS * BS + k] += (double)fl[pb * BS * BS + k];
         }
         __syncthreads();
     };
     int since = 0;
-    const int64_t ntiles = (n + GSYM_TR - 1) / GSYM_TR;
+    const int64_t ntiles = (n + TR - 1) / TR;
     // copies of the rows of `tile` that exist (pair k: 2 rows' values per row, contiguous)
     // into ring buffer stg; one commit group per call, empty past the last tile
     auto issue = [&](int64_t tile, int stg) {
         if (tile < ntiles) {
-            const int64_t r0 = tile * GSYM_TR;
-            const int vals = 2 * (int)(n - r0 < GSYM_TR ? n - r0 : GSYM_TR);
+            const int64_t r0 = tile * TR;
+            const int vals = 2 * (int)(n - r0 < TR ? n - r0 : TR);
             T *dst = sY + stg * stage;
             for (int idx = t; idx < np * CH; idx += blockDim.x) {
                 const int k = idx / CH, e = (idx % CH) * CE;
@@ -2043,7 +2053,7 @@ __global__ void __launch_bounds__(256) gram_sym_kernel(const T *Y, int64_t ldv, 
         cp_async_wait<GSYM_STAGES - 1>();
         __syncthreads();
         const T *sb = sY + (it % GSYM_STAGES) * stage;
-        const int rows = (int)(n - tile * GSYM_TR < GSYM_TR ? n - tile * GSYM_TR : GSYM_TR);
+        const int rows = (int)(n - tile * TR < TR ? n - tile * TR : TR);
         if (act) {
             for (int r = g; r < rows; r += RG) {
                 T xa[BS], xb[BS];
@@ -2072,10 +2082,7 @@ __global__ void __launch_bounds__(256) gram_sym_kernel(const T *Y, int64_t ldv, 
     __syncthreads();
     flush();
     const int m = NBP * BS * BS;
-    if (act && g == 0) {
-#pragma unroll
-        for (int k = 0; k < BS * BS; k++) part[(int64_t)blockIdx.x * m + pb * BS * BS + k] = acc[k];
-    }
+    for (int i = t; i < m; i += blockDim.x) part[(int64_t)blockIdx.x * m + i] = acc[i];
 }
 
 // x += scale * Y x' (in the basis precision, added to the FP64 x); p = Y p' and r = Y r' in
@@ -2190,7 +2197,7 @@ struct CgSolver {
     }
     // G = Y^T Y over the basis storage: upper triangle packed by blocks (gram_sym_kernel)
     static constexpr int BS = gsym_bs<T>();
-    int gsym_grid() const { return (int)std::min<int64_t>(2 * P->n_sm, std::max<int64_t>(1, ceil_div(n, GSYM_TR))); }
+    int gsym_grid() const { return (int)std::min<int64_t>(2 * P->n_sm, std::max<int64_t>(1, ceil_div(n, gsym_tr<T>()))); }
     // G over the basis storage's 2 sc + 2 columns (pair order)
     mpk_status gram(int sc) {
         const int g = gsym_grid();
@@ -2569,7 +2576,7 @@ mpk_status gram_pairs_launch(const T *Y, int64_t ldv, int s, int64_t n, double *
     int nsm = 1;
     MPK_TRY(sm_count(&nsm));
     constexpr int BS = gsym_bs<T>();
-    const int g = (int)std::min<int64_t>(2 * nsm, std::max<int64_t>(1, ceil_div(n, GSYM_TR)));
+    const int g = (int)std::min<int64_t>(2 * nsm, std::max<int64_t>(1, ceil_div(n, gsym_tr<T>())));
     const int M = 2 * s + 2;
     const int m = gsym_nbp(M, BS) * BS * BS;
     DevBuf part, packed;
