@@ -187,8 +187,8 @@ __device__ __forceinline__ void row_batch_g(const int32_t *colp, const T *valp, 
 // Global: full batches of BG entries (row_batch_g), then the remainder in batches of 4, 2 and
 // 1.  The slice length is the same for every lane, so those branches are uniform and no
 // multiply-add is issued past the end of the slice (on the FP64 pipe, the bound of the FP64
-// kernels, a predicated 8-wide tail cost 32 FMAs for a 27-entry row).  FP32 with one
-// right-hand side keeps one predicated whole-row batch instead (memory-bound: all loads in
+// kernels, a predicated 8-wide tail cost 32 FMAs for a 27-entry row).  FP32 with one or
+// two right-hand sides keeps predicated whole-row batches instead (memory-bound: all loads in
 // flight).  Every variant visits entries and partial sums in the same order, so the values do
 // not depend on the variant.
 template <typename T, int NR, bool SM, bool SV, int BGMAX = 8, int LD = LD_KEEP>
@@ -206,14 +206,17 @@ __device__ __forceinline__ void row_sum(const int32_t *colp, const T *valp, int3
         acc[q] = (T)0;
         acc2[q] = (T)0;
     }
-    // FP32 with one right-hand side is bound by memory: there a whole row's loads in flight at
-    // once (one predicated batch of BT entries, unrolled) beats skipping the tail's FMAs
-    constexpr bool WHOLE_ROW = sizeof(T) == 4 && NR == 1;
+    // FP32 with one or two right-hand sides is bound by memory: there a whole row's loads in
+    // flight at once (one predicated batch of BW entries, unrolled) beats skipping the tail's
+    // FMAs.  Two right-hand sides take batches of BG entries: a 7-entry row then issues all
+    // its loads together instead of in dependent batches of 4, 2 and 1.
+    constexpr bool WHOLE_ROW = sizeof(T) == 4 && NR <= 2;
     if constexpr (!SM && WHOLE_ROW) {
         constexpr int BG = BT > BGMAX ? BGMAX : BT;
-        for (int32_t j = 0; j < L; j += BT) {
+        constexpr int BW = NR == 1 ? BT : BG;
+        for (int32_t j = 0; j < L; j += BW) {
 #pragma unroll
-            for (int j2 = 0; j2 < BT; j2 += BG) {
+            for (int j2 = 0; j2 < BW; j2 += BG) {
                 int32_t cc[BG];
                 T vv[BG];
                 T xx[BG][NR];
@@ -2624,9 +2627,11 @@ mpk_status launch_powers(mpk_plan_s *P, const SellView &A, int n_rhs, const VecS
     if (!blocked) {
         // p back-to-back SpMV launches (Alg. 1)
         const bool pairs = NR == 1 && P->short_rows;
-        // blocks of right-hand sides keep one CTA per eight slices: capped, they measured
-        // 8-18 % slower at n_rhs = 8, 16 and 32 (128^3 27-point, FP32)
-        const unsigned grid = NR == 1 ? power_grid(P, pairs ? 16 : 8)
+        // one or two right-hand sides run on the persistent grid (two: the s-step CG basis, 9 %
+        // less MPK time on the 256^3 7-point FP32 solve); wider blocks keep one CTA per eight
+        // slices: capped, they measured 8-18 % slower at n_rhs = 8, 16 and 32 (128^3 27-point,
+        // FP32)
+        const unsigned grid = NR <= 2 ? power_grid(P, pairs ? 16 : 8)
                                       : (unsigned)std::min<int64_t>(ceil_div(std::max<int64_t>(P->n_slices, 1), 8), 1 << 30);
         auto kern = mpk_power_kernel<T, NR, false>;
         if constexpr (NR == 1) {

@@ -254,7 +254,7 @@ def test_permuted_io_and_y0_is_x(m):
         assert max_rel_err(full[k], ref[k], den[k]) <= 64 * k * U64
 
 
-@pytest.mark.parametrize("n_rhs", [1, 3, 8, 16, 32])
+@pytest.mark.parametrize("n_rhs", [1, 2, 3, 8, 16, 32])
 @pytest.mark.parametrize("interleaved", [False, True])
 def test_block_mpk_n_rhs(m, n_rhs, interleaved):
     import torch
