@@ -141,7 +141,7 @@ def test_staged_path_ragged_rows(m, K, S, n):
 
 
 @pytest.mark.parametrize("dtype", [np.float32, np.float64])
-@pytest.mark.parametrize("s,n", [(8, 1_000_000), (3, 257), (15, 300_001), (1, 99_999)])
+@pytest.mark.parametrize("s,n", [(8, 1_000_000), (3, 257), (15, 300_001), (1, 99_999), (10, 200_003), (12, 168 * 1001)])
 def test_gram_pairs(m, dtype, s, n):
     """The CG basis Gram over the 2s + 2 storage columns in pair order, ragged n included."""
     import torch
